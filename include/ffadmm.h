@@ -1,0 +1,205 @@
+/*
+ * ffadmm.h - C ABI of the GB300 flip-free ADMM library (libffadmm.so).
+ *
+ * The library minimizes a flip-free distortion energy
+ *     E(W) = sum_i w_i f((G W)_i) + chi_+(det (G W)_i)              (paper Eq. 3.3)
+ * over target vertex positions W with the three-block splitting scheme of
+ * Stein, Li & Solomon, "A Splitting Scheme for Flip-Free Distortion Energies"
+ * (Algorithm 1; Algorithm 2 without penalty rescaling): a global W step with a
+ * fixed operator L = sum_i mu_i G_i^T G_i (Eq. 3.6), closed-form per-element U
+ * (Procrustes, Eq. 4.3-4.4) and P (prox, Eq. 4.5-4.6) steps, and the scaled
+ * multiplier update (Eq. 4.7), with the primal/dual errors of Eq. 6.1-6.2.
+ *
+ * Conventions shared by every call:
+ *   - Sizes: n vertices, m elements, element dimension d (2 = triangles,
+ *     3 = tetrahedra), source dimension d_in (2 or 3; d_in = 3 with d = 2 means a
+ *     surface mesh with intrinsic 2x2 Jacobians, paper Supplemental).  The target
+ *     dimension is d.
+ *   - Arrays are dense and row-major: V is n x d_in, T is m x (d+1), W is n x d,
+ *     per-element matrices are m x d x d.  Doubles unless stated otherwise.
+ *   - J_i = (G W)_i has column k equal to the gradient of target coordinate k on
+ *     element i (paper Supplemental, "Computing the Jacobian map").
+ *   - Pointer arguments marked "host or device" may point to host memory or to
+ *     device memory of the context's GPU; the library copies through unified
+ *     addressing.  Input memory is owned by the caller and only read during the
+ *     call; output memory is owned by the caller and written by the call.  The
+ *     library never frees caller memory.
+ *   - Every call returns an ffa_status; no exception crosses the ABI.  On error,
+ *     ffa_last_error(ctx) returns a message owned by the context (valid until the
+ *     next call on it).  A context is used by one host thread at a time.
+ *   - All GPU work of a context runs on its stream, in order.  Calls that return
+ *     values to the host synchronize that stream.
+ */
+#ifndef FFADMM_H
+#define FFADMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffa_ctx ffa_ctx;
+
+typedef enum {
+  FFA_OK = 0,
+  FFA_ERR_INVALID_ARG = 1,        /* bad size, index, pointer or parameter */
+  FFA_ERR_DEGENERATE_ELEMENT = 2, /* a source element has w_i <= 0 */
+  FFA_ERR_SINGULAR_SYSTEM = 3,    /* L restricted to free vertices is not SPD */
+  FFA_ERR_CUDA = 4,               /* a CUDA runtime call failed */
+  FFA_ERR_OOM = 5,                /* host or device allocation failed */
+  FFA_ERR_NAN = 6,                /* a non-finite value appeared in the iterate */
+  FFA_ERR_NOT_INITIALIZED = 7,    /* ffa_iterate before ffa_init */
+  FFA_ERR_FLIPPED = 8             /* gradient requested at a map with det J_i <= 0 */
+} ffa_status;
+
+typedef enum {
+  FFA_SYM_DIRICHLET = 0, /* f(X) = (|X|^2 + |X^-1|^2) / 2          (Eq. A.2) */
+  FFA_SYM_GRADIENT = 1   /* f(X) = |X|^2 / 2 - log det X            (Eq. 7.1) */
+} ffa_energy_kind;
+
+typedef enum {
+  FFA_LOCAL_FP32 = 0, /* local step in float; reductions and the W step in double */
+  FFA_LOCAL_FP64 = 1  /* local step in double as well */
+} ffa_precision;
+
+typedef struct {
+  int32_t n;         /* vertices, >= d+1 */
+  int32_t m;         /* elements, >= 1 */
+  int32_t d;         /* 2 or 3 */
+  int32_t d_in;      /* 2 or 3, >= d */
+  const double* V;   /* n x d_in source positions, host or device */
+  const int32_t* T;  /* m x (d+1) vertex indices, host or device; positively oriented */
+} ffa_mesh;
+
+typedef struct {
+  ffa_energy_kind energy;
+  double rho;              /* penalties mu_i = rho * w_i (rho = 1: the paper's initial mu_i = w_i) */
+  double eps_abs;          /* thresholds of Eq. 6.2 */
+  double eps_rel;
+  int32_t check_every;     /* evaluate the termination test every this many iterations (>= 1) */
+  int32_t require_flip_free; /* 1: convergence also needs det J_i > 0 for all i (Sec. 6) */
+  ffa_precision local_precision;
+  int32_t refine_sweeps;   /* W step: residual-correction sweeps per iteration (>= 1) */
+  int32_t nd_leaf_size;    /* W step setup: nested-dissection leaf size (8..512) */
+  int32_t host_threads;    /* W step setup: host threads for the factorization (0 = all) */
+} ffa_params;
+
+typedef struct {
+  int32_t iters;           /* iterations performed by the call */
+  int32_t converged;       /* 1 if the termination test of Eq. 6.2 passed */
+  int32_t n_flipped;       /* elements with det (G W)_i <= 0 at the last check */
+  int32_t checked_iter;    /* total iteration count at which the stats were taken */
+  double e_prim, e_dual;   /* Eq. 6.1 */
+  double thr_prim, thr_dual; /* Eq. 6.2 */
+  double energy_P;         /* sum_i w_i f(P_i) */
+  double norm_GW, norm_P, norm_GtLambda;
+} ffa_stats;
+
+typedef struct {
+  int32_t n, m, d, d_in, n_pin, n_free;
+  int64_t factor_entries;  /* stored entries of the supernodal factor blocks */
+  int64_t factor_flops;    /* floating-point operations of the numeric factorization */
+  int32_t n_supernodes, n_levels;
+  double setup_seconds_analyze;   /* ordering + symbolic analysis (host) */
+  double setup_seconds_factor;    /* numeric factorization (host) */
+  int64_t device_bytes;    /* device memory held by the context */
+  int64_t bytes_local_step;   /* algorithmic bytes of one local-step launch */
+  int64_t bytes_global_sweep; /* algorithmic bytes of one W-step refinement sweep */
+  int32_t kernels_per_iteration; /* kernel launches of one iteration without the test */
+  int32_t kernels_per_check;     /* extra launches of an iteration that runs the test */
+} ffa_info;
+
+typedef struct {
+  int32_t reps;        /* iterations timed */
+  double ms_gather;    /* W step: right-hand side G^T r */
+  double ms_wstep;     /* W step: all refinement sweeps (residual + triangular solves) */
+  double ms_vertex;    /* vertex update */
+  double ms_local;     /* fused local step (U, P, Lambda) */
+  double ms_check;     /* termination test of one check iteration */
+  double ms_iteration; /* whole iteration, launched one kernel at a time */
+} ffa_phase_times;
+
+/* Fill *p with the defaults: symmetric Dirichlet, rho 1, eps_abs 1e-6, eps_rel 1e-5,
+ * check_every 10, require_flip_free 1, FP32 local step, 2 refine sweeps,
+ * leaf size 64, all host threads. */
+ffa_status ffa_default_params(ffa_params* p);
+
+/* Prepare a solver for one mesh: element gradients and measures w_i (Supplemental,
+ * "Computing the Jacobian map"; w_i of Sec. 3.1), the fixed operator
+ * L = sum_i mu_i G_i^T G_i of Eq. 3.6 restricted to the free vertices, and its
+ * factorization, done once per mesh and rho (Sec. 4, "Efficient evaluation";
+ * Algorithm 2, decompose(L)).
+ *   mesh      : sizes and source geometry (host or device).
+ *   pin_idx   : n_pin distinct vertex indices fixed by the constraint A W = b
+ *               (Eq. 3.6 / Algorithm 1); n_pin = 0 pins vertex 0 at the origin
+ *               (Sec. 4, "Updating W").  Host or device; may be NULL if n_pin = 0.
+ *   pin_pos   : n_pin x d positions b of the pinned vertices, host or device.
+ *   params    : solver parameters (NULL = defaults).
+ *   stream    : cudaStream_t to run on (NULL = a stream owned by the context).
+ *   out       : receives the context; NULL on failure.
+ * Errors: FFA_ERR_INVALID_ARG (sizes, indices out of range, repeated pins),
+ * FFA_ERR_DEGENERATE_ELEMENT, FFA_ERR_SINGULAR_SYSTEM, FFA_ERR_OOM, FFA_ERR_CUDA. */
+ffa_status ffa_create(const ffa_mesh* mesh, const int32_t* pin_idx, int32_t n_pin,
+                      const double* pin_pos, const ffa_params* params, void* stream,
+                      ffa_ctx** out);
+
+/* Release every resource of the context (NULL is ignored). */
+void ffa_destroy(ffa_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none).  With ctx NULL: the message
+ * of the last failed ffa_create on the calling thread. */
+const char* ffa_last_error(const ffa_ctx* ctx);
+
+/* Replace the pinned positions b (n_pin x d, host or device).  The operator is
+ * unchanged, so no refactorization happens; the next W step uses the new b. */
+ffa_status ffa_set_handles(ffa_ctx* ctx, const double* pin_pos);
+
+/* Start a solve from W0 (n x d, host or device): U0, P0 from the polar
+ * decomposition of G W0 with singular values clamped to eps and the flipped case
+ * of Eq. 6.4 (eps = eps_m^(1/4) for SG, eps_m^(1/8) for SD, eps_m = 2^-52);
+ * Lambda0 = 0.  Pinned rows of W0 are replaced by the pinned positions. */
+ffa_status ffa_init(ffa_ctx* ctx, const double* W0);
+
+/* Run up to max_iter iterations of Algorithm 1 (W, U, P, Lambda steps, h = 0).
+ * With stop_at_tol = 1 the termination test of Eq. 6.2 (plus flip-freeness when
+ * require_flip_free) is evaluated every check_every iterations and the call
+ * returns as soon as it passes; with stop_at_tol = 0 exactly max_iter iterations
+ * run and the test is still evaluated at the last one.  *stats (may be NULL)
+ * receives the last evaluated statistics.  Returns FFA_ERR_NAN if an evaluated
+ * statistic is not finite; the state is then left as computed. */
+ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_stats* stats);
+
+/* Copy the current W (n x d doubles) to W_out (host or device). */
+ffa_status ffa_get_W(ffa_ctx* ctx, double* W_out);
+
+/* Copy the per-element state out as doubles (m x d x d each, host or device;
+ * any pointer may be NULL to skip it). */
+ffa_status ffa_get_state(ffa_ctx* ctx, double* U, double* P, double* Lambda);
+
+/* Energy of Eq. 3.3 at W (n x d, host or device; NULL = the current iterate):
+ * sum_i w_i f((G W)_i), or +infinity (with FFA_OK) if some det (G W)_i <= 0. */
+ffa_status ffa_energy(ffa_ctx* ctx, const double* W, double* E);
+
+/* Gradient of the energy at W: dE/dW = G^T (w_i grad f((G W)_i)) with
+ * grad f from Eq. 7.2 / A.3, written to dEdW (n x d, host or device).
+ * FFA_ERR_FLIPPED if some det (G W)_i <= 0 (the energy is infinite there). */
+ffa_status ffa_gradient(ffa_ctx* ctx, const double* W, double* dEdW);
+
+/* Sizes, setup timings and the algorithmic byte counts used for roofline reports. */
+ffa_status ffa_get_info(ffa_ctx* ctx, ffa_info* info);
+
+/* Average device time of each phase of an iteration, measured with CUDA events
+ * on the context stream over reps iterations launched eagerly (not as a graph).
+ * The iterations are real: the state advances by reps iterations. */
+ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out);
+
+/* Relative residual |L_FF W_F - b_F| / |b_F| of the last W step, measured in
+ * double on the device (a diagnostic of the refinement sweeps; Eq. 3.6). */
+ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel_residual);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFADMM_H */

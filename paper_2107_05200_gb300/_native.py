@@ -1,0 +1,119 @@
+"""ctypes declarations of the libffadmm C ABI (include/ffadmm.h).
+
+Argument marshalling only: every computation happens in the library.  Loading
+fails loudly when the shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffadmm.so")
+
+FFA_OK = 0
+STATUS_NAMES = {
+    0: "FFA_OK", 1: "FFA_ERR_INVALID_ARG", 2: "FFA_ERR_DEGENERATE_ELEMENT",
+    3: "FFA_ERR_SINGULAR_SYSTEM", 4: "FFA_ERR_CUDA", 5: "FFA_ERR_OOM", 6: "FFA_ERR_NAN",
+    7: "FFA_ERR_NOT_INITIALIZED", 8: "FFA_ERR_FLIPPED",
+}
+
+EXPORTED = [
+    "ffa_default_params", "ffa_create", "ffa_destroy", "ffa_last_error", "ffa_set_handles",
+    "ffa_init", "ffa_iterate", "ffa_get_W", "ffa_get_state", "ffa_energy", "ffa_gradient",
+    "ffa_get_info", "ffa_last_wstep_residual", "ffa_profile_phases",
+]
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("d", C.c_int32), ("d_in", C.c_int32),
+                ("V", C.c_void_p), ("T", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("energy", C.c_int), ("rho", C.c_double), ("eps_abs", C.c_double),
+                ("eps_rel", C.c_double), ("check_every", C.c_int32),
+                ("require_flip_free", C.c_int32), ("local_precision", C.c_int),
+                ("refine_sweeps", C.c_int32), ("nd_leaf_size", C.c_int32),
+                ("host_threads", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("n_flipped", C.c_int32),
+                ("checked_iter", C.c_int32), ("e_prim", C.c_double), ("e_dual", C.c_double),
+                ("thr_prim", C.c_double), ("thr_dual", C.c_double), ("energy_P", C.c_double),
+                ("norm_GW", C.c_double), ("norm_P", C.c_double), ("norm_GtLambda", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("d", C.c_int32), ("d_in", C.c_int32),
+                ("n_pin", C.c_int32), ("n_free", C.c_int32), ("factor_entries", C.c_int64),
+                ("factor_flops", C.c_int64), ("n_supernodes", C.c_int32), ("n_levels", C.c_int32),
+                ("setup_seconds_analyze", C.c_double), ("setup_seconds_factor", C.c_double),
+                ("device_bytes", C.c_int64), ("bytes_local_step", C.c_int64),
+                ("bytes_global_sweep", C.c_int64), ("kernels_per_iteration", C.c_int32),
+                ("kernels_per_check", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PhaseTimes(C.Structure):
+    _fields_ = [("reps", C.c_int32), ("ms_gather", C.c_double), ("ms_wstep", C.c_double),
+                ("ms_vertex", C.c_double), ("ms_local", C.c_double), ("ms_check", C.c_double),
+                ("ms_iteration", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libffadmm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libffadmm.so is not built ({LIB_PATH}); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, dbl = C.c_void_p, C.c_int32, C.c_double
+    sig = {
+        "ffa_default_params": ([C.POINTER(Params)], C.c_int),
+        "ffa_create": ([C.POINTER(Mesh), vp, i32, vp, C.POINTER(Params), vp, C.POINTER(vp)], C.c_int),
+        "ffa_destroy": ([vp], None),
+        "ffa_last_error": ([vp], C.c_char_p),
+        "ffa_set_handles": ([vp, vp], C.c_int),
+        "ffa_init": ([vp, vp], C.c_int),
+        "ffa_iterate": ([vp, i32, i32, C.POINTER(Stats)], C.c_int),
+        "ffa_get_W": ([vp, vp], C.c_int),
+        "ffa_get_state": ([vp, vp, vp, vp], C.c_int),
+        "ffa_energy": ([vp, vp, C.POINTER(dbl)], C.c_int),
+        "ffa_gradient": ([vp, vp, vp], C.c_int),
+        "ffa_get_info": ([vp, C.POINTER(Info)], C.c_int),
+        "ffa_last_wstep_residual": ([vp, C.POINTER(dbl)], C.c_int),
+        "ffa_profile_phases": ([vp, i32, C.POINTER(PhaseTimes)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+class FFAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(lib: C.CDLL, ctx, status: int) -> None:
+    if status != FFA_OK:
+        msg = lib.ffa_last_error(ctx)
+        raise FFAError(status, msg.decode() if msg else "")

@@ -1,0 +1,135 @@
+// Internal interfaces between the C ABI (ffa_api.cu) and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ffadmm.h"
+#include "ffa_factor.h"
+
+namespace ffa {
+
+// Quantities reduced by the local step on check iterations (FP64 partials per block).
+enum { Q_EPRIM = 0, Q_EDUAL, Q_GW, Q_P, Q_ENERGY, Q_FLIPS, Q_NONFINITE, NQ };
+// Quantities reduced by the vertex gathers.
+enum { QV_GTL = 0, QV_NUM, QV_DEN, NQV };
+
+constexpr int kLocalBlock = 128;
+constexpr int kVertexBlock = 256;
+constexpr int kFwdRows = 128;     // forward tile rows (one thread per row)
+constexpr int kFwdCols = 128;     // forward tile columns
+constexpr int kBwdCols = 32;      // backward tile: output columns (4 per warp, 8 warps)
+constexpr int kBwdRows = 256;     // backward tile: rows reduced per task
+
+struct Task {
+  int32_t node, r0, c0, pad;
+};
+
+struct NodeDev {
+  int32_t col0, ncol, nrow, pad;
+  int64_t row_off, blk_off;
+};
+
+// Element state.  Real-typed arrays are float or double depending on the
+// precision of the local step; all are structure-of-arrays with stride m,
+// except contrib (m x (d+1) x d, element-major).
+struct ElemBufs {
+  int32_t* idx = nullptr;  // (d+1) x m
+  void* g = nullptr;       // d*d x m  (hat gradients of vertices 1..d)
+  void* w = nullptr;       // m
+  void* mu = nullptr;      // m
+  void* P = nullptr;       // d(d+1)/2 x m  (00,01,11 | 00,01,02,11,12,22)
+  void* Lam = nullptr;     // d*d x m  (row-major entries)
+  void* U = nullptr;       // 2 x m (cos, sin) for d = 2, 4 x m quaternion for d = 3
+  void* contrib = nullptr;   // m x (d+1) x d : g_j . r_i  (W-step right-hand side terms)
+  void* contrib2 = nullptr;  // m x (d+1) x d : g_j . Lambda_i (check iterations) / energy gradient
+};
+
+struct LocalLaunch {
+  int d, energy, fp64, check;
+  int m;
+  ElemBufs e;
+  const void* vrec;   // vertex records
+  double* partials;   // [blocks][NQ]
+  int64_t n_blocks;
+};
+
+void launch_local_step(const LocalLaunch& L, cudaStream_t s);
+void launch_init_polar(const LocalLaunch& L, cudaStream_t s);
+// energy (mode 0: sum w f(J) + flips into partials) or gradient terms (mode 1: contrib2)
+void launch_energy_terms(const LocalLaunch& L, int mode, cudaStream_t s);
+
+// vertex records from W (double, n x d) and the previous W; also writes W_out.
+struct VertexLaunch {
+  int d, fp64;
+  int n;
+  const double* Wnew_free;   // eliminated-order values of the free vertices (nF x d) or null
+  const float* corr;         // eliminated-order correction added to Wnew_free (or null)
+  const int32_t* v2e;        // vertex -> eliminated index (-1 if pinned)
+  const int32_t* v2pin;      // vertex -> pin slot (-1 if free)
+  const double* pin_pos;     // n_pin x d
+  const double* W_in;        // full W (n x d) used instead of the free/pinned sources if non-null
+  double* W;                 // n x d: current W, overwritten with the new W
+  double* X;                 // eliminated-order free W (nF x d) to keep in sync, or null
+  void* vrec;                // records written
+  int write_dw;              // 1: dW = new - old; 0: dW = 0
+};
+void launch_vertex_update(const VertexLaunch& V, cudaStream_t s);
+
+struct GatherLaunch {
+  int d, fp64;
+  int rows;                  // vertices gathered
+  const int32_t* row_vertex; // row -> original vertex (null = identity)
+  const int64_t* inc_ptr;    // incidence CSR over original vertices
+  const int32_t* inc;        // element * (d+1) + slot
+  const void* contrib;       // element terms
+  const double* add;         // optional row-aligned addend (rows x d)
+  double* out;               // rows x d
+  double* partials;          // optional: sum of squares of out per block (QV_GTL)
+};
+void launch_gather(const GatherLaunch& G, cudaStream_t s);
+
+struct SolveData {
+  int d;
+  int nF;
+  int ell_width;
+  const int32_t* ell_col;    // width x nF (eliminated numbering)
+  const double* ell_val;     // width x nF
+  const NodeDev* nodes;
+  const int32_t* rows;
+  const float* blocks;
+  const Task* fwd_tasks;
+  const Task* bwd_tasks;
+  std::vector<int64_t> fwd_off, bwd_off;  // per level task ranges (host)
+  float* y;                  // nF x d residual / forward work vector
+  float* z;                  // nF x d forward result
+  float* x;                  // nF x d correction
+  double* X;                 // nF x d current free W (eliminated order)
+  const double* b;           // nF x d right-hand side
+};
+// y = float(b - L_FF X); partials (optional) gets |b - L X|^2 and |b|^2
+void launch_residual(const SolveData& S, double* partials, int n_blocks, cudaStream_t s);
+void launch_axpy_correction(const SolveData& S, cudaStream_t s);   // X += x
+void launch_supernodal_solve(const SolveData& S, cudaStream_t s);  // x = L_FF^{-1} y (FP32)
+
+// constant part of the right-hand side: cst = -L_FC b (eliminated order)
+void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, const double* val,
+                    const double* pin_pos, double* cst, cudaStream_t s);
+
+struct FinalLaunch {
+  const double* local_partials;
+  int64_t n_local_blocks;
+  const double* vert_partials;
+  int64_t n_vert_blocks;
+  double eps_abs, eps_rel;
+  int d, m, require_flip_free;
+  int32_t iter;
+  ffa_stats* out;
+};
+void launch_final_reduce(const FinalLaunch& F, cudaStream_t s);
+void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s);
+
+}  // namespace ffa

@@ -1,0 +1,589 @@
+// Per-element kernels: the fused local step (Jacobian assembly, U step, P step,
+// multiplier update, right-hand-side terms and error terms; paper Sec. 4 and
+// Eq. 6.1), the polar initialization (Eq. 6.3-6.4) and the energy terms
+// (Eq. 3.3, 7.1-7.2, A.2-A.3).  One thread per element; all per-element math
+// stays in registers; element data are structure-of-arrays (coalesced).
+#include "ffa_internal.h"
+#include "ffa_math.cuh"
+
+namespace ffa {
+namespace {
+
+// ---------------------------------------------------------------------------
+// vertex records (written by the vertex-update kernel)
+//   float, d=3: 3 float4 = (hi.xyz, dW.x) (lo.xyz, dW.y) (dW.z, -, -, -)
+//   float, d=2: 2 float4 = (hi.xy, lo.xy) (dW.xy, -, -)
+//   double, d=3: 3 double2 = (W.xy) (W.z, dW.x) (dW.yz)
+//   double, d=2: 2 double2 = (W.xy) (dW.xy)
+// hi + lo is W split into two floats, so differences of nearby vertices keep
+// their relative accuracy in float arithmetic.
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__device__ __forceinline__ void load_vertex(const void* rec, int v, R hi[D], R lo[D], R dw[D]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4* r = reinterpret_cast<const float4*>(rec) + (int64_t)v * D;
+    if constexpr (D == 3) {
+      const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+      hi[0] = a.x; hi[1] = a.y; hi[2] = a.z;
+      lo[0] = b.x; lo[1] = b.y; lo[2] = b.z;
+      dw[0] = a.w; dw[1] = b.w; dw[2] = c.x;
+    } else {
+      const float4 a = __ldg(r), b = __ldg(r + 1);
+      hi[0] = a.x; hi[1] = a.y; lo[0] = a.z; lo[1] = a.w;
+      dw[0] = b.x; dw[1] = b.y;
+    }
+  } else {
+    const double2* r = reinterpret_cast<const double2*>(rec) + (int64_t)v * D;
+    if constexpr (D == 3) {
+      const double2 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+      hi[0] = a.x; hi[1] = a.y; hi[2] = b.x;
+      dw[0] = b.y; dw[1] = c.x; dw[2] = c.y;
+    } else {
+      const double2 a = __ldg(r), b = __ldg(r + 1);
+      hi[0] = a.x; hi[1] = a.y; dw[0] = b.x; dw[1] = b.y;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) lo[k] = R(0);
+  }
+}
+
+// J = G W and dJ = G (W - W_prev) of element i (Supplemental: column k of J is
+// the gradient of target coordinate k), from the hat gradients of vertices 1..d.
+template <int D, typename R>
+__device__ __forceinline__ void element_jacobians(const int vid[D + 1], const R g[D][D], const void* vrec,
+                                                  R J[D][D], R dJ[D][D]) {
+  R h0[D], l0[D], d0[D];
+  load_vertex<D, R>(vrec, vid[0], h0, l0, d0);
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int k = 0; k < D; ++k) { J[a][k] = R(0); dJ[a][k] = R(0); }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    R hj[D], lj[D], dj[D];
+    load_vertex<D, R>(vrec, vid[j + 1], hj, lj, dj);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const R del = (hj[k] - h0[k]) + (lj[k] - l0[k]);
+      const R ddel = dj[k] - d0[k];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        J[a][k] = fma(g[j][a], del, J[a][k]);
+        dJ[a][k] = fma(g[j][a], ddel, dJ[a][k]);
+      }
+    }
+  }
+}
+
+template <int D, typename R>
+__device__ __forceinline__ void load_element(const ElemBufs& e, int m, int i, int vid[D + 1], R g[D][D],
+                                             R& w, R& mu) {
+  const R* gp = reinterpret_cast<const R*>(e.g);
+#pragma unroll
+  for (int j = 0; j <= D; ++j) vid[j] = __ldg(e.idx + (int64_t)j * m + i);
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+#pragma unroll
+    for (int a = 0; a < D; ++a) g[j][a] = __ldg(gp + (int64_t)(j * D + a) * m + i);
+  w = __ldg(reinterpret_cast<const R*>(e.w) + i);
+  mu = __ldg(reinterpret_cast<const R*>(e.mu) + i);
+}
+
+// contributions g_j . X[:, k] for the d+1 element vertices (j = 0 is minus the sum)
+template <int D, typename R>
+__device__ __forceinline__ void store_terms(void* dst, int i, const R g[D][D], const R X[D][D]) {
+  R c[D + 1][D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) c[0][k] = R(0);
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      R s = R(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) s = fma(g[j][a], X[a][k], s);
+      c[j + 1][k] = s;
+      c[0][k] -= s;
+    }
+  R* out = reinterpret_cast<R*>(dst) + (int64_t)i * (D + 1) * D;
+#pragma unroll
+  for (int j = 0; j <= D; ++j)
+#pragma unroll
+    for (int k = 0; k < D; ++k) out[j * D + k] = c[j][k];
+}
+
+// ---------------------------------------------------------------------------
+// block reduction of NQ per-thread values into one double partial per block
+// ---------------------------------------------------------------------------
+template <typename R, int N>
+__device__ __forceinline__ void block_reduce(R v[N], double* out) {
+  __shared__ double red[kLocalBlock / 32][N];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    double tot;
+    if constexpr (sizeof(R) == 4) {
+      FF a{v[q], 0.0f};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        a = ff_add(a, b);
+      }
+      tot = (double)a.hi + (double)a.lo;
+    } else {
+      double a = v[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      tot = a;
+    }
+    if (lane == 0) red[warp][q] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+#pragma unroll
+    for (int wv = 0; wv < kLocalBlock / 32; ++wv) s += red[wv][threadIdx.x];
+    out[(int64_t)blockIdx.x * N + threadIdx.x] = s;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ bool finite_(R x) { return isfinite(x); }
+
+// ---------------------------------------------------------------------------
+// the fused local step
+// ---------------------------------------------------------------------------
+template <int D, typename R, int EN, bool CHECK>
+__global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, const void* __restrict__ vrec,
+                                                            double* __restrict__ partials) {
+  const int i = blockIdx.x * kLocalBlock + threadIdx.x;
+  R qv[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) qv[q] = R(0);
+  if (i < m) {
+    int vid[D + 1];
+    R g[D][D], w, mu;
+    load_element<D, R>(e, m, i, vid, g, w, mu);
+    R J[D][D], dJ[D][D];
+    element_jacobians<D, R>(vid, g, vrec, J, dJ);
+    R* Pp = reinterpret_cast<R*>(e.P);
+    R* Lp = reinterpret_cast<R*>(e.Lam);
+    R* Up = reinterpret_cast<R*>(e.U);
+    R A[D][D], Lam[D][D], P[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        Lam[a][k] = Lp[(int64_t)(a * D + k) * m + i];
+        A[a][k] = J[a][k] + Lam[a][k];
+      }
+    if constexpr (D == 2) {
+      P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[1][1] = Pp[2 * (int64_t)m + i];
+    } else {
+      P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[0][2] = P[2][0] = Pp[2 * (int64_t)m + i];
+      P[1][1] = Pp[3 * (int64_t)m + i]; P[1][2] = P[2][1] = Pp[4 * (int64_t)m + i]; P[2][2] = Pp[5 * (int64_t)m + i];
+    }
+    // ---- U step: nearest rotation to Q = (J + Lambda) P (Eq. 4.3-4.4, h = 0)
+    R Q[D][D], U[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        R s = R(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fma(A[a][l], P[l][k], s);
+        Q[a][k] = s;
+      }
+    if constexpr (D == 2) {
+      // maximize U(phi) . Q: (cos, sin) along (q00 + q11, q10 - q01); tie keeps U^{k-1}
+      const R ca = Q[0][0] + Q[1][1], sa = Q[1][0] - Q[0][1];
+      const R r2 = ca * ca + sa * sa;
+      R c, s;
+      if (r2 > R(0)) {
+        const R ir = Tr<R>::rsqrt_(r2);
+        c = ca * ir;
+        s = sa * ir;
+      } else {
+        c = Up[i];
+        s = Up[(int64_t)m + i];
+      }
+      U[0][0] = c; U[0][1] = -s; U[1][0] = s; U[1][1] = c;
+      Up[i] = c;
+      Up[(int64_t)m + i] = s;
+    } else {
+      R Us[3][3], sv[3], Vs[3][3];
+      svd3_signed<R>(Q, Us, sv, Vs);
+      if constexpr (sizeof(R) == 4) {
+        // the rotation is ill-conditioned when s1 + s2 is tiny against s0: redo in double
+        if (sv[1] + sv[2] < R(1e-3) * sv[0]) {
+          double Qd[3][3], Ud[3][3], sd[3], Vd[3][3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Qd[a][k] = (double)Q[a][k];
+          svd3_signed<double>(Qd, Ud, sd, Vd);
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+              U[a][k] = (R)(Ud[a][0] * Vd[k][0] + Ud[a][1] * Vd[k][1] + Ud[a][2] * Vd[k][2]);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) U[a][k] = Us[a][0] * Vs[k][0] + Us[a][1] * Vs[k][1] + Us[a][2] * Vs[k][2];
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) U[a][k] = Us[a][0] * Vs[k][0] + Us[a][1] * Vs[k][1] + Us[a][2] * Vs[k][2];
+      }
+      R qt[4];
+      rot_to_quat<R>(U, qt);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Up[(int64_t)k * m + i] = qt[k];
+    }
+    // ---- P step: S = symm(U^T (J + Lambda)), per-eigenvalue prox root (Eq. 4.5-4.6)
+    R S[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        R s = R(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fma(U[l][a], A[l][k], s);
+        S[a][k] = s;
+      }
+    R p[D];
+    if constexpr (D == 2) {
+      const R s00 = S[0][0], s11 = S[1][1], s01 = R(0.5) * (S[0][1] + S[1][0]);
+      const R mean = R(0.5) * (s00 + s11), dl = R(0.5) * (s00 - s11);
+      const R rr = Tr<R>::sqrt_(dl * dl + s01 * s01);
+      p[0] = prox_root<R, EN>(mean + rr, w, mu);
+      p[1] = prox_root<R, EN>(mean - rr, w, mu);
+      if (p[0] * p[1] < R(kSqrtEpsM) || p[0] + p[1] < R(kSqrtEpsM)) {
+        p[0] = fmax(p[0], R(kSqrtEpsM));
+        p[1] = fmax(p[1], R(kSqrtEpsM));
+      }
+      const R pm = R(0.5) * (p[0] + p[1]);
+      const R dd = (rr > R(0)) ? (p[0] - p[1]) / (R(2) * rr) : R(0);
+      P[0][0] = pm + dd * dl;
+      P[1][1] = pm - dd * dl;
+      P[0][1] = P[1][0] = dd * s01;
+    } else {
+      R ev[3], E[3][3];
+      sym3_eig<R>(S[0][0], R(0.5) * (S[0][1] + S[1][0]), R(0.5) * (S[0][2] + S[2][0]), S[1][1],
+                  R(0.5) * (S[1][2] + S[2][1]), S[2][2], ev, E);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) p[j] = prox_root<R, EN>(ev[j], w, mu);
+      if (p[0] * p[1] * p[2] < R(kSqrtEpsM) || p[0] + p[1] + p[2] < R(kSqrtEpsM)) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) p[j] = fmax(p[j], R(kSqrtEpsM));
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = a; k < 3; ++k) {
+          const R v = E[a][0] * p[0] * E[k][0] + E[a][1] * p[1] * E[k][1] + E[a][2] * p[2] * E[k][2];
+          P[a][k] = v;
+          P[k][a] = v;
+        }
+    }
+    // ---- multiplier update (Eq. 4.7) and the next right-hand-side terms (Eq. 3.6)
+    R UP[D][D], Rm[D][D], Rhs[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        R s = R(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fma(U[a][l], P[l][k], s);
+        UP[a][k] = s;
+        Rm[a][k] = J[a][k] - s;
+        Lam[a][k] += Rm[a][k];
+        Rhs[a][k] = mu * (s - Lam[a][k]);
+      }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int k = 0; k < D; ++k) Lp[(int64_t)(a * D + k) * m + i] = Lam[a][k];
+    if constexpr (D == 2) {
+      Pp[i] = P[0][0]; Pp[(int64_t)m + i] = P[0][1]; Pp[2 * (int64_t)m + i] = P[1][1];
+    } else {
+      Pp[i] = P[0][0]; Pp[(int64_t)m + i] = P[0][1]; Pp[2 * (int64_t)m + i] = P[0][2];
+      Pp[3 * (int64_t)m + i] = P[1][1]; Pp[4 * (int64_t)m + i] = P[1][2]; Pp[5 * (int64_t)m + i] = P[2][2];
+    }
+    store_terms<D, R>(e.contrib, i, g, Rhs);
+    if constexpr (CHECK) {
+      store_terms<D, R>(e.contrib2, i, g, Lam);
+      R ep = 0, ed = 0, gw = 0, pp = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          ep = fma(Rm[a][k], Rm[a][k], ep);
+          ed = fma(dJ[a][k], dJ[a][k], ed);
+          gw = fma(J[a][k], J[a][k], gw);
+          pp = fma(P[a][k], P[a][k], pp);
+        }
+      R det;
+      if constexpr (D == 2) det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      else
+        det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      qv[Q_EPRIM] = ep;
+      qv[Q_EDUAL] = mu * mu * ed;
+      qv[Q_GW] = gw;
+      qv[Q_P] = pp;
+      qv[Q_ENERGY] = w * f_of_eigs<R, EN, D>(p);
+      qv[Q_FLIPS] = (det <= R(0)) ? R(1) : R(0);
+      qv[Q_NONFINITE] = (finite_(ep) && finite_(pp) && finite_(gw)) ? R(0) : R(1);
+    }
+  }
+  if constexpr (CHECK) block_reduce<R, NQ>(qv, partials);
+}
+
+// ---------------------------------------------------------------------------
+// polar initialization (Eq. 6.3-6.4): U0, P0 from the SVD of G W0, Lambda0 = 0
+// ---------------------------------------------------------------------------
+template <int D, typename R, int EN>
+__global__ void __launch_bounds__(kLocalBlock) k_init_polar(ElemBufs e, int m, const void* __restrict__ vrec) {
+  const int i = blockIdx.x * kLocalBlock + threadIdx.x;
+  if (i >= m) return;
+  int vid[D + 1];
+  R g[D][D], w, mu;
+  load_element<D, R>(e, m, i, vid, g, w, mu);
+  R J[D][D], dJ[D][D];
+  element_jacobians<D, R>(vid, g, vrec, J, dJ);
+  const R eps = (EN == 0) ? R(kEpsInitSD) : R(kEpsInitSG);
+  R U[D][D], P[D][D];
+  R* Up = reinterpret_cast<R*>(e.U);
+  if constexpr (D == 2) {
+    const R det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    R c, s;
+    if (det > R(0)) {
+      // rotation maximizing tr(U^T J), then P = U^T J, singular values clamped
+      const R ca = J[0][0] + J[1][1], sa = J[1][0] - J[0][1];
+      const R ir = Tr<R>::rsqrt_(ca * ca + sa * sa);
+      c = ca * ir;
+      s = sa * ir;
+      U[0][0] = c; U[0][1] = -s; U[1][0] = s; U[1][1] = c;
+      R S[2][2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) S[a][k] = U[0][a] * J[0][k] + U[1][a] * J[1][k];
+      const R s01 = R(0.5) * (S[0][1] + S[1][0]);
+      const R mean = R(0.5) * (S[0][0] + S[1][1]), dl = R(0.5) * (S[0][0] - S[1][1]);
+      const R rr = Tr<R>::sqrt_(dl * dl + s01 * s01);
+      const R p0 = fmax(mean + rr, eps), p1 = fmax(mean - rr, eps);
+      const R pm = R(0.5) * (p0 + p1), dd = (rr > R(0)) ? (p0 - p1) / (R(2) * rr) : R(0);
+      P[0][0] = pm + dd * dl; P[1][1] = pm - dd * dl; P[0][1] = P[1][0] = dd * s01;
+    } else {
+      // polar factor is the reflection [[c, s], [s, -c]] maximizing tr(O^T J);
+      // negating its last column gives the rotation (c, s); P0 = eps I
+      const R ca = J[0][0] - J[1][1], sa = J[0][1] + J[1][0];
+      const R r2 = ca * ca + sa * sa;
+      if (r2 > R(0)) {
+        const R ir = Tr<R>::rsqrt_(r2);
+        c = ca * ir;
+        s = sa * ir;
+      } else {
+        c = R(1);
+        s = R(0);
+      }
+      U[0][0] = c; U[0][1] = -s; U[1][0] = s; U[1][1] = c;
+      P[0][0] = eps; P[1][1] = eps; P[0][1] = P[1][0] = R(0);
+    }
+    Up[i] = c;
+    Up[(int64_t)m + i] = s;
+  } else {
+    R Us[3][3], sv[3], Vs[3][3];
+    svd3_signed<R>(J, Us, sv, Vs);
+    const bool flipped = !(sv[2] > R(0));
+    if (flipped && sv[2] < R(0)) {
+      // polar factor U diag(1,1,-1) V^T, then its last column negated
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const R o = Us[a][0] * Vs[k][0] + Us[a][1] * Vs[k][1] - Us[a][2] * Vs[k][2];
+          U[a][k] = (k == 2) ? -o : o;
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) U[a][k] = Us[a][0] * Vs[k][0] + Us[a][1] * Vs[k][1] + Us[a][2] * Vs[k][2];
+    }
+    R sc[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sc[j] = flipped ? eps : fmax(sv[j], eps);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        P[a][k] = Vs[a][0] * sc[0] * Vs[k][0] + Vs[a][1] * sc[1] * Vs[k][1] + Vs[a][2] * sc[2] * Vs[k][2];
+    R qt[4];
+    rot_to_quat<R>(U, qt);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Up[(int64_t)k * m + i] = qt[k];
+  }
+  R* Pp = reinterpret_cast<R*>(e.P);
+  R* Lp = reinterpret_cast<R*>(e.Lam);
+  if constexpr (D == 2) {
+    Pp[i] = P[0][0]; Pp[(int64_t)m + i] = P[0][1]; Pp[2 * (int64_t)m + i] = P[1][1];
+  } else {
+    Pp[i] = P[0][0]; Pp[(int64_t)m + i] = P[0][1]; Pp[2 * (int64_t)m + i] = P[0][2];
+    Pp[3 * (int64_t)m + i] = P[1][1]; Pp[4 * (int64_t)m + i] = P[1][2]; Pp[5 * (int64_t)m + i] = P[2][2];
+  }
+  R Rhs[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      Lp[(int64_t)(a * D + k) * m + i] = R(0);
+      R s = R(0);
+#pragma unroll
+      for (int l = 0; l < D; ++l) s = fma(U[a][l], P[l][k], s);
+      Rhs[a][k] = mu * s;
+    }
+  store_terms<D, R>(e.contrib, i, g, Rhs);
+}
+
+// ---------------------------------------------------------------------------
+// energy terms at a given W: mode 0 -> partials (w f(J), flips); mode 1 -> the
+// per-vertex terms of G^T (w grad f(J)) into contrib2 (Eq. 7.2 / A.3)
+// ---------------------------------------------------------------------------
+template <int D, typename R, int EN, int MODE>
+__global__ void __launch_bounds__(kLocalBlock) k_energy_terms(ElemBufs e, int m, const void* __restrict__ vrec,
+                                                              double* __restrict__ partials) {
+  const int i = blockIdx.x * kLocalBlock + threadIdx.x;
+  R qv[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) qv[q] = R(0);
+  if (i < m) {
+    int vid[D + 1];
+    R g[D][D], w, mu;
+    load_element<D, R>(e, m, i, vid, g, w, mu);
+    R J[D][D], dJ[D][D];
+    element_jacobians<D, R>(vid, g, vrec, J, dJ);
+    // inverse by the adjugate
+    R Ji[D][D], det;
+    if constexpr (D == 2) {
+      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det; Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+    } else {
+      const R c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      const R c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      const R c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+      const R id = R(1) / det;
+      Ji[0][0] = c00 * id; Ji[1][0] = c01 * id; Ji[2][0] = c02 * id;
+      Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+      Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+      Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+      Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+      Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+      Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    }
+    const bool flipped = !(det > R(0));
+    if constexpr (MODE == 0) {
+      R fro = 0, fri = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          fro = fma(J[a][k], J[a][k], fro);
+          fri = fma(Ji[a][k], Ji[a][k], fri);
+        }
+      const R f = (EN == 0) ? R(0.5) * (fro + fri) : R(0.5) * fro - Tr<R>::log_(det);
+      qv[Q_ENERGY] = flipped ? R(0) : w * f;
+      qv[Q_FLIPS] = flipped ? R(1) : R(0);
+    } else {
+      // grad f_SG = J - J^-T ; grad f_SD = J - J^-T J^-1 J^-T
+      R Gr[D][D];
+      if constexpr (EN == 1) {
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int k = 0; k < D; ++k) Gr[a][k] = w * (J[a][k] - Ji[k][a]);
+      } else {
+        R T1[D][D];  // J^-T J^-1
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            R s = R(0);
+#pragma unroll
+            for (int l = 0; l < D; ++l) s = fma(Ji[l][a], Ji[l][k], s);
+            T1[a][k] = s;
+          }
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            R s = R(0);
+#pragma unroll
+            for (int l = 0; l < D; ++l) s = fma(T1[a][l], Ji[k][l], s);
+            Gr[a][k] = w * (J[a][k] - s);
+          }
+      }
+      store_terms<D, R>(e.contrib2, i, g, Gr);
+      qv[Q_FLIPS] = flipped ? R(1) : R(0);
+    }
+  }
+  block_reduce<R, NQ>(qv, partials);
+}
+
+template <int D, typename R, int EN>
+void dispatch_local(const LocalLaunch& L, cudaStream_t s) {
+  const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
+  if (L.check) k_local_step<D, R, EN, true><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+  else k_local_step<D, R, EN, false><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+}
+
+}  // namespace
+
+void launch_local_step(const LocalLaunch& L, cudaStream_t s) {
+  if (L.d == 2) {
+    if (L.fp64) { if (L.energy == 0) dispatch_local<2, double, 0>(L, s); else dispatch_local<2, double, 1>(L, s); }
+    else { if (L.energy == 0) dispatch_local<2, float, 0>(L, s); else dispatch_local<2, float, 1>(L, s); }
+  } else {
+    if (L.fp64) { if (L.energy == 0) dispatch_local<3, double, 0>(L, s); else dispatch_local<3, double, 1>(L, s); }
+    else { if (L.energy == 0) dispatch_local<3, float, 0>(L, s); else dispatch_local<3, float, 1>(L, s); }
+  }
+}
+
+void launch_init_polar(const LocalLaunch& L, cudaStream_t s) {
+  const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
+#define FFA_INIT(D, R, EN) k_init_polar<D, R, EN><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec)
+  if (L.d == 2) {
+    if (L.fp64) { if (L.energy == 0) FFA_INIT(2, double, 0); else FFA_INIT(2, double, 1); }
+    else { if (L.energy == 0) FFA_INIT(2, float, 0); else FFA_INIT(2, float, 1); }
+  } else {
+    if (L.fp64) { if (L.energy == 0) FFA_INIT(3, double, 0); else FFA_INIT(3, double, 1); }
+    else { if (L.energy == 0) FFA_INIT(3, float, 0); else FFA_INIT(3, float, 1); }
+  }
+#undef FFA_INIT
+}
+
+void launch_energy_terms(const LocalLaunch& L, int mode, cudaStream_t s) {
+  const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
+#define FFA_EN(D, R, EN)                                                                           \
+  do {                                                                                             \
+    if (mode == 0) k_energy_terms<D, R, EN, 0><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials); \
+    else k_energy_terms<D, R, EN, 1><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials);           \
+  } while (0)
+  if (L.d == 2) {
+    if (L.fp64) { if (L.energy == 0) FFA_EN(2, double, 0); else FFA_EN(2, double, 1); }
+    else { if (L.energy == 0) FFA_EN(2, float, 0); else FFA_EN(2, float, 1); }
+  } else {
+    if (L.fp64) { if (L.energy == 0) FFA_EN(3, double, 0); else FFA_EN(3, double, 1); }
+    else { if (L.energy == 0) FFA_EN(3, float, 0); else FFA_EN(3, float, 1); }
+  }
+#undef FFA_EN
+}
+
+}  // namespace ffa

@@ -1,0 +1,280 @@
+// Register-resident per-element math for the local steps (paper Sec. 4 and the
+// Supplemental "Solving the optimization in P / in U").  Templated on the scalar
+// type: float for the FP32 local step, double for the FP64 one.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace ffa {
+
+template <typename R> struct Tr;
+template <> struct Tr<float> {
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
+  static __device__ __forceinline__ float log_(float x) { return logf(x); }
+  static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+  static __device__ __forceinline__ float tiny() { return 1e-30f; }
+  static __device__ __forceinline__ float eps() { return 1.1920929e-07f; }
+  static constexpr int jacobi_sweeps = 6;
+  static constexpr int newton_iters = 24;
+};
+template <> struct Tr<double> {
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+  static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
+  static __device__ __forceinline__ double log_(double x) { return log(x); }
+  static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+  static __device__ __forceinline__ double tiny() { return 1e-300; }
+  static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
+  static constexpr int jacobi_sweeps = 10;
+  static constexpr int newton_iters = 48;
+};
+
+// Constants of the method, all in terms of the double machine epsilon 2^-52:
+// eps_init = eps_m^(1/4) (SG) or eps_m^(1/8) (SD) for the polar initialization
+// (Eq. 6.4) and the eigenvalue floor sqrt(eps_m) of the P step (Supplemental).
+constexpr double kEpsInitSG = 1.220703125e-04;          // 2^-13
+constexpr double kEpsInitSD = 1.104854345603981e-02;    // 2^-6.5
+constexpr double kSqrtEpsM = 1.4901161193847656e-08;    // 2^-26
+
+// ---------------------------------------------------------------------------
+// scalar prox roots: the per-eigenvalue form of w grad f(P) + mu P = mu S
+// ---------------------------------------------------------------------------
+
+// Symmetric gradient: (w + mu) p^2 - mu q p - w = 0, positive root (Eq. S.3 per
+// eigenvalue).  Divided by (w + mu): p^2 - t q p - c = 0 with t = mu/(w+mu),
+// c = w/(w+mu); for q < 0 the cancellation-free form 2c / (sqrt(disc) - t q).
+template <typename R>
+__device__ __forceinline__ R prox_root_sg(R q, R w, R mu) {
+  const R inv = R(1) / (w + mu);
+  const R t = mu * inv, c = w * inv;
+  const R tq = t * q;
+  const R sd = Tr<R>::sqrt_(tq * tq + R(4) * c);
+  return (q >= R(0)) ? R(0.5) * (tq + sd) : (R(2) * c) / (sd - tq);
+}
+
+// Symmetric Dirichlet: (w + mu) p^4 - mu q p^3 - w = 0 (Eq. S.4 per eigenvalue),
+// i.e. g(p) = p^3 (p - a) - c with a = t q.  g is convex and increasing to the
+// right of its unique positive root, so Newton started above the root decreases
+// monotonically onto it.  Start: for a > 0 the root lies in (a, a + min(c^(1/4),
+// c / a^3)]; for a <= 0 it lies in (0, min(c^(1/4), (c/|a|)^(1/3))].
+template <typename R>
+__device__ __forceinline__ R prox_root_sd(R q, R w, R mu) {
+  const R inv = R(1) / (w + mu);
+  const R a = mu * inv * q, c = w * inv;
+  const R c4 = Tr<R>::sqrt_(Tr<R>::sqrt_(c));
+  R p;
+  if (a > R(0)) {
+    const R a3 = a * a * a;
+    p = a + fmin(c4, c / a3);
+  } else if (a < R(0)) {
+    p = fmin(c4, Tr<R>::cbrt_(c / (-a)));
+  } else {
+    return c4;
+  }
+#pragma unroll 1
+  for (int it = 0; it < Tr<R>::newton_iters; ++it) {
+    const R p2 = p * p;
+    const R g = p2 * p * (p - a) - c;
+    const R dg = p2 * (R(4) * p - R(3) * a);
+    if (!(dg > R(0))) break;
+    const R step = g / dg;
+    p -= step;
+    if (Tr<R>::abs_(step) <= R(2) * Tr<R>::eps() * p) break;
+  }
+  return p;
+}
+
+template <typename R, int ENERGY>
+__device__ __forceinline__ R prox_root(R q, R w, R mu) {
+  return ENERGY == 0 ? prox_root_sd<R>(q, w, mu) : prox_root_sg<R>(q, w, mu);
+}
+
+// f on an SPD matrix with eigenvalues p: SD (sum p^2 + sum p^-2)/2, SG sum p^2/2 - log p.
+template <typename R, int ENERGY, int D>
+__device__ __forceinline__ R f_of_eigs(const R p[D]) {
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (ENERGY == 0) s += R(0.5) * (p[j] * p[j] + R(1) / (p[j] * p[j]));
+    else s += R(0.5) * p[j] * p[j] - Tr<R>::log_(p[j]);
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void jacobi_rotate(R& app, R& aqq, R& apq, R& arp, R& arq, R V[3][3],
+                                              int p, int q) {
+  if (apq == R(0)) return;
+  const R theta = (aqq - app) / (R(2) * apq);
+  const R at = Tr<R>::abs_(theta);
+  R t = R(1) / (at + Tr<R>::sqrt_(at * at + R(1)));
+  if (at * Tr<R>::eps() > R(1)) t = R(0.5) / at;  // theta^2 would overflow
+  t = (theta < R(0)) ? -t : t;
+  const R c = Tr<R>::rsqrt_(t * t + R(1));
+  const R s = t * c;
+  app -= t * apq;
+  aqq += t * apq;
+  apq = R(0);
+  const R rp = c * arp - s * arq;
+  const R rq = s * arp + c * arq;
+  arp = rp;
+  arq = rq;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const R vp = V[r][p], vq = V[r][q];
+    V[r][p] = c * vp - s * vq;
+    V[r][q] = s * vp + c * vq;
+  }
+}
+
+// In: symmetric (a00,a01,a02,a11,a12,a22).  Out: eigenvalues ev and eigenvectors
+// in the columns of V (orthonormal, det +1).
+template <typename R>
+__device__ __forceinline__ void sym3_eig(R a00, R a01, R a02, R a11, R a12, R a22, R ev[3], R V[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? R(1) : R(0);
+  const R scale2 = a00 * a00 + a11 * a11 + a22 * a22 + R(2) * (a01 * a01 + a02 * a02 + a12 * a12);
+#pragma unroll 1
+  for (int sw = 0; sw < Tr<R>::jacobi_sweeps; ++sw) {
+    const R off = a01 * a01 + a02 * a02 + a12 * a12;
+    if (off <= Tr<R>::eps() * Tr<R>::eps() * R(0.01) * scale2 || off <= Tr<R>::tiny()) break;
+    jacobi_rotate<R>(a00, a11, a01, a02, a12, V, 0, 1);  // r = 2: (a20, a21)
+    jacobi_rotate<R>(a00, a22, a02, a01, a12, V, 0, 2);  // r = 1: (a10, a12)
+    jacobi_rotate<R>(a11, a22, a12, a01, a02, V, 1, 2);  // r = 0: (a01, a02)
+  }
+  ev[0] = a00;
+  ev[1] = a11;
+  ev[2] = a22;
+}
+
+// ---------------------------------------------------------------------------
+// signed 3x3 SVD: Q = U diag(s) V^T with U, V in SO(3), |s0| >= |s1| >= |s2|,
+// s0, s1 >= 0 and sign(s2) = sign(det Q).  Jacobi on Q^T Q gives V; Givens QR
+// of Q V gives U and the signed diagonal.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void givens_rows(R B[3][3], R U[3][3], int p, int q, int col) {
+  const R a = B[p][col], b = B[q][col];
+  const R r2 = a * a + b * b;
+  R c = R(1), s = R(0);
+  if (r2 > Tr<R>::tiny()) {
+    const R ir = Tr<R>::rsqrt_(r2);
+    c = a * ir;
+    s = b * ir;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const R bp = B[p][k], bq = B[q][k];
+    B[p][k] = c * bp + s * bq;
+    B[q][k] = -s * bp + c * bq;
+    const R up = U[k][p], uq = U[k][q];
+    U[k][p] = c * up + s * uq;
+    U[k][q] = -s * up + c * uq;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void swap_cols_neg(R A[3][3], int i, int j) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const R t = A[r][i];
+    A[r][i] = A[r][j];
+    A[r][j] = -t;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void svd3_signed(const R Q[3][3], R U[3][3], R s[3], R V[3][3]) {
+  R a00 = 0, a01 = 0, a02 = 0, a11 = 0, a12 = 0, a22 = 0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    a00 += Q[r][0] * Q[r][0];
+    a01 += Q[r][0] * Q[r][1];
+    a02 += Q[r][0] * Q[r][2];
+    a11 += Q[r][1] * Q[r][1];
+    a12 += Q[r][1] * Q[r][2];
+    a22 += Q[r][2] * Q[r][2];
+  }
+  R ev[3];
+  sym3_eig<R>(a00, a01, a02, a11, a12, a22, ev, V);
+  R B[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) B[i][j] = Q[i][0] * V[0][j] + Q[i][1] * V[1][j] + Q[i][2] * V[2][j];
+  R n0 = B[0][0] * B[0][0] + B[1][0] * B[1][0] + B[2][0] * B[2][0];
+  R n1 = B[0][1] * B[0][1] + B[1][1] * B[1][1] + B[2][1] * B[2][1];
+  R n2 = B[0][2] * B[0][2] + B[1][2] * B[1][2] + B[2][2] * B[2][2];
+  if (n0 < n1) { swap_cols_neg<R>(B, 0, 1); swap_cols_neg<R>(V, 0, 1); R t = n0; n0 = n1; n1 = t; }
+  if (n0 < n2) { swap_cols_neg<R>(B, 0, 2); swap_cols_neg<R>(V, 0, 2); R t = n0; n0 = n2; n2 = t; }
+  if (n1 < n2) { swap_cols_neg<R>(B, 1, 2); swap_cols_neg<R>(V, 1, 2); R t = n1; n1 = n2; n2 = t; }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) U[i][j] = (i == j) ? R(1) : R(0);
+  givens_rows<R>(B, U, 0, 1, 0);
+  givens_rows<R>(B, U, 0, 2, 0);
+  givens_rows<R>(B, U, 1, 2, 1);
+  s[0] = B[0][0];
+  s[1] = B[1][1];
+  s[2] = B[2][2];
+}
+
+// ---------------------------------------------------------------------------
+// rotations <-> compact storage
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void rot_to_quat(const R M[3][3], R qv[4]) {  // (w, x, y, z)
+  const R tr = M[0][0] + M[1][1] + M[2][2];
+  R w, x, y, z;
+  if (tr > R(0)) {
+    const R s = Tr<R>::sqrt_(tr + R(1)) * R(2);
+    w = R(0.25) * s; x = (M[2][1] - M[1][2]) / s; y = (M[0][2] - M[2][0]) / s; z = (M[1][0] - M[0][1]) / s;
+  } else if (M[0][0] > M[1][1] && M[0][0] > M[2][2]) {
+    const R s = Tr<R>::sqrt_(R(1) + M[0][0] - M[1][1] - M[2][2]) * R(2);
+    w = (M[2][1] - M[1][2]) / s; x = R(0.25) * s; y = (M[0][1] + M[1][0]) / s; z = (M[0][2] + M[2][0]) / s;
+  } else if (M[1][1] > M[2][2]) {
+    const R s = Tr<R>::sqrt_(R(1) + M[1][1] - M[0][0] - M[2][2]) * R(2);
+    w = (M[0][2] - M[2][0]) / s; x = (M[0][1] + M[1][0]) / s; y = R(0.25) * s; z = (M[1][2] + M[2][1]) / s;
+  } else {
+    const R s = Tr<R>::sqrt_(R(1) + M[2][2] - M[0][0] - M[1][1]) * R(2);
+    w = (M[1][0] - M[0][1]) / s; x = (M[0][2] + M[2][0]) / s; y = (M[1][2] + M[2][1]) / s; z = R(0.25) * s;
+  }
+  const R nrm = Tr<R>::rsqrt_(w * w + x * x + y * y + z * z);
+  qv[0] = w * nrm; qv[1] = x * nrm; qv[2] = y * nrm; qv[3] = z * nrm;
+}
+
+template <typename R>
+__device__ __forceinline__ void quat_to_rot(const R qv[4], R M[3][3]) {
+  const R w = qv[0], x = qv[1], y = qv[2], z = qv[3];
+  M[0][0] = R(1) - R(2) * (y * y + z * z); M[0][1] = R(2) * (x * y - z * w); M[0][2] = R(2) * (x * z + y * w);
+  M[1][0] = R(2) * (x * y + z * w); M[1][1] = R(1) - R(2) * (x * x + z * z); M[1][2] = R(2) * (y * z - x * w);
+  M[2][0] = R(2) * (x * z - y * w); M[2][1] = R(2) * (y * z + x * w); M[2][2] = R(1) - R(2) * (x * x + y * y);
+}
+
+// ---------------------------------------------------------------------------
+// double-float accumulation (two floats carry ~48 significant bits), used where
+// sums of many float terms must keep double-level accuracy on the FP32 path.
+// ---------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return FF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ FF ff_addf(FF a, float b) { return ff_add(a, FF{b, 0.0f}); }
+
+}  // namespace ffa

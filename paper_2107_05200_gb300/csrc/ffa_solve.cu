@@ -1,0 +1,451 @@
+// Vertex-side kernels of the W step (Eq. 3.6): right-hand-side gather G^T r,
+// the double-precision residual b - L_FF W_F, the float supernodal triangular
+// solves that turn the residual into a correction (mixed-precision refinement),
+// and the vertex update that publishes W for the next local step.  Also the
+// reductions that evaluate the termination test of Eq. 6.1-6.2.
+#include <math.h>
+
+#include "ffa_internal.h"
+#include "ffa_math.cuh"
+
+namespace ffa {
+namespace {
+
+// ---------------------------------------------------------------------------
+// vertex update: W_new from the eliminated-order solution (free vertices) or the
+// pinned positions; writes W, optionally X, dW = W_new - W_old, and the records
+// ---------------------------------------------------------------------------
+template <int D, bool FP64>
+__global__ void __launch_bounds__(kVertexBlock) k_vertex_update(VertexLaunch V) {
+  const int v = blockIdx.x * kVertexBlock + threadIdx.x;
+  if (v >= V.n) return;
+  double wn[D], wo[D];
+  const int e = V.v2e[v];
+#pragma unroll
+  for (int k = 0; k < D; ++k) wo[k] = V.W[(int64_t)v * D + k];
+  if (V.W_in) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) wn[k] = V.W_in[(int64_t)v * D + k];
+    if (e < 0 && V.v2pin != nullptr) {
+      const int p = V.v2pin[v];
+#pragma unroll
+      for (int k = 0; k < D; ++k) wn[k] = V.pin_pos[(int64_t)p * D + k];
+    }
+  } else if (e >= 0) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      double x = V.Wnew_free[(int64_t)e * D + k];
+      if (V.corr) x += (double)V.corr[(int64_t)e * D + k];
+      wn[k] = x;
+    }
+  } else {
+    const int p = V.v2pin[v];
+#pragma unroll
+    for (int k = 0; k < D; ++k) wn[k] = V.pin_pos[(int64_t)p * D + k];
+  }
+  double dw[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    dw[k] = V.write_dw ? wn[k] - wo[k] : 0.0;
+    V.W[(int64_t)v * D + k] = wn[k];
+    if (V.X && e >= 0) V.X[(int64_t)e * D + k] = wn[k];
+  }
+  if constexpr (FP64) {
+    double2* r = reinterpret_cast<double2*>(V.vrec) + (int64_t)v * D;
+    if constexpr (D == 3) {
+      r[0] = make_double2(wn[0], wn[1]);
+      r[1] = make_double2(wn[2], dw[0]);
+      r[2] = make_double2(dw[1], dw[2]);
+    } else {
+      r[0] = make_double2(wn[0], wn[1]);
+      r[1] = make_double2(dw[0], dw[1]);
+    }
+  } else {
+    float hi[D], lo[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      hi[k] = (float)wn[k];
+      lo[k] = (float)(wn[k] - (double)hi[k]);
+    }
+    float4* r = reinterpret_cast<float4*>(V.vrec) + (int64_t)v * D;
+    if constexpr (D == 3) {
+      r[0] = make_float4(hi[0], hi[1], hi[2], (float)dw[0]);
+      r[1] = make_float4(lo[0], lo[1], lo[2], (float)dw[1]);
+      r[2] = make_float4((float)dw[2], 0.f, 0.f, 0.f);
+    } else {
+      r[0] = make_float4(hi[0], hi[1], lo[0], lo[1]);
+      r[1] = make_float4((float)dw[0], (float)dw[1], 0.f, 0.f);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// gather of per-element vertex terms: out_row = sum over the incidences of the
+// row's vertex (+ add_row); float terms are summed in double-float
+// ---------------------------------------------------------------------------
+template <int D, bool FP64>
+__global__ void __launch_bounds__(kVertexBlock) k_gather(GatherLaunch G) {
+  const int row = blockIdx.x * kVertexBlock + threadIdx.x;
+  double outv[D];
+  double sq = 0.0;
+  if (row < G.rows) {
+    const int v = G.row_vertex ? G.row_vertex[row] : row;
+    const int64_t q0 = G.inc_ptr[v], q1 = G.inc_ptr[v + 1];
+    if constexpr (FP64) {
+      const double* c = reinterpret_cast<const double*>(G.contrib);
+      double acc[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = 0.0;
+      for (int64_t q = q0; q < q1; ++q) {
+        const int64_t base = (int64_t)__ldg(G.inc + q) * D;
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] += __ldg(c + base + k);
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) outv[k] = acc[k];
+    } else {
+      const float* c = reinterpret_cast<const float*>(G.contrib);
+      FF acc[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = FF{0.f, 0.f};
+      for (int64_t q = q0; q < q1; ++q) {
+        const int64_t base = (int64_t)__ldg(G.inc + q) * D;
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] = ff_addf(acc[k], __ldg(c + base + k));
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) outv[k] = (double)acc[k].hi + (double)acc[k].lo;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (G.add) outv[k] += G.add[(int64_t)row * D + k];
+      if (G.out) G.out[(int64_t)row * D + k] = outv[k];
+      sq += outv[k] * outv[k];
+    }
+  }
+  if (G.partials) {
+    __shared__ double red[kVertexBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kVertexBlock / 32; ++w) s += red[w];
+      G.partials[blockIdx.x] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// residual y = float(b - L_FF X) in double (ELL, column-major, eliminated order)
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kVertexBlock) k_residual(const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                            int width, int nF, const double* __restrict__ X,
+                                                            const double* __restrict__ b, float* __restrict__ y,
+                                                            double* __restrict__ partials) {
+  const int i = blockIdx.x * kVertexBlock + threadIdx.x;
+  double rr = 0.0, bb = 0.0;
+  if (i < nF) {
+    double acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = b[(int64_t)i * D + k];
+    for (int q = 0; q < width; ++q) {
+      const int j = __ldg(col + (int64_t)q * nF + i);
+      const double a = __ldg(val + (int64_t)q * nF + i);
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = fma(-a, X[(int64_t)j * D + k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      y[(int64_t)i * D + k] = (float)acc[k];
+      rr += acc[k] * acc[k];
+      const double bk = b[(int64_t)i * D + k];
+      bb += bk * bk;
+    }
+  }
+  if (partials) {
+    __shared__ double red[2][kVertexBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rr += __shfl_xor_sync(0xffffffffu, rr, o);
+      bb += __shfl_xor_sync(0xffffffffu, bb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = rr;
+      red[1][threadIdx.x >> 5] = bb;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double s = 0.0;
+      for (int w = 0; w < kVertexBlock / 32; ++w) s += red[threadIdx.x][w];
+      partials[(int64_t)blockIdx.x * 2 + threadIdx.x] = s;
+    }
+  }
+}
+
+__global__ void k_axpy(int n, double* __restrict__ X, const float* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) X[i] += (double)x[i];
+}
+
+// ---------------------------------------------------------------------------
+// supernodal solves.  Forward task (node, r0, c0): rows [r0, r0+128) x columns
+// [c0, c0+128) of B_s times f = y[cols(s)]; rows < n_s add into z, rows >= n_s
+// subtract from y at the structure rows.  One thread per row; B_s is
+// column-major so each column read is coalesced across the warp.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kFwdRows) k_forward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+                                                      const int32_t* __restrict__ rows, const float* __restrict__ blocks,
+                                                      float* __restrict__ y, float* __restrict__ z) {
+  const Task t = tasks[blockIdx.x];
+  const NodeDev nd = nodes[t.node];
+  const int ld = nd.ncol + nd.nrow;
+  const int nc = min(kFwdCols, nd.ncol - t.c0);
+  __shared__ float fs[kFwdCols][D];
+  for (int q = threadIdx.x; q < nc * D; q += kFwdRows) {
+    const int c = q / D, k = q - c * D;
+    fs[c][k] = y[(int64_t)(nd.col0 + t.c0 + c) * D + k];
+  }
+  __syncthreads();
+  const int row = t.r0 + threadIdx.x;
+  if (row >= ld) return;
+  // in the inverse-diagonal part only columns <= row are nonzero
+  const int cend = (row < nd.ncol) ? min(nc, row - t.c0 + 1) : nc;
+  const float* B = blocks + nd.blk_off + (int64_t)t.c0 * ld + row;
+  float acc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = 0.f;
+  int c = 0;
+  for (; c + 4 <= cend; c += 4) {
+    const float b0 = __ldg(B + (int64_t)c * ld), b1 = __ldg(B + (int64_t)(c + 1) * ld);
+    const float b2 = __ldg(B + (int64_t)(c + 2) * ld), b3 = __ldg(B + (int64_t)(c + 3) * ld);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      acc[k] = fmaf(b0, fs[c][k], acc[k]);
+      acc[k] = fmaf(b1, fs[c + 1][k], acc[k]);
+      acc[k] = fmaf(b2, fs[c + 2][k], acc[k]);
+      acc[k] = fmaf(b3, fs[c + 3][k], acc[k]);
+    }
+  }
+  for (; c < cend; ++c) {
+    const float bv = __ldg(B + (int64_t)c * ld);
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = fmaf(bv, fs[c][k], acc[k]);
+  }
+  if (cend <= 0) return;
+  if (row < nd.ncol) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) atomicAdd(z + (int64_t)(nd.col0 + row) * D + k, acc[k]);
+  } else {
+    const int r = __ldg(rows + nd.row_off + (row - nd.ncol));
+#pragma unroll
+    for (int k = 0; k < D; ++k) atomicAdd(y + (int64_t)r * D + k, -acc[k]);
+  }
+}
+
+// Backward task (node, r0, c0): output columns [c0, c0+32) of x_s, rows
+// [r0, r0+256) of B_s; v = [z_s ; -x at the structure].  A warp owns one column
+// at a time and reads it coalesced; partial dot products go to x atomically.
+template <int D>
+__global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+                                                  const int32_t* __restrict__ rows, const float* __restrict__ blocks,
+                                                  const float* __restrict__ z, float* __restrict__ x) {
+  const Task t = tasks[blockIdx.x];
+  const NodeDev nd = nodes[t.node];
+  const int ld = nd.ncol + nd.nrow;
+  const int nr = min(kBwdRows, ld - t.r0);
+  __shared__ float vs[kBwdRows][D];
+  for (int q = threadIdx.x; q < nr * D; q += 256) {
+    const int r = q / D, k = q - r * D;
+    const int row = t.r0 + r;
+    float v;
+    if (row < nd.ncol) v = z[(int64_t)(nd.col0 + row) * D + k];
+    else v = -x[(int64_t)__ldg(rows + nd.row_off + (row - nd.ncol)) * D + k];
+    vs[r][k] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncols = min(kBwdCols, nd.ncol - t.c0);
+  for (int cc = warp; cc < ncols; cc += 8) {
+    const int j = t.c0 + cc;
+    const float* B = blocks + nd.blk_off + (int64_t)j * ld;
+    // rows < j of the inverse-diagonal part are zero
+    const int rstart = max(0, j - t.r0);
+    float acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = 0.f;
+    for (int r = rstart + lane; r < nr; r += 32) {
+      const float bv = __ldg(B + t.r0 + r);
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = fmaf(bv, vs[r][k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float a = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      acc[k] = a;
+    }
+    if (lane == 0 && rstart < nr) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) atomicAdd(x + (int64_t)(nd.col0 + j) * D + k, acc[k]);
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kVertexBlock) k_pin_rhs(int nF, const int64_t* __restrict__ ptr,
+                                                          const int32_t* __restrict__ pc, const double* __restrict__ val,
+                                                          const double* __restrict__ pin_pos, double* __restrict__ cst) {
+  const int i = blockIdx.x * kVertexBlock + threadIdx.x;
+  if (i >= nF) return;
+  double acc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = 0.0;
+  for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+    const double a = val[q];
+    const int p = pc[q];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] -= a * pin_pos[(int64_t)p * D + k];
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) cst[(int64_t)i * D + k] = acc[k];
+}
+
+// ---------------------------------------------------------------------------
+// termination test (Eq. 6.1-6.2), single block
+// ---------------------------------------------------------------------------
+__global__ void k_final(FinalLaunch F) {
+  __shared__ double acc[NQ + 1];
+  const int tid = threadIdx.x;
+  for (int q = 0; q <= NQ; ++q) {
+    double s = 0.0;
+    if (q < NQ) {
+      for (int64_t b = tid; b < F.n_local_blocks; b += blockDim.x) s += F.local_partials[b * NQ + q];
+    } else {
+      for (int64_t b = tid; b < F.n_vert_blocks; b += blockDim.x) s += F.vert_partials[b];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double wsum[32];
+    if ((tid & 31) == 0) wsum[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+      acc[q] = t;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    ffa_stats st;
+    st.iters = 0;
+    st.checked_iter = F.iter;
+    st.e_prim = sqrt(acc[Q_EPRIM]);
+    st.e_dual = sqrt(acc[Q_EDUAL]);
+    st.norm_GW = sqrt(acc[Q_GW]);
+    st.norm_P = sqrt(acc[Q_P]);
+    st.norm_GtLambda = sqrt(acc[NQ]);
+    st.energy_P = acc[Q_ENERGY];
+    st.n_flipped = (int32_t)(acc[Q_FLIPS] + 0.5);
+    const double base = F.eps_abs * sqrt((double)F.d * (double)F.m);
+    st.thr_prim = base + F.eps_rel * fmax(st.norm_GW, st.norm_P);
+    st.thr_dual = base + F.eps_rel * st.norm_GtLambda;
+    const bool finite_ok = acc[Q_NONFINITE] == 0.0 && isfinite(st.e_prim) && isfinite(st.e_dual);
+    st.converged = (finite_ok && st.e_prim < st.thr_prim && st.e_dual < st.thr_dual &&
+                    (!F.require_flip_free || st.n_flipped == 0)) ? 1 : 0;
+    if (!finite_ok) st.converged = -1;
+    *F.out = st;
+  }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ p, int64_t nb, int nq, double* __restrict__ out) {
+  const int q = blockIdx.x;
+  double s = 0.0;
+  for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) s += p[b * nq + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double wsum[32];
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+    out[q] = t;
+  }
+}
+
+inline int blocks_for(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_vertex_update(const VertexLaunch& V, cudaStream_t s) {
+  const int g = blocks_for(V.n, kVertexBlock);
+  if (V.d == 2) {
+    if (V.fp64) k_vertex_update<2, true><<<g, kVertexBlock, 0, s>>>(V);
+    else k_vertex_update<2, false><<<g, kVertexBlock, 0, s>>>(V);
+  } else {
+    if (V.fp64) k_vertex_update<3, true><<<g, kVertexBlock, 0, s>>>(V);
+    else k_vertex_update<3, false><<<g, kVertexBlock, 0, s>>>(V);
+  }
+}
+
+void launch_gather(const GatherLaunch& G, cudaStream_t s) {
+  const int g = blocks_for(G.rows, kVertexBlock);
+  if (G.d == 2) {
+    if (G.fp64) k_gather<2, true><<<g, kVertexBlock, 0, s>>>(G);
+    else k_gather<2, false><<<g, kVertexBlock, 0, s>>>(G);
+  } else {
+    if (G.fp64) k_gather<3, true><<<g, kVertexBlock, 0, s>>>(G);
+    else k_gather<3, false><<<g, kVertexBlock, 0, s>>>(G);
+  }
+}
+
+void launch_residual(const SolveData& S, double* partials, int n_blocks, cudaStream_t s) {
+  (void)n_blocks;
+  const int g = blocks_for(S.nF, kVertexBlock);
+  if (S.d == 2) k_residual<2><<<g, kVertexBlock, 0, s>>>(S.ell_col, S.ell_val, S.ell_width, S.nF, S.X, S.b, S.y, partials);
+  else k_residual<3><<<g, kVertexBlock, 0, s>>>(S.ell_col, S.ell_val, S.ell_width, S.nF, S.X, S.b, S.y, partials);
+}
+
+void launch_axpy_correction(const SolveData& S, cudaStream_t s) {
+  const int64_t n = (int64_t)S.nF * S.d;
+  k_axpy<<<blocks_for(n, 256), 256, 0, s>>>((int)n, S.X, S.x);
+}
+
+void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
+  const size_t bytes = (size_t)S.nF * S.d * sizeof(float);
+  cudaMemsetAsync(S.z, 0, bytes, s);
+  cudaMemsetAsync(S.x, 0, bytes, s);
+  const int L = (int)S.fwd_off.size() - 1;
+  for (int l = 0; l < L; ++l) {
+    const int64_t nt = S.fwd_off[l + 1] - S.fwd_off[l];
+    if (nt <= 0) continue;
+    if (S.d == 2) k_forward<2><<<(unsigned)nt, kFwdRows, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+    else k_forward<3><<<(unsigned)nt, kFwdRows, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const int64_t nt = S.bwd_off[l + 1] - S.bwd_off[l];
+    if (nt <= 0) continue;
+    if (S.d == 2) k_backward<2><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
+    else k_backward<3><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
+  }
+}
+
+void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, const double* val,
+                    const double* pin_pos, double* cst, cudaStream_t s) {
+  const int g = blocks_for(nF, kVertexBlock);
+  if (d == 2) k_pin_rhs<2><<<g, kVertexBlock, 0, s>>>(nF, ptr, pin_col, val, pin_pos, cst);
+  else k_pin_rhs<3><<<g, kVertexBlock, 0, s>>>(nF, ptr, pin_col, val, pin_pos, cst);
+}
+
+void launch_final_reduce(const FinalLaunch& F, cudaStream_t s) { k_final<<<1, 256, 0, s>>>(F); }
+
+void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s) {
+  k_sum_partials<<<nq, 256, 0, s>>>(partials, n_blocks, nq, out);
+}
+
+}  // namespace ffa

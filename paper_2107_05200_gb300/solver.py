@@ -1,0 +1,165 @@
+"""Python binding of the flip-free ADMM library: argument marshalling only.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); they are passed to the C ABI by pointer.  Names follow the paper:
+V, T (source mesh), W (target vertices), U, P, Lambda (per-element splitting
+variables), rho (penalty scale, mu_i = rho w_i).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+
+ENERGIES = {"sd": 0, "sg": 1}
+PRECISIONS = {"fp32": 0, "fp64": 1}
+
+
+def _ptr(a, dtype):
+    """Pointer of a contiguous numpy array / torch tensor of the given dtype."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        return C.c_void_p(a.ctypes.data), a
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        tdt = torch.float64 if dtype == np.float64 else torch.int32
+        if a.dtype != tdt or not a.is_contiguous():
+            a = a.to(tdt).contiguous()
+        return C.c_void_p(a.data_ptr()), a
+    a = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+    return C.c_void_p(a.ctypes.data), a
+
+
+class Solver:
+    """One mesh, one energy, fixed penalties: setup once, then init / iterate."""
+
+    def __init__(self, V, T, pins=None, pin_pos=None, energy: str = "sd", rho: float = 1.0,
+                 eps_abs: float = 1e-6, eps_rel: float = 1e-5, check_every: int = 10,
+                 precision: str = "fp32", refine_sweeps: int = 2, leaf_size: int = 64,
+                 require_flip_free: bool = True, host_threads: int = 0, stream=None):
+        self._lib = N.load()
+        self._ctx = None
+        Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
+        Tn = np.asarray(T) if isinstance(T, (list, tuple)) else T
+        n, d_in = int(Vn.shape[0]), int(Vn.shape[1])
+        m, d = int(Tn.shape[0]), int(Tn.shape[1]) - 1
+        self.n, self.m, self.d, self.d_in = n, m, d, d_in
+        pV, self._V = _ptr(Vn, np.float64)
+        pT, self._T = _ptr(Tn, np.int32)
+        mesh = N.Mesh(n, m, d, d_in, pV, pT)
+        prm = N.Params()
+        N.check(self._lib, None, self._lib.ffa_default_params(C.byref(prm)))
+        prm.energy = ENERGIES[energy]
+        prm.rho = float(rho)
+        prm.eps_abs = float(eps_abs)
+        prm.eps_rel = float(eps_rel)
+        prm.check_every = int(check_every)
+        prm.require_flip_free = 1 if require_flip_free else 0
+        prm.local_precision = PRECISIONS[precision]
+        prm.refine_sweeps = int(refine_sweeps)
+        prm.nd_leaf_size = int(leaf_size)
+        prm.host_threads = int(host_threads)
+        n_pin = 0 if pins is None else int(len(pins))
+        pP, self._pins = _ptr(pins, np.int32) if n_pin else (None, None)
+        pB, self._pinpos = _ptr(pin_pos, np.float64) if n_pin else (None, None)
+        ctx = C.c_void_p()
+        st = self._lib.ffa_create(C.byref(mesh), pP, n_pin, pB, C.byref(prm),
+                                  C.c_void_p(stream) if stream else None, C.byref(ctx))
+        N.check(self._lib, None, st)
+        self._ctx = ctx
+        self.energy_name = energy
+        self.precision = precision
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self) -> None:
+        if self._ctx is not None:
+            self._lib.ffa_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int) -> None:
+        N.check(self._lib, self._ctx, st)
+
+    # -- the method ----------------------------------------------------------
+    def set_handles(self, pin_pos) -> None:
+        p, keep = _ptr(pin_pos, np.float64)
+        self._check(self._lib.ffa_set_handles(self._ctx, p))
+
+    def init(self, W0) -> None:
+        p, keep = _ptr(W0, np.float64)
+        self._check(self._lib.ffa_init(self._ctx, p))
+
+    def iterate(self, max_iter: int, stop_at_tol: bool = True) -> dict:
+        st = N.Stats()
+        self._check(self._lib.ffa_iterate(self._ctx, int(max_iter), 1 if stop_at_tol else 0, C.byref(st)))
+        return st.as_dict()
+
+    def W(self, out=None):
+        if out is None:
+            out = np.empty((self.n, self.d), np.float64)
+        p, _ = _ptr(out, np.float64)
+        self._check(self._lib.ffa_get_W(self._ctx, p))
+        return out
+
+    def state(self):
+        U = np.empty((self.m, self.d, self.d))
+        P = np.empty_like(U)
+        L = np.empty_like(U)
+        self._check(self._lib.ffa_get_state(self._ctx, C.c_void_p(U.ctypes.data), C.c_void_p(P.ctypes.data),
+                                            C.c_void_p(L.ctypes.data)))
+        return U, P, L
+
+    def energy(self, W=None) -> float:
+        p, keep = _ptr(W, np.float64)
+        E = C.c_double()
+        self._check(self._lib.ffa_energy(self._ctx, p, C.byref(E)))
+        return E.value
+
+    def gradient(self, W=None, out=None):
+        p, keep = _ptr(W, np.float64)
+        if out is None:
+            out = np.empty((self.n, self.d), np.float64)
+        po, _ = _ptr(out, np.float64)
+        self._check(self._lib.ffa_gradient(self._ctx, p, po))
+        return out
+
+    def info(self) -> dict:
+        inf = N.Info()
+        self._check(self._lib.ffa_get_info(self._ctx, C.byref(inf)))
+        return inf.as_dict()
+
+    def profile_phases(self, reps: int) -> dict:
+        t = N.PhaseTimes()
+        self._check(self._lib.ffa_profile_phases(self._ctx, int(reps), C.byref(t)))
+        return t.as_dict()
+
+    def wstep_residual(self) -> float:
+        r = C.c_double()
+        self._check(self._lib.ffa_last_wstep_residual(self._ctx, C.byref(r)))
+        return r.value
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        kw.setdefault("energy", wl.energy)
+        kw.setdefault("rho", wl.rho)
+        kw.setdefault("eps_abs", wl.eps_abs)
+        kw.setdefault("eps_rel", wl.eps_rel)
+        return cls(wl.V, wl.T, wl.pins, wl.pin_pos, **kw)

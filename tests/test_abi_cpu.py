@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every declared symbol (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_2107_05200_gb300 import _native
+    if not os.path.exists(_native.LIB_PATH):
+        from paper_2107_05200_gb300 import build
+        build.build()
+    return _native, _native.load()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ffadmm.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ffa_[A-Za-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_api():
+    names = _declared()
+    for must in ("ffa_create", "ffa_init", "ffa_iterate", "ffa_energy", "ffa_gradient", "ffa_destroy"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    native, lib = _lib()
+    names = _declared()
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(native.EXPORTED) == names
+
+
+def test_default_params_and_struct_layout():
+    native, lib = _lib()
+    p = native.Params()
+    assert lib.ffa_default_params(C.byref(p)) == 0
+    assert p.energy == 0 and p.rho == 1.0 and p.eps_abs == 1e-6 and p.eps_rel == 1e-5
+    assert p.check_every == 10 and p.require_flip_free == 1 and p.refine_sweeps == 2
+    assert p.nd_leaf_size == 64
+    assert lib.ffa_default_params(None) == 1
+    assert isinstance(lib.ffa_last_error(None), bytes)
+
+
+def test_null_arguments_are_rejected_without_a_device():
+    native, lib = _lib()
+    out = C.c_void_p()
+    assert lib.ffa_create(None, None, 0, None, None, None, C.byref(out)) == 1
+    assert out.value is None
+    assert lib.ffa_create(None, None, 0, None, None, None, None) == 1
+    lib.ffa_destroy(None)
+
+
+def test_bad_parameters_are_rejected_before_any_device_work():
+    native, lib = _lib()
+    import numpy as np
+    V = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    T = np.array([[0, 1, 2]], np.int32)
+    mesh = native.Mesh(3, 1, 2, 2, C.c_void_p(V.ctypes.data), C.c_void_p(T.ctypes.data))
+    p = native.Params()
+    lib.ffa_default_params(C.byref(p))
+    p.refine_sweeps = 0
+    out = C.c_void_p()
+    assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
+    assert b"refine_sweeps" in lib.ffa_last_error(None)
+    lib.ffa_default_params(C.byref(p))
+    mesh.d = 4
+    assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
