@@ -1,0 +1,272 @@
+#!/usr/bin/env python
+"""Throughput of the flip-free ADMM loop on one GB300.
+
+Workload: 3D deformation of a jittered unit cube, 64^3 cells x 6 tetrahedra
+(1,572,864 tets, 274,625 vertices), bottom face fixed, top face rotated 45
+degrees and shifted, symmetric Dirichlet energy, mu_i = w_i, FP32 local step
+with the W step and reductions in double.  One step = one ADMM iteration
+(W step, U/P/Lambda steps, error terms; the termination test every
+check_every iterations).  The per-iteration working set (factor blocks and
+element state, > 1 GB) is larger than L2, so no flush is needed between
+iterations.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload family instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADMM iterations/sec and element-updates/sec at ~1.5M tets; % HBM roofline"
+UNIT = "iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=64)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--check-every", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-cells", type=int, default=16)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(cells: int, seconds: float, steps: int | None = None):
+    """Time the FP64 oracle on a smaller cube of the same recipe; returns per-iteration seconds."""
+    from oracle import admm
+    from paper_2107_05200_gb300 import workloads as wk
+    wl = wk.cube_deform(cells=cells)
+    o = admm.Oracle.from_workload(wl)
+    s = o.init(wl.W0)
+    s, _ = o.step(s)                     # first iteration outside the timing
+    times = []
+    t_end = time.perf_counter() + seconds
+    n = 0
+    while (steps is None and time.perf_counter() < t_end) or (steps is not None and n < steps):
+        t0 = time.perf_counter()
+        s, _ = o.step(s)
+        times.append(time.perf_counter() - t0)
+        n += 1
+    return wl, times
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    from paper_2107_05200_gb300 import workloads as wk
+    V, T = wk.cube_tets(args.cells)
+    m_full = T.shape[0]
+    wl, times = cpu_oracle_sample(args.cpu_sample_cells, 0.0, steps=args.warmup + args.steps)
+    t = sum(times[args.warmup:])
+    per_it = t / max(1, args.steps)
+    elem_rate = wl.m / per_it
+    value = elem_rate / m_full
+    sample = (f"FP64 numpy/scipy oracle, cube {args.cpu_sample_cells}^3 cells ({wl.m} tets), "
+              f"{args.steps} timed iterations after {args.warmup} warm-up; value = element-updates/s "
+              f"divided by the {m_full} tets of the full workload")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "elem_updates_per_s": elem_rate,
+            "config": {"workload": f"cube_deform_{args.cells}", "tets": m_full, "energy": "sym_dirichlet"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_2107_05200_gb300 import workloads as wk
+    from paper_2107_05200_gb300.solver import Solver
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    stream = torch.cuda.current_stream()
+    wl = wk.cube_deform(cells=args.cells)
+    sol = Solver.from_workload(wl, precision=args.precision, refine_sweeps=args.sweeps,
+                               check_every=args.check_every, stream=stream.cuda_stream)
+    info = sol.info()
+    W0 = torch.tensor(wl.W0, dtype=torch.float64, device="cuda")
+    sol.init(W0)
+    if args.warmup > 0:
+        sol.iterate(args.warmup, stop_at_tol=False)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st = sol.iterate(args.steps, stop_at_tol=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    value = world * args.steps / (ms / 1e3)
+
+    # per-phase device times (CUDA events on the solver stream, eager launches)
+    ph = sol.profile_phases(10)
+    hbm_peak, peak_kind = measured_peaks()
+    local_gbs = info["bytes_local_step"] / (ph["ms_local"] / 1e3) / 1e9
+    wstep_gbs = args.sweeps * info["bytes_global_sweep"] / (ph["ms_wstep"] / 1e3) / 1e9
+    resid = sol.wstep_residual()
+
+    # end to end through the public API with host buffers: init from pinned host W0,
+    # iterate, read W back to pinned host memory
+    W0h = torch.tensor(wl.W0, dtype=torch.float64).pin_memory()
+    Wout = torch.empty_like(W0h).pin_memory()
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sol.init(W0h)
+    sol.iterate(e2e_steps, stop_at_tol=False)
+    sol.W(Wout)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * e2e_steps / e2e_s
+    nbytes = wl.n * 3 * 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "elem_updates_per_s": value * wl.m,
+        "config": {"workload": f"cube_deform_{args.cells}", "tets": wl.m, "vertices": wl.n,
+                   "energy": "sym_dirichlet", "rho": 1.0, "local_precision": args.precision,
+                   "refine_sweeps": args.sweeps, "check_every": args.check_every,
+                   "l2": "working set > L2 (factor + element state), no flush",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": local_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": local_gbs / hbm_peak, "traffic": None,
+                     "kernel": "k_local_step", "peak_kind": peak_kind},
+        "phases_ms": {k: v for k, v in ph.items() if k != "reps"},
+        "wstep": {"achieved_gbs": wstep_gbs, "frac": wstep_gbs / hbm_peak,
+                  "factor_entries": info["factor_entries"], "rel_residual": resid},
+        "gpu_launches": int(args.steps * info["kernels_per_iteration"] +
+                            math.ceil(args.steps / args.check_every) * info["kernels_per_check"]),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes / e2e_steps,
+                "d2h_bytes_per_step": (nbytes + 96) / e2e_steps,
+                "note": f"one solve call: init from host W0, {e2e_steps} iterations, W read back"},
+        "clocks": clk,
+        "final": {"e_prim": st["e_prim"], "e_dual": st["e_dual"], "n_flipped": st["n_flipped"]},
+        "setup_s": {"analyze": info["setup_seconds_analyze"], "factor": info["setup_seconds_factor"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cwl, times = cpu_oracle_sample(args.cpu_sample_cells, args.cpu_seconds)
+        per_it = statistics.median(times)
+        rate = cwl.m / per_it
+        line["cpu_baseline"] = {
+            "value": rate / wl.m, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle on cube {args.cpu_sample_cells}^3 ({cwl.m} tets), {len(times)} iterations "
+                      f"in ~{args.cpu_seconds:.0f} s, element-updates/s scaled to {wl.m} tets",
+            "elem_updates_per_s": rate}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sol.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -2,13 +2,13 @@
  * ffadmm.h - C ABI of the GB300 flip-free ADMM library (libffadmm.so).
  *
  * The library minimizes a flip-free distortion energy
- *     E(W) = sum_i w_i f((G W)_i) + chi_+(det (G W)_i)              (paper Eq. 3.3)
+ *     E(W) = sum_i w_i f((G W)_i) + chi_+(det (G W)_i)              (paper eq. genericdeformationenergy
  * over target vertex positions W with the three-block splitting scheme of
  * Stein, Li & Solomon, "A Splitting Scheme for Flip-Free Distortion Energies"
  * (Algorithm 1; Algorithm 2 without penalty rescaling): a global W step with a
- * fixed operator L = sum_i mu_i G_i^T G_i (Eq. 3.6), closed-form per-element U
- * (Procrustes, Eq. 4.3-4.4) and P (prox, Eq. 4.5-4.6) steps, and the scaled
- * multiplier update (Eq. 4.7), with the primal/dual errors of Eq. 6.1-6.2.
+ * fixed operator L = sum_i mu_i G_i^T G_i (eq. solvinginw), closed-form per-element U
+ * (Procrustes, eqs. rawoptimizationinudecoupled/optimizationinudecoupled and P (prox, eqs. optimizinginp/rootfindinginp steps, and the scaled
+ * multiplier update (eq. lambdaupdate), with the primal/dual errors of eqs. primaldualerror/primaldualthresholds.
  *
  * Conventions shared by every call:
  *   - Sizes: n vertices, m elements, element dimension d (2 = triangles,
@@ -54,8 +54,8 @@ typedef enum {
 } ffa_status;
 
 typedef enum {
-  FFA_SYM_DIRICHLET = 0, /* f(X) = (|X|^2 + |X^-1|^2) / 2          (Eq. A.2) */
-  FFA_SYM_GRADIENT = 1   /* f(X) = |X|^2 / 2 - log det X            (Eq. 7.1) */
+  FFA_SYM_DIRICHLET = 0, /* f(X) = (|X|^2 + |X^-1|^2) / 2          (eq. symmetricdirichletdefiningfunction) */
+  FFA_SYM_GRADIENT = 1   /* f(X) = |X|^2 / 2 - log det X            (eq. symmetricgradientdefiningfunction) */
 } ffa_energy_kind;
 
 typedef enum {
@@ -75,7 +75,7 @@ typedef struct {
 typedef struct {
   ffa_energy_kind energy;
   double rho;              /* penalties mu_i = rho * w_i (rho = 1: the paper's initial mu_i = w_i) */
-  double eps_abs;          /* thresholds of Eq. 6.2 */
+  double eps_abs;          /* thresholds of eq. primaldualthresholds */
   double eps_rel;
   int32_t check_every;     /* evaluate the termination test every this many iterations (>= 1) */
   int32_t require_flip_free; /* 1: convergence also needs det J_i > 0 for all i (Sec. 6) */
@@ -87,11 +87,11 @@ typedef struct {
 
 typedef struct {
   int32_t iters;           /* iterations performed by the call */
-  int32_t converged;       /* 1 if the termination test of Eq. 6.2 passed */
+  int32_t converged;       /* 1 if the termination test of eq. primaldualthresholds passed */
   int32_t n_flipped;       /* elements with det (G W)_i <= 0 at the last check */
   int32_t checked_iter;    /* total iteration count at which the stats were taken */
-  double e_prim, e_dual;   /* Eq. 6.1 */
-  double thr_prim, thr_dual; /* Eq. 6.2 */
+  double e_prim, e_dual;   /* eq. primaldualerror */
+  double thr_prim, thr_dual; /* eq. primaldualthresholds */
   double energy_P;         /* sum_i w_i f(P_i) */
   double norm_GW, norm_P, norm_GtLambda;
 } ffa_stats;
@@ -127,12 +127,12 @@ ffa_status ffa_default_params(ffa_params* p);
 
 /* Prepare a solver for one mesh: element gradients and measures w_i (Supplemental,
  * "Computing the Jacobian map"; w_i of Sec. 3.1), the fixed operator
- * L = sum_i mu_i G_i^T G_i of Eq. 3.6 restricted to the free vertices, and its
+ * L = sum_i mu_i G_i^T G_i of eq. solvinginw restricted to the free vertices, and its
  * factorization, done once per mesh and rho (Sec. 4, "Efficient evaluation";
  * Algorithm 2, decompose(L)).
  *   mesh      : sizes and source geometry (host or device).
  *   pin_idx   : n_pin distinct vertex indices fixed by the constraint A W = b
- *               (Eq. 3.6 / Algorithm 1); n_pin = 0 pins vertex 0 at the origin
+ *               (eq. solvinginw / Algorithm 1); n_pin = 0 pins vertex 0 at the origin
  *               (Sec. 4, "Updating W").  Host or device; may be NULL if n_pin = 0.
  *   pin_pos   : n_pin x d positions b of the pinned vertices, host or device.
  *   params    : solver parameters (NULL = defaults).
@@ -157,12 +157,12 @@ ffa_status ffa_set_handles(ffa_ctx* ctx, const double* pin_pos);
 
 /* Start a solve from W0 (n x d, host or device): U0, P0 from the polar
  * decomposition of G W0 with singular values clamped to eps and the flipped case
- * of Eq. 6.4 (eps = eps_m^(1/4) for SG, eps_m^(1/8) for SD, eps_m = 2^-52);
+ * of eq. polardecompositionapplied (eps = eps_m^(1/4) for SG, eps_m^(1/8) for SD, eps_m = 2^-52);
  * Lambda0 = 0.  Pinned rows of W0 are replaced by the pinned positions. */
 ffa_status ffa_init(ffa_ctx* ctx, const double* W0);
 
 /* Run up to max_iter iterations of Algorithm 1 (W, U, P, Lambda steps, h = 0).
- * With stop_at_tol = 1 the termination test of Eq. 6.2 (plus flip-freeness when
+ * With stop_at_tol = 1 the termination test of eq. primaldualthresholds (plus flip-freeness when
  * require_flip_free) is evaluated every check_every iterations and the call
  * returns as soon as it passes; with stop_at_tol = 0 exactly max_iter iterations
  * run and the test is still evaluated at the last one.  *stats (may be NULL)
@@ -177,12 +177,12 @@ ffa_status ffa_get_W(ffa_ctx* ctx, double* W_out);
  * any pointer may be NULL to skip it). */
 ffa_status ffa_get_state(ffa_ctx* ctx, double* U, double* P, double* Lambda);
 
-/* Energy of Eq. 3.3 at W (n x d, host or device; NULL = the current iterate):
+/* Energy of eq. genericdeformationenergy at W (n x d, host or device; NULL = the current iterate):
  * sum_i w_i f((G W)_i), or +infinity (with FFA_OK) if some det (G W)_i <= 0. */
 ffa_status ffa_energy(ffa_ctx* ctx, const double* W, double* E);
 
 /* Gradient of the energy at W: dE/dW = G^T (w_i grad f((G W)_i)) with
- * grad f from Eq. 7.2 / A.3, written to dEdW (n x d, host or device).
+ * grad f from eq. symmetricgradientdefininggrad / eq. symmetricdirichletdefininggrad, written to dEdW (n x d, host or device).
  * FFA_ERR_FLIPPED if some det (G W)_i <= 0 (the energy is infinite there). */
 ffa_status ffa_gradient(ffa_ctx* ctx, const double* W, double* dEdW);
 
@@ -195,7 +195,7 @@ ffa_status ffa_get_info(ffa_ctx* ctx, ffa_info* info);
 ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out);
 
 /* Relative residual |L_FF W_F - b_F| / |b_F| of the last W step, measured in
- * double on the device (a diagnostic of the refinement sweeps; Eq. 3.6). */
+ * double on the device (a diagnostic of the refinement sweeps; eq. solvinginw. */
 ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel_residual);
 
 #ifdef __cplusplus

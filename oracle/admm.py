@@ -11,11 +11,11 @@ Element data are batched numpy arrays; numpy/scipy primitives (SVD, symmetric
 eigendecomposition, sparse LU) serve as single steps, and the steps follow the
 paper's order (Algorithm 1 / Algorithm 2 without the rescaling branch).
 
-Notation (Sec. 3.1, Def. 3.1): V source vertices (n, d_in), W target vertices
+Notation (Sec. 3.1, Def. jacobian (Sec. 3.1)): V source vertices (n, d_in), W target vertices
 (n, d), T elements (m, d+1), w_i element area/volume, J = GW the per-element
 Jacobians with column k equal to the gradient of target coordinate k
 (Supplemental, "Computing the Jacobian map").  U_i in SO(d), P_i SPD, Lambda_i
-the scaled multiplier, mu_i the penalties (Eq. 3.5).
+the scaled multiplier, mu_i the penalties (eq. augmentedlagrangian.
 
 Readings of points the paper leaves open (each one is also listed in the
 design notes):
@@ -24,7 +24,7 @@ design notes):
   * h_i = 0 unless a proximal weight is passed (Sec. 6: disabled when many
     flipped elements are expected).
   * eps_m is the double-precision machine epsilon 2^-52 for every constant.
-  * sqrt(d m) in the thresholds of Eq. (6.2) is taken literally.
+  * sqrt(d m) in the thresholds of eq. primaldualthresholds is taken literally.
   * 2D Procrustes tie (Q with q11+q22 = q21-q12 = 0): keep the previous U.
   * Flipped init: R1 R2^T gets its last column negated when its determinant is
     negative, and Sigma = eps I whenever det J0 <= 0.
@@ -43,7 +43,7 @@ SQRT_EPS_M = 2.0 ** -26
 
 
 # ----------------------------------------------------------------------------
-# mesh operators (Supplemental, "Computing the Jacobian map"; Def. 3.1)
+# mesh operators (Supplemental, "Computing the Jacobian map"; Def. jacobian (Sec. 3.1))
 # ----------------------------------------------------------------------------
 
 def element_frames(V: np.ndarray, T: np.ndarray) -> np.ndarray:
@@ -99,7 +99,7 @@ def gradient_adjoint(g: np.ndarray, T: np.ndarray, R: np.ndarray, n: int) -> np.
 
 
 def assemble_L(g: np.ndarray, T: np.ndarray, mu: np.ndarray, n: int) -> sp.csr_matrix:
-    """L = sum_i mu_i G_i^T G_i (Eq. 3.6): L[u, v] += mu_i g_iu . g_iv."""
+    """L = sum_i mu_i G_i^T G_i (eq. solvinginw): L[u, v] += mu_i g_iu . g_iv."""
     k = T.shape[1]
     loc = mu[:, None, None] * np.einsum("mja,mla->mjl", g, g)
     rows = np.repeat(T, k, axis=1).ravel()
@@ -108,7 +108,7 @@ def assemble_L(g: np.ndarray, T: np.ndarray, mu: np.ndarray, n: int) -> sp.csr_m
 
 
 # ----------------------------------------------------------------------------
-# defining functions and gradients (Eq. 7.1-7.2, Eq. A.2-A.3)
+# defining functions and gradients (eqs. symmetricgradientdefiningfunction/symmetricgradientdefininggrad, eqs. symmetricdirichletdefiningfunction/symmetricdirichletdefininggrad)
 # ----------------------------------------------------------------------------
 
 def f_energy(X: np.ndarray, energy: str) -> np.ndarray:
@@ -130,7 +130,7 @@ def grad_f(X: np.ndarray, energy: str) -> np.ndarray:
 
 
 def energy(g, T, W, w, energy_name: str) -> float:
-    """E(W) = sum_i w_i f((GW)_i) + chi_+(det (GW)_i)  (Eq. 3.3)."""
+    """E(W) = sum_i w_i f((GW)_i) + chi_+(det (GW)_i)  (eq. genericdeformationenergy)."""
     J = jacobians(g, T, W)
     if np.any(np.linalg.det(J) <= 0.0):
         return math.inf
@@ -154,7 +154,7 @@ def rot2(c: np.ndarray, s: np.ndarray) -> np.ndarray:
 
 
 def procrustes(Q: np.ndarray, U_prev: np.ndarray) -> np.ndarray:
-    """argmin_{U in SO(d)} |U - Q|^2 (Eq. 4.4).
+    """argmin_{U in SO(d)} |U - Q|^2 (eq. optimizationinudecoupled.
 
     d = 2: U(phi) maximizes U(phi).Q = cos(phi)(q11+q22) + sin(phi)(q21-q12),
     so (cos, sin) is that vector normalized (Supplemental, d = 2); a zero vector
@@ -181,7 +181,7 @@ def procrustes(Q: np.ndarray, U_prev: np.ndarray) -> np.ndarray:
 
 
 def root_sg(q: np.ndarray, w: np.ndarray, mu: np.ndarray) -> np.ndarray:
-    """Positive root of (w+mu) p^2 - mu q p - w = 0 (Eq. S.2 per eigenvalue, Eq. S.3).
+    """Positive root of (w+mu) p^2 - mu q p - w = 0 (eq. peqfsgpluggedin per eigenvalue, eq. solvesgwithquadraticformula).
 
     For q >= 0 the quadratic formula as printed; for q < 0 the algebraically equal
     form 2w / (sqrt(disc) - mu q), which avoids cancelling two large terms.
@@ -193,7 +193,7 @@ def root_sg(q: np.ndarray, w: np.ndarray, mu: np.ndarray) -> np.ndarray:
 
 
 def root_sd(q: np.ndarray, w: np.ndarray, mu: np.ndarray) -> np.ndarray:
-    """Unique positive root of (w+mu) p^4 - mu q p^3 - w = 0 (Eq. S.4 per eigenvalue).
+    """Unique positive root of (w+mu) p^4 - mu q p^3 - w = 0 (eq. peqfsdpluggedin per eigenvalue).
 
     With a = mu q/(w+mu) and c = w/(w+mu) the root lies in
     (0, max(a, 0) + c^{1/4}]: the quartic is -c < 0 at 0, and at
@@ -223,10 +223,10 @@ def root_sd(q: np.ndarray, w: np.ndarray, mu: np.ndarray) -> np.ndarray:
 
 
 def p_step(S: np.ndarray, w: np.ndarray, mu: np.ndarray, energy_name: str) -> np.ndarray:
-    """argmin_{P SPD} w f(P) + mu/2 |P - S|^2 for symmetric S (Eq. 4.5-4.6, Supplemental).
+    """argmin_{P SPD} w f(P) + mu/2 |P - S|^2 for symmetric S (eqs. optimizinginp/rootfindinginp, Supplemental).
 
     S = E diag(q) E^T; each eigenvalue is mapped to the positive root of the
-    scalar version of Eq. (S.2)/(S.4); if det P or tr P falls below sqrt(eps_m)
+    scalar version of eq. peqfsgpluggedin/(S.4); if det P or tr P falls below sqrt(eps_m)
     the eigenvalues are raised to at least sqrt(eps_m).
     """
     q, E = np.linalg.eigh(S)
@@ -243,7 +243,7 @@ def symm(X: np.ndarray) -> np.ndarray:
 
 
 def polar_init(J0: np.ndarray, energy_name: str) -> tuple[np.ndarray, np.ndarray]:
-    """U0, P0 from the polar decomposition of GW0 (Eq. 6.3-6.4).
+    """U0, P0 from the polar decomposition of GW0 (eqs. initialpolardecomposition/polardecompositionapplied.
 
     J0 = R1 S R2^T, U0 = R1 R2^T, P0 = R2 S R2^T; singular values below eps are
     raised to eps, eps = eps_m^{1/4} (SG) or eps_m^{1/8} (SD).  A flipped J0
@@ -264,11 +264,11 @@ def polar_init(J0: np.ndarray, energy_name: str) -> tuple[np.ndarray, np.ndarray
 
 
 # ----------------------------------------------------------------------------
-# global step (Eq. 3.6 with constraints A W = b as pinned vertices)
+# global step (eq. solvinginw with constraints A W = b as pinned vertices)
 # ----------------------------------------------------------------------------
 
 class WStep:
-    """Exact minimizer of Phi over W with pinned vertices (Eq. 3.6).
+    """Exact minimizer of Phi over W with pinned vertices (eq. solvinginw.
 
     L = sum mu_i G_i^T G_i is split into free (F) and pinned (C) blocks;
     L_FF W_F = (G^T r)_F - L_FC b.  L_FF is factored once (sparse LU), as the
@@ -350,7 +350,7 @@ class Oracle:
         return cls(wl.V, wl.T, wl.pins, wl.pin_pos, wl.energy, wl.rho, **kw)
 
     def init(self, W0) -> State:
-        """U0, P0 by polar decomposition, Lambda0 = 0 (Algorithm 2, Eq. 6.3-6.4)."""
+        """U0, P0 by polar decomposition, Lambda0 = 0 (Algorithm 2, eqs. initialpolardecomposition/polardecompositionapplied."""
         W0 = np.asarray(W0, np.float64)
         J0 = jacobians(self.g, self.T, W0)
         U0, P0 = polar_init(J0, self.energy_name)
@@ -377,7 +377,7 @@ class Oracle:
         return s1, self.stats(s, s1)
 
     def stats(self, s0: State, s1: State, k: int = 0) -> Stats:
-        """Primal/dual errors and thresholds (Eq. 6.1-6.2), flips, sum w f(P)."""
+        """Primal/dual errors and thresholds (eqs. primaldualerror/primaldualthresholds), flips, sum w f(P)."""
         R = s1.J - s1.U @ s1.P
         e_prim = math.sqrt(np.sum(R * R))
         D = s1.J - s0.J

@@ -2,7 +2,7 @@
 // evaluation": L does not change while the penalties do not, so it is decomposed
 // once and only back-substitution runs per iteration; Algorithm 2, decompose(L)).
 //
-// The free-vertex block L_FF of L = sum_i mu_i G_i^T G_i (Eq. 3.6) is ordered by
+// The free-vertex block L_FF of L = sum_i mu_i G_i^T G_i (eq. solvinginw) is ordered by
 // geometric nested dissection and factored by a multifrontal Cholesky in double.
 // Every supernode s (a separator or a leaf block) stores one dense block
 //     B_s = [ inv(L_ss) ; L_rs inv(L_ss) ]     ((n_s + m_s) x n_s, column-major)

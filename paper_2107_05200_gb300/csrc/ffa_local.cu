@@ -1,8 +1,10 @@
 // Per-element kernels: the fused local step (Jacobian assembly, U step, P step,
-// multiplier update, right-hand-side terms and error terms; paper Sec. 4 and
-// Eq. 6.1), the polar initialization (Eq. 6.3-6.4) and the energy terms
-// (Eq. 3.3, 7.1-7.2, A.2-A.3).  One thread per element; all per-element math
-// stays in registers; element data are structure-of-arrays (coalesced).
+// multiplier update, right-hand-side terms and the error terms of
+// eq. primaldualerror; paper Sec. 4), the polar initialization (Sec. 6,
+// eqs. initialpolardecomposition/polardecompositionapplied) and the energy terms
+// (eq. genericdeformationenergy with the defining functions of Sec. 7 and App. A).
+// One thread per element; all per-element math stays in registers; element data
+// are structure-of-arrays (coalesced).
 #include "ffa_internal.h"
 #include "ffa_math.cuh"
 
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
       P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[0][2] = P[2][0] = Pp[2 * (int64_t)m + i];
       P[1][1] = Pp[3 * (int64_t)m + i]; P[1][2] = P[2][1] = Pp[4 * (int64_t)m + i]; P[2][2] = Pp[5 * (int64_t)m + i];
     }
-    // ---- U step: nearest rotation to Q = (J + Lambda) P (Eq. 4.3-4.4, h = 0)
+    // ---- U step: nearest rotation to Q = (J + Lambda) P (eqs. rawoptimizationinudecoupled/optimizationinudecoupled, h = 0)
     R Q[D][D], U[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
 #pragma unroll
       for (int k = 0; k < 4; ++k) Up[(int64_t)k * m + i] = qt[k];
     }
-    // ---- P step: S = symm(U^T (J + Lambda)), per-eigenvalue prox root (Eq. 4.5-4.6)
+    // ---- P step: S = symm(U^T (J + Lambda)), per-eigenvalue prox root (eqs. optimizinginp/rootfindinginp
     R S[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
           P[k][a] = v;
         }
     }
-    // ---- multiplier update (Eq. 4.7) and the next right-hand-side terms (Eq. 3.6)
+    // ---- multiplier update (eq. lambdaupdate) and the next right-hand-side terms (eq. solvinginw)
     R UP[D][D], Rm[D][D], Rhs[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
 }
 
 // ---------------------------------------------------------------------------
-// polar initialization (Eq. 6.3-6.4): U0, P0 from the SVD of G W0, Lambda0 = 0
+// polar initialization (eqs. initialpolardecomposition/polardecompositionapplied): U0, P0 from the SVD of G W0, Lambda0 = 0
 // ---------------------------------------------------------------------------
 template <int D, typename R, int EN>
 __global__ void __launch_bounds__(kLocalBlock) k_init_polar(ElemBufs e, int m, const void* __restrict__ vrec) {
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(kLocalBlock) k_init_polar(ElemBufs e, int m, c
 
 // ---------------------------------------------------------------------------
 // energy terms at a given W: mode 0 -> partials (w f(J), flips); mode 1 -> the
-// per-vertex terms of G^T (w grad f(J)) into contrib2 (Eq. 7.2 / A.3)
+// per-vertex terms of G^T (w grad f(J)) into contrib2 (eq. symmetricgradientdefininggrad / eq. symmetricdirichletdefininggrad)
 // ---------------------------------------------------------------------------
 template <int D, typename R, int EN, int MODE>
 __global__ void __launch_bounds__(kLocalBlock) k_energy_terms(ElemBufs e, int m, const void* __restrict__ vrec,

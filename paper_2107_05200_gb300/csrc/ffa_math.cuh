@@ -34,7 +34,7 @@ template <> struct Tr<double> {
 
 // Constants of the method, all in terms of the double machine epsilon 2^-52:
 // eps_init = eps_m^(1/4) (SG) or eps_m^(1/8) (SD) for the polar initialization
-// (Eq. 6.4) and the eigenvalue floor sqrt(eps_m) of the P step (Supplemental).
+// (eq. polardecompositionapplied) and the eigenvalue floor sqrt(eps_m) of the P step (Supplemental).
 constexpr double kEpsInitSG = 1.220703125e-04;          // 2^-13
 constexpr double kEpsInitSD = 1.104854345603981e-02;    // 2^-6.5
 constexpr double kSqrtEpsM = 1.4901161193847656e-08;    // 2^-26
@@ -43,7 +43,7 @@ constexpr double kSqrtEpsM = 1.4901161193847656e-08;    // 2^-26
 // scalar prox roots: the per-eigenvalue form of w grad f(P) + mu P = mu S
 // ---------------------------------------------------------------------------
 
-// Symmetric gradient: (w + mu) p^2 - mu q p - w = 0, positive root (Eq. S.3 per
+// Symmetric gradient: (w + mu) p^2 - mu q p - w = 0, positive root (eq. solvesgwithquadraticformula per
 // eigenvalue).  Divided by (w + mu): p^2 - t q p - c = 0 with t = mu/(w+mu),
 // c = w/(w+mu); for q < 0 the cancellation-free form 2c / (sqrt(disc) - t q).
 template <typename R>
@@ -55,7 +55,7 @@ __device__ __forceinline__ R prox_root_sg(R q, R w, R mu) {
   return (q >= R(0)) ? R(0.5) * (tq + sd) : (R(2) * c) / (sd - tq);
 }
 
-// Symmetric Dirichlet: (w + mu) p^4 - mu q p^3 - w = 0 (Eq. S.4 per eigenvalue),
+// Symmetric Dirichlet: (w + mu) p^4 - mu q p^3 - w = 0 (eq. peqfsdpluggedin per eigenvalue),
 // i.e. g(p) = p^3 (p - a) - c with a = t q.  g is convex and increasing to the
 // right of its unique positive root, so Newton started above the root decreases
 // monotonically onto it.  Start: for a > 0 the root lies in (a, a + min(c^(1/4),
@@ -145,7 +145,7 @@ __device__ __forceinline__ void sym3_eig(R a00, R a01, R a02, R a11, R a12, R a2
 #pragma unroll 1
   for (int sw = 0; sw < Tr<R>::jacobi_sweeps; ++sw) {
     const R off = a01 * a01 + a02 * a02 + a12 * a12;
-    if (off <= Tr<R>::eps() * Tr<R>::eps() * R(0.01) * scale2 || off <= Tr<R>::tiny()) break;
+    if (off <= Tr<R>::eps() * Tr<R>::eps() * scale2 || off <= Tr<R>::tiny()) break;
     jacobi_rotate<R>(a00, a11, a01, a02, a12, V, 0, 1);  // r = 2: (a20, a21)
     jacobi_rotate<R>(a00, a22, a02, a01, a12, V, 0, 2);  // r = 1: (a10, a12)
     jacobi_rotate<R>(a11, a22, a12, a01, a02, V, 1, 2);  // r = 0: (a01, a02)

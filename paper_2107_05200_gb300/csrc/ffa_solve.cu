@@ -1,8 +1,8 @@
-// Vertex-side kernels of the W step (Eq. 3.6): right-hand-side gather G^T r,
+// Vertex-side kernels of the W step (eq. solvinginw): right-hand-side gather G^T r,
 // the double-precision residual b - L_FF W_F, the float supernodal triangular
 // solves that turn the residual into a correction (mixed-precision refinement),
 // and the vertex update that publishes W for the next local step.  Also the
-// reductions that evaluate the termination test of Eq. 6.1-6.2.
+// reductions that evaluate the termination test of eqs. primaldualerror/primaldualthresholds.
 #include <math.h>
 
 #include "ffa_internal.h"
@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks
     float acc[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) acc[k] = 0.f;
+#pragma unroll 8
     for (int r = rstart + lane; r < nr; r += 32) {
       const float bv = __ldg(B + t.r0 + r);
 #pragma unroll
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kVertexBlock) k_pin_rhs(int nF, const int64_t*
 }
 
 // ---------------------------------------------------------------------------
-// termination test (Eq. 6.1-6.2), single block
+// termination test (eqs. primaldualerror/primaldualthresholds), single block
 // ---------------------------------------------------------------------------
 __global__ void k_final(FinalLaunch F) {
   __shared__ double acc[NQ + 1];

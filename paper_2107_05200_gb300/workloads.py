@@ -8,7 +8,7 @@ CUDA path and the FP64 oracle can be fed from it without sharing method code.
 The paper's meshes and datasets (Table 2, Sec. 7) are not available, so these
 workloads stand in for them.  Their shapes follow the paper's problem setup
 (Sec. 3.1: triangle meshes mapped to the plane, tetrahedral meshes mapped to
-R^3) and the initializers it uses (Sec. 6: Tutte embeddings; App. A.1).
+R^3) and the initializers it uses (Sec. 6: Tutte embeddings; App. A, Tutte's energy).
 
 Conventions (Sec. 3.1): V is (n, d_in) float64, T is (m, d+1) int32 with
 positively oriented elements, W is (n, d_out) float64 row-major, pins are int32
@@ -158,7 +158,7 @@ def _edges(T: np.ndarray) -> np.ndarray:
 
 def tutte_embedding(V: np.ndarray, T: np.ndarray, boundary: np.ndarray,
                     boundary_pos: np.ndarray) -> np.ndarray:
-    """Minimizer of the Tutte energy with fixed boundary (App. A.1).
+    """Minimizer of the Tutte energy with fixed boundary (App. A, Tutte's energy).
 
     Edge weights are 1/|V_i - V_j|; interior vertices solve the weighted
     graph-Laplacian system.  Input construction only.
@@ -240,10 +240,12 @@ def uv_disk(grid: int = 48, seed: int = 1, target_flip: float | None = 0.03,
 
 
 def uv_heightfield(grid: int = 512, seed: int = 2, energy: str = SYM_GRADIENT,
-                   target_flip: float = 0.05, rho: float = 1.0, max_iter: int = 2000,
+                   target_flip: float = 0.05, rho: float = 3.0, max_iter: int = 2000,
                    tol: float = 1e-5) -> Workload:
     """2D UV-scale loop: grid^2 vertices on z = 0.3 sin(3x) cos(2y), flattened.
 
+    Penalties mu_i = rho w_i with rho = 3: with rho = 1 (mu_i = w_i, below the
+    lower bound the paper's convergence analysis asks for) the iteration stalls.
     Source V is the 3D surface (intrinsic 2x2 Jacobians).  Two pinned vertices,
     (0,0) and (grid-1,0), at their projected positions.  W0 = projection (x, y) plus
     Gaussian noise whose scale is found by bisection so that target_flip of the
@@ -265,7 +267,7 @@ def uv_heightfield(grid: int = 512, seed: int = 2, energy: str = SYM_GRADIENT,
 
 
 def cube_deform(cells: int = 64, seed: int = 3, jitter: float = 0.1,
-                energy: str = SYM_DIRICHLET, rho: float = 1.0, max_iter: int = 1000,
+                energy: str = SYM_DIRICHLET, rho: float = 3.0, max_iter: int = 1000,
                 angle_deg: float = 45.0, shift_x: float = 0.3) -> Workload:
     """3D deformation: unit cube, cells^3 cubes, 6 tets each.
 
@@ -273,6 +275,7 @@ def cube_deform(cells: int = 64, seed: int = 3, jitter: float = 0.1,
     planar).  Bottom face z=0 is fixed; every top-face vertex is a handle, rotated
     by angle_deg about the z axis through (0.5, 0.5, 1) and then translated by
     shift_x in x.  W0 = rest pose with the handles snapped to their targets.
+    Penalties mu_i = rho w_i with rho = 3 (rho = 1 stalls, as for the surface).
     """
     rng = np.random.default_rng(seed)
     V, T = cube_tets(cells)
@@ -304,7 +307,7 @@ def bend_map(X: np.ndarray, radius: float = 2.0) -> np.ndarray:
 
 
 def cube_handles(cells: int = 32, seed: int = 5, n_targets: int = 1000,
-                 energy: str = SYM_DIRICHLET, rho: float = 1.0) -> Workload:
+                 energy: str = SYM_DIRICHLET, rho: float = 3.0) -> Workload:
     """Differentiation workload: cube, bottom fixed, 8x8 top-face handle lattice.
 
     Handles are the top-face vertices with lattice indices in {2, 6, ..., cells-2}^2

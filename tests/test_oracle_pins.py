@@ -34,7 +34,7 @@ def _small_meshes():
 
 @pytest.mark.parametrize("k", [0, 1])
 def test_affine_maps_reproduce_their_matrix(k):
-    """Def. 3.1 + Supplemental: for W = V M + t every J_i equals M (column k = grad W_k)."""
+    """Def. jacobian (Sec. 3.1) + Supplemental: for W = V M + t every J_i equals M (column k = grad W_k)."""
     V, T = _small_meshes()[k]
     g, w = admm.element_gradients(V, T)
     rng = np.random.default_rng(1)
@@ -77,7 +77,7 @@ def test_element_measures_sum_to_domain():
 
 @pytest.mark.parametrize("k", [0, 1, 2])
 def test_adjoint_and_quadratic_form(k):
-    """<GW, R> = <W, G^T R>, and sum_i mu_i |(GW)_i|^2 = sum_k W_k^T L W_k (Eq. 3.6)."""
+    """<GW, R> = <W, G^T R>, and sum_i mu_i |(GW)_i|^2 = sum_k W_k^T L W_k (eq. solvinginw)."""
     V, T = _small_meshes()[k]
     g, w = admm.element_gradients(V, T)
     rng = np.random.default_rng(2)
@@ -101,7 +101,7 @@ def test_adjoint_and_quadratic_form(k):
 
 @pytest.mark.parametrize("d", [2, 3])
 def test_energy_closed_forms_and_rotation_invariance(d):
-    """f_SD(sI) = d(s^2+s^-2)/2, f_SG(sI) = d s^2/2 - d log s; f(RX) = f(X) (Eq. 7.1, A.2)."""
+    """f_SD(sI) = d(s^2+s^-2)/2, f_SG(sI) = d s^2/2 - d log s; f(RX) = f(X) (eqs. symmetricgradientdefiningfunction, symmetricdirichletdefiningfunction)."""
     s = 1.7
     X = (s * np.eye(d))[None]
     assert math.isclose(admm.f_energy(X, "sd")[0], d * (s * s + 1 / (s * s)) / 2, rel_tol=1e-14)
@@ -120,7 +120,7 @@ def test_energy_closed_forms_and_rotation_invariance(d):
 
 @pytest.mark.parametrize("energy", ["sd", "sg"])
 def test_grad_f_matches_finite_differences(energy):
-    """Eq. (7.2) / (A.3) against central differences of f."""
+    """eq. symmetricgradientdefininggrad / eq. symmetricdirichletdefininggrad against central differences of f."""
     rng = np.random.default_rng(5)
     X = np.eye(3)[None] + 0.3 * rng.normal(size=(1, 3, 3))
     G = admm.grad_f(X, energy)[0]
@@ -134,7 +134,7 @@ def test_grad_f_matches_finite_differences(energy):
 
 
 # --------------------------------------------------------------------------
-# P step (Eq. 4.5-4.6, Supplemental Eq. S.1-S.4)
+# P step (eqs. optimizinginp/rootfindinginp, Supplemental eqs. genericpeqtosolve..peqfsdpluggedin)
 # --------------------------------------------------------------------------
 
 QS = [-100.0, -3.0, -1e-3, 0.0, 1e-9, 0.5, 1.0, 2.0, 50.0]
@@ -231,7 +231,7 @@ def test_eigenvalue_floor():
 
 
 # --------------------------------------------------------------------------
-# U step (Eq. 4.3-4.4, Supplemental)
+# U step (eqs. rawoptimizationinudecoupled/optimizationinudecoupled, Supplemental)
 # --------------------------------------------------------------------------
 
 def test_procrustes_2d_against_angle_grid():
@@ -272,7 +272,7 @@ def test_procrustes_3d_against_rotation_search():
 
 
 # --------------------------------------------------------------------------
-# initialization (Eq. 6.3-6.4)
+# initialization (eqs. initialpolardecomposition/polardecompositionapplied
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("d", [2, 3])
@@ -298,7 +298,7 @@ def test_polar_init(d):
 
 
 # --------------------------------------------------------------------------
-# W step (Eq. 3.6) against a dense least-squares solve
+# W step (eq. solvinginw) against a dense least-squares solve
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("k", [0, 1, 2])
@@ -392,7 +392,7 @@ def test_local_output_is_flip_free_and_kkt_holds():
 
 def test_convergence_unflips_and_meets_thresholds():
     """Fig. 3 / Sec. 6: from an initial map with flipped triangles the iteration removes the
-    flips and drives e_prim and e_dual below the thresholds of Eq. (6.2)."""
+    flips and drives e_prim and e_dual below the thresholds of eq. primaldualthresholds."""
     wl = wk.uv_disk(grid=24, seed=22, rho=3.0)
     assert wl.meta["flipped0"] > 0.01
     o = admm.Oracle.from_workload(wl)
@@ -429,7 +429,7 @@ def test_energy_is_infinite_when_flipped():
 
 @pytest.mark.parametrize("k", [0, 1])
 def test_local_steps_minimize_the_augmented_lagrangian(k):
-    """U^k and P^k are the minimizers of Phi in U (Eq. 4.2, h = 0) and in P (Eq. 4.5),
+    """U^k and P^k are the minimizers of Phi in U (eq. rawoptimizationinudecoupled, h = 0) and in P (eq. optimizinginp),
     found by brute force on the raw objective |J - U P + Lambda|^2, not through Q or S."""
     V, T = _small_meshes()[k]
     d = V.shape[1]
