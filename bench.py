@@ -232,7 +232,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "elem_updates_per_s": value * wl.m,
         "config": {"workload": f"cube_deform_{args.cells}", "tets": wl.m, "vertices": wl.n,
-                   "energy": "sym_dirichlet", "rho": 1.0, "local_precision": args.precision,
+                   "energy": "sym_dirichlet", "rho": wl.rho, "local_precision": args.precision,
                    "refine_sweeps": args.sweeps, "check_every": args.check_every,
                    "l2": "working set > L2 (factor + element state), no flush",
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -158,7 +158,8 @@ ffa_status ffa_set_handles(ffa_ctx* ctx, const double* pin_pos);
 /* Start a solve from W0 (n x d, host or device): U0, P0 from the polar
  * decomposition of G W0 with singular values clamped to eps and the flipped case
  * of eq. polardecompositionapplied (eps = eps_m^(1/4) for SG, eps_m^(1/8) for SD, eps_m = 2^-52);
- * Lambda0 = 0.  Pinned rows of W0 are replaced by the pinned positions. */
+ * Lambda0 = 0 (Algorithm 2).  W0 is used as given, pinned rows included; the
+ * pinned positions take effect from the first W step on. */
 ffa_status ffa_init(ffa_ctx* ctx, const double* W0);
 
 /* Run up to max_iter iterations of Algorithm 1 (W, U, P, Lambda steps, h = 0).

@@ -302,6 +302,7 @@ void enqueue_iteration(ffa_ctx* ctx, bool check, cudaEvent_t* ev = nullptr) {
     F.require_flip_free = ctx->prm.require_flip_free;
     F.iter = 0;
     F.out = ctx->stats_d;
+    F.scratch = ctx->sums_d + 8;
     launch_final_reduce(F, s);
   }
   if (ev) cudaEventRecord(ev[PH_CHECK], s);
@@ -543,18 +544,18 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   std::vector<std::vector<Task>> fl(fac.n_levels), bl(fac.n_levels);
   for (size_t s = 0; s < fac.nodes.size(); ++s) {
     const Supernode& sn = fac.nodes[s];
-    nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, 0, sn.row_off, sn.blk_off};
-    const int ld = sn.ncol + sn.nrow;
+    nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, sn.ld, sn.row_off, sn.blk_off};
+    const int ntot = sn.ncol + sn.nrow;
     if (sn.ncol == 0) continue;
-    for (int r0 = 0; r0 < ld; r0 += kFwdRows)
+    for (int r0 = 0; r0 < ntot; r0 += kFwdRows)
       for (int c0 = 0; c0 < sn.ncol; c0 += kFwdCols) {
-        const int rmax = std::min(r0 + kFwdRows, ld) - 1;
+        const int rmax = std::min(r0 + kFwdRows, ntot) - 1;
         if (rmax < c0) continue;  // entirely above the diagonal of inv(L_ss)
         fl[sn.level].push_back(Task{(int32_t)s, r0, c0, 0});
       }
     for (int c0 = 0; c0 < sn.ncol; c0 += kBwdCols)
-      for (int r0 = 0; r0 < ld; r0 += kBwdRows) {
-        const int rmax = std::min(r0 + kBwdRows, ld) - 1;
+      for (int r0 = 0; r0 < ntot; r0 += kBwdRows) {
+        const int rmax = std::min(r0 + kBwdRows, ntot) - 1;
         if (rmax < c0) continue;
         bl[sn.level].push_back(Task{(int32_t)s, r0, c0, 0});
       }
@@ -644,6 +645,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
       (int64_t)n * d * 16;
   int64_t nz = 0;
   for (const Supernode& sn : fac.nodes) nz += (int64_t)sn.ncol * sn.nrow + (int64_t)sn.ncol * (sn.ncol + 1) / 2;
+  // (forward and backward each read every nonzero of every B_s once)
   ctx->info.bytes_global_sweep = 2 * nz * 4 + (int64_t)width * nF * 12 + (int64_t)nF * d * (8 * 3 + 4 * 6);
   ctx->info.n = n;
   ctx->info.m = m;
@@ -656,7 +658,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     lev_launch += (ctx->fwd_off[l + 1] > ctx->fwd_off[l]) + (ctx->bwd_off[l + 1] > ctx->bwd_off[l]);
   const int sweeps = ctx->prm.refine_sweeps;
   ctx->info.kernels_per_iteration = 1 + sweeps * (1 + lev_launch) + (sweeps - 1) + 1 + 1;
-  ctx->info.kernels_per_check = 2;
+  ctx->info.kernels_per_check = 3;
   (void)t_setup0;
   return FFA_OK;
 }
@@ -671,24 +673,20 @@ void destroy_impl(ffa_ctx* ctx) {
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
 }
 
-ffa_status load_W_records(ffa_ctx* ctx, const double* W, bool pin_override, double* W_target, void* vrec) {
+ffa_status load_W_records(ffa_ctx* ctx, const double* W, bool write_X, double* W_target, void* vrec) {
   FFA_CUDA(cudaMemcpyAsync(ctx->Wtmp, W, (size_t)ctx->n * ctx->d * 8, cudaMemcpyDefault, ctx->stream));
   VertexLaunch V{};
   V.d = ctx->d;
   V.fp64 = ctx->fp64;
   V.n = ctx->n;
   V.v2e = ctx->v2e;
-  V.v2pin = ctx->v2pin;
+  V.v2pin = nullptr;  // every row comes from the input as given
   V.pin_pos = ctx->pin_pos;
   V.W_in = ctx->Wtmp;
   V.W = W_target;
-  V.X = pin_override ? ctx->X : nullptr;
+  V.X = write_X ? ctx->X : nullptr;
   V.vrec = vrec;
   V.write_dw = 0;
-  if (!pin_override) {
-    // every row from the input: point the pinned lookup at the input as well
-    V.v2pin = nullptr;
-  }
   launch_vertex_update(V, ctx->stream);
   FFA_CUDA(cudaGetLastError());
   return FFA_OK;

@@ -331,8 +331,9 @@ int build_factor(const FactorInput& in, Factor& f, std::string& err) {
   }
   int64_t total = 0, flops = 0;
   for (auto& sn : f.nodes) {
+    sn.ld = (sn.ncol + sn.nrow + 3) / 4 * 4;
     sn.blk_off = total;
-    total += (int64_t)(sn.ncol + sn.nrow) * sn.ncol;
+    total += (int64_t)sn.ld * sn.ncol;
     const double ns = sn.ncol, ms = sn.nrow;
     // partial Cholesky + explicit inverse + M = L21 inv(L11), FMA = 2 flops
     flops += (int64_t)(ns * ns * ns / 3.0 + ns * ns * ms + ns * ms * ms + ns * ns * ns / 3.0 + ms * ns * ns);
@@ -417,9 +418,13 @@ int build_factor(const FactorInput& in, Factor& f, std::string& err) {
         }
       }
     });
-    float* dst = f.blocks.data() + sn.blk_off;
-    for (int64_t q = 0; q < (int64_t)N * ns; ++q) dst[q] = static_cast<float>(B[q]);
-    if (in.keep_double) std::copy(B.begin(), B.end(), f.blocks64.begin() + sn.blk_off);
+    for (int j = 0; j < ns; ++j) {
+      float* dst = f.blocks.data() + sn.blk_off + (int64_t)j * sn.ld;
+      const double* src = B.data() + (int64_t)j * N;
+      for (int i = 0; i < N; ++i) dst[i] = static_cast<float>(src[i]);
+      if (in.keep_double)
+        std::copy(src, src + N, f.blocks64.begin() + sn.blk_off + (int64_t)j * sn.ld);
+    }
   };
 
   // independent subtrees go to a pool; the top of the tree runs with parallel dense kernels
@@ -492,7 +497,7 @@ void host_solve(const Factor& f, const double* b, double* x, int nrhs) {
   for (int64_t c = 0; c < nF; ++c)
     for (int k = 0; k < nrhs; ++k) y[c * nrhs + k] = b[(int64_t)f.perm[c] * nrhs + k];
   for (const Supernode& sn : f.nodes) {
-    const int ns = sn.ncol, ms = sn.nrow, N = ns + ms;
+    const int ns = sn.ncol, ms = sn.nrow, N = sn.ld;
     const double* B = f.blocks64.data() + sn.blk_off;
     const int32_t* R = f.rows.data() + sn.row_off;
     for (int j = 0; j < ns; ++j)
@@ -504,7 +509,7 @@ void host_solve(const Factor& f, const double* b, double* x, int nrhs) {
   }
   for (auto it = f.nodes.rbegin(); it != f.nodes.rend(); ++it) {
     const Supernode& sn = *it;
-    const int ns = sn.ncol, ms = sn.nrow, N = ns + ms;
+    const int ns = sn.ncol, ms = sn.nrow, N = sn.ld;
     const double* B = f.blocks64.data() + sn.blk_off;
     const int32_t* R = f.rows.data() + sn.row_off;
     for (int j = 0; j < ns; ++j)

@@ -5,7 +5,8 @@
 // The free-vertex block L_FF of L = sum_i mu_i G_i^T G_i (eq. solvinginw) is ordered by
 // geometric nested dissection and factored by a multifrontal Cholesky in double.
 // Every supernode s (a separator or a leaf block) stores one dense block
-//     B_s = [ inv(L_ss) ; L_rs inv(L_ss) ]     ((n_s + m_s) x n_s, column-major)
+//     B_s = [ inv(L_ss) ; L_rs inv(L_ss) ]     ((n_s + m_s) x n_s, column-major,
+//                                               zero-padded to ld rows)
 // so that the forward solve is  z_s = inv(L_ss) y_s,  y_r -= (L_rs inv(L_ss)) y_s
 // and the backward solve is     x_s = inv(L_ss)^T z_s - (L_rs inv(L_ss))^T x_r:
 // both passes become dense matrix-vector products that the GPU runs in parallel.
@@ -23,8 +24,9 @@ struct Supernode {
   int32_t nrow = 0;     // m_s: rows below the diagonal block (the structure)
   int32_t parent = -1;
   int32_t level = 0;    // 0 = leaf; 1 + max(children) otherwise
+  int32_t ld = 0;       // leading dimension of B_s: n_s + m_s rounded up to 4 (16-byte columns)
   int64_t row_off = 0;  // offset of the structure in Factor::rows
-  int64_t blk_off = 0;  // offset of B_s in Factor::blocks
+  int64_t blk_off = 0;  // offset of B_s in Factor::blocks (a multiple of 4 floats)
 };
 
 struct Factor {
@@ -33,8 +35,8 @@ struct Factor {
   std::vector<int32_t> iperm;  // free index -> eliminated position
   std::vector<Supernode> nodes;  // postorder: children before parents
   std::vector<int32_t> rows;     // concatenated structures (eliminated numbering)
-  std::vector<float> blocks;     // B_s in float, column-major, leading dim n_s + m_s
-  std::vector<double> blocks64;  // B_s in double (kept only on request)
+  std::vector<float> blocks;     // B_s in float, column-major, leading dimension ld
+  std::vector<double> blocks64;  // B_s in double (kept only on request), same layout
   int32_t n_levels = 0;
   int64_t flops = 0;
   double t_analyze = 0.0, t_factor = 0.0;

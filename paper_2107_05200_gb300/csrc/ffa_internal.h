@@ -19,17 +19,17 @@ enum { QV_GTL = 0, QV_NUM, QV_DEN, NQV };
 
 constexpr int kLocalBlock = 128;
 constexpr int kVertexBlock = 256;
-constexpr int kFwdRows = 128;     // forward tile rows (one thread per row)
-constexpr int kFwdCols = 128;     // forward tile columns
-constexpr int kBwdCols = 32;      // backward tile: output columns (4 per warp, 8 warps)
-constexpr int kBwdRows = 256;     // backward tile: rows reduced per task
+constexpr int kFwdRows = 128;     // forward task rows (4 per lane)
+constexpr int kFwdCols = 256;     // forward task columns (32 per warp, 8 warps)
+constexpr int kBwdCols = 32;      // backward task: output columns (4 per warp, 8 warps)
+constexpr int kBwdRows = 1024;    // backward task: rows reduced per task
 
 struct Task {
   int32_t node, r0, c0, pad;
 };
 
 struct NodeDev {
-  int32_t col0, ncol, nrow, pad;
+  int32_t col0, ncol, nrow, ld;   // ld: leading dimension of B_s (multiple of 4)
   int64_t row_off, blk_off;
 };
 
@@ -128,6 +128,7 @@ struct FinalLaunch {
   int d, m, require_flip_free;
   int32_t iter;
   ffa_stats* out;
+  double* scratch;   // NQ + 1 doubles
 };
 void launch_final_reduce(const FinalLaunch& F, cudaStream_t s);
 void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s);

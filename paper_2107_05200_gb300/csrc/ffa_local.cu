@@ -213,33 +213,23 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
       Up[i] = c;
       Up[(int64_t)m + i] = s;
     } else {
-      R Us[3][3], sv[3], Vs[3][3];
-      svd3_signed<R>(Q, Us, sv, Vs);
+      R cond;
+      nearest_rotation3<R>(Q, U, cond);
       if constexpr (sizeof(R) == 4) {
-        // the rotation is ill-conditioned when s1 + s2 is tiny against s0: redo in double
-        if (sv[1] + sv[2] < R(1e-3) * sv[0]) {
-          double Qd[3][3], Ud[3][3], sd[3], Vd[3][3];
+        // the rotation is ill-conditioned when s_mid + s_min is tiny against s_max:
+        // redo it in double for those few elements
+        if (cond < R(1e-3)) {
+          double Qd[3][3], Ud[3][3], cd;
 #pragma unroll
           for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int k = 0; k < 3; ++k) Qd[a][k] = (double)Q[a][k];
-          svd3_signed<double>(Qd, Ud, sd, Vd);
+          nearest_rotation3<double>(Qd, Ud, cd);
 #pragma unroll
           for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-              U[a][k] = (R)(Ud[a][0] * Vd[k][0] + Ud[a][1] * Vd[k][1] + Ud[a][2] * Vd[k][2]);
-        } else {
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) U[a][k] = Us[a][0] * Vs[k][0] + Us[a][1] * Vs[k][1] + Us[a][2] * Vs[k][2];
+            for (int k = 0; k < 3; ++k) U[a][k] = (R)Ud[a][k];
         }
-      } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) U[a][k] = Us[a][0] * Vs[k][0] + Us[a][1] * Vs[k][1] + Us[a][2] * Vs[k][2];
       }
       R qt[4];
       rot_to_quat<R>(U, qt);

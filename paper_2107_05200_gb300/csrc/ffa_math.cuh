@@ -229,6 +229,124 @@ __device__ __forceinline__ void svd3_signed(const R Q[3][3], R U[3][3], R s[3], 
 }
 
 // ---------------------------------------------------------------------------
+// nearest rotation (SO(3) Procrustes, eq. optimizationinudecoupled) by one-sided
+// Jacobi: plane rotations of the columns of B = Q V until they are orthogonal
+// (no Q^T Q, so the condition number is not squared).  Then Q = [s_j u_j] V^T;
+// with k the smallest column, u_k := u_{k+1} x u_{k+2} makes U a rotation and
+// puts the sign of det Q on the smallest singular value, so R = U V^T is the
+// rotation closest to Q.  cond returns (s_mid + s_min_signed) / s_max, the
+// conditioning of R (R is ill-determined when it is tiny).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void onesided_rotate(R B[3][3], R V[3][3], int p, int q) {
+  R al = 0, be = 0, ga = 0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    al = fma(B[r][p], B[r][p], al);
+    be = fma(B[r][q], B[r][q], be);
+    ga = fma(B[r][p], B[r][q], ga);
+  }
+  if (!(Tr<R>::abs_(ga) > Tr<R>::eps() * Tr<R>::sqrt_(al * be)) || ga == R(0)) return;
+  const R zeta = (be - al) / (R(2) * ga);
+  const R az = Tr<R>::abs_(zeta);
+  R t = R(1) / (az + Tr<R>::sqrt_(az * az + R(1)));
+  if (az * Tr<R>::eps() > R(1)) t = R(0.5) / az;
+  t = (zeta < R(0)) ? -t : t;
+  const R c = Tr<R>::rsqrt_(t * t + R(1));
+  const R sn = t * c;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const R bp = B[r][p], bq = B[r][q];
+    B[r][p] = c * bp - sn * bq;
+    B[r][q] = sn * bp + c * bq;
+    const R vp = V[r][p], vq = V[r][q];
+    V[r][p] = c * vp - sn * vq;
+    V[r][q] = sn * vp + c * vq;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void nearest_rotation3(const R Q[3][3], R Rot[3][3], R& cond) {
+  R B[3][3], V[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      B[i][j] = Q[i][j];
+      V[i][j] = (i == j) ? R(1) : R(0);
+    }
+#pragma unroll 1
+  for (int sw = 0; sw < Tr<R>::jacobi_sweeps; ++sw) {
+    onesided_rotate<R>(B, V, 0, 1);
+    onesided_rotate<R>(B, V, 0, 2);
+    onesided_rotate<R>(B, V, 1, 2);
+    // converged when every column pair is orthogonal to working precision
+    R worst = 0;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      R al = 0, be = 0, ga = 0;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        al = fma(B[r][p], B[r][p], al);
+        be = fma(B[r][q], B[r][q], be);
+        ga = fma(B[r][p], B[r][q], ga);
+      }
+      worst = fmax(worst, ga * ga - R(16) * Tr<R>::eps() * Tr<R>::eps() * al * be);
+    }
+    if (!(worst > R(0))) break;
+  }
+  R n[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) n[j] = B[0][j] * B[0][j] + B[1][j] * B[1][j] + B[2][j] * B[2][j];
+  const int k = (n[0] <= n[1] && n[0] <= n[2]) ? 0 : ((n[1] <= n[2]) ? 1 : 2);
+  const int a = (k + 1) % 3, b = (k + 2) % 3;
+  const int big = n[a] >= n[b] ? a : b, mid = n[a] >= n[b] ? b : a;
+  R U[3][3];
+  // u_big: normalized largest column (Q = 0: any rotation is optimal, take I)
+  R ub[3], um[3];
+  if (n[big] > Tr<R>::tiny()) {
+    const R inv = Tr<R>::rsqrt_(n[big]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) ub[r] = B[r][big] * inv;
+  } else {
+    ub[0] = R(big == 0); ub[1] = R(big == 1); ub[2] = R(big == 2);
+  }
+  // u_mid: middle column made orthogonal to u_big (rank-1 Q: any orthogonal unit vector)
+  R dp = B[0][mid] * ub[0] + B[1][mid] * ub[1] + B[2][mid] * ub[2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) um[r] = B[r][mid] - dp * ub[r];
+  R nm = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+  if (!(nm > Tr<R>::eps() * Tr<R>::eps() * n[big]) || !(nm > Tr<R>::tiny())) {
+    // pick the coordinate axis least aligned with u_big and orthogonalize it
+    const int ax = (Tr<R>::abs_(ub[0]) <= Tr<R>::abs_(ub[1]) && Tr<R>::abs_(ub[0]) <= Tr<R>::abs_(ub[2])) ? 0
+                   : (Tr<R>::abs_(ub[1]) <= Tr<R>::abs_(ub[2]) ? 1 : 2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) um[r] = R(r == ax) - ub[ax] * ub[r];
+    nm = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+  }
+  const R invm = Tr<R>::rsqrt_(nm);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    um[r] *= invm;
+    U[r][big] = ub[r];
+    U[r][mid] = um[r];
+  }
+  // u_k = u_a x u_b (cyclic order keeps det U = +1)
+  U[0][k] = U[1][a] * U[2][b] - U[2][a] * U[1][b];
+  U[1][k] = U[2][a] * U[0][b] - U[0][a] * U[2][b];
+  U[2][k] = U[0][a] * U[1][b] - U[1][a] * U[0][b];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Rot[i][j] = U[i][0] * V[j][0] + U[i][1] * V[j][1] + U[i][2] * V[j][2];
+  // signed smallest singular value: s_k = u_k . B_k (negative when det Q < 0)
+  const R sk = U[0][k] * B[0][k] + U[1][k] * B[1][k] + U[2][k] * B[2][k];
+  const R smax = Tr<R>::sqrt_(n[big]);
+  cond = (smax > R(0)) ? (Tr<R>::sqrt_(n[mid]) + sk) / smax : R(1);
+}
+
+// ---------------------------------------------------------------------------
 // rotations <-> compact storage
 // ---------------------------------------------------------------------------
 template <typename R>

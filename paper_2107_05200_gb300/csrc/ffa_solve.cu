@@ -105,16 +105,34 @@ __global__ void __launch_bounds__(kVertexBlock) k_gather(GatherLaunch G) {
       for (int k = 0; k < D; ++k) outv[k] = acc[k];
     } else {
       const float* c = reinterpret_cast<const float*>(G.contrib);
-      FF acc[D];
+      FF acc[2][D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) acc[k] = FF{0.f, 0.f};
-      for (int64_t q = q0; q < q1; ++q) {
+      for (int k = 0; k < D; ++k) acc[0][k] = acc[1][k] = FF{0.f, 0.f};
+      int64_t q = q0;
+      for (; q + 4 <= q1; q += 4) {
+        int64_t base[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) base[u] = (int64_t)__ldg(G.inc + q + u) * D;
+        float v[4][D];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int k = 0; k < D; ++k) v[u][k] = __ldg(c + base[u] + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int k = 0; k < D; ++k) acc[u & 1][k] = ff_addf(acc[u & 1][k], v[u][k]);
+      }
+      for (; q < q1; ++q) {
         const int64_t base = (int64_t)__ldg(G.inc + q) * D;
 #pragma unroll
-        for (int k = 0; k < D; ++k) acc[k] = ff_addf(acc[k], __ldg(c + base + k));
+        for (int k = 0; k < D; ++k) acc[0][k] = ff_addf(acc[0][k], __ldg(c + base + k));
       }
 #pragma unroll
-      for (int k = 0; k < D; ++k) outv[k] = (double)acc[k].hi + (double)acc[k].lo;
+      for (int k = 0; k < D; ++k) {
+        const FF a = ff_add(acc[0][k], acc[1][k]);
+        outv[k] = (double)a.hi + (double)a.lo;
+      }
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -191,109 +209,169 @@ __global__ void k_axpy(int n, double* __restrict__ X, const float* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// supernodal solves.  Forward task (node, r0, c0): rows [r0, r0+128) x columns
-// [c0, c0+128) of B_s times f = y[cols(s)]; rows < n_s add into z, rows >= n_s
-// subtract from y at the structure rows.  One thread per row; B_s is
-// column-major so each column read is coalesced across the warp.
+// supernodal solves.  B_s is column-major with a leading dimension ld that is a
+// multiple of 4, so every lane reads 4 consecutive rows of a column as one
+// float4 and a warp reads 512 contiguous bytes per column.
+//
+// Forward task (node, r0, c0): rows [r0, r0+128) of B_s times the slice
+// [c0, c0+256) of f = y[cols(s)]; warp w takes columns c0+32w .. c0+32w+31, the
+// eight partial sums are added in shared memory and the 128 row results go out
+// as one set of atomics: rows < n_s into z, rows >= n_s subtracted from y at the
+// structure rows.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ldg_stream(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+
 template <int D>
-__global__ void __launch_bounds__(kFwdRows) k_forward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
-                                                      const int32_t* __restrict__ rows, const float* __restrict__ blocks,
-                                                      float* __restrict__ y, float* __restrict__ z) {
+__global__ void __launch_bounds__(256) k_forward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+                                                 const int32_t* __restrict__ rows, const float* __restrict__ blocks,
+                                                 float* __restrict__ y, float* __restrict__ z) {
   const Task t = tasks[blockIdx.x];
   const NodeDev nd = nodes[t.node];
-  const int ld = nd.ncol + nd.nrow;
-  const int nc = min(kFwdCols, nd.ncol - t.c0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntot = nd.ncol + nd.nrow;
   __shared__ float fs[kFwdCols][D];
-  for (int q = threadIdx.x; q < nc * D; q += kFwdRows) {
+  __shared__ float red[8][kFwdRows][D];
+  const int nc = min(kFwdCols, nd.ncol - t.c0);
+  for (int q = threadIdx.x; q < nc * D; q += 256) {
     const int c = q / D, k = q - c * D;
     fs[c][k] = y[(int64_t)(nd.col0 + t.c0 + c) * D + k];
   }
   __syncthreads();
-  const int row = t.r0 + threadIdx.x;
-  if (row >= ld) return;
-  // in the inverse-diagonal part only columns <= row are nonzero
-  const int cend = (row < nd.ncol) ? min(nc, row - t.c0 + 1) : nc;
-  const float* B = blocks + nd.blk_off + (int64_t)t.c0 * ld + row;
-  float acc[D];
+  const int r = t.r0 + 4 * lane;
+  const int cw0 = 32 * warp;                       // this warp's columns within the task
+  const int ncw = max(0, min(32, nc - cw0));
+  float acc[4][D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) acc[k] = 0.f;
-  int c = 0;
-  for (; c + 4 <= cend; c += 4) {
-    const float b0 = __ldg(B + (int64_t)c * ld), b1 = __ldg(B + (int64_t)(c + 1) * ld);
-    const float b2 = __ldg(B + (int64_t)(c + 2) * ld), b3 = __ldg(B + (int64_t)(c + 3) * ld);
+  for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      acc[k] = fmaf(b0, fs[c][k], acc[k]);
-      acc[k] = fmaf(b1, fs[c + 1][k], acc[k]);
-      acc[k] = fmaf(b2, fs[c + 2][k], acc[k]);
-      acc[k] = fmaf(b3, fs[c + 3][k], acc[k]);
+    for (int k = 0; k < D; ++k) acc[q][k] = 0.f;
+  if (r < nd.ld && ncw > 0) {
+    const float* B = blocks + nd.blk_off + (int64_t)(t.c0 + cw0) * nd.ld + r;
+    int c = 0;
+    for (; c + 8 <= ncw; c += 8) {
+      float4 b[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float f = fs[cw0 + c + u][k];
+          acc[0][k] = fmaf(b[u].x, f, acc[0][k]);
+          acc[1][k] = fmaf(b[u].y, f, acc[1][k]);
+          acc[2][k] = fmaf(b[u].z, f, acc[2][k]);
+          acc[3][k] = fmaf(b[u].w, f, acc[3][k]);
+        }
+    }
+    for (; c < ncw; ++c) {
+      const float4 bv = ldg_stream(B + (int64_t)c * nd.ld);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float f = fs[cw0 + c][k];
+        acc[0][k] = fmaf(bv.x, f, acc[0][k]);
+        acc[1][k] = fmaf(bv.y, f, acc[1][k]);
+        acc[2][k] = fmaf(bv.z, f, acc[2][k]);
+        acc[3][k] = fmaf(bv.w, f, acc[3][k]);
+      }
     }
   }
-  for (; c < cend; ++c) {
-    const float bv = __ldg(B + (int64_t)c * ld);
 #pragma unroll
-    for (int k = 0; k < D; ++k) acc[k] = fmaf(bv, fs[c][k], acc[k]);
-  }
-  if (cend <= 0) return;
-  if (row < nd.ncol) {
+  for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int k = 0; k < D; ++k) atomicAdd(z + (int64_t)(nd.col0 + row) * D + k, acc[k]);
-  } else {
-    const int r = __ldg(rows + nd.row_off + (row - nd.ncol));
+    for (int k = 0; k < D; ++k) red[warp][4 * lane + q][k] = acc[q][k];
+  __syncthreads();
+  if (threadIdx.x < kFwdRows) {
+    const int row = t.r0 + threadIdx.x;
+    if (row < ntot && !(row < nd.ncol && row < t.c0)) {
+      float sum[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) atomicAdd(y + (int64_t)r * D + k, -acc[k]);
+      for (int k = 0; k < D; ++k) {
+        float a = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) a += red[w][threadIdx.x][k];
+        sum[k] = a;
+      }
+      if (row < nd.ncol) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) atomicAdd(z + (int64_t)(nd.col0 + row) * D + k, sum[k]);
+      } else {
+        const int rr = __ldg(rows + nd.row_off + (row - nd.ncol));
+#pragma unroll
+        for (int k = 0; k < D; ++k) atomicAdd(y + (int64_t)rr * D + k, -sum[k]);
+      }
+    }
   }
 }
 
-// Backward task (node, r0, c0): output columns [c0, c0+32) of x_s, rows
-// [r0, r0+256) of B_s; v = [z_s ; -x at the structure].  A warp owns one column
-// at a time and reads it coalesced; partial dot products go to x atomically.
+// Backward task (node, r0, c0): output columns [c0, c0+32) of x_s against rows
+// [r0, r0+1024) of B_s, v = [z_s ; -x at the structure rows] staged in shared
+// memory.  Warp w owns columns c0+4w .. c0+4w+3; each lane reads 4 rows of each
+// of them per step; the 4 column dot products are reduced across the warp.
 template <int D>
 __global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
                                                   const int32_t* __restrict__ rows, const float* __restrict__ blocks,
                                                   const float* __restrict__ z, float* __restrict__ x) {
   const Task t = tasks[blockIdx.x];
   const NodeDev nd = nodes[t.node];
-  const int ld = nd.ncol + nd.nrow;
-  const int nr = min(kBwdRows, ld - t.r0);
-  __shared__ float vs[kBwdRows][D];
-  for (int q = threadIdx.x; q < nr * D; q += 256) {
-    const int r = q / D, k = q - r * D;
+  const int ntot = nd.ncol + nd.nrow;
+  const int nr = min(kBwdRows, nd.ld - t.r0);     // rows of this task, a multiple of 4
+  __shared__ __align__(16) float vs[D][kBwdRows];
+  for (int r = threadIdx.x; r < nr; r += 256) {
     const int row = t.r0 + r;
-    float v;
-    if (row < nd.ncol) v = z[(int64_t)(nd.col0 + row) * D + k];
-    else v = -x[(int64_t)__ldg(rows + nd.row_off + (row - nd.ncol)) * D + k];
-    vs[r][k] = v;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ncols = min(kBwdCols, nd.ncol - t.c0);
-  for (int cc = warp; cc < ncols; cc += 8) {
-    const int j = t.c0 + cc;
-    const float* B = blocks + nd.blk_off + (int64_t)j * ld;
-    // rows < j of the inverse-diagonal part are zero
-    const int rstart = max(0, j - t.r0);
-    float acc[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) acc[k] = 0.f;
-#pragma unroll 8
-    for (int r = rstart + lane; r < nr; r += 32) {
-      const float bv = __ldg(B + t.r0 + r);
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc[k] = fmaf(bv, vs[r][k], acc[k]);
-    }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      float a = acc[k];
+      float v = 0.f;
+      if (row < nd.ncol) v = z[(int64_t)(nd.col0 + row) * D + k];
+      else if (row < ntot) v = -x[(int64_t)__ldg(rows + nd.row_off + (row - nd.ncol)) * D + k];
+      vs[k][r] = v;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = t.c0 + 4 * warp;                  // first of this warp's 4 columns
+  if (j0 >= nd.ncol) return;
+  const int ncw = min(4, nd.ncol - j0);
+  float acc[4][D];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[q][k] = 0.f;
+  const float* B = blocks + nd.blk_off + (int64_t)j0 * nd.ld + t.r0;
+  // rows above the diagonal of inv(L_ss) are stored zeros: start at the first
+  // 4-row group that can be nonzero for this warp's first column
+  const int rs = max(0, (j0 - t.r0) & ~3);
+#pragma unroll 2
+  for (int r = rs + 4 * lane; r < nr; r += 128) {
+    float4 b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = (q < ncw) ? ldg_stream(B + (int64_t)q * nd.ld + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float4 v = *reinterpret_cast<const float4*>(&vs[k][r]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q][k] = fmaf(b[q].x, v.x, acc[q][k]);
+        acc[q][k] = fmaf(b[q].y, v.y, acc[q][k]);
+        acc[q][k] = fmaf(b[q].z, v.z, acc[q][k]);
+        acc[q][k] = fmaf(b[q].w, v.w, acc[q][k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float a = acc[q][k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      acc[k] = a;
+      acc[q][k] = a;
     }
-    if (lane == 0 && rstart < nr) {
+  if (lane == 0) {
+    for (int q = 0; q < ncw; ++q)
 #pragma unroll
-      for (int k = 0; k < D; ++k) atomicAdd(x + (int64_t)(nd.col0 + j) * D + k, acc[k]);
-    }
+      for (int k = 0; k < D; ++k) atomicAdd(x + (int64_t)(nd.col0 + j0 + q) * D + k, acc[q][k]);
   }
 }
 
@@ -317,50 +395,49 @@ __global__ void __launch_bounds__(kVertexBlock) k_pin_rhs(int nF, const int64_t*
 }
 
 // ---------------------------------------------------------------------------
-// termination test (eqs. primaldualerror/primaldualthresholds), single block
+// termination test (eqs. primaldualerror/primaldualthresholds): block q sums
+// quantity q of the per-block partials; one thread then forms the statistics
 // ---------------------------------------------------------------------------
-__global__ void k_final(FinalLaunch F) {
-  __shared__ double acc[NQ + 1];
-  const int tid = threadIdx.x;
-  for (int q = 0; q <= NQ; ++q) {
-    double s = 0.0;
-    if (q < NQ) {
-      for (int64_t b = tid; b < F.n_local_blocks; b += blockDim.x) s += F.local_partials[b * NQ + q];
-    } else {
-      for (int64_t b = tid; b < F.n_vert_blocks; b += blockDim.x) s += F.vert_partials[b];
-    }
+__global__ void k_reduce_quantities(FinalLaunch F, double* __restrict__ sums) {
+  const int q = blockIdx.x;
+  double s = 0.0;
+  if (q < NQ) {
+    for (int64_t b = threadIdx.x; b < F.n_local_blocks; b += blockDim.x) s += F.local_partials[b * NQ + q];
+  } else {
+    for (int64_t b = threadIdx.x; b < F.n_vert_blocks; b += blockDim.x) s += F.vert_partials[b];
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ double wsum[32];
-    if ((tid & 31) == 0) wsum[tid >> 5] = s;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-      acc[q] = t;
-    }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double wsum[32];
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+    sums[q] = t;
   }
-  if (tid == 0) {
-    ffa_stats st;
-    st.iters = 0;
-    st.checked_iter = F.iter;
-    st.e_prim = sqrt(acc[Q_EPRIM]);
-    st.e_dual = sqrt(acc[Q_EDUAL]);
-    st.norm_GW = sqrt(acc[Q_GW]);
-    st.norm_P = sqrt(acc[Q_P]);
-    st.norm_GtLambda = sqrt(acc[NQ]);
-    st.energy_P = acc[Q_ENERGY];
-    st.n_flipped = (int32_t)(acc[Q_FLIPS] + 0.5);
-    const double base = F.eps_abs * sqrt((double)F.d * (double)F.m);
-    st.thr_prim = base + F.eps_rel * fmax(st.norm_GW, st.norm_P);
-    st.thr_dual = base + F.eps_rel * st.norm_GtLambda;
-    const bool finite_ok = acc[Q_NONFINITE] == 0.0 && isfinite(st.e_prim) && isfinite(st.e_dual);
-    st.converged = (finite_ok && st.e_prim < st.thr_prim && st.e_dual < st.thr_dual &&
-                    (!F.require_flip_free || st.n_flipped == 0)) ? 1 : 0;
-    if (!finite_ok) st.converged = -1;
-    *F.out = st;
-  }
+}
+
+__global__ void k_stats(FinalLaunch F, const double* __restrict__ acc) {
+  if (threadIdx.x != 0) return;
+  ffa_stats st;
+  st.iters = 0;
+  st.checked_iter = F.iter;
+  st.e_prim = sqrt(acc[Q_EPRIM]);
+  st.e_dual = sqrt(acc[Q_EDUAL]);
+  st.norm_GW = sqrt(acc[Q_GW]);
+  st.norm_P = sqrt(acc[Q_P]);
+  st.norm_GtLambda = sqrt(acc[NQ]);
+  st.energy_P = acc[Q_ENERGY];
+  st.n_flipped = (int32_t)(acc[Q_FLIPS] + 0.5);
+  const double base = F.eps_abs * sqrt((double)F.d * (double)F.m);
+  st.thr_prim = base + F.eps_rel * fmax(st.norm_GW, st.norm_P);
+  st.thr_dual = base + F.eps_rel * st.norm_GtLambda;
+  const bool finite_ok = acc[Q_NONFINITE] == 0.0 && isfinite(st.e_prim) && isfinite(st.e_dual);
+  st.converged = (finite_ok && st.e_prim < st.thr_prim && st.e_dual < st.thr_dual &&
+                  (!F.require_flip_free || st.n_flipped == 0)) ? 1 : 0;
+  if (!finite_ok) st.converged = -1;
+  *F.out = st;
 }
 
 __global__ void k_sum_partials(const double* __restrict__ p, int64_t nb, int nq, double* __restrict__ out) {
@@ -425,8 +502,8 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   for (int l = 0; l < L; ++l) {
     const int64_t nt = S.fwd_off[l + 1] - S.fwd_off[l];
     if (nt <= 0) continue;
-    if (S.d == 2) k_forward<2><<<(unsigned)nt, kFwdRows, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
-    else k_forward<3><<<(unsigned)nt, kFwdRows, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+    if (S.d == 2) k_forward<2><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+    else k_forward<3><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
   }
   for (int l = L - 1; l >= 0; --l) {
     const int64_t nt = S.bwd_off[l + 1] - S.bwd_off[l];
@@ -443,7 +520,10 @@ void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, c
   else k_pin_rhs<3><<<g, kVertexBlock, 0, s>>>(nF, ptr, pin_col, val, pin_pos, cst);
 }
 
-void launch_final_reduce(const FinalLaunch& F, cudaStream_t s) { k_final<<<1, 256, 0, s>>>(F); }
+void launch_final_reduce(const FinalLaunch& F, cudaStream_t s) {
+  k_reduce_quantities<<<NQ + 1, 512, 0, s>>>(F, F.scratch);
+  k_stats<<<1, 32, 0, s>>>(F, F.scratch);
+}
 
 void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s) {
   k_sum_partials<<<nq, 256, 0, s>>>(partials, n_blocks, nq, out);
