@@ -148,7 +148,7 @@ ffa_status ffa_create(const ffa_mesh* mesh, const int32_t* pin_idx, int32_t n_pi
 void ffa_destroy(ffa_ctx* ctx);
 
 /* Message of the last failed call on ctx ("" if none).  With ctx NULL: the message
- * of the last failed ffa_create on the calling thread. */
+ * of the last failed ffa_create or ffa_energy_noalloc on the calling thread. */
 const char* ffa_last_error(const ffa_ctx* ctx);
 
 /* Replace the pinned positions b (n_pin x d, host or device).  The operator is
@@ -198,6 +198,36 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out);
 /* Relative residual |L_FF W_F - b_F| / |b_F| of the last W step, measured in
  * double on the device (a diagnostic of the refinement sweeps; eq. solvinginw. */
 ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel_residual);
+
+/* Energy of a map without a context and without allocating memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- code that runs under a custom or frozen device allocator,
+ * inside a memory pool that must not grow, or in a process that only receives
+ * device buffers from elsewhere -- and therefore cannot create a context.
+ * It evaluates sum_i w_i f((G W)_i) (+infinity if some det (G W)_i <= 0) for the
+ * mesh (V, T) and the map W directly, computing every element's frame, hat
+ * gradients and Jacobian on the fly in double precision.
+ *   n, m, d, d_in : sizes as in ffa_mesh; m may be at most 16,777,216
+ *                   (larger m is rejected with FFA_ERR_INVALID_ARG).
+ *   V, T, W       : device pointers (n x d_in doubles, m x (d+1) int32,
+ *                   n x d doubles), read only.
+ *   energy        : which defining function f.
+ *   E             : device pointer to one double, written by the call.
+ *   stream        : cudaStream_t to run on (NULL = the legacy default stream).
+ * The call only enqueues two kernels on the stream and returns; E is valid once
+ * the stream has reached that point.  The per-block partial sums live in one
+ * fixed static device array (1 MiB, held by every GPU that loads the library
+ * until the process exits).  The first call on each device looks up that array's
+ * device address (cudaGetSymbolAddress, with that device current), so make the
+ * first call on a device before any stream capture.  All calls share the array:
+ * each call overwrites the slots it reads, so nothing has to be cleared, but calls
+ * that overlap on the GPU (other streams, other host threads) race on it.
+ * Errors: FFA_ERR_INVALID_ARG (sizes, NULL pointers, unknown energy),
+ * FFA_ERR_CUDA; the message is returned by ffa_last_error(NULL). */
+ffa_status ffa_energy_noalloc(int32_t n, int32_t m, int32_t d, int32_t d_in, const double* V,
+                              const int32_t* T, const double* W, ffa_energy_kind energy, double* E,
+                              void* stream);
 
 #ifdef __cplusplus
 }

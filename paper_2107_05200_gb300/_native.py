@@ -21,7 +21,7 @@ STATUS_NAMES = {
 EXPORTED = [
     "ffa_default_params", "ffa_create", "ffa_destroy", "ffa_last_error", "ffa_set_handles",
     "ffa_init", "ffa_iterate", "ffa_get_W", "ffa_get_state", "ffa_energy", "ffa_gradient",
-    "ffa_get_info", "ffa_last_wstep_residual", "ffa_profile_phases",
+    "ffa_get_info", "ffa_last_wstep_residual", "ffa_profile_phases", "ffa_energy_noalloc",
 ]
 
 
@@ -98,6 +98,7 @@ def load() -> C.CDLL:
         "ffa_get_info": ([vp, C.POINTER(Info)], C.c_int),
         "ffa_last_wstep_residual": ([vp, C.POINTER(dbl)], C.c_int),
         "ffa_profile_phases": ([vp, i32, C.POINTER(PhaseTimes)], C.c_int),
+        "ffa_energy_noalloc": ([i32, i32, i32, i32, vp, vp, vp, C.c_int, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -694,6 +694,8 @@ ffa_status load_W_records(ffa_ctx* ctx, const double* W, bool write_X, double* W
 
 }  // namespace
 
+void ffa::set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 // ===========================================================================
 extern "C" {
 

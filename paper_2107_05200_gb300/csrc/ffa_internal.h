@@ -133,4 +133,7 @@ struct FinalLaunch {
 void launch_final_reduce(const FinalLaunch& F, cudaStream_t s);
 void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s);
 
+// message returned by ffa_last_error(NULL) on the calling thread
+void set_thread_error(const std::string& msg);
+
 }  // namespace ffa
