@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="cube_deform", choices=["cube_deform", "batch256"])
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -155,11 +157,66 @@ def run_reference(args, rank):
     return 0
 
 
+def run_batch(args, rank, world, local):
+    """256 independent meshes solved to tolerance in one batch (one graph launch per
+    check_every iterations for all of them) against the same meshes solved one after
+    another with single-mesh contexts.  Metric: mesh-iterations per second."""
+    import torch
+
+    from paper_2107_05200_gb300 import workloads as wk
+    from paper_2107_05200_gb300.solver import BatchSolver, Solver
+
+    torch.cuda.set_device(local)
+    wls = wk.batched_meshes(count=args.batch_count)
+    max_iter = 2000
+    t0 = time.perf_counter()
+    bs = BatchSolver(wls, precision=args.precision, check_every=10, refine_sweeps=args.sweeps)
+    t_setup = time.perf_counter() - t0
+    bs.init([wl.W0 for wl in wls])
+    tuning = bs.autotune(5)
+    bs.init([wl.W0 for wl in wls])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats, nconv = bs.iterate(max_iter, stop_at_tol=True)
+    t_batch = time.perf_counter() - t0
+    iters_b = stats[0]["iters"]
+    bs.close()
+    # sequential: each mesh alone, to the same tolerance
+    t_seq = 0.0
+    iters_seq = 0
+    conv_seq = 0
+    for wl in wls:
+        with Solver.from_workload(wl, precision=args.precision, check_every=10, refine_sweeps=args.sweeps) as sol:
+            sol.init(wl.W0)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            st = sol.iterate(max_iter, stop_at_tol=True)
+            t_seq += time.perf_counter() - t1
+            iters_seq += st["iters"]
+            conv_seq += int(st["converged"] == 1)
+    m_tot = sum(wl.m for wl in wls)
+    line = {"metric": "batched meshes: mesh-iterations/sec to tolerance", "unit": "mesh-iter/s",
+            "value": len(wls) * iters_b / t_batch, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": f"batch{len(wls)}", "meshes": len(wls), "elements": m_tot,
+                       "tol": wls[0].eps_abs, "max_iter": max_iter},
+            "batched": {"seconds": t_batch, "iterations": iters_b, "converged": nconv,
+                        "setup_s": t_setup, "tuning": tuning},
+            "sequential": {"seconds": t_seq, "mesh_iterations": iters_seq, "converged": conv_seq,
+                           "value": iters_seq / t_seq},
+            "speedup_time_to_tolerance": t_seq / t_batch}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == "batch256":
+        return run_batch(args, rank, world, local)
 
     import numpy as np
     import torch

@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct ffa_ctx ffa_ctx;
+typedef struct ffa_batch ffa_batch;
 
 typedef enum {
   FFA_OK = 0,
@@ -195,9 +196,68 @@ ffa_status ffa_get_info(ffa_ctx* ctx, ffa_info* info);
  * The iterations are real: the state advances by reps iterations. */
 ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out);
 
+/* Launch shapes picked by ffa_autotune (the paper has no counterpart). */
+typedef struct {
+  int32_t local_block;  /* threads per block of the local step: 64, 128 or 256 */
+  int32_t narrow_cols;  /* supernodes with at most this many columns take one warp each: 32 or 64 */
+  double ms_local[3];   /* measured local step for 64, 128, 256 threads */
+  double ms_solve[2];   /* measured supernodal solve (forward + backward) for 32, 64 */
+} ffa_tuning;
+
+/* Time the candidate launch shapes of the local step and of the supernodal solves
+ * with CUDA events over reps launches each, keep the fastest, and restore the
+ * iterate (needs ffa_init first; the state is saved and put back). */
+ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out);
+
+/* Differentiation through K unrolled iterations (the paper has no counterpart;
+ * it is the adjoint of Algorithm 1's W, U, P and Lambda steps with h = 0).
+ * ffa_forward_unrolled runs K iterations from the state set by ffa_init (no
+ * termination test), storing the element state and W every ckpt_every
+ * iterations.  ffa_backward_unrolled then takes dL/dW^K (n x d, host or device)
+ * and writes dL/db (n_pin x d, host or device) for the pinned positions b: it
+ * walks the checkpoint segments backwards, recomputes each segment's iterations,
+ * applies the per-element vector-Jacobian products of the Lambda, P (matrix
+ * function of S, divided differences of the scalar prox root) and U (polar
+ * rotation) steps, and solves the W step's adjoint with the same factorized
+ * L_FF (symmetric).  W^0 is taken as independent of b.  After the call the live
+ * state is again the state after iteration K. */
+ffa_status ffa_forward_unrolled(ffa_ctx* ctx, int32_t K, int32_t ckpt_every);
+ffa_status ffa_backward_unrolled(ffa_ctx* ctx, const double* dL_dW, double* dL_db);
+
 /* Relative residual |L_FF W_F - b_F| / |b_F| of the last W step, measured in
  * double on the device (a diagnostic of the refinement sweeps; eq. solvinginw. */
 ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel_residual);
+
+/* Many independent meshes solved together (the paper solves one mesh at a time;
+ * this batches its Algorithm 1 over independent problems).  Meshes of equal
+ * (d, d_in) are concatenated into one block-diagonal problem: one factorization
+ * per group, one set of launches per iteration for all meshes of the group,
+ * element energy and penalty per mesh, and the termination test of
+ * eq. primaldualthresholds evaluated per mesh.  All groups of a batch share one
+ * stream and one CUDA graph per launch.
+ *   meshes[k], pin_idx[k] / n_pin[k] / pin_pos[k] : as in ffa_create for mesh k
+ *                   (n_pin[k] = 0 pins its vertex 0 at the origin); host or device.
+ *   energies, rho : per mesh (NULL = params->energy / params->rho for all).
+ *   params        : eps_abs, eps_rel, check_every, precision, sweeps, leaf size.
+ * ffa_batch_iterate runs until every mesh passed its test (stop_at_tol = 1) or
+ * max_iter iterations; stats[k] (may be NULL) receives mesh k's last statistics
+ * and *n_converged (may be NULL) the number of meshes that passed.
+ * ffa_batch_last_error(NULL) reports a failed ffa_batch_create. */
+ffa_status ffa_batch_create(int32_t n_meshes, const ffa_mesh* meshes, const int32_t* const* pin_idx,
+                            const int32_t* n_pin, const double* const* pin_pos, const ffa_energy_kind* energies,
+                            const double* rho, const ffa_params* params, void* stream, ffa_batch** out);
+void ffa_batch_destroy(ffa_batch* b);
+const char* ffa_batch_last_error(const ffa_batch* b);
+/* W0[k]: n_k x d initial map of mesh k (host or device), used as given. */
+ffa_status ffa_batch_init(ffa_batch* b, const double* const* W0);
+ffa_status ffa_batch_iterate(ffa_batch* b, int32_t max_iter, int32_t stop_at_tol, ffa_stats* stats,
+                             int32_t* n_converged);
+/* ffa_autotune for every group of the batch (one context per (d, d_in));
+ * out (may be NULL) has ffa_batch_groups(b) entries. */
+ffa_status ffa_batch_autotune(ffa_batch* b, int32_t reps, ffa_tuning* out);
+int32_t ffa_batch_groups(const ffa_batch* b);
+/* Copy mesh k's current W (n_k x d) to W_out (host or device). */
+ffa_status ffa_batch_get_W(ffa_batch* b, int32_t mesh, double* W_out);
 
 /* Energy of a map without a context and without allocating memory.
  *

@@ -22,6 +22,9 @@ EXPORTED = [
     "ffa_default_params", "ffa_create", "ffa_destroy", "ffa_last_error", "ffa_set_handles",
     "ffa_init", "ffa_iterate", "ffa_get_W", "ffa_get_state", "ffa_energy", "ffa_gradient",
     "ffa_get_info", "ffa_last_wstep_residual", "ffa_profile_phases", "ffa_energy_noalloc",
+    "ffa_forward_unrolled", "ffa_backward_unrolled",
+    "ffa_batch_create", "ffa_batch_destroy", "ffa_batch_last_error", "ffa_batch_init", "ffa_batch_iterate",
+    "ffa_batch_get_W", "ffa_autotune", "ffa_batch_autotune", "ffa_batch_groups",
 ]
 
 
@@ -59,6 +62,15 @@ class Info(C.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Tuning(C.Structure):
+    _fields_ = [("local_block", C.c_int32), ("narrow_cols", C.c_int32), ("ms_local", C.c_double * 3),
+                ("ms_solve", C.c_double * 2)]
+
+    def as_dict(self) -> dict:
+        return {"local_block": self.local_block, "narrow_cols": self.narrow_cols,
+                "ms_local": list(self.ms_local), "ms_solve": list(self.ms_solve)}
 
 
 class PhaseTimes(C.Structure):
@@ -99,6 +111,18 @@ def load() -> C.CDLL:
         "ffa_last_wstep_residual": ([vp, C.POINTER(dbl)], C.c_int),
         "ffa_profile_phases": ([vp, i32, C.POINTER(PhaseTimes)], C.c_int),
         "ffa_energy_noalloc": ([i32, i32, i32, i32, vp, vp, vp, C.c_int, vp, vp], C.c_int),
+        "ffa_forward_unrolled": ([vp, i32, i32], C.c_int),
+        "ffa_backward_unrolled": ([vp, vp, vp], C.c_int),
+        "ffa_batch_create": ([i32, C.POINTER(Mesh), C.POINTER(vp), vp, C.POINTER(vp), vp, vp, C.POINTER(Params), vp,
+                              C.POINTER(vp)], C.c_int),
+        "ffa_batch_destroy": ([vp], None),
+        "ffa_batch_last_error": ([vp], C.c_char_p),
+        "ffa_batch_init": ([vp, C.POINTER(vp)], C.c_int),
+        "ffa_batch_iterate": ([vp, i32, i32, C.POINTER(Stats), C.POINTER(i32)], C.c_int),
+        "ffa_batch_get_W": ([vp, i32, vp], C.c_int),
+        "ffa_autotune": ([vp, i32, C.POINTER(Tuning)], C.c_int),
+        "ffa_batch_autotune": ([vp, i32, C.POINTER(Tuning)], C.c_int),
+        "ffa_batch_groups": ([vp], C.c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

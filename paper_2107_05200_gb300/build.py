@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libffadmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["ffa_api.cu", "ffa_local.cu", "ffa_solve.cu", "ffa_noalloc.cu"]
+CU_SOURCES = ["ffa_api.cu", "ffa_local.cu", "ffa_solve.cu", "ffa_adjoint.cu", "ffa_noalloc.cu"]
 CXX_SOURCES = ["ffa_factor.cpp"]
 
 

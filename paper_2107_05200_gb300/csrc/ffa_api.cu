@@ -16,6 +16,17 @@
 
 using namespace ffa;
 
+// Per-element and per-mesh data of a group of batched meshes concatenated into
+// one context (disjoint vertex sets, so L_FF is block diagonal).
+struct BatchSpec {
+  std::vector<int8_t> energy_of;       // per element: 0 SD, 1 SG
+  std::vector<double> rho_of;          // per element penalty scale
+  std::vector<int32_t> mesh_of_elem;   // per element
+  std::vector<int32_t> mesh_of_vertex; // per vertex
+  std::vector<int32_t> mesh_d, mesh_m; // per mesh
+  std::vector<double> mesh_eps;        // per mesh: eps_abs, eps_rel
+};
+
 struct ffa_ctx {
   int n = 0, m = 0, d = 0, d_in = 0, n_pin = 0, nF = 0;
   ffa_params prm{};
@@ -44,7 +55,7 @@ struct ffa_ctx {
   int32_t* rows = nullptr;
   float* blocks = nullptr;
   Task *fwd_t = nullptr, *bwd_t = nullptr;
-  std::vector<int64_t> fwd_off, bwd_off;
+  std::vector<int64_t> fwd_off, bwd_off, fwd_wide, bwd_wide;
   double* local_partials = nullptr;
   int64_t n_local_blocks = 0;
   double* vert_partials = nullptr;
@@ -62,6 +73,54 @@ struct ffa_ctx {
   ffa_stats last{};
   ffa_info info{};
   std::vector<int32_t> pins_h;
+
+  // differentiation through unrolled iterations (ffa_forward_unrolled / ffa_backward_unrolled)
+  struct Slot {
+    void* P = nullptr;
+    void* Lam = nullptr;
+    void* U = nullptr;
+    double* W = nullptr;
+    double* X = nullptr;
+  };
+  int32_t adj_K = 0, adj_C = 0;
+  std::vector<Slot> ckpt, seg;
+  Slot final_state;
+  void *Pbar = nullptr, *Lbar = nullptr, *xi_v = nullptr;
+  double *Wbar = nullptr, *Wloss = nullptr, *Xadj = nullptr, *b_adj = nullptr, *bbar = nullptr;
+  int64_t* cf_ptr = nullptr;
+  int32_t* cf_row = nullptr;
+  double* cf_val = nullptr;
+  int32_t* pins_d = nullptr;
+
+  // launch shapes chosen by ffa_autotune
+  int local_block = 128;
+  int narrow_cols = 64;
+  std::vector<Supernode> nodes_h;  // host copy of the supernode table (task lists are rebuilt from it)
+  int n_levels = 0;
+  Slot tune_slot;
+
+  // batched meshes (set for contexts made by ffa_batch_create)
+  int n_mesh = 0;
+  int8_t* energy_of = nullptr;
+  int32_t *mesh_of_elem = nullptr, *mesh_of_vertex = nullptr, *mesh_d = nullptr, *mesh_m = nullptr;
+  double *mesh_eps = nullptr, *mesh_acc = nullptr;
+  ffa_stats* mesh_stats = nullptr;
+  int32_t* n_converged = nullptr;
+};
+
+struct ffa_batch {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int n_mesh = 0;
+  int check_every = 10;
+  std::vector<ffa_ctx*> groups;            // one context per (d, d_in)
+  std::vector<int> mesh_group, mesh_local;  // group of each mesh and its index there
+  std::vector<int64_t> mesh_voff;           // first vertex of each mesh in its group
+  std::vector<int32_t> mesh_n, mesh_dim;
+  cudaGraphExec_t g_batch = nullptr, g_one = nullptr, g_one_check = nullptr;
+  bool initialized = false;
+  std::vector<ffa_stats> host_stats;
 };
 
 namespace {
@@ -206,6 +265,7 @@ LocalLaunch local_launch(ffa_ctx* ctx, bool check, const void* vrec) {
   L.vrec = vrec;
   L.partials = ctx->local_partials;
   L.n_blocks = ctx->n_local_blocks;
+  L.block = ctx->local_block;
   return L;
 }
 
@@ -223,6 +283,8 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.bwd_tasks = ctx->bwd_t;
   S.fwd_off = ctx->fwd_off;
   S.bwd_off = ctx->bwd_off;
+  S.fwd_wide = ctx->fwd_wide;
+  S.bwd_wide = ctx->bwd_wide;
   S.y = ctx->y;
   S.z = ctx->z;
   S.x = ctx->x;
@@ -275,9 +337,38 @@ void enqueue_iteration(ffa_ctx* ctx, bool check, cudaEvent_t* ev = nullptr) {
   launch_vertex_update(V, s);
   if (ev) cudaEventRecord(ev[PH_VERTEX], s);
   // U, P, Lambda steps
+  if (check && ctx->n_mesh > 0) {
+    cudaMemsetAsync(ctx->mesh_acc, 0, (size_t)ctx->n_mesh * (NQ + 1) * sizeof(double), s);
+    cudaMemsetAsync(ctx->n_converged, 0, sizeof(int32_t), s);
+  }
   launch_local_step(local_launch(ctx, check, ctx->vrec), s);
   if (ev) cudaEventRecord(ev[PH_LOCAL], s);
-  if (check) {
+  if (check && ctx->n_mesh > 0) {
+    GatherLaunch H{};
+    H.d = ctx->d;
+    H.fp64 = ctx->fp64;
+    H.rows = ctx->n;
+    H.row_vertex = nullptr;
+    H.inc_ptr = ctx->inc_ptr;
+    H.inc = ctx->inc;
+    H.contrib = ctx->e.contrib2;
+    H.add = nullptr;
+    H.out = nullptr;
+    H.partials = nullptr;
+    H.mesh_of = ctx->mesh_of_vertex;
+    H.mesh_acc = ctx->mesh_acc;
+    launch_gather(H, s);
+    MeshStatsLaunch M{};
+    M.n_mesh = ctx->n_mesh;
+    M.mesh_acc = ctx->mesh_acc;
+    M.mesh_d = ctx->mesh_d;
+    M.mesh_m = ctx->mesh_m;
+    M.mesh_eps = ctx->mesh_eps;
+    M.require_flip_free = ctx->prm.require_flip_free;
+    M.out = ctx->mesh_stats;
+    M.n_converged = ctx->n_converged;
+    launch_mesh_stats(M, s);
+  } else if (check) {
     GatherLaunch H{};
     H.d = ctx->d;
     H.fp64 = ctx->fp64;
@@ -341,8 +432,72 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   return FFA_ERR_INVALID_ARG;
 }
 
+// Supernode table and per-level task lists of the supernodal solves.  Per level:
+// wide tasks (one block each) first, then narrow warp tasks padded to a
+// multiple of 8.  A node is narrow when it has at most narrow_cols columns.
+ffa_status build_tasks(ffa_ctx* ctx) {
+  const std::vector<Supernode>& nd_h = ctx->nodes_h;
+  const int nl = ctx->n_levels;
+  const int narrow = ctx->narrow_cols;
+  std::vector<NodeDev> nodes(nd_h.size());
+  std::vector<std::vector<Task>> fl(nl), bl(nl), fn(nl), bn(nl);
+  for (size_t s = 0; s < nd_h.size(); ++s) {
+    const Supernode& sn = nd_h[s];
+    nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, sn.ld, sn.row_off, sn.blk_off};
+    const int ntot = sn.ncol + sn.nrow;
+    if (sn.ncol == 0) continue;
+    if (sn.ncol <= narrow) {
+      for (int r0 = 0; r0 < ntot; r0 += kFwdRows) fn[sn.level].push_back(Task{(int32_t)s, r0, 0, 1});
+    } else {
+      for (int r0 = 0; r0 < ntot; r0 += kFwdRows)
+        for (int c0 = 0; c0 < sn.ncol; c0 += kFwdCols) {
+          const int rmax = std::min(r0 + kFwdRows, ntot) - 1;
+          if (rmax < c0) continue;  // entirely above the diagonal of inv(L_ss)
+          fl[sn.level].push_back(Task{(int32_t)s, r0, c0, 0});
+        }
+    }
+    if (sn.ncol <= narrow && sn.ld <= 256) {
+      bn[sn.level].push_back(Task{(int32_t)s, 0, 0, 1});
+    } else {
+      for (int c0 = 0; c0 < sn.ncol; c0 += kBwdCols)
+        for (int r0 = 0; r0 < ntot; r0 += kBwdRows) {
+          const int rmax = std::min(r0 + kBwdRows, ntot) - 1;
+          if (rmax < c0) continue;
+          bl[sn.level].push_back(Task{(int32_t)s, r0, c0, 0});
+        }
+    }
+  }
+  std::vector<Task> fwd_all, bwd_all;
+  ctx->fwd_off.assign(1, 0);
+  ctx->bwd_off.assign(1, 0);
+  ctx->fwd_wide.clear();
+  ctx->bwd_wide.clear();
+  auto pad8 = [](std::vector<Task>& v) {
+    while (v.size() % 8) v.push_back(Task{-1, 0, 0, 1});
+  };
+  for (int l = 0; l < nl; ++l) {
+    pad8(fn[l]);
+    pad8(bn[l]);
+    ctx->fwd_wide.push_back((int64_t)fl[l].size());
+    ctx->bwd_wide.push_back((int64_t)bl[l].size());
+    fwd_all.insert(fwd_all.end(), fl[l].begin(), fl[l].end());
+    fwd_all.insert(fwd_all.end(), fn[l].begin(), fn[l].end());
+    bwd_all.insert(bwd_all.end(), bl[l].begin(), bl[l].end());
+    bwd_all.insert(bwd_all.end(), bn[l].begin(), bn[l].end());
+    ctx->fwd_off.push_back((int64_t)fwd_all.size());
+    ctx->bwd_off.push_back((int64_t)bwd_all.size());
+  }
+  ffa_status st;
+  if (!ctx->nodes && (st = upload(ctx, &ctx->nodes, nodes)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->fwd_t, fwd_all)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->bwd_t, bwd_all)) != FFA_OK) return st;
+  FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  return FFA_OK;
+}
+
 ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_idx, int32_t n_pin,
-                       const double* pin_pos_in, const ffa_params* params, void* stream) {
+                       const double* pin_pos_in, const ffa_params* params, void* stream,
+                       const BatchSpec* batch = nullptr) {
   if (!mesh) return fail(ctx, FFA_ERR_INVALID_ARG, "mesh is NULL");
   ffa_default_params(&ctx->prm);
   if (params) ctx->prm = *params;
@@ -454,7 +609,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
         const int i = inc[q] / (d + 1), j = inc[q] % (d + 1);
         double gj[3], gl[3];
         grad_of(i, j, gj);
-        const double mu = rho * w[i];
+        const double mu = (batch ? batch->rho_of[i] : rho) * w[i];
         for (int l = 0; l <= d; ++l) {
           grad_of(i, l, gl);
           double dotv = 0;
@@ -538,44 +693,28 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     fc_ptr[c + 1] = (int64_t)fc_col.size();
   }
   ctx->ell_width = width;
-
-  // ---- supernode tables and per-level task lists
-  std::vector<NodeDev> nodes(fac.nodes.size());
-  std::vector<std::vector<Task>> fl(fac.n_levels), bl(fac.n_levels);
-  for (size_t s = 0; s < fac.nodes.size(); ++s) {
-    const Supernode& sn = fac.nodes[s];
-    nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, sn.ld, sn.row_off, sn.blk_off};
-    const int ntot = sn.ncol + sn.nrow;
-    if (sn.ncol == 0) continue;
-    for (int r0 = 0; r0 < ntot; r0 += kFwdRows)
-      for (int c0 = 0; c0 < sn.ncol; c0 += kFwdCols) {
-        const int rmax = std::min(r0 + kFwdRows, ntot) - 1;
-        if (rmax < c0) continue;  // entirely above the diagonal of inv(L_ss)
-        fl[sn.level].push_back(Task{(int32_t)s, r0, c0, 0});
-      }
-    for (int c0 = 0; c0 < sn.ncol; c0 += kBwdCols)
-      for (int r0 = 0; r0 < ntot; r0 += kBwdRows) {
-        const int rmax = std::min(r0 + kBwdRows, ntot) - 1;
-        if (rmax < c0) continue;
-        bl[sn.level].push_back(Task{(int32_t)s, r0, c0, 0});
+  // transpose of L_FC: for every pin, its (eliminated row, value) entries
+  std::vector<int64_t> cf_ptr(n_pin + 1, 0);
+  for (int32_t p : fc_col) cf_ptr[p + 1]++;
+  for (int p = 0; p < n_pin; ++p) cf_ptr[p + 1] += cf_ptr[p];
+  std::vector<int32_t> cf_row(fc_col.size());
+  std::vector<double> cf_val(fc_col.size());
+  {
+    std::vector<int64_t> fill(cf_ptr.begin(), cf_ptr.end() - 1);
+    for (int c = 0; c < nF; ++c)
+      for (int64_t q = fc_ptr[c]; q < fc_ptr[c + 1]; ++q) {
+        const int64_t dst = fill[fc_col[q]]++;
+        cf_row[dst] = c;
+        cf_val[dst] = fc_val[q];
       }
   }
-  std::vector<Task> fwd_all, bwd_all;
-  ctx->fwd_off.assign(1, 0);
-  ctx->bwd_off.assign(1, 0);
-  for (int l = 0; l < fac.n_levels; ++l) {
-    fwd_all.insert(fwd_all.end(), fl[l].begin(), fl[l].end());
-    bwd_all.insert(bwd_all.end(), bl[l].begin(), bl[l].end());
-    ctx->fwd_off.push_back((int64_t)fwd_all.size());
-    ctx->bwd_off.push_back((int64_t)bwd_all.size());
-  }
 
+  ctx->nodes_h = fac.nodes;
+  ctx->n_levels = fac.n_levels;
   // ---- device uploads
-  if ((st = upload(ctx, &ctx->nodes, nodes)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->rows, fac.rows)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->blocks, fac.blocks)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->fwd_t, fwd_all)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->bwd_t, bwd_all)) != FFA_OK) return st;
+  if ((st = build_tasks(ctx)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->ell_col, ell_col)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->ell_val, ell_val)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->fc_ptr, fc_ptr)) != FFA_OK) return st;
@@ -587,6 +726,10 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   if ((st = upload(ctx, &ctx->v2e, v2e)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->v2pin, v2pin)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->pin_pos, pin_pos)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->pins_d, pins)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->cf_ptr, cf_ptr)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->cf_row, cf_row)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->cf_val, cf_val)) != FFA_OK) return st;
   // element arrays: indices (d+1) x m, gradients d*d x m, w, mu
   {
     std::vector<int32_t> idx((size_t)(d + 1) * m);
@@ -596,11 +739,29 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     std::vector<double> gs((size_t)d * d * m), mu(m);
     for (int i = 0; i < m; ++i) {
       for (int q = 0; q < d * d; ++q) gs[(size_t)q * m + i] = g[(int64_t)i * d * d + q];
-      mu[i] = rho * w[i];
+      mu[i] = (batch ? batch->rho_of[i] : rho) * w[i];
     }
     if ((st = upload_real(ctx, &ctx->e.g, gs)) != FFA_OK) return st;
     if ((st = upload_real(ctx, &ctx->e.w, w)) != FFA_OK) return st;
     if ((st = upload_real(ctx, &ctx->e.mu, mu)) != FFA_OK) return st;
+  }
+  if (batch) {
+    ctx->n_mesh = (int)batch->mesh_m.size();
+    bool mixed = false;
+    for (int8_t en : batch->energy_of) mixed |= (en != batch->energy_of[0]);
+    ctx->prm.energy = mixed ? (ffa_energy_kind)2 : (ffa_energy_kind)batch->energy_of[0];
+    if ((st = upload(ctx, &ctx->energy_of, batch->energy_of)) != FFA_OK) return st;
+    if ((st = upload(ctx, &ctx->mesh_of_elem, batch->mesh_of_elem)) != FFA_OK) return st;
+    if ((st = upload(ctx, &ctx->mesh_of_vertex, batch->mesh_of_vertex)) != FFA_OK) return st;
+    if ((st = upload(ctx, &ctx->mesh_d, batch->mesh_d)) != FFA_OK) return st;
+    if ((st = upload(ctx, &ctx->mesh_m, batch->mesh_m)) != FFA_OK) return st;
+    if ((st = upload(ctx, &ctx->mesh_eps, batch->mesh_eps)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->mesh_acc, (size_t)ctx->n_mesh * (NQ + 1))) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->mesh_stats, (size_t)ctx->n_mesh)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->n_converged, 1)) != FFA_OK) return st;
+    ctx->e.energy_of = ctx->energy_of;
+    ctx->e.mesh_of = ctx->mesh_of_elem;
+    ctx->e.mesh_acc = ctx->mesh_acc;
   }
   const size_t R = ctx->rsz;
   if ((st = dalloc_bytes(ctx, &ctx->e.P, (size_t)m * (d == 2 ? 3 : 6) * R)) != FFA_OK) return st;
@@ -621,10 +782,11 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   const size_t rec_bytes = (size_t)n * d * (ctx->fp64 ? 16 : 16);
   if ((st = dalloc_bytes(ctx, &ctx->vrec, rec_bytes)) != FFA_OK) return st;
   if ((st = dalloc_bytes(ctx, &ctx->vrec_scratch, rec_bytes)) != FFA_OK) return st;
-  ctx->n_local_blocks = (m + kLocalBlock - 1) / kLocalBlock;
+  ctx->n_local_blocks = (m + ctx->local_block - 1) / ctx->local_block;
   ctx->n_vert_blocks = (n + kVertexBlock - 1) / kVertexBlock;
   ctx->n_res_blocks = (nF + kVertexBlock - 1) / kVertexBlock;
-  if ((st = dalloc(ctx, &ctx->local_partials, (size_t)ctx->n_local_blocks * NQ)) != FFA_OK) return st;
+  // sized for the smallest local-step block (64 threads) the autotuner may pick
+  if ((st = dalloc(ctx, &ctx->local_partials, (size_t)((m + 63) / 64) * NQ)) != FFA_OK) return st;
   if ((st = dalloc(ctx, &ctx->vert_partials, (size_t)ctx->n_vert_blocks)) != FFA_OK) return st;
   if ((st = dalloc(ctx, &ctx->res_partials, (size_t)ctx->n_res_blocks * 2)) != FFA_OK) return st;
   if ((st = dalloc(ctx, &ctx->stats_d, 1)) != FFA_OK) return st;
@@ -686,6 +848,77 @@ ffa_status load_W_records(ffa_ctx* ctx, const double* W, bool write_X, double* W
   V.W = W_target;
   V.X = write_X ? ctx->X : nullptr;
   V.vrec = vrec;
+  V.write_dw = 0;
+  launch_vertex_update(V, ctx->stream);
+  FFA_CUDA(cudaGetLastError());
+  return FFA_OK;
+}
+
+// ---- state slots for checkpointed differentiation ---------------------------
+size_t state_bytes_P(const ffa_ctx* c) { return (size_t)c->m * (c->d == 2 ? 3 : 6) * c->rsz; }
+size_t state_bytes_L(const ffa_ctx* c) { return (size_t)c->m * c->d * c->d * c->rsz; }
+size_t state_bytes_U(const ffa_ctx* c) { return (size_t)c->m * (c->d == 2 ? 2 : 4) * c->rsz; }
+
+ffa_status alloc_slot(ffa_ctx* ctx, ffa_ctx::Slot& sl) {
+  ffa_status st;
+  if ((st = dalloc_bytes(ctx, &sl.P, state_bytes_P(ctx))) != FFA_OK) return st;
+  if ((st = dalloc_bytes(ctx, &sl.Lam, state_bytes_L(ctx))) != FFA_OK) return st;
+  if ((st = dalloc_bytes(ctx, &sl.U, state_bytes_U(ctx))) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &sl.W, (size_t)ctx->n * ctx->d)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &sl.X, (size_t)ctx->nF * ctx->d)) != FFA_OK) return st;
+  return FFA_OK;
+}
+
+ffa_status save_slot(ffa_ctx* ctx, ffa_ctx::Slot& sl) {
+  cudaStream_t s = ctx->stream;
+  FFA_CUDA(cudaMemcpyAsync(sl.P, ctx->e.P, state_bytes_P(ctx), cudaMemcpyDeviceToDevice, s));
+  FFA_CUDA(cudaMemcpyAsync(sl.Lam, ctx->e.Lam, state_bytes_L(ctx), cudaMemcpyDeviceToDevice, s));
+  FFA_CUDA(cudaMemcpyAsync(sl.U, ctx->e.U, state_bytes_U(ctx), cudaMemcpyDeviceToDevice, s));
+  FFA_CUDA(cudaMemcpyAsync(sl.W, ctx->W, (size_t)ctx->n * ctx->d * 8, cudaMemcpyDeviceToDevice, s));
+  FFA_CUDA(cudaMemcpyAsync(sl.X, ctx->X, (size_t)ctx->nF * ctx->d * 8, cudaMemcpyDeviceToDevice, s));
+  return FFA_OK;
+}
+
+// make a slot the live state (element state, W, X, and the vertex records of W)
+ffa_status load_slot(ffa_ctx* ctx, const ffa_ctx::Slot& sl) {
+  cudaStream_t s = ctx->stream;
+  FFA_CUDA(cudaMemcpyAsync(ctx->e.P, sl.P, state_bytes_P(ctx), cudaMemcpyDeviceToDevice, s));
+  FFA_CUDA(cudaMemcpyAsync(ctx->e.Lam, sl.Lam, state_bytes_L(ctx), cudaMemcpyDeviceToDevice, s));
+  FFA_CUDA(cudaMemcpyAsync(ctx->e.U, sl.U, state_bytes_U(ctx), cudaMemcpyDeviceToDevice, s));
+  FFA_CUDA(cudaMemcpyAsync(ctx->X, sl.X, (size_t)ctx->nF * ctx->d * 8, cudaMemcpyDeviceToDevice, s));
+  FFA_CUDA(cudaMemcpyAsync(ctx->Wtmp, sl.W, (size_t)ctx->n * ctx->d * 8, cudaMemcpyDeviceToDevice, s));
+  VertexLaunch V{};
+  V.d = ctx->d;
+  V.fp64 = ctx->fp64;
+  V.n = ctx->n;
+  V.v2e = ctx->v2e;
+  V.v2pin = nullptr;
+  V.pin_pos = ctx->pin_pos;
+  V.W_in = ctx->Wtmp;
+  V.W = ctx->W;
+  V.X = nullptr;
+  V.vrec = ctx->vrec;
+  V.write_dw = 0;
+  launch_vertex_update(V, s);
+  // the next W step reads the right-hand-side terms of the restored state
+  launch_rhs_terms(local_launch(ctx, false, ctx->vrec), s);
+  FFA_CUDA(cudaGetLastError());
+  return FFA_OK;
+}
+
+// vertex records of a stored W into vrec_scratch
+ffa_status records_of(ffa_ctx* ctx, const double* W) {
+  VertexLaunch V{};
+  V.d = ctx->d;
+  V.fp64 = ctx->fp64;
+  V.n = ctx->n;
+  V.v2e = ctx->v2e;
+  V.v2pin = nullptr;
+  V.pin_pos = ctx->pin_pos;
+  V.W_in = W;
+  V.W = ctx->Wtmp2;
+  V.X = nullptr;
+  V.vrec = ctx->vrec_scratch;
   V.write_dw = 0;
   launch_vertex_update(V, ctx->stream);
   FFA_CUDA(cudaGetLastError());
@@ -879,7 +1112,7 @@ ffa_status ffa_energy(ffa_ctx* ctx, const double* W, double* E) {
   if (st != FFA_OK) return st;
   LocalLaunch L = local_launch(ctx, false, ctx->vrec_scratch);
   launch_energy_terms(L, 0, ctx->stream);
-  launch_sum_partials(ctx->local_partials, ctx->n_local_blocks, NQ, ctx->sums_d, ctx->stream);
+  launch_sum_partials(ctx->local_partials, (ctx->m + kLocalBlock - 1) / kLocalBlock, NQ, ctx->sums_d, ctx->stream);
   FFA_CUDA(cudaGetLastError());
   FFA_CUDA(cudaMemcpyAsync(ctx->sums_h, ctx->sums_d, NQ * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -895,7 +1128,7 @@ ffa_status ffa_gradient(ffa_ctx* ctx, const double* W, double* dEdW) {
   if (st != FFA_OK) return st;
   LocalLaunch L = local_launch(ctx, false, ctx->vrec_scratch);
   launch_energy_terms(L, 1, ctx->stream);
-  launch_sum_partials(ctx->local_partials, ctx->n_local_blocks, NQ, ctx->sums_d, ctx->stream);
+  launch_sum_partials(ctx->local_partials, (ctx->m + kLocalBlock - 1) / kLocalBlock, NQ, ctx->sums_d, ctx->stream);
   GatherLaunch G{};
   G.d = ctx->d;
   G.fp64 = ctx->fp64;
@@ -957,6 +1190,200 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out) 
   return FFA_OK;
 }
 
+ffa_status ffa_forward_unrolled(ffa_ctx* ctx, int32_t K, int32_t ckpt_every) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ctx->initialized) return fail(ctx, FFA_ERR_NOT_INITIALIZED, "ffa_init has not been called");
+  if (K < 1 || ckpt_every < 1) return fail(ctx, FFA_ERR_INVALID_ARG, "K and ckpt_every must be >= 1");
+  ffa_status st = ensure_graphs(ctx);
+  if (st != FFA_OK) return st;
+  const int C = std::min(ckpt_every, K);
+  const int nseg = (K + C - 1) / C;
+  while ((int)ctx->ckpt.size() < nseg) {
+    ctx->ckpt.emplace_back();
+    if ((st = alloc_slot(ctx, ctx->ckpt.back())) != FFA_OK) return st;
+  }
+  while ((int)ctx->seg.size() < C + 1) {
+    ctx->seg.emplace_back();
+    if ((st = alloc_slot(ctx, ctx->seg.back())) != FFA_OK) return st;
+  }
+  if (!ctx->final_state.P && (st = alloc_slot(ctx, ctx->final_state)) != FFA_OK) return st;
+  const size_t md = (size_t)ctx->m * ctx->d * ctx->d * ctx->rsz;
+  if (!ctx->Pbar) {
+    if ((st = dalloc_bytes(ctx, &ctx->Pbar, md)) != FFA_OK) return st;
+    if ((st = dalloc_bytes(ctx, &ctx->Lbar, md)) != FFA_OK) return st;
+    if ((st = dalloc_bytes(ctx, &ctx->xi_v, (size_t)ctx->n * ctx->d * ctx->rsz)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->Wbar, (size_t)ctx->n * ctx->d)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->Wloss, (size_t)ctx->n * ctx->d)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->Xadj, (size_t)ctx->nF * ctx->d)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->b_adj, (size_t)ctx->nF * ctx->d)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->bbar, (size_t)ctx->n_pin * ctx->d)) != FFA_OK) return st;
+  }
+  for (int sgi = 0; sgi < nseg; ++sgi) {
+    if ((st = save_slot(ctx, ctx->ckpt[sgi])) != FFA_OK) return st;
+    const int steps = std::min(C, K - sgi * C);
+    for (int j = 0; j < steps; ++j) FFA_CUDA(cudaGraphLaunch(ctx->g_one, ctx->stream));
+  }
+  if ((st = save_slot(ctx, ctx->final_state)) != FFA_OK) return st;
+  FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->iter_total += K;
+  ctx->adj_K = K;
+  ctx->adj_C = C;
+  return FFA_OK;
+}
+
+ffa_status ffa_backward_unrolled(ffa_ctx* ctx, const double* dL_dW, double* dL_db) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->adj_K < 1) return fail(ctx, FFA_ERR_NOT_INITIALIZED, "ffa_forward_unrolled has not been called");
+  if (!dL_dW || !dL_db) return fail(ctx, FFA_ERR_INVALID_ARG, "dL_dW or dL_db is NULL");
+  cudaStream_t s = ctx->stream;
+  const int K = ctx->adj_K, C = ctx->adj_C, d = ctx->d;
+  const size_t md = (size_t)ctx->m * d * d * ctx->rsz;
+  FFA_CUDA(cudaMemcpyAsync(ctx->Wloss, dL_dW, (size_t)ctx->n * d * 8, cudaMemcpyDefault, s));
+  FFA_CUDA(cudaMemsetAsync(ctx->Pbar, 0, md, s));
+  FFA_CUDA(cudaMemsetAsync(ctx->Lbar, 0, md, s));
+  FFA_CUDA(cudaMemsetAsync(ctx->bbar, 0, (size_t)ctx->n_pin * d * 8, s));
+  ffa_status st;
+  bool have_xi = false;
+  const int nseg = (K + C - 1) / C;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int k0 = sgi * C, k1 = std::min(K, k0 + C);
+    // recompute the segment's states from its checkpoint
+    if ((st = load_slot(ctx, ctx->ckpt[sgi])) != FFA_OK) return st;
+    if ((st = save_slot(ctx, ctx->seg[0])) != FFA_OK) return st;
+    for (int j = 1; j <= k1 - k0; ++j) {
+      FFA_CUDA(cudaGraphLaunch(ctx->g_one, s));
+      if ((st = save_slot(ctx, ctx->seg[j])) != FFA_OK) return st;
+    }
+    for (int k = k1; k > k0; --k) {
+      const int j = k - k0;
+      if ((st = records_of(ctx, ctx->seg[j].W)) != FFA_OK) return st;
+      if (have_xi) launch_xi_to_vertices(ctx->n, d, ctx->fp64, ctx->v2e, ctx->Xadj, ctx->xi_v, s);
+      AdjointLaunch a{};
+      a.d = d;
+      a.energy = (int)ctx->prm.energy;
+      a.fp64 = ctx->fp64;
+      a.m = ctx->m;
+      a.e = ctx->e;
+      a.P_prev = ctx->seg[j - 1].P;
+      a.Lam_prev = ctx->seg[j - 1].Lam;
+      a.U_prev = ctx->seg[j - 1].U;
+      a.vrec = ctx->vrec_scratch;
+      a.xi = have_xi ? ctx->xi_v : nullptr;
+      a.Pbar = ctx->Pbar;
+      a.Lbar = ctx->Lbar;
+      a.contribJ = ctx->e.contrib2;
+      launch_adjoint_local(a, s);
+      // W_bar = G^T J_bar (+ the loss gradient at the last iteration)
+      GatherLaunch G{};
+      G.d = d;
+      G.fp64 = ctx->fp64;
+      G.rows = ctx->n;
+      G.row_vertex = nullptr;
+      G.inc_ptr = ctx->inc_ptr;
+      G.inc = ctx->inc;
+      G.contrib = ctx->e.contrib2;
+      G.add = (k == K) ? ctx->Wloss : nullptr;
+      G.out = ctx->Wbar;
+      G.partials = nullptr;
+      launch_gather(G, s);
+      launch_adj_rhs(ctx->nF, ctx->n_pin, d, ctx->row_vertex, ctx->pins_d, ctx->Wbar, ctx->b_adj, ctx->bbar, s);
+      // xi = L_FF^{-1} W_bar_F with the same factor (L is symmetric) and refinement
+      FFA_CUDA(cudaMemsetAsync(ctx->Xadj, 0, (size_t)ctx->nF * d * 8, s));
+      SolveData S = solve_data(ctx);
+      S.X = ctx->Xadj;
+      S.b = ctx->b_adj;
+      for (int sw = 0; sw < ctx->prm.refine_sweeps; ++sw) {
+        if (sw > 0) launch_axpy_correction(S, s);
+        launch_residual(S, nullptr, 0, s);
+        launch_supernodal_solve(S, s);
+      }
+      launch_axpy_correction(S, s);
+      launch_adj_pins(ctx->n_pin, d, ctx->cf_ptr, ctx->cf_row, ctx->cf_val, ctx->Xadj, ctx->bbar, s);
+      FFA_CUDA(cudaGetLastError());
+      have_xi = true;
+    }
+  }
+  // leave the live state at the end of the forward pass
+  if ((st = load_slot(ctx, ctx->final_state)) != FFA_OK) return st;
+  FFA_CUDA(cudaMemcpyAsync(dL_db, ctx->bbar, (size_t)ctx->n_pin * d * 8, cudaMemcpyDefault, s));
+  FFA_CUDA(cudaStreamSynchronize(s));
+  return FFA_OK;
+}
+
+ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ctx->initialized) return fail(ctx, FFA_ERR_NOT_INITIALIZED, "ffa_init has not been called");
+  if (reps < 1) return fail(ctx, FFA_ERR_INVALID_ARG, "reps < 1");
+  ffa_status st;
+  if (!ctx->tune_slot.P && (st = alloc_slot(ctx, ctx->tune_slot)) != FFA_OK) return st;
+  if ((st = save_slot(ctx, ctx->tune_slot)) != FFA_OK) return st;
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t e0, e1;
+  FFA_CUDA(cudaEventCreate(&e0));
+  FFA_CUDA(cudaEventCreate(&e1));
+  ffa_tuning t{};
+  // 1) local step: threads per block
+  const int blocks[3] = {64, 128, 256};
+  double best = 1e300;
+  int best_block = ctx->local_block;
+  for (int c = 0; c < 3; ++c) {
+    ctx->local_block = blocks[c];
+    ctx->n_local_blocks = (ctx->m + blocks[c] - 1) / blocks[c];
+    launch_local_step(local_launch(ctx, false, ctx->vrec), s);  // warm-up
+    FFA_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) launch_local_step(local_launch(ctx, false, ctx->vrec), s);
+    FFA_CUDA(cudaEventRecord(e1, s));
+    FFA_CUDA(cudaEventSynchronize(e1));
+    float ms;
+    FFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    t.ms_local[c] = ms / reps;
+    if (t.ms_local[c] < best) {
+      best = t.ms_local[c];
+      best_block = blocks[c];
+    }
+  }
+  ctx->local_block = best_block;
+  ctx->n_local_blocks = (ctx->m + best_block - 1) / best_block;
+  // 2) supernodal solves: which nodes take the narrow (warp per node) path
+  const int narrows[2] = {32, 64};
+  best = 1e300;
+  int best_narrow = ctx->narrow_cols;
+  for (int c = 0; c < 2; ++c) {
+    ctx->narrow_cols = narrows[c];
+    if ((st = build_tasks(ctx)) != FFA_OK) return st;
+    SolveData S = solve_data(ctx);
+    launch_supernodal_solve(S, s);
+    FFA_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) launch_supernodal_solve(S, s);
+    FFA_CUDA(cudaEventRecord(e1, s));
+    FFA_CUDA(cudaEventSynchronize(e1));
+    float ms;
+    FFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    t.ms_solve[c] = ms / reps;
+    if (t.ms_solve[c] < best) {
+      best = t.ms_solve[c];
+      best_narrow = narrows[c];
+    }
+  }
+  ctx->narrow_cols = best_narrow;
+  if ((st = build_tasks(ctx)) != FFA_OK) return st;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the graphs captured the old launch shapes
+  if (ctx->g_batch) { cudaGraphExecDestroy(ctx->g_batch); ctx->g_batch = nullptr; }
+  if (ctx->g_one) { cudaGraphExecDestroy(ctx->g_one); ctx->g_one = nullptr; }
+  if (ctx->g_one_check) { cudaGraphExecDestroy(ctx->g_one_check); ctx->g_one_check = nullptr; }
+  if ((st = load_slot(ctx, ctx->tune_slot)) != FFA_OK) return st;
+  FFA_CUDA(cudaStreamSynchronize(s));
+  t.local_block = ctx->local_block;
+  t.narrow_cols = ctx->narrow_cols;
+  if (out) *out = t;
+  return FFA_OK;
+}
+
 ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel) {
   if (!ctx || !rel) return FFA_ERR_INVALID_ARG;
   ctx->err.clear();
@@ -967,6 +1394,325 @@ ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel) {
   FFA_CUDA(cudaMemcpyAsync(ctx->sums_h, ctx->sums_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   *rel = ctx->sums_h[1] > 0 ? std::sqrt(ctx->sums_h[0] / ctx->sums_h[1]) : std::sqrt(ctx->sums_h[0]);
+  return FFA_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// batched meshes
+// ===========================================================================
+namespace {
+
+#define FFA_BCUDA(call)                                                                 \
+  do {                                                                                  \
+    cudaError_t _e = (call);                                                            \
+    if (_e != cudaSuccess) {                                                            \
+      b->err = std::string(#call) + ": " + cudaGetErrorString(_e);                     \
+      return FFA_ERR_CUDA;                                                              \
+    }                                                                                   \
+  } while (0)
+
+ffa_status batch_capture(ffa_batch* b, int n_iter, bool check_last, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  FFA_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < n_iter; ++k)
+    for (ffa_ctx* c : b->groups) enqueue_iteration(c, check_last && k == n_iter - 1);
+  cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  if (e != cudaSuccess) {
+    b->err = std::string("graph capture: ") + cudaGetErrorString(e);
+    return FFA_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+    return FFA_ERR_CUDA;
+  }
+  return FFA_OK;
+}
+
+void batch_destroy_impl(ffa_batch* b) {
+  if (b->g_batch) cudaGraphExecDestroy(b->g_batch);
+  if (b->g_one) cudaGraphExecDestroy(b->g_one);
+  if (b->g_one_check) cudaGraphExecDestroy(b->g_one_check);
+  for (ffa_ctx* c : b->groups) {
+    destroy_impl(c);
+    delete c;
+  }
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+ffa_status batch_create_impl(ffa_batch* b, int32_t n_meshes, const ffa_mesh* meshes, const int32_t* const* pin_idx,
+                             const int32_t* n_pin, const double* const* pin_pos, const ffa_energy_kind* energies,
+                             const double* rho, const ffa_params* params, void* stream) {
+  if (n_meshes < 1 || !meshes) {
+    b->err = "need at least one mesh";
+    return FFA_ERR_INVALID_ARG;
+  }
+  ffa_params prm;
+  ffa_default_params(&prm);
+  if (params) prm = *params;
+  b->check_every = prm.check_every;
+  b->n_mesh = n_meshes;
+  if (stream) {
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+  } else {
+    FFA_BCUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  // group the meshes by (d, d_in)
+  std::vector<std::pair<int, int>> keys;
+  b->mesh_group.assign(n_meshes, -1);
+  b->mesh_local.assign(n_meshes, -1);
+  b->mesh_voff.assign(n_meshes, 0);
+  b->mesh_n.assign(n_meshes, 0);
+  b->mesh_dim.assign(n_meshes, 0);
+  for (int k = 0; k < n_meshes; ++k) {
+    const ffa_mesh& mk = meshes[k];
+    if ((mk.d != 2 && mk.d != 3) || mk.d_in < mk.d || mk.d_in > 3 || mk.n < mk.d + 1 || mk.m < 1 || !mk.V || !mk.T) {
+      b->err = "mesh " + std::to_string(k) + ": invalid sizes or pointers";
+      return FFA_ERR_INVALID_ARG;
+    }
+    const std::pair<int, int> key{mk.d, mk.d_in};
+    auto it = std::find(keys.begin(), keys.end(), key);
+    if (it == keys.end()) {
+      keys.push_back(key);
+      it = keys.end() - 1;
+    }
+    b->mesh_group[k] = (int)(it - keys.begin());
+    b->mesh_n[k] = mk.n;
+    b->mesh_dim[k] = mk.d;
+  }
+  for (size_t gi = 0; gi < keys.size(); ++gi) {
+    const int d = keys[gi].first, d_in = keys[gi].second;
+    std::vector<double> V;
+    std::vector<int32_t> T, pins;
+    std::vector<double> pos;
+    BatchSpec spec;
+    int64_t n_tot = 0, m_tot = 0;
+    double xoff = 0.0;
+    int local = 0;
+    for (int k = 0; k < n_meshes; ++k) {
+      if (b->mesh_group[k] != (int)gi) continue;
+      const ffa_mesh& mk = meshes[k];
+      std::vector<double> Vk((size_t)mk.n * d_in);
+      std::vector<int32_t> Tk((size_t)mk.m * (d + 1));
+      FFA_BCUDA(cudaMemcpy(Vk.data(), mk.V, Vk.size() * 8, cudaMemcpyDefault));
+      FFA_BCUDA(cudaMemcpy(Tk.data(), mk.T, Tk.size() * 4, cudaMemcpyDefault));
+      // shift the source along x so that the meshes do not overlap (the nested
+      // dissection then separates them first); gradients and areas do not change
+      double lo = 1e300, hi = -1e300;
+      for (int v = 0; v < mk.n; ++v) {
+        lo = std::min(lo, Vk[(size_t)v * d_in]);
+        hi = std::max(hi, Vk[(size_t)v * d_in]);
+      }
+      const double shift = xoff - lo;
+      for (int v = 0; v < mk.n; ++v) Vk[(size_t)v * d_in] += shift;
+      xoff += (hi - lo) * 1.5 + 1.0;
+      for (int32_t t : Tk) {
+        if (t < 0 || t >= mk.n) {
+          b->err = "mesh " + std::to_string(k) + ": element index out of range";
+          return FFA_ERR_INVALID_ARG;
+        }
+      }
+      for (auto& t : Tk) t += (int32_t)n_tot;
+      V.insert(V.end(), Vk.begin(), Vk.end());
+      T.insert(T.end(), Tk.begin(), Tk.end());
+      const int np = n_pin ? n_pin[k] : 0;
+      if (np > 0) {
+        std::vector<int32_t> pk(np);
+        std::vector<double> bk((size_t)np * d);
+        FFA_BCUDA(cudaMemcpy(pk.data(), pin_idx[k], pk.size() * 4, cudaMemcpyDefault));
+        FFA_BCUDA(cudaMemcpy(bk.data(), pin_pos[k], bk.size() * 8, cudaMemcpyDefault));
+        for (int32_t p : pk) {
+          if (p < 0 || p >= mk.n) {
+            b->err = "mesh " + std::to_string(k) + ": pin index out of range";
+            return FFA_ERR_INVALID_ARG;
+          }
+          pins.push_back(p + (int32_t)n_tot);
+        }
+        pos.insert(pos.end(), bk.begin(), bk.end());
+      } else {
+        pins.push_back((int32_t)n_tot);       // vertex 0 of this mesh at the origin
+        for (int c = 0; c < d; ++c) pos.push_back(0.0);
+      }
+      const int8_t en = energies ? (int8_t)energies[k] : (int8_t)prm.energy;
+      const double rk = rho ? rho[k] : prm.rho;
+      for (int i = 0; i < mk.m; ++i) {
+        spec.energy_of.push_back(en);
+        spec.rho_of.push_back(rk);
+        spec.mesh_of_elem.push_back(local);
+      }
+      for (int v = 0; v < mk.n; ++v) spec.mesh_of_vertex.push_back(local);
+      spec.mesh_d.push_back(d);
+      spec.mesh_m.push_back(mk.m);
+      spec.mesh_eps.push_back(prm.eps_abs);
+      spec.mesh_eps.push_back(prm.eps_rel);
+      b->mesh_local[k] = local++;
+      b->mesh_voff[k] = n_tot;
+      n_tot += mk.n;
+      m_tot += mk.m;
+    }
+    if (n_tot >= INT32_MAX || m_tot * (d + 1) >= INT32_MAX) {
+      b->err = "batch group too large for int32 indices";
+      return FFA_ERR_INVALID_ARG;
+    }
+    ffa_mesh gm{(int32_t)n_tot, (int32_t)m_tot, d, d_in, V.data(), T.data()};
+    ffa_ctx* c = new ffa_ctx();
+    b->groups.push_back(c);
+    ffa_params gp = prm;
+    ffa_status st = create_impl(c, &gm, pins.data(), (int32_t)pins.size(), pos.data(), &gp, b->stream, &spec);
+    if (st != FFA_OK) {
+      b->err = c->err;
+      return st;
+    }
+  }
+  b->host_stats.assign(n_meshes, ffa_stats{});
+  return FFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ffa_status ffa_batch_create(int32_t n_meshes, const ffa_mesh* meshes, const int32_t* const* pin_idx,
+                            const int32_t* n_pin, const double* const* pin_pos, const ffa_energy_kind* energies,
+                            const double* rho, const ffa_params* params, void* stream, ffa_batch** out) {
+  if (!out) return FFA_ERR_INVALID_ARG;
+  *out = nullptr;
+  ffa_batch* b = new (std::nothrow) ffa_batch();
+  if (!b) return FFA_ERR_OOM;
+  ffa_status st;
+  try {
+    st = batch_create_impl(b, n_meshes, meshes, pin_idx, n_pin, pin_pos, energies, rho, params, stream);
+  } catch (const std::bad_alloc&) {
+    st = FFA_ERR_OOM;
+  } catch (...) {
+    st = FFA_ERR_INVALID_ARG;
+  }
+  if (st != FFA_OK) {
+    g_create_error = b->err.empty() ? "ffa_batch_create failed" : b->err;
+    batch_destroy_impl(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return FFA_OK;
+}
+
+void ffa_batch_destroy(ffa_batch* b) {
+  if (!b) return;
+  batch_destroy_impl(b);
+  delete b;
+}
+
+const char* ffa_batch_last_error(const ffa_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+ffa_status ffa_batch_init(ffa_batch* b, const double* const* W0) {
+  if (!b || !W0) return FFA_ERR_INVALID_ARG;
+  b->err.clear();
+  for (int k = 0; k < b->n_mesh; ++k) {
+    ffa_ctx* c = b->groups[b->mesh_group[k]];
+    FFA_BCUDA(cudaMemcpyAsync(c->Wtmp2 + b->mesh_voff[k] * c->d, W0[k], (size_t)b->mesh_n[k] * c->d * 8,
+                              cudaMemcpyDefault, b->stream));
+  }
+  for (ffa_ctx* c : b->groups) {
+    ffa_status st = load_W_records(c, c->Wtmp2, true, c->W, c->vrec);
+    if (st != FFA_OK) {
+      b->err = c->err;
+      return st;
+    }
+    launch_init_polar(local_launch(c, false, c->vrec), b->stream);
+    c->initialized = true;
+    c->iter_total = 0;
+  }
+  FFA_BCUDA(cudaGetLastError());
+  FFA_BCUDA(cudaStreamSynchronize(b->stream));
+  b->initialized = true;
+  return FFA_OK;
+}
+
+ffa_status ffa_batch_iterate(ffa_batch* b, int32_t max_iter, int32_t stop_at_tol, ffa_stats* stats,
+                             int32_t* n_converged) {
+  if (!b) return FFA_ERR_INVALID_ARG;
+  b->err.clear();
+  if (!b->initialized) {
+    b->err = "ffa_batch_init has not been called";
+    return FFA_ERR_NOT_INITIALIZED;
+  }
+  if (max_iter < 0) {
+    b->err = "max_iter < 0";
+    return FFA_ERR_INVALID_ARG;
+  }
+  ffa_status st;
+  if (!b->g_batch && (st = batch_capture(b, b->check_every, true, &b->g_batch)) != FFA_OK) return st;
+  if (!b->g_one && (st = batch_capture(b, 1, false, &b->g_one)) != FFA_OK) return st;
+  if (!b->g_one_check && (st = batch_capture(b, 1, true, &b->g_one_check)) != FFA_OK) return st;
+  const int ce = b->check_every;
+  int done = 0, conv = 0;
+  std::vector<int32_t> nconv(b->groups.size(), 0);
+  while (done < max_iter) {
+    const int left = max_iter - done;
+    if (left >= ce) {
+      FFA_BCUDA(cudaGraphLaunch(b->g_batch, b->stream));
+      done += ce;
+    } else {
+      for (int k = 0; k < left - 1; ++k) FFA_BCUDA(cudaGraphLaunch(b->g_one, b->stream));
+      FFA_BCUDA(cudaGraphLaunch(b->g_one_check, b->stream));
+      done += left;
+    }
+    if (stop_at_tol || done == max_iter) {
+      for (size_t gi = 0; gi < b->groups.size(); ++gi)
+        FFA_BCUDA(cudaMemcpyAsync(&nconv[gi], b->groups[gi]->n_converged, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  b->stream));
+      FFA_BCUDA(cudaStreamSynchronize(b->stream));
+      conv = 0;
+      for (int32_t x : nconv) conv += x;
+      if (stop_at_tol && conv == b->n_mesh) break;
+    }
+  }
+  for (ffa_ctx* c : b->groups) c->iter_total += done;
+  if (stats) {
+    for (int k = 0; k < b->n_mesh; ++k) {
+      ffa_ctx* c = b->groups[b->mesh_group[k]];
+      FFA_BCUDA(cudaMemcpy(&b->host_stats[k], c->mesh_stats + b->mesh_local[k], sizeof(ffa_stats),
+                           cudaMemcpyDeviceToHost));
+      b->host_stats[k].iters = done;
+      b->host_stats[k].checked_iter = (int32_t)c->iter_total;
+      stats[k] = b->host_stats[k];
+    }
+  }
+  if (n_converged) *n_converged = conv;
+  return FFA_OK;
+}
+
+ffa_status ffa_batch_autotune(ffa_batch* b, int32_t reps, ffa_tuning* out) {
+  if (!b) return FFA_ERR_INVALID_ARG;
+  b->err.clear();
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    ffa_tuning t{};
+    ffa_status st = ffa_autotune(b->groups[gi], reps, &t);
+    if (st != FFA_OK) {
+      b->err = b->groups[gi]->err;
+      return st;
+    }
+    if (out) out[gi] = t;
+  }
+  if (b->g_batch) { cudaGraphExecDestroy(b->g_batch); b->g_batch = nullptr; }
+  if (b->g_one) { cudaGraphExecDestroy(b->g_one); b->g_one = nullptr; }
+  if (b->g_one_check) { cudaGraphExecDestroy(b->g_one_check); b->g_one_check = nullptr; }
+  return FFA_OK;
+}
+
+int32_t ffa_batch_groups(const ffa_batch* b) { return b ? (int32_t)b->groups.size() : 0; }
+
+ffa_status ffa_batch_get_W(ffa_batch* b, int32_t mesh, double* W_out) {
+  if (!b || !W_out || mesh < 0 || mesh >= b->n_mesh) return FFA_ERR_INVALID_ARG;
+  ffa_ctx* c = b->groups[b->mesh_group[mesh]];
+  FFA_BCUDA(cudaMemcpyAsync(W_out, c->W + b->mesh_voff[mesh] * c->d, (size_t)b->mesh_n[mesh] * c->d * 8,
+                            cudaMemcpyDefault, b->stream));
+  FFA_BCUDA(cudaStreamSynchronize(b->stream));
   return FFA_OK;
 }
 

@@ -46,11 +46,16 @@ struct ElemBufs {
   void* U = nullptr;       // 2 x m (cos, sin) for d = 2, 4 x m quaternion for d = 3
   void* contrib = nullptr;   // m x (d+1) x d : g_j . r_i  (W-step right-hand side terms)
   void* contrib2 = nullptr;  // m x (d+1) x d : g_j . Lambda_i (check iterations) / energy gradient
+  // batched meshes (null for a single mesh)
+  const int8_t* energy_of = nullptr;   // m: 0 = SD, 1 = SG (kernels instantiated with EN = 2)
+  const int32_t* mesh_of = nullptr;    // m: mesh of each element
+  double* mesh_acc = nullptr;          // n_mesh x (NQ + 1) per-mesh sums of the check quantities
 };
 
 struct LocalLaunch {
   int d, energy, fp64, check;
   int m;
+  int block;          // threads per block of the local step (64, 128 or 256; 0 = 128)
   ElemBufs e;
   const void* vrec;   // vertex records
   double* partials;   // [blocks][NQ]
@@ -59,6 +64,8 @@ struct LocalLaunch {
 
 void launch_local_step(const LocalLaunch& L, cudaStream_t s);
 void launch_init_polar(const LocalLaunch& L, cudaStream_t s);
+// W-step right-hand-side terms from the stored U, P, Lambda (after a state restore)
+void launch_rhs_terms(const LocalLaunch& L, cudaStream_t s);
 // energy (mode 0: sum w f(J) + flips into partials) or gradient terms (mode 1: contrib2)
 void launch_energy_terms(const LocalLaunch& L, int mode, cudaStream_t s);
 
@@ -89,6 +96,8 @@ struct GatherLaunch {
   const double* add;         // optional row-aligned addend (rows x d)
   double* out;               // rows x d
   double* partials;          // optional: sum of squares of out per block (QV_GTL)
+  const int32_t* mesh_of;    // optional (batched meshes): mesh of each row's vertex
+  double* mesh_acc;          // with mesh_of: sums of squares go to mesh_acc[mesh * (NQ + 1) + NQ]
 };
 void launch_gather(const GatherLaunch& G, cudaStream_t s);
 
@@ -104,6 +113,7 @@ struct SolveData {
   const Task* fwd_tasks;
   const Task* bwd_tasks;
   std::vector<int64_t> fwd_off, bwd_off;  // per level task ranges (host)
+  std::vector<int64_t> fwd_wide, bwd_wide; // per level: leading wide tasks (rest: narrow, padded to 8)
   float* y;                  // nF x d residual / forward work vector
   float* z;                  // nF x d forward result
   float* x;                  // nF x d correction
@@ -131,7 +141,40 @@ struct FinalLaunch {
   double* scratch;   // NQ + 1 doubles
 };
 void launch_final_reduce(const FinalLaunch& F, cudaStream_t s);
+// per-mesh statistics of batched meshes from mesh_acc (one thread per mesh)
+struct MeshStatsLaunch {
+  int n_mesh;
+  const double* mesh_acc;     // n_mesh x (NQ + 1)
+  const int32_t* mesh_d;      // element dimension of each mesh
+  const int32_t* mesh_m;      // elements of each mesh
+  const double* mesh_eps;     // n_mesh x 2 (eps_abs, eps_rel)
+  int require_flip_free;
+  ffa_stats* out;             // n_mesh
+  int32_t* n_converged;       // incremented per converged mesh (zeroed by the caller)
+};
+void launch_mesh_stats(const MeshStatsLaunch& M, cudaStream_t s);
 void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s);
+
+// adjoint of one unrolled iteration, per element (ffa_adjoint.cu)
+struct AdjointLaunch {
+  int d, energy, fp64, m;
+  ElemBufs e;            // idx, g, w, mu
+  const void* P_prev;    // state_{k-1}: P (d(d+1)/2 x m), Lambda (d*d x m), U (2 or 4 x m)
+  const void* Lam_prev;
+  const void* U_prev;
+  const void* vrec;      // vertex records of W^k
+  const void* xi;        // xi^{k+1} per vertex (n x d, Real; zero at pins) or null
+  void* Pbar;            // d*d x m, in: adjoint of P^k, out: adjoint of P^{k-1}
+  void* Lbar;            // d*d x m, same for Lambda
+  void* contribJ;        // m x (d+1) x d: g_j . J_bar
+};
+void launch_adjoint_local(const AdjointLaunch& a, cudaStream_t s);
+void launch_xi_to_vertices(int n, int d, int fp64, const int32_t* v2e, const double* xi_e, void* xi_v,
+                           cudaStream_t s);
+void launch_adj_rhs(int nF, int n_pin, int d, const int32_t* row_vertex, const int32_t* pins, const double* Wbar,
+                    double* b_adj, double* bbar, cudaStream_t s);
+void launch_adj_pins(int n_pin, int d, const int64_t* ptr, const int32_t* row, const double* val, const double* xi,
+                     double* bbar, cudaStream_t s);
 
 // message returned by ffa_last_error(NULL) on the calling thread
 void set_thread_error(const std::string& msg);

@@ -119,7 +119,7 @@ __device__ __forceinline__ void store_terms(void* dst, int i, const R g[D][D], c
 // ---------------------------------------------------------------------------
 template <typename R, int N>
 __device__ __forceinline__ void block_reduce(R v[N], double* out) {
-  __shared__ double red[kLocalBlock / 32][N];
+  __shared__ double red[8][N];   // up to 256 threads
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < N; ++q) {
@@ -144,7 +144,7 @@ __device__ __forceinline__ void block_reduce(R v[N], double* out) {
   if (threadIdx.x < N) {
     double s = 0.0;
 #pragma unroll
-    for (int wv = 0; wv < kLocalBlock / 32; ++wv) s += red[wv][threadIdx.x];
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += red[wv][threadIdx.x];
     out[(int64_t)blockIdx.x * N + threadIdx.x] = s;
   }
 }
@@ -152,13 +152,49 @@ __device__ __forceinline__ void block_reduce(R v[N], double* out) {
 template <typename R>
 __device__ __forceinline__ bool finite_(R x) { return isfinite(x); }
 
+// batched meshes: per-mesh sums of the check quantities.  A warp whose elements
+// all belong to one mesh reduces first (double-float for float values) and adds
+// once per quantity; otherwise every lane adds its own values.
+template <typename R>
+__device__ __forceinline__ void mesh_reduce(const R v[NQ], const ElemBufs& e, int m, int i) {
+  const int mesh = (i < m) ? e.mesh_of[i] : -1;
+  const int m0 = __shfl_sync(0xffffffffu, mesh, 0);
+  const bool uniform = __all_sync(0xffffffffu, mesh == m0);
+  const int lane = threadIdx.x & 31;
+  if (uniform) {
+    if (m0 < 0) return;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double tot;
+      if constexpr (sizeof(R) == 4) {
+        FF a{v[q], 0.0f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+          a = ff_add(a, b);
+        }
+        tot = (double)a.hi + (double)a.lo;
+      } else {
+        double a = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        tot = a;
+      }
+      if (lane == 0) atomicAdd(e.mesh_acc + (int64_t)m0 * (NQ + 1) + q, tot);
+    }
+  } else if (mesh >= 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) atomicAdd(e.mesh_acc + (int64_t)mesh * (NQ + 1) + q, (double)v[q]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // the fused local step
 // ---------------------------------------------------------------------------
 template <int D, typename R, int EN, bool CHECK>
-__global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, const void* __restrict__ vrec,
-                                                            double* __restrict__ partials) {
-  const int i = blockIdx.x * kLocalBlock + threadIdx.x;
+__global__ void __launch_bounds__(256) k_local_step(ElemBufs e, int m, const void* __restrict__ vrec,
+                                                    double* __restrict__ partials) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   R qv[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) qv[q] = R(0);
@@ -166,6 +202,7 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
     int vid[D + 1];
     R g[D][D], w, mu;
     load_element<D, R>(e, m, i, vid, g, w, mu);
+    const int en = (EN == 2) ? (int)e.energy_of[i] : EN;
     R J[D][D], dJ[D][D];
     element_jacobians<D, R>(vid, g, vrec, J, dJ);
     R* Pp = reinterpret_cast<R*>(e.P);
@@ -216,9 +253,11 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
       R cond;
       nearest_rotation3<R>(Q, U, cond);
       if constexpr (sizeof(R) == 4) {
-        // the rotation is ill-conditioned when s_mid + s_min is tiny against s_max:
-        // redo it in double for those few elements
-        if (cond < R(1e-3)) {
+        // When s_mid + s_min is tiny against s_max the rotation is ill-determined.
+        // Q itself carries float rounding, so double cannot add accuracy there;
+        // only the (near-)degenerate cases are redone in double, so that the
+        // orthonormal frame is built from well-separated columns.
+        if (cond < R(1e-5)) {
           double Qd[3][3], Ud[3][3], cd;
 #pragma unroll
           for (int a = 0; a < 3; ++a)
@@ -252,8 +291,8 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
       const R s00 = S[0][0], s11 = S[1][1], s01 = R(0.5) * (S[0][1] + S[1][0]);
       const R mean = R(0.5) * (s00 + s11), dl = R(0.5) * (s00 - s11);
       const R rr = Tr<R>::sqrt_(dl * dl + s01 * s01);
-      p[0] = prox_root<R, EN>(mean + rr, w, mu);
-      p[1] = prox_root<R, EN>(mean - rr, w, mu);
+      p[0] = prox_root_en<R, EN>(mean + rr, w, mu, en);
+      p[1] = prox_root_en<R, EN>(mean - rr, w, mu, en);
       if (p[0] * p[1] < R(kSqrtEpsM) || p[0] + p[1] < R(kSqrtEpsM)) {
         p[0] = fmax(p[0], R(kSqrtEpsM));
         p[1] = fmax(p[1], R(kSqrtEpsM));
@@ -268,7 +307,7 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
       sym3_eig<R>(S[0][0], R(0.5) * (S[0][1] + S[1][0]), R(0.5) * (S[0][2] + S[2][0]), S[1][1],
                   R(0.5) * (S[1][2] + S[2][1]), S[2][2], ev, E);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) p[j] = prox_root<R, EN>(ev[j], w, mu);
+      for (int j = 0; j < 3; ++j) p[j] = prox_root_en<R, EN>(ev[j], w, mu, en);
       if (p[0] * p[1] * p[2] < R(kSqrtEpsM) || p[0] + p[1] + p[2] < R(kSqrtEpsM)) {
 #pragma unroll
         for (int j = 0; j < 3; ++j) p[j] = fmax(p[j], R(kSqrtEpsM));
@@ -328,12 +367,15 @@ __global__ void __launch_bounds__(kLocalBlock) k_local_step(ElemBufs e, int m, c
       qv[Q_EDUAL] = mu * mu * ed;
       qv[Q_GW] = gw;
       qv[Q_P] = pp;
-      qv[Q_ENERGY] = w * f_of_eigs<R, EN, D>(p);
+      qv[Q_ENERGY] = w * f_of_eigs_en<R, EN, D>(p, en);
       qv[Q_FLIPS] = (det <= R(0)) ? R(1) : R(0);
       qv[Q_NONFINITE] = (finite_(ep) && finite_(pp) && finite_(gw)) ? R(0) : R(1);
     }
   }
-  if constexpr (CHECK) block_reduce<R, NQ>(qv, partials);
+  if constexpr (CHECK) {
+    if (e.mesh_of) mesh_reduce<R>(qv, e, m, i);
+    else block_reduce<R, NQ>(qv, partials);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -348,7 +390,8 @@ __global__ void __launch_bounds__(kLocalBlock) k_init_polar(ElemBufs e, int m, c
   load_element<D, R>(e, m, i, vid, g, w, mu);
   R J[D][D], dJ[D][D];
   element_jacobians<D, R>(vid, g, vrec, J, dJ);
-  const R eps = (EN == 0) ? R(kEpsInitSD) : R(kEpsInitSG);
+  const int en = (EN == 2) ? (int)e.energy_of[i] : EN;
+  const R eps = (en == 0) ? R(kEpsInitSD) : R(kEpsInitSG);
   R U[D][D], P[D][D];
   R* Up = reinterpret_cast<R*>(e.U);
   if constexpr (D == 2) {
@@ -490,13 +533,15 @@ __global__ void __launch_bounds__(kLocalBlock) k_energy_terms(ElemBufs e, int m,
           fro = fma(J[a][k], J[a][k], fro);
           fri = fma(Ji[a][k], Ji[a][k], fri);
         }
-      const R f = (EN == 0) ? R(0.5) * (fro + fri) : R(0.5) * fro - Tr<R>::log_(det);
+      const int en = (EN == 2) ? (int)e.energy_of[i] : EN;
+      const R f = (en == 0) ? R(0.5) * (fro + fri) : R(0.5) * fro - Tr<R>::log_(det);
       qv[Q_ENERGY] = flipped ? R(0) : w * f;
       qv[Q_FLIPS] = flipped ? R(1) : R(0);
     } else {
       // grad f_SG = J - J^-T ; grad f_SD = J - J^-T J^-1 J^-T
       R Gr[D][D];
-      if constexpr (EN == 1) {
+      const int en = (EN == 2) ? (int)e.energy_of[i] : EN;
+      if (en == 1) {
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -529,35 +574,84 @@ __global__ void __launch_bounds__(kLocalBlock) k_energy_terms(ElemBufs e, int m,
   block_reduce<R, NQ>(qv, partials);
 }
 
+// ---------------------------------------------------------------------------
+// W-step right-hand-side terms g_j . r_i, r_i = mu_i (U_i P_i - Lambda_i)
+// (eq. solvinginw), from a stored state (used when a checkpoint is restored)
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(kLocalBlock) k_rhs_terms(ElemBufs e, int m) {
+  const int i = blockIdx.x * kLocalBlock + threadIdx.x;
+  if (i >= m) return;
+  int vid[D + 1];
+  R g[D][D], w, mu;
+  load_element<D, R>(e, m, i, vid, g, w, mu);
+  const R* Pp = reinterpret_cast<const R*>(e.P);
+  const R* Lp = reinterpret_cast<const R*>(e.Lam);
+  const R* Up = reinterpret_cast<const R*>(e.U);
+  R P[D][D], U[D][D];
+  if constexpr (D == 2) {
+    P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[1][1] = Pp[2 * (int64_t)m + i];
+    const R c = Up[i], s = Up[(int64_t)m + i];
+    U[0][0] = c; U[0][1] = -s; U[1][0] = s; U[1][1] = c;
+  } else {
+    P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[0][2] = P[2][0] = Pp[2 * (int64_t)m + i];
+    P[1][1] = Pp[3 * (int64_t)m + i]; P[1][2] = P[2][1] = Pp[4 * (int64_t)m + i]; P[2][2] = Pp[5 * (int64_t)m + i];
+    R qt[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qt[k] = Up[(int64_t)k * m + i];
+    quat_to_rot<R>(qt, U);
+  }
+  R Rhs[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      R s = R(0);
+#pragma unroll
+      for (int l = 0; l < D; ++l) s = fma(U[a][l], P[l][k], s);
+      Rhs[a][k] = mu * (s - Lp[(int64_t)(a * D + k) * m + i]);
+    }
+  store_terms<D, R>(e.contrib, i, g, Rhs);
+}
+
 template <int D, typename R, int EN>
 void dispatch_local(const LocalLaunch& L, cudaStream_t s) {
-  const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
-  if (L.check) k_local_step<D, R, EN, true><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials);
-  else k_local_step<D, R, EN, false><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+  const int bs = L.block > 0 ? L.block : kLocalBlock;
+  const int grid = (L.m + bs - 1) / bs;
+  if (L.check) k_local_step<D, R, EN, true><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+  else k_local_step<D, R, EN, false><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
 }
 
 }  // namespace
 
 void launch_local_step(const LocalLaunch& L, cudaStream_t s) {
+#define FFA_LS(D, R) \
+  do { if (L.energy == 0) dispatch_local<D, R, 0>(L, s); else if (L.energy == 1) dispatch_local<D, R, 1>(L, s); \
+       else dispatch_local<D, R, 2>(L, s); } while (0)
+  if (L.d == 2) { if (L.fp64) FFA_LS(2, double); else FFA_LS(2, float); }
+  else { if (L.fp64) FFA_LS(3, double); else FFA_LS(3, float); }
+#undef FFA_LS
+}
+
+void launch_rhs_terms(const LocalLaunch& L, cudaStream_t s) {
+  const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
   if (L.d == 2) {
-    if (L.fp64) { if (L.energy == 0) dispatch_local<2, double, 0>(L, s); else dispatch_local<2, double, 1>(L, s); }
-    else { if (L.energy == 0) dispatch_local<2, float, 0>(L, s); else dispatch_local<2, float, 1>(L, s); }
+    if (L.fp64) k_rhs_terms<2, double><<<grid, kLocalBlock, 0, s>>>(L.e, L.m);
+    else k_rhs_terms<2, float><<<grid, kLocalBlock, 0, s>>>(L.e, L.m);
   } else {
-    if (L.fp64) { if (L.energy == 0) dispatch_local<3, double, 0>(L, s); else dispatch_local<3, double, 1>(L, s); }
-    else { if (L.energy == 0) dispatch_local<3, float, 0>(L, s); else dispatch_local<3, float, 1>(L, s); }
+    if (L.fp64) k_rhs_terms<3, double><<<grid, kLocalBlock, 0, s>>>(L.e, L.m);
+    else k_rhs_terms<3, float><<<grid, kLocalBlock, 0, s>>>(L.e, L.m);
   }
 }
 
 void launch_init_polar(const LocalLaunch& L, cudaStream_t s) {
   const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
-#define FFA_INIT(D, R, EN) k_init_polar<D, R, EN><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec)
-  if (L.d == 2) {
-    if (L.fp64) { if (L.energy == 0) FFA_INIT(2, double, 0); else FFA_INIT(2, double, 1); }
-    else { if (L.energy == 0) FFA_INIT(2, float, 0); else FFA_INIT(2, float, 1); }
-  } else {
-    if (L.fp64) { if (L.energy == 0) FFA_INIT(3, double, 0); else FFA_INIT(3, double, 1); }
-    else { if (L.energy == 0) FFA_INIT(3, float, 0); else FFA_INIT(3, float, 1); }
-  }
+#define FFA_INIT(D, R) \
+  do { if (L.energy == 0) k_init_polar<D, R, 0><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); \
+       else if (L.energy == 1) k_init_polar<D, R, 1><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); \
+       else k_init_polar<D, R, 2><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); } while (0)
+  if (L.d == 2) { if (L.fp64) FFA_INIT(2, double); else FFA_INIT(2, float); }
+  else { if (L.fp64) FFA_INIT(3, double); else FFA_INIT(3, float); }
 #undef FFA_INIT
 }
 
@@ -568,13 +662,11 @@ void launch_energy_terms(const LocalLaunch& L, int mode, cudaStream_t s) {
     if (mode == 0) k_energy_terms<D, R, EN, 0><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials); \
     else k_energy_terms<D, R, EN, 1><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials);           \
   } while (0)
-  if (L.d == 2) {
-    if (L.fp64) { if (L.energy == 0) FFA_EN(2, double, 0); else FFA_EN(2, double, 1); }
-    else { if (L.energy == 0) FFA_EN(2, float, 0); else FFA_EN(2, float, 1); }
-  } else {
-    if (L.fp64) { if (L.energy == 0) FFA_EN(3, double, 0); else FFA_EN(3, double, 1); }
-    else { if (L.energy == 0) FFA_EN(3, float, 0); else FFA_EN(3, float, 1); }
-  }
+#define FFA_EN3(D, R) \
+  do { if (L.energy == 0) FFA_EN(D, R, 0); else if (L.energy == 1) FFA_EN(D, R, 1); else FFA_EN(D, R, 2); } while (0)
+  if (L.d == 2) { if (L.fp64) FFA_EN3(2, double); else FFA_EN3(2, float); }
+  else { if (L.fp64) FFA_EN3(3, double); else FFA_EN3(3, float); }
+#undef FFA_EN3
 #undef FFA_EN
 }
 

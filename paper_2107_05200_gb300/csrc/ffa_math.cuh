@@ -92,6 +92,13 @@ __device__ __forceinline__ R prox_root(R q, R w, R mu) {
   return ENERGY == 0 ? prox_root_sd<R>(q, w, mu) : prox_root_sg<R>(q, w, mu);
 }
 
+// EN = 0 / 1: one energy for all elements; EN = 2: per element (en = 0 SD, 1 SG)
+template <typename R, int EN>
+__device__ __forceinline__ R prox_root_en(R q, R w, R mu, int en) {
+  if constexpr (EN == 2) return en == 0 ? prox_root_sd<R>(q, w, mu) : prox_root_sg<R>(q, w, mu);
+  else return prox_root<R, EN>(q, w, mu);
+}
+
 // f on an SPD matrix with eigenvalues p: SD (sum p^2 + sum p^-2)/2, SG sum p^2/2 - log p.
 template <typename R, int ENERGY, int D>
 __device__ __forceinline__ R f_of_eigs(const R p[D]) {
@@ -102,6 +109,12 @@ __device__ __forceinline__ R f_of_eigs(const R p[D]) {
     else s += R(0.5) * p[j] * p[j] - Tr<R>::log_(p[j]);
   }
   return s;
+}
+
+template <typename R, int EN, int D>
+__device__ __forceinline__ R f_of_eigs_en(const R p[D], int en) {
+  if constexpr (EN == 2) return en == 0 ? f_of_eigs<R, 0, D>(p) : f_of_eigs<R, 1, D>(p);
+  else return f_of_eigs<R, EN, D>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -265,8 +278,11 @@ __device__ __forceinline__ void onesided_rotate(R B[3][3], R V[3][3], int p, int
   }
 }
 
+// Full form: also returns V (columns = right singular vectors, det +1) and the
+// signed singular values sig with Q = Rot V diag(sig) V^T (sig[k] < 0 when
+// det Q < 0), which the adjoint of the rotation needs.
 template <typename R>
-__device__ __forceinline__ void nearest_rotation3(const R Q[3][3], R Rot[3][3], R& cond) {
+__device__ __forceinline__ void polar3(const R Q[3][3], R Rot[3][3], R Vout[3][3], R sig[3], R& cond) {
   R B[3][3], V[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -340,10 +356,21 @@ __device__ __forceinline__ void nearest_rotation3(const R Q[3][3], R Rot[3][3], 
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) Rot[i][j] = U[i][0] * V[j][0] + U[i][1] * V[j][1] + U[i][2] * V[j][2];
-  // signed smallest singular value: s_k = u_k . B_k (negative when det Q < 0)
-  const R sk = U[0][k] * B[0][k] + U[1][k] * B[1][k] + U[2][k] * B[2][k];
+  // signed singular values: s_j = u_j . B_j (s_k < 0 when det Q < 0)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) sig[j] = U[0][j] * B[0][j] + U[1][j] * B[1][j] + U[2][j] * B[2][j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Vout[i][j] = V[i][j];
   const R smax = Tr<R>::sqrt_(n[big]);
-  cond = (smax > R(0)) ? (Tr<R>::sqrt_(n[mid]) + sk) / smax : R(1);
+  cond = (smax > R(0)) ? (Tr<R>::sqrt_(n[mid]) + sig[k]) / smax : R(1);
+}
+
+template <typename R>
+__device__ __forceinline__ void nearest_rotation3(const R Q[3][3], R Rot[3][3], R& cond) {
+  R V[3][3], sig[3];
+  polar3<R>(Q, Rot, V, sig, cond);
 }
 
 // ---------------------------------------------------------------------------

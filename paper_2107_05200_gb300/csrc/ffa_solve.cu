@@ -141,7 +141,18 @@ __global__ void __launch_bounds__(kVertexBlock) k_gather(GatherLaunch G) {
       sq += outv[k] * outv[k];
     }
   }
-  if (G.partials) {
+  if (G.mesh_of) {
+    // batched meshes: per-mesh sum of squares, warp-aggregated when the warp is uniform
+    const int mesh = (row < G.rows) ? G.mesh_of[G.row_vertex ? G.row_vertex[row] : row] : -1;
+    const int m0 = __shfl_sync(0xffffffffu, mesh, 0);
+    if (__all_sync(0xffffffffu, mesh == m0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if ((threadIdx.x & 31) == 0 && m0 >= 0) atomicAdd(G.mesh_acc + (int64_t)m0 * (NQ + 1) + NQ, sq);
+    } else if (mesh >= 0) {
+      atomicAdd(G.mesh_acc + (int64_t)mesh * (NQ + 1) + NQ, sq);
+    }
+  } else if (G.partials) {
     __shared__ double red[kVertexBlock / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -223,16 +234,21 @@ __device__ __forceinline__ float4 ldg_stream(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
 
+// Narrow nodes (at most 64 columns, the leaves and small separators) would
+// leave most of a wide task's warps idle, so one warp takes one 128-row slice of
+// such a node over all its columns, eight independent warps per block.  The
+// level's task list holds its wide tasks first, then the narrow warp tasks
+// (padded with node = -1 to a multiple of 8).
+constexpr int kNarrowCols = 64;
+
 template <int D>
-__global__ void __launch_bounds__(256) k_forward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
-                                                 const int32_t* __restrict__ rows, const float* __restrict__ blocks,
-                                                 float* __restrict__ y, float* __restrict__ z) {
-  const Task t = tasks[blockIdx.x];
-  const NodeDev nd = nodes[t.node];
+__device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
+                                             const float* __restrict__ blocks, float* __restrict__ y,
+                                             float* __restrict__ z, float* smem) {
+  float (*fs)[D] = reinterpret_cast<float (*)[D]>(smem);                       // [256][D]
+  float (*red)[kFwdRows][D] = reinterpret_cast<float (*)[kFwdRows][D]>(smem + kFwdCols * D);  // [8][128][D]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntot = nd.ncol + nd.nrow;
-  __shared__ float fs[kFwdCols][D];
-  __shared__ float red[8][kFwdRows][D];
   const int nc = min(kFwdCols, nd.ncol - t.c0);
   for (int q = threadIdx.x; q < nc * D; q += 256) {
     const int c = q / D, k = q - c * D;
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(256) k_forward(const Task* __restrict__ tasks,
   }
   __syncthreads();
   const int r = t.r0 + 4 * lane;
-  const int cw0 = 32 * warp;                       // this warp's columns within the task
+  const int cw0 = 32 * warp;
   const int ncw = max(0, min(32, nc - cw0));
   float acc[4][D];
 #pragma unroll
@@ -250,12 +266,12 @@ __global__ void __launch_bounds__(256) k_forward(const Task* __restrict__ tasks,
   if (r < nd.ld && ncw > 0) {
     const float* B = blocks + nd.blk_off + (int64_t)(t.c0 + cw0) * nd.ld + r;
     int c = 0;
-    for (; c + 8 <= ncw; c += 8) {
-      float4 b[8];
+    for (; c + 16 <= ncw; c += 16) {
+      float4 b[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld);
+      for (int u = 0; u < 16; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld);
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < 16; ++u)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           const float f = fs[cw0 + c + u][k];
@@ -305,19 +321,101 @@ __global__ void __launch_bounds__(256) k_forward(const Task* __restrict__ tasks,
   }
 }
 
+// one warp: rows [r0, r0+128) of a narrow node times all of f = y[cols(s)].
+// The node's z rows lie in its first slice and only this warp writes them.
+template <int D>
+__device__ __forceinline__ void forward_narrow(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
+                                               const float* __restrict__ blocks, float* __restrict__ y,
+                                               float* __restrict__ z, float (*fw)[D]) {
+  const int lane = threadIdx.x & 31;
+  const int ntot = nd.ncol + nd.nrow;
+  for (int q = lane; q < nd.ncol * D; q += 32) {
+    const int c = q / D, k = q - c * D;
+    fw[c][k] = y[(int64_t)(nd.col0 + c) * D + k];
+  }
+  __syncwarp();
+  const int r = t.r0 + 4 * lane;
+  float acc[4][D];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[q][k] = 0.f;
+  if (r < nd.ld) {
+    const float* B = blocks + nd.blk_off + r;
+    int c = 0;
+    for (; c + 8 <= nd.ncol; c += 8) {
+      float4 b[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float f = fw[c + u][k];
+          acc[0][k] = fmaf(b[u].x, f, acc[0][k]);
+          acc[1][k] = fmaf(b[u].y, f, acc[1][k]);
+          acc[2][k] = fmaf(b[u].z, f, acc[2][k]);
+          acc[3][k] = fmaf(b[u].w, f, acc[3][k]);
+        }
+    }
+    for (; c < nd.ncol; ++c) {
+      const float4 bv = ldg_stream(B + (int64_t)c * nd.ld);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float f = fw[c][k];
+        acc[0][k] = fmaf(bv.x, f, acc[0][k]);
+        acc[1][k] = fmaf(bv.y, f, acc[1][k]);
+        acc[2][k] = fmaf(bv.z, f, acc[2][k]);
+        acc[3][k] = fmaf(bv.w, f, acc[3][k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int row = r + q;
+    if (row >= ntot) break;
+    if (row < nd.ncol) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) z[(int64_t)(nd.col0 + row) * D + k] = acc[q][k];
+    } else {
+      const int rr = __ldg(rows + nd.row_off + (row - nd.ncol));
+#pragma unroll
+      for (int k = 0; k < D; ++k) atomicAdd(y + (int64_t)rr * D + k, -acc[q][k]);
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_forward(const Task* __restrict__ tasks, int n_wide,
+                                                 const NodeDev* __restrict__ nodes, const int32_t* __restrict__ rows,
+                                                 const float* __restrict__ blocks, float* __restrict__ y,
+                                                 float* __restrict__ z) {
+  __shared__ __align__(16) float smem[kFwdCols * D + 8 * kFwdRows * D];
+  if ((int)blockIdx.x < n_wide) {
+    const Task t = tasks[blockIdx.x];
+    const NodeDev nd = nodes[t.node];
+    forward_wide<D>(t, nd, rows, blocks, y, z, smem);
+    return;
+  }
+  const int warp = threadIdx.x >> 5;
+  const Task t = tasks[n_wide + ((int)blockIdx.x - n_wide) * 8 + warp];
+  if (t.node < 0) return;
+  const NodeDev nd = nodes[t.node];
+  float (*fw)[D] = reinterpret_cast<float (*)[D]>(smem + warp * kNarrowCols * D);
+  forward_narrow<D>(t, nd, rows, blocks, y, z, fw);
+}
+
 // Backward task (node, r0, c0): output columns [c0, c0+32) of x_s against rows
 // [r0, r0+1024) of B_s, v = [z_s ; -x at the structure rows] staged in shared
 // memory.  Warp w owns columns c0+4w .. c0+4w+3; each lane reads 4 rows of each
 // of them per step; the 4 column dot products are reduced across the warp.
 template <int D>
-__global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
-                                                  const int32_t* __restrict__ rows, const float* __restrict__ blocks,
-                                                  const float* __restrict__ z, float* __restrict__ x) {
-  const Task t = tasks[blockIdx.x];
-  const NodeDev nd = nodes[t.node];
+__device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
+                                              const float* __restrict__ blocks, const float* __restrict__ z,
+                                              float* __restrict__ x, float* smem) {
+  float (*vs)[kBwdRows] = reinterpret_cast<float (*)[kBwdRows]>(smem);   // [D][1024]
   const int ntot = nd.ncol + nd.nrow;
-  const int nr = min(kBwdRows, nd.ld - t.r0);     // rows of this task, a multiple of 4
-  __shared__ __align__(16) float vs[D][kBwdRows];
+  const int nr = min(kBwdRows, nd.ld - t.r0);     // a multiple of 4
   for (int r = threadIdx.x; r < nr; r += 256) {
     const int row = t.r0 + r;
 #pragma unroll
@@ -330,7 +428,7 @@ __global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j0 = t.c0 + 4 * warp;                  // first of this warp's 4 columns
+  const int j0 = t.c0 + 4 * warp;
   if (j0 >= nd.ncol) return;
   const int ncw = min(4, nd.ncol - j0);
   float acc[4][D];
@@ -342,7 +440,7 @@ __global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks
   // rows above the diagonal of inv(L_ss) are stored zeros: start at the first
   // 4-row group that can be nonzero for this warp's first column
   const int rs = max(0, (j0 - t.r0) & ~3);
-#pragma unroll 2
+#pragma unroll 4
   for (int r = rs + 4 * lane; r < nr; r += 128) {
     float4 b[4];
 #pragma unroll
@@ -373,6 +471,82 @@ __global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks
 #pragma unroll
       for (int k = 0; k < D; ++k) atomicAdd(x + (int64_t)(nd.col0 + j0 + q) * D + k, acc[q][k]);
   }
+}
+
+// one warp: a whole narrow node (<= 64 columns, ld <= 256).  v is staged in the
+// warp's shared slice; lane j owns output columns j and j+32 and streams its own
+// column of B_s (rows below the diagonal only), so no cross-lane reduction is
+// needed and x_s is written directly (no other task touches it).
+template <int D>
+__device__ __forceinline__ void backward_narrow(const NodeDev& nd, const int32_t* __restrict__ rows,
+                                                const float* __restrict__ blocks, const float* __restrict__ z,
+                                                float* __restrict__ x, float (*vw)[256]) {
+  const int lane = threadIdx.x & 31;
+  const int ntot = nd.ncol + nd.nrow;
+  for (int r = lane; r < nd.ld; r += 32) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float val = 0.f;
+      if (r < nd.ncol) val = z[(int64_t)(nd.col0 + r) * D + k];
+      else if (r < ntot) val = -x[(int64_t)__ldg(rows + nd.row_off + (r - nd.ncol)) * D + k];
+      vw[k][r] = val;
+    }
+  }
+  __syncwarp();
+  for (int j = lane; j < nd.ncol; j += 32) {
+    const float* B = blocks + nd.blk_off + (int64_t)j * nd.ld;
+    float acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = 0.f;
+    int r = j & ~3;
+    for (; r + 16 <= nd.ld; r += 16) {
+      float4 b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b[u] = ldg_stream(B + r + 4 * u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float4 v = *reinterpret_cast<const float4*>(&vw[k][r + 4 * u]);
+          acc[k] = fmaf(b[u].x, v.x, acc[k]);
+          acc[k] = fmaf(b[u].y, v.y, acc[k]);
+          acc[k] = fmaf(b[u].z, v.z, acc[k]);
+          acc[k] = fmaf(b[u].w, v.w, acc[k]);
+        }
+    }
+    for (; r < nd.ld; r += 4) {
+      const float4 bv = ldg_stream(B + r);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float4 v = *reinterpret_cast<const float4*>(&vw[k][r]);
+        acc[k] = fmaf(bv.x, v.x, acc[k]);
+        acc[k] = fmaf(bv.y, v.y, acc[k]);
+        acc[k] = fmaf(bv.z, v.z, acc[k]);
+        acc[k] = fmaf(bv.w, v.w, acc[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[(int64_t)(nd.col0 + j) * D + k] = acc[k];
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks, int n_wide,
+                                                  const NodeDev* __restrict__ nodes, const int32_t* __restrict__ rows,
+                                                  const float* __restrict__ blocks, const float* __restrict__ z,
+                                                  float* __restrict__ x) {
+  constexpr int kSmem = (D * kBwdRows > 8 * D * 256) ? D * kBwdRows : 8 * D * 256;
+  __shared__ __align__(16) float smem[kSmem];
+  if ((int)blockIdx.x < n_wide) {
+    const Task t = tasks[blockIdx.x];
+    const NodeDev nd = nodes[t.node];
+    backward_wide<D>(t, nd, rows, blocks, z, x, smem);
+    return;
+  }
+  const int warp = threadIdx.x >> 5;
+  const Task t = tasks[n_wide + ((int)blockIdx.x - n_wide) * 8 + warp];
+  if (t.node < 0) return;
+  backward_narrow<D>(nodes[t.node], rows, blocks, z, x, reinterpret_cast<float (*)[256]>(smem + warp * D * 256));
 }
 
 template <int D>
@@ -440,6 +614,31 @@ __global__ void k_stats(FinalLaunch F, const double* __restrict__ acc) {
   *F.out = st;
 }
 
+__global__ void k_mesh_stats(MeshStatsLaunch M) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M.n_mesh) return;
+  const double* acc = M.mesh_acc + (int64_t)k * (NQ + 1);
+  ffa_stats st;
+  st.iters = 0;
+  st.checked_iter = 0;
+  st.e_prim = sqrt(acc[Q_EPRIM]);
+  st.e_dual = sqrt(acc[Q_EDUAL]);
+  st.norm_GW = sqrt(acc[Q_GW]);
+  st.norm_P = sqrt(acc[Q_P]);
+  st.norm_GtLambda = sqrt(acc[NQ]);
+  st.energy_P = acc[Q_ENERGY];
+  st.n_flipped = (int32_t)(acc[Q_FLIPS] + 0.5);
+  const double base = M.mesh_eps[2 * k] * sqrt((double)M.mesh_d[k] * (double)M.mesh_m[k]);
+  st.thr_prim = base + M.mesh_eps[2 * k + 1] * fmax(st.norm_GW, st.norm_P);
+  st.thr_dual = base + M.mesh_eps[2 * k + 1] * st.norm_GtLambda;
+  const bool finite_ok = acc[Q_NONFINITE] == 0.0 && isfinite(st.e_prim) && isfinite(st.e_dual);
+  st.converged = (finite_ok && st.e_prim < st.thr_prim && st.e_dual < st.thr_dual &&
+                  (!M.require_flip_free || st.n_flipped == 0)) ? 1 : 0;
+  if (!finite_ok) st.converged = -1;
+  if (st.converged == 1) atomicAdd(M.n_converged, 1);
+  M.out[k] = st;
+}
+
 __global__ void k_sum_partials(const double* __restrict__ p, int64_t nb, int nq, double* __restrict__ out) {
   const int q = blockIdx.x;
   double s = 0.0;
@@ -502,14 +701,18 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   for (int l = 0; l < L; ++l) {
     const int64_t nt = S.fwd_off[l + 1] - S.fwd_off[l];
     if (nt <= 0) continue;
-    if (S.d == 2) k_forward<2><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
-    else k_forward<3><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+    const int nw = (int)S.fwd_wide[l];
+    const unsigned grid = (unsigned)(nw + (nt - nw) / 8);
+    if (S.d == 2) k_forward<2><<<grid, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], nw, S.nodes, S.rows, S.blocks, S.y, S.z);
+    else k_forward<3><<<grid, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], nw, S.nodes, S.rows, S.blocks, S.y, S.z);
   }
   for (int l = L - 1; l >= 0; --l) {
     const int64_t nt = S.bwd_off[l + 1] - S.bwd_off[l];
     if (nt <= 0) continue;
-    if (S.d == 2) k_backward<2><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
-    else k_backward<3><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
+    const int nw = (int)S.bwd_wide[l];
+    const unsigned grid = (unsigned)(nw + (nt - nw) / 8);
+    if (S.d == 2) k_backward<2><<<grid, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], nw, S.nodes, S.rows, S.blocks, S.z, S.x);
+    else k_backward<3><<<grid, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], nw, S.nodes, S.rows, S.blocks, S.z, S.x);
   }
 }
 
@@ -523,6 +726,10 @@ void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, c
 void launch_final_reduce(const FinalLaunch& F, cudaStream_t s) {
   k_reduce_quantities<<<NQ + 1, 512, 0, s>>>(F, F.scratch);
   k_stats<<<1, 32, 0, s>>>(F, F.scratch);
+}
+
+void launch_mesh_stats(const MeshStatsLaunch& M, cudaStream_t s) {
+  k_mesh_stats<<<(M.n_mesh + 127) / 128, 128, 0, s>>>(M);
 }
 
 void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s) {

@@ -67,6 +67,7 @@ class Solver:
         prm.nd_leaf_size = int(leaf_size)
         prm.host_threads = int(host_threads)
         n_pin = 0 if pins is None else int(len(pins))
+        self.n_pin = max(n_pin, 1)
         pP, self._pins = _ptr(pins, np.int32) if n_pin else (None, None)
         pB, self._pinpos = _ptr(pin_pos, np.float64) if n_pin else (None, None)
         ctx = C.c_void_p()
@@ -146,10 +147,28 @@ class Solver:
         self._check(self._lib.ffa_get_info(self._ctx, C.byref(inf)))
         return inf.as_dict()
 
+    def autotune(self, reps: int = 5) -> dict:
+        t = N.Tuning()
+        self._check(self._lib.ffa_autotune(self._ctx, int(reps), C.byref(t)))
+        return t.as_dict()
+
     def profile_phases(self, reps: int) -> dict:
         t = N.PhaseTimes()
         self._check(self._lib.ffa_profile_phases(self._ctx, int(reps), C.byref(t)))
         return t.as_dict()
+
+    def forward_unrolled(self, K: int, ckpt_every: int = 20) -> None:
+        """K iterations from the state set by init(), keeping checkpoints for backward_unrolled."""
+        self._check(self._lib.ffa_forward_unrolled(self._ctx, int(K), int(ckpt_every)))
+
+    def backward_unrolled(self, dL_dW, out=None):
+        """dL/db for the pinned positions b, given dL/dW^K of the last forward_unrolled."""
+        p, keep = _ptr(dL_dW, np.float64)
+        if out is None:
+            out = np.empty((self.n_pin, self.d), np.float64)
+        po, _ = _ptr(out, np.float64)
+        self._check(self._lib.ffa_backward_unrolled(self._ctx, p, po))
+        return out
 
     def wstep_residual(self) -> float:
         r = C.c_double()
@@ -163,3 +182,102 @@ class Solver:
         kw.setdefault("eps_abs", wl.eps_abs)
         kw.setdefault("eps_rel", wl.eps_rel)
         return cls(wl.V, wl.T, wl.pins, wl.pin_pos, **kw)
+
+
+class BatchSolver:
+    """Many independent meshes solved together (one graph launch for all of them)."""
+
+    def __init__(self, workloads, precision: str = "fp32", check_every: int = 10, refine_sweeps: int = 2,
+                 leaf_size: int = 64, eps_abs=None, eps_rel=None, stream=None):
+        self._lib = N.load()
+        self._b = None
+        k = len(workloads)
+        self._keep = []
+        meshes = (N.Mesh * k)()
+        pin_ptrs = (C.c_void_p * k)()
+        pos_ptrs = (C.c_void_p * k)()
+        npin = np.zeros(k, np.int32)
+        energies = np.zeros(k, np.int32)
+        rho = np.zeros(k, np.float64)
+        self.n, self.d = [], []
+        for j, wl in enumerate(workloads):
+            pV, V = _ptr(wl.V, np.float64)
+            pT, T = _ptr(wl.T, np.int32)
+            pP, P = _ptr(wl.pins, np.int32)
+            pB, B = _ptr(wl.pin_pos, np.float64)
+            self._keep += [V, T, P, B]
+            meshes[j] = N.Mesh(wl.n, wl.m, wl.d, wl.V.shape[1], pV, pT)
+            pin_ptrs[j] = pP
+            pos_ptrs[j] = pB
+            npin[j] = len(wl.pins)
+            energies[j] = ENERGIES[wl.energy]
+            rho[j] = wl.rho
+            self.n.append(wl.n)
+            self.d.append(wl.d)
+        prm = N.Params()
+        N.check(self._lib, None, self._lib.ffa_default_params(C.byref(prm)))
+        prm.local_precision = PRECISIONS[precision]
+        prm.check_every = int(check_every)
+        prm.refine_sweeps = int(refine_sweeps)
+        prm.nd_leaf_size = int(leaf_size)
+        prm.eps_abs = float(workloads[0].eps_abs if eps_abs is None else eps_abs)
+        prm.eps_rel = float(workloads[0].eps_rel if eps_rel is None else eps_rel)
+        self._keep += [npin, energies, rho]
+        b = C.c_void_p()
+        st = self._lib.ffa_batch_create(k, meshes, pin_ptrs, C.c_void_p(npin.ctypes.data), pos_ptrs,
+                                        C.c_void_p(energies.ctypes.data), C.c_void_p(rho.ctypes.data),
+                                        C.byref(prm), C.c_void_p(stream) if stream else None, C.byref(b))
+        if st != N.FFA_OK:
+            raise N.FFAError(st, self._lib.ffa_batch_last_error(None).decode())
+        self._b = b
+        self.k = k
+
+    def _check(self, st):
+        if st != N.FFA_OK:
+            raise N.FFAError(st, self._lib.ffa_batch_last_error(self._b).decode())
+
+    def close(self):
+        if self._b is not None:
+            self._lib.ffa_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, W0s):
+        ptrs = (C.c_void_p * self.k)()
+        keep = []
+        for j, W in enumerate(W0s):
+            p, a = _ptr(W, np.float64)
+            ptrs[j] = p
+            keep.append(a)
+        self._check(self._lib.ffa_batch_init(self._b, ptrs))
+
+    def iterate(self, max_iter: int, stop_at_tol: bool = True):
+        stats = (N.Stats * self.k)()
+        nconv = C.c_int32()
+        self._check(self._lib.ffa_batch_iterate(self._b, int(max_iter), 1 if stop_at_tol else 0, stats,
+                                                C.byref(nconv)))
+        return [s.as_dict() for s in stats], nconv.value
+
+    def autotune(self, reps: int = 5) -> list:
+        g = int(self._lib.ffa_batch_groups(self._b))
+        arr = (N.Tuning * max(g, 1))()
+        self._check(self._lib.ffa_batch_autotune(self._b, int(reps), arr))
+        return [arr[i].as_dict() for i in range(g)]
+
+    def W(self, j: int, out=None):
+        if out is None:
+            out = np.empty((self.n[j], self.d[j]), np.float64)
+        p, _ = _ptr(out, np.float64)
+        self._check(self._lib.ffa_batch_get_W(self._b, int(j), p))
+        return out

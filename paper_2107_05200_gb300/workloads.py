@@ -307,12 +307,15 @@ def bend_map(X: np.ndarray, radius: float = 2.0) -> np.ndarray:
 
 
 def cube_handles(cells: int = 32, seed: int = 5, n_targets: int = 1000,
-                 energy: str = SYM_DIRICHLET, rho: float = 3.0) -> Workload:
-    """Differentiation workload: cube, bottom fixed, 8x8 top-face handle lattice.
+                 energy: str = SYM_DIRICHLET, rho: float = 3.0, lattice_start: int = 2,
+                 lattice_step: int = 4, pre_bend: float = 0.0) -> Workload:
+    """Differentiation workload: cube, bottom fixed, a lattice of top-face handles.
 
-    Handles are the top-face vertices with lattice indices in {2, 6, ..., cells-2}^2
-    (64 for cells=32).  Their initial positions are the rest positions; the loss
-    targets are the bend map of n_targets seeded interior vertices.
+    Handles are the top-face vertices with lattice indices in
+    {lattice_start, lattice_start + lattice_step, ...}^2 (64 for cells=32).  The
+    handles' positions b (the parameters) start part-way along the bend map,
+    b = rest + pre_bend (bend(rest) - rest), at rest by default; W0 is the rest
+    pose (independent of b).  The loss targets are the bend map of n_targets seeded interior vertices.
     """
     rng = np.random.default_rng(seed)
     V, T = cube_tets(cells)
@@ -322,17 +325,64 @@ def cube_handles(cells: int = 32, seed: int = 5, n_targets: int = 1000,
     inner = ~on_face
     V[inner] += rng.uniform(-0.1 * h, 0.1 * h, size=(inner.sum(), 3))
     bottom = np.nonzero(V[:, 2] < 0.5 * h)[0]
-    lat = np.arange(2, cells, 4)
+    lat = np.arange(lattice_start, cells, lattice_step)
     hi_, hj_ = np.meshgrid(lat, lat, indexing="ij")
     handles = ((hi_.ravel() * k1 + hj_.ravel()) * k1 + cells).astype(np.int32)
     pins = np.concatenate([bottom, handles]).astype(np.int32)
     pin_pos = V[pins].copy()
+    hp = V[handles]
+    pin_pos[len(bottom):] = hp + pre_bend * (bend_map(hp) - hp)
+    n_targets = min(n_targets, int(inner.sum()))
     targets_idx = np.sort(rng.choice(np.nonzero(inner)[0], size=n_targets, replace=False))
     wl = Workload(f"cube_handles_{cells}", V, T, pins, pin_pos, V.copy(), energy, rho,
                   eps_abs=1e-6, eps_rel=1e-5, max_iter=200)
     wl.meta = dict(handles=handles, n_bottom=len(bottom), target_idx=targets_idx.astype(np.int32),
                    targets=bend_map(V[targets_idx]))
     return wl
+
+
+def batched_meshes(count: int = 256, seed: int = 4, m_min: int = 500, m_max: int = 50_000,
+                   rho: float = 3.0, tol: float = 1e-5) -> list[Workload]:
+    """Independent meshes for the batched solver.
+
+    Sizes are drawn log-uniformly in [m_min, m_max] elements; even entries are
+    jittered triangle grids (two corner vertices pinned), odd entries jittered
+    cube tet meshes (bottom face pinned).  W0 is the rest pose plus Gaussian
+    noise scaled so that a fraction drawn uniformly in [1%, 5%] of the elements
+    starts flipped; the energy is symmetric Dirichlet or symmetric gradient at
+    random.  Mesh j uses the seed 1000 + j.
+    """
+    top = np.random.default_rng(seed)
+    sizes = np.exp(top.uniform(np.log(m_min), np.log(m_max), size=count))
+    out = []
+    for j in range(count):
+        rng = np.random.default_rng(1000 + j)
+        energy = SYM_DIRICHLET if rng.uniform() < 0.5 else SYM_GRADIENT
+        frac = rng.uniform(0.01, 0.05)
+        if j % 2 == 0:
+            g = max(3, int(round(math.sqrt(sizes[j] / 2.0))) + 1)
+            V, T = grid_triangles(g, g)
+            h = 1.0 / (g - 1)
+            bnd = np.zeros(V.shape[0], bool)
+            bnd[_grid_boundary_cycle(g, g)] = True
+            V[~bnd] += rng.uniform(-0.2 * h, 0.2 * h, size=((~bnd).sum(), 2))
+            pins = np.array([0, (g - 1) * g], dtype=np.int32)
+        else:
+            c = max(2, int(round((sizes[j] / 6.0) ** (1.0 / 3.0))))
+            V, T = cube_tets(c)
+            h = 1.0 / c
+            on_face = np.any((V < 0.5 * h) | (V > 1 - 0.5 * h), axis=1)
+            V[~on_face] += rng.uniform(-0.1 * h, 0.1 * h, size=((~on_face).sum(), 3))
+            pins = np.nonzero(V[:, 2] < 0.5 * h)[0].astype(np.int32)
+        xi = rng.standard_normal(size=V.shape)
+        xi[pins] = 0.0
+        sigma = _noise_scale_for_flips(V, xi, T, frac, hi=2.0 * h)
+        W0 = V + sigma * xi
+        wl = Workload(f"batch_{j}", V, T, pins, V[pins].copy(), W0, energy, rho,
+                      eps_abs=tol, eps_rel=10 * tol, max_iter=1000)
+        wl.meta = dict(flipped0=flipped_fraction(W0, T), sigma=sigma)
+        out.append(wl)
+    return out
 
 
 def by_name(name: str) -> Workload:

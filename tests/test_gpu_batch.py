@@ -1,0 +1,70 @@
+"""Batched meshes: every mesh of a batch follows the same iterates as its own
+single-mesh solve (and therefore the oracle), with per-mesh statistics and
+per-mesh termination."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import admm
+from paper_2107_05200_gb300 import workloads as wk
+
+pytestmark = pytest.mark.gpu
+
+
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _batch_workloads():
+    wls = wk.batched_meshes(count=6, seed=7, m_min=300, m_max=3000)
+    # a mesh without pins: vertex 0 is fixed at the origin
+    nop = wk.uv_disk(grid=10, seed=8, rho=3.0, tol=1e-5)
+    nop.pins = np.zeros(0, np.int32)
+    nop.pin_pos = np.zeros((0, 2))
+    return wls + [nop]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_batch_matches_single_mesh_solves(precision, tol):
+    _need_gpu()
+    from paper_2107_05200_gb300.solver import BatchSolver, Solver
+    wls = _batch_workloads()
+    K = 30
+    with BatchSolver(wls, precision=precision, check_every=10) as bs:
+        bs.init([wl.W0 for wl in wls])
+        stats, _ = bs.iterate(K, stop_at_tol=False)
+        Wb = [bs.W(j) for j in range(len(wls))]
+    for j, wl in enumerate(wls):
+        with Solver.from_workload(wl, precision=precision, check_every=10) as sol:
+            sol.init(wl.W0)
+            st = sol.iterate(K, stop_at_tol=False)
+            W = sol.W()
+        err = np.abs(Wb[j] - W).max() / np.abs(W).max()
+        assert err < tol, (j, err)
+        for key in ("e_prim", "e_dual", "thr_prim", "thr_dual", "energy_P"):
+            assert math.isclose(stats[j][key], st[key], rel_tol=1e-6 if precision == "fp64" else 1e-2,
+                                abs_tol=1e-12), (j, key, stats[j][key], st[key])
+        assert stats[j]["n_flipped"] == st["n_flipped"]
+
+
+def test_batch_matches_the_oracle_and_stops_when_all_meshes_converged():
+    _need_gpu()
+    from paper_2107_05200_gb300.solver import BatchSolver
+    wls = wk.batched_meshes(count=4, seed=9, m_min=300, m_max=1500)
+    K = 20
+    with BatchSolver(wls, precision="fp64", check_every=5) as bs:
+        bs.init([wl.W0 for wl in wls])
+        bs.iterate(K, stop_at_tol=False)
+        Wb = [bs.W(j) for j in range(len(wls))]
+        stats, nconv = bs.iterate(2000, stop_at_tol=True)
+    for j, wl in enumerate(wls):
+        o = admm.Oracle.from_workload(wl)
+        s = o.init(wl.W0)
+        for _ in range(K):
+            s, _ = o.step(s)
+        assert np.abs(Wb[j] - s.W).max() / np.abs(s.W).max() < 1e-8, j
+    assert nconv == len(wls)
+    assert all(st["converged"] == 1 and st["n_flipped"] == 0 for st in stats)
