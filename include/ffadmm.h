@@ -51,7 +51,8 @@ typedef enum {
   FFA_ERR_OOM = 5,                /* host or device allocation failed */
   FFA_ERR_NAN = 6,                /* a non-finite value appeared in the iterate */
   FFA_ERR_NOT_INITIALIZED = 7,    /* ffa_iterate before ffa_init */
-  FFA_ERR_FLIPPED = 8             /* gradient requested at a map with det J_i <= 0 */
+  FFA_ERR_FLIPPED = 8,            /* gradient requested at a map with det J_i <= 0 */
+  FFA_ERR_TIMEOUT = 9             /* a bounded device-side wait gave up; results are invalid */
 } ffa_status;
 
 typedef enum {
@@ -84,6 +85,8 @@ typedef struct {
   int32_t refine_sweeps;   /* W step: residual-correction sweeps per iteration (>= 1) */
   int32_t nd_leaf_size;    /* W step setup: nested-dissection leaf size (8..512) */
   int32_t host_threads;    /* W step setup: host threads for the factorization (0 = all) */
+  int32_t solve_schedule;  /* W step: 0 one launch per elimination-tree level, 1 one persistent
+                              launch per triangular solve (blocks wait for their dependencies) */
 } ffa_params;
 
 typedef struct {
@@ -123,7 +126,7 @@ typedef struct {
 
 /* Fill *p with the defaults: symmetric Dirichlet, rho 1, eps_abs 1e-6, eps_rel 1e-5,
  * check_every 10, require_flip_free 1, FP32 local step, 2 refine sweeps,
- * leaf size 64, all host threads. */
+ * leaf size 64, all host threads, solve schedule 1. */
 ffa_status ffa_default_params(ffa_params* p);
 
 /* Prepare a solver for one mesh: element gradients and measures w_i (Supplemental,
@@ -200,11 +203,14 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out);
 typedef struct {
   int32_t local_block;  /* threads per block of the local step: 64, 128 or 256 */
   int32_t narrow_cols;  /* supernodes with at most this many columns take one warp each: 32 or 64 */
+  int32_t schedule;     /* supernodal solves: 0 per-level launches, 1 persistent */
   double ms_local[3];   /* measured local step for 64, 128, 256 threads */
   double ms_solve[2];   /* measured supernodal solve (forward + backward) for 32, 64 */
+  double ms_schedule[2];/* measured supernodal solve for schedules 0 and 1 */
 } ffa_tuning;
 
-/* Time the candidate launch shapes of the local step and of the supernodal solves
+/* Time the candidate launch shapes of the local step, of the supernodal solves and
+ * their schedule
  * with CUDA events over reps launches each, keep the fastest, and restore the
  * iterate (needs ffa_init first; the state is saved and put back). */
 ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out);

@@ -15,7 +15,7 @@ FFA_OK = 0
 STATUS_NAMES = {
     0: "FFA_OK", 1: "FFA_ERR_INVALID_ARG", 2: "FFA_ERR_DEGENERATE_ELEMENT",
     3: "FFA_ERR_SINGULAR_SYSTEM", 4: "FFA_ERR_CUDA", 5: "FFA_ERR_OOM", 6: "FFA_ERR_NAN",
-    7: "FFA_ERR_NOT_INITIALIZED", 8: "FFA_ERR_FLIPPED",
+    7: "FFA_ERR_NOT_INITIALIZED", 8: "FFA_ERR_FLIPPED", 9: "FFA_ERR_TIMEOUT",
 }
 
 EXPORTED = [
@@ -38,7 +38,7 @@ class Params(C.Structure):
                 ("eps_rel", C.c_double), ("check_every", C.c_int32),
                 ("require_flip_free", C.c_int32), ("local_precision", C.c_int),
                 ("refine_sweeps", C.c_int32), ("nd_leaf_size", C.c_int32),
-                ("host_threads", C.c_int32)]
+                ("host_threads", C.c_int32), ("solve_schedule", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -65,12 +65,13 @@ class Info(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("local_block", C.c_int32), ("narrow_cols", C.c_int32), ("ms_local", C.c_double * 3),
-                ("ms_solve", C.c_double * 2)]
+    _fields_ = [("local_block", C.c_int32), ("narrow_cols", C.c_int32), ("schedule", C.c_int32),
+                ("ms_local", C.c_double * 3), ("ms_solve", C.c_double * 2), ("ms_schedule", C.c_double * 2)]
 
     def as_dict(self) -> dict:
-        return {"local_block": self.local_block, "narrow_cols": self.narrow_cols,
-                "ms_local": list(self.ms_local), "ms_solve": list(self.ms_solve)}
+        return {"local_block": self.local_block, "narrow_cols": self.narrow_cols, "schedule": self.schedule,
+                "ms_local": list(self.ms_local), "ms_solve": list(self.ms_solve),
+                "ms_schedule": list(self.ms_schedule)}
 
 
 class PhaseTimes(C.Structure):

@@ -95,6 +95,12 @@ struct ffa_ctx {
   // launch shapes chosen by ffa_autotune
   int local_block = 128;
   int narrow_cols = 64;
+  int schedule = 0;             // supernodal solves: 0 one launch per level, 1 persistent
+  int2 *items_f = nullptr, *items_b = nullptr;
+  int n_items_f = 0, n_items_b = 0;
+  int32_t *need_f = nullptr, *need_b = nullptr, *fchild_ptr = nullptr, *fchild = nullptr, *bpar = nullptr;
+  int32_t *sync = nullptr, *err_flag = nullptr;
+  int grid_f = 0, grid_b = 0;
   std::vector<Supernode> nodes_h;  // host copy of the supernode table (task lists are rebuilt from it)
   int n_levels = 0;
   Slot tune_slot;
@@ -285,6 +291,21 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.bwd_off = ctx->bwd_off;
   S.fwd_wide = ctx->fwd_wide;
   S.bwd_wide = ctx->bwd_wide;
+  S.schedule = ctx->schedule;
+  S.items_f = ctx->items_f;
+  S.items_b = ctx->items_b;
+  S.n_items_f = ctx->n_items_f;
+  S.n_items_b = ctx->n_items_b;
+  S.need_f = ctx->need_f;
+  S.need_b = ctx->need_b;
+  S.fchild_ptr = ctx->fchild_ptr;
+  S.fchild = ctx->fchild;
+  S.bpar = ctx->bpar;
+  S.sync = ctx->sync;
+  S.n_nodes = (int)ctx->nodes_h.size();
+  S.err_flag = ctx->err_flag;
+  S.grid_f = ctx->grid_f;
+  S.grid_b = ctx->grid_b;
   S.y = ctx->y;
   S.z = ctx->z;
   S.x = ctx->x;
@@ -428,6 +449,7 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   else if (p.refine_sweeps < 1 || p.refine_sweeps > 16) msg = "refine_sweeps must be in [1, 16]";
   else if (p.nd_leaf_size < 8 || p.nd_leaf_size > 512) msg = "nd_leaf_size must be in [8, 512]";
   else if (p.host_threads < 0) msg = "host_threads must be >= 0";
+  else if (p.solve_schedule != 0 && p.solve_schedule != 1) msg = "solve_schedule must be 0 or 1";
   else return FFA_OK;
   return FFA_ERR_INVALID_ARG;
 }
@@ -491,6 +513,60 @@ ffa_status build_tasks(ffa_ctx* ctx) {
   if (!ctx->nodes && (st = upload(ctx, &ctx->nodes, nodes)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->fwd_t, fwd_all)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->bwd_t, bwd_all)) != FFA_OK) return st;
+
+  // persistent schedule: work items in dependency order, task counts per node,
+  // nearest descendants (forward) / ancestor (backward) that have tasks
+  const int nn = (int)nd_h.size();
+  std::vector<int2> items_f, items_b;
+  std::vector<int32_t> need_f(nn, 0), need_b(nn, 0);
+  for (const Task& t : fwd_all)
+    if (t.node >= 0) need_f[t.node]++;
+  for (const Task& t : bwd_all)
+    if (t.node >= 0) need_b[t.node]++;
+  for (int l = 0; l < nl; ++l) {
+    const int64_t a = ctx->fwd_off[l], w = ctx->fwd_wide[l], b = ctx->fwd_off[l + 1];
+    for (int64_t q = a; q < a + w; ++q) items_f.push_back(make_int2((int)q, 0));
+    for (int64_t q = a + w; q < b; q += 8) items_f.push_back(make_int2((int)q, 1));
+  }
+  for (int l = nl - 1; l >= 0; --l) {
+    const int64_t a = ctx->bwd_off[l], w = ctx->bwd_wide[l], b = ctx->bwd_off[l + 1];
+    for (int64_t q = a; q < a + w; ++q) items_b.push_back(make_int2((int)q, 0));
+    for (int64_t q = a + w; q < b; q += 8) items_b.push_back(make_int2((int)q, 1));
+  }
+  std::vector<std::vector<int>> kids(nn);
+  for (int i = 0; i < nn; ++i)
+    if (nd_h[i].parent >= 0) kids[nd_h[i].parent].push_back(i);
+  std::vector<int32_t> fchild_ptr(nn + 1, 0), fchild, bpar(nn, -1);
+  for (int i = 0; i < nn; ++i) {
+    std::vector<int> stack(kids[i].begin(), kids[i].end());
+    while (!stack.empty()) {
+      const int c = stack.back();
+      stack.pop_back();
+      if (need_f[c] > 0) fchild.push_back(c);
+      else stack.insert(stack.end(), kids[c].begin(), kids[c].end());
+    }
+    fchild_ptr[i + 1] = (int32_t)fchild.size();
+    int p = nd_h[i].parent;
+    while (p >= 0 && need_b[p] == 0) p = nd_h[p].parent;
+    bpar[i] = p;
+  }
+  if (fchild.empty()) fchild.push_back(0);
+  ctx->n_items_f = (int)items_f.size();
+  ctx->n_items_b = (int)items_b.size();
+  if ((st = upload(ctx, &ctx->items_f, items_f)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->items_b, items_b)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->need_f, need_f)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->need_b, need_b)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->fchild_ptr, fchild_ptr)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->fchild, fchild)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->bpar, bpar)) != FFA_OK) return st;
+  if (!ctx->sync && (st = dalloc(ctx, &ctx->sync, (size_t)2 * nn + 2)) != FFA_OK) return st;
+  if (!ctx->err_flag) {
+    if ((st = dalloc(ctx, &ctx->err_flag, 1)) != FFA_OK) return st;
+    FFA_CUDA(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), ctx->stream));
+  }
+  ctx->grid_f = std::max(1, std::min(persistent_grid(ctx->d, true), ctx->n_items_f));
+  ctx->grid_b = std::max(1, std::min(persistent_grid(ctx->d, false), ctx->n_items_b));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   return FFA_OK;
 }
@@ -519,6 +595,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   ctx->d_in = d_in;
   ctx->fp64 = ctx->prm.local_precision == FFA_LOCAL_FP64;
   ctx->rsz = ctx->fp64 ? 8 : 4;
+  ctx->schedule = ctx->prm.solve_schedule;
   if (stream) {
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
   } else {
@@ -925,6 +1002,15 @@ ffa_status records_of(ffa_ctx* ctx, const double* W) {
   return FFA_OK;
 }
 
+// reads (and clears) the flag the persistent solve kernels set when a bounded wait ran out
+bool device_wait_failed(ffa_ctx* ctx) {
+  if (!ctx->err_flag) return false;
+  int32_t f = 0;
+  if (cudaMemcpy(&f, ctx->err_flag, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+  if (f) cudaMemset(ctx->err_flag, 0, sizeof(f));
+  return f != 0;
+}
+
 }  // namespace
 
 void ffa::set_thread_error(const std::string& msg) { g_create_error = msg; }
@@ -945,6 +1031,7 @@ ffa_status ffa_default_params(ffa_params* p) {
   p->refine_sweeps = 2;
   p->nd_leaf_size = 64;
   p->host_threads = 0;
+  p->solve_schedule = 1;
   return FFA_OK;
 }
 
@@ -1033,6 +1120,10 @@ ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_
     if (stop_at_tol || done == max_iter) {
       FFA_CUDA(cudaMemcpyAsync(ctx->stats_h, ctx->stats_d, sizeof(ffa_stats), cudaMemcpyDeviceToHost, ctx->stream));
       FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+      if (device_wait_failed(ctx)) {
+        ctx->iter_total += done;
+        return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait of the supernodal solve gave up");
+      }
       have = true;
       ctx->last = *ctx->stats_h;
       ctx->last.checked_iter = (int32_t)(ctx->iter_total + done);
@@ -1056,6 +1147,7 @@ ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_
 }
 
 ffa_status ffa_get_W(ffa_ctx* ctx, double* W_out) {
+  if (ctx && device_wait_failed(ctx)) return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait of the supernodal solve gave up");
   if (!ctx) return FFA_ERR_INVALID_ARG;
   if (!W_out) return fail(ctx, FFA_ERR_INVALID_ARG, "W_out is NULL");
   ctx->err.clear();
@@ -1370,6 +1462,27 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
   }
   ctx->narrow_cols = best_narrow;
   if ((st = build_tasks(ctx)) != FFA_OK) return st;
+  // 3) supernodal solves: per-level launches or one persistent launch per pass
+  best = 1e300;
+  int best_sched = ctx->schedule;
+  for (int c = 0; c < 2; ++c) {
+    ctx->schedule = c;
+    SolveData S = solve_data(ctx);
+    launch_supernodal_solve(S, s);
+    FFA_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) launch_supernodal_solve(S, s);
+    FFA_CUDA(cudaEventRecord(e1, s));
+    FFA_CUDA(cudaEventSynchronize(e1));
+    float ms;
+    FFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    t.ms_schedule[c] = ms / reps;
+    if (t.ms_schedule[c] < best) {
+      best = t.ms_schedule[c];
+      best_sched = c;
+    }
+  }
+  ctx->schedule = best_sched;
+  if (device_wait_failed(ctx)) return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait gave up during tuning");
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // the graphs captured the old launch shapes
@@ -1380,6 +1493,7 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
   FFA_CUDA(cudaStreamSynchronize(s));
   t.local_block = ctx->local_block;
   t.narrow_cols = ctx->narrow_cols;
+  t.schedule = ctx->schedule;
   if (out) *out = t;
   return FFA_OK;
 }

@@ -114,6 +114,20 @@ struct SolveData {
   const Task* bwd_tasks;
   std::vector<int64_t> fwd_off, bwd_off;  // per level task ranges (host)
   std::vector<int64_t> fwd_wide, bwd_wide; // per level: leading wide tasks (rest: narrow, padded to 8)
+  // persistent schedule (schedule = 1): work items in dependency order and counters
+  int schedule = 0;          // 0: one launch per level, 1: one persistent launch per pass
+  const int2* items_f = nullptr;   // (task index, kind 0 wide / 1 group of 8 narrow)
+  const int2* items_b = nullptr;
+  int n_items_f = 0, n_items_b = 0;
+  const int32_t* need_f = nullptr;  // per node: forward tasks
+  const int32_t* need_b = nullptr;  // per node: backward tasks
+  const int32_t* fchild_ptr = nullptr;  // per node: nearest descendants with tasks (CSR)
+  const int32_t* fchild = nullptr;
+  const int32_t* bpar = nullptr;    // per node: nearest ancestor with tasks (-1: none)
+  int32_t* sync = nullptr;          // [n_nodes done_f][n_nodes done_b][2 claim counters]
+  int n_nodes = 0;
+  int32_t* err_flag = nullptr;      // set to 1 if a wait ran out of polls
+  int grid_f = 0, grid_b = 0;
   float* y;                  // nF x d residual / forward work vector
   float* z;                  // nF x d forward result
   float* x;                  // nF x d correction
@@ -124,6 +138,7 @@ struct SolveData {
 void launch_residual(const SolveData& S, double* partials, int n_blocks, cudaStream_t s);
 void launch_axpy_correction(const SolveData& S, cudaStream_t s);   // X += x
 void launch_supernodal_solve(const SolveData& S, cudaStream_t s);  // x = L_FF^{-1} y (FP32)
+int persistent_grid(int d, bool forward);  // resident blocks of the persistent solve kernels
 
 // constant part of the right-hand side: cst = -L_FC b (eliminated order)
 void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, const double* val,

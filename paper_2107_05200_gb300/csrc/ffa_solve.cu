@@ -252,7 +252,7 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
   const int nc = min(kFwdCols, nd.ncol - t.c0);
   for (int q = threadIdx.x; q < nc * D; q += 256) {
     const int c = q / D, k = q - c * D;
-    fs[c][k] = y[(int64_t)(nd.col0 + t.c0 + c) * D + k];
+    fs[c][k] = __ldcg(y + (int64_t)(nd.col0 + t.c0 + c) * D + k);
   }
   __syncthreads();
   const int r = t.r0 + 4 * lane;
@@ -331,7 +331,7 @@ __device__ __forceinline__ void forward_narrow(const Task& t, const NodeDev& nd,
   const int ntot = nd.ncol + nd.nrow;
   for (int q = lane; q < nd.ncol * D; q += 32) {
     const int c = q / D, k = q - c * D;
-    fw[c][k] = y[(int64_t)(nd.col0 + c) * D + k];
+    fw[c][k] = __ldcg(y + (int64_t)(nd.col0 + c) * D + k);
   }
   __syncwarp();
   const int r = t.r0 + 4 * lane;
@@ -421,8 +421,8 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       float v = 0.f;
-      if (row < nd.ncol) v = z[(int64_t)(nd.col0 + row) * D + k];
-      else if (row < ntot) v = -x[(int64_t)__ldg(rows + nd.row_off + (row - nd.ncol)) * D + k];
+      if (row < nd.ncol) v = __ldcg(z + (int64_t)(nd.col0 + row) * D + k);
+      else if (row < ntot) v = -__ldcg(x + (int64_t)__ldg(rows + nd.row_off + (row - nd.ncol)) * D + k);
       vs[k][r] = v;
     }
   }
@@ -487,8 +487,8 @@ __device__ __forceinline__ void backward_narrow(const NodeDev& nd, const int32_t
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       float val = 0.f;
-      if (r < nd.ncol) val = z[(int64_t)(nd.col0 + r) * D + k];
-      else if (r < ntot) val = -x[(int64_t)__ldg(rows + nd.row_off + (r - nd.ncol)) * D + k];
+      if (r < nd.ncol) val = __ldcg(z + (int64_t)(nd.col0 + r) * D + k);
+      else if (r < ntot) val = -__ldcg(x + (int64_t)__ldg(rows + nd.row_off + (r - nd.ncol)) * D + k);
       vw[k][r] = val;
     }
   }
@@ -547,6 +547,146 @@ __global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks
   const Task t = tasks[n_wide + ((int)blockIdx.x - n_wide) * 8 + warp];
   if (t.node < 0) return;
   backward_narrow<D>(nodes[t.node], rows, blocks, z, x, reinterpret_cast<float (*)[256]>(smem + warp * D * 256));
+}
+
+// ---------------------------------------------------------------------------
+// Persistent schedule: one launch per pass.  Blocks claim work items in
+// dependency order (forward: leaves first; backward: root first) from a global
+// counter, wait until the tasks their node depends on are done (forward: its
+// nearest descendants with tasks; backward: its nearest ancestor with tasks),
+// run the same per-task code as the level-synchronous kernels, and count the
+// task as done.  Every waited-on task was claimed earlier by a running block,
+// so the waits end; each wait is still bounded and sets err_flag instead of
+// spinning on.
+// ---------------------------------------------------------------------------
+constexpr long long kSpinLimit = 1LL << 22;   // polls of ~100 ns (~0.4 s) before giving up
+
+// the plain-data part of SolveData that the persistent kernels need
+struct PersistView {
+  const Task* fwd_tasks;
+  const Task* bwd_tasks;
+  const NodeDev* nodes;
+  const int32_t* rows;
+  const float* blocks;
+  float* y;
+  float* z;
+  float* x;
+  const int2* items_f;
+  const int2* items_b;
+  int n_items_f, n_items_b;
+  const int32_t* need_f;
+  const int32_t* need_b;
+  const int32_t* fchild_ptr;
+  const int32_t* fchild;
+  const int32_t* bpar;
+  int32_t* sync;
+  int n_nodes;
+  int32_t* err_flag;
+};
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Once any wait has given up (err set), every later wait returns at once, so a
+// failure costs one timeout, not one per task.
+__device__ __forceinline__ void wait_count(const int32_t* p, int need, int32_t* err) {
+  long long it = 0;
+  while (ld_acquire(p) < need) {
+    if (++it > kSpinLimit || ld_acquire(err) != 0) {
+      atomicExch(err, 1);
+      return;
+    }
+    __nanosleep(100);
+  }
+}
+
+__device__ __forceinline__ void wait_children(const PersistView& S, int node) {
+  for (int q = S.fchild_ptr[node]; q < S.fchild_ptr[node + 1]; ++q) {
+    const int c = S.fchild[q];
+    wait_count(S.sync + c, S.need_f[c], S.err_flag);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_forward_persistent(PersistView S) {
+  __shared__ __align__(16) float smem[kFwdCols * D + 8 * kFwdRows * D];
+  __shared__ int item_s;
+  int32_t* counter = S.sync + 2 * S.n_nodes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    if (item >= S.n_items_f) break;
+    const int2 it = S.items_f[item];
+    if (it.y == 0) {
+      const Task t = S.fwd_tasks[it.x];
+      const NodeDev nd = S.nodes[t.node];
+      if (threadIdx.x == 0) wait_children(S, t.node);
+      __syncthreads();
+      forward_wide<D>(t, nd, S.rows, S.blocks, S.y, S.z, smem);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(S.sync + t.node, 1);
+    } else {
+      const Task t = S.fwd_tasks[it.x + warp];
+      if (t.node >= 0) {
+        if (lane == 0) wait_children(S, t.node);
+        __syncwarp();
+        const NodeDev nd = S.nodes[t.node];
+        forward_narrow<D>(t, nd, S.rows, S.blocks, S.y, S.z,
+                          reinterpret_cast<float (*)[D]>(smem + warp * kNarrowCols * D));
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(S.sync + t.node, 1);
+      }
+    }
+    __syncthreads();   // item_s and smem are reused by the next item
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_backward_persistent(PersistView S) {
+  constexpr int kSmem = (D * kBwdRows > 8 * D * 256) ? D * kBwdRows : 8 * D * 256;
+  __shared__ __align__(16) float smem[kSmem];
+  __shared__ int item_s;
+  int32_t* counter = S.sync + 2 * S.n_nodes + 1;
+  int32_t* done_b = S.sync + S.n_nodes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    if (item >= S.n_items_b) break;
+    const int2 it = S.items_b[item];
+    if (it.y == 0) {
+      const Task t = S.bwd_tasks[it.x];
+      const NodeDev nd = S.nodes[t.node];
+      const int p = S.bpar[t.node];
+      if (threadIdx.x == 0 && p >= 0) wait_count(done_b + p, S.need_b[p], S.err_flag);
+      __syncthreads();
+      backward_wide<D>(t, nd, S.rows, S.blocks, S.z, S.x, smem);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(done_b + t.node, 1);
+    } else {
+      const Task t = S.bwd_tasks[it.x + warp];
+      if (t.node >= 0) {
+        const int p = S.bpar[t.node];
+        if (lane == 0 && p >= 0) wait_count(done_b + p, S.need_b[p], S.err_flag);
+        __syncwarp();
+        backward_narrow<D>(S.nodes[t.node], S.rows, S.blocks, S.z, S.x,
+                           reinterpret_cast<float (*)[256]>(smem + warp * D * 256));
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(done_b + t.node, 1);
+      }
+    }
+    __syncthreads();
+  }
 }
 
 template <int D>
@@ -697,6 +837,20 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   const size_t bytes = (size_t)S.nF * S.d * sizeof(float);
   cudaMemsetAsync(S.z, 0, bytes, s);
   cudaMemsetAsync(S.x, 0, bytes, s);
+  if (S.schedule == 1) {
+    cudaMemsetAsync(S.sync, 0, (size_t)(2 * S.n_nodes + 2) * sizeof(int32_t), s);
+    PersistView v{S.fwd_tasks, S.bwd_tasks, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.items_f, S.items_b,
+                  S.n_items_f, S.n_items_b, S.need_f, S.need_b, S.fchild_ptr, S.fchild, S.bpar, S.sync,
+                  S.n_nodes, S.err_flag};
+    if (S.d == 2) {
+      k_forward_persistent<2><<<S.grid_f, 256, 0, s>>>(v);
+      k_backward_persistent<2><<<S.grid_b, 256, 0, s>>>(v);
+    } else {
+      k_forward_persistent<3><<<S.grid_f, 256, 0, s>>>(v);
+      k_backward_persistent<3><<<S.grid_b, 256, 0, s>>>(v);
+    }
+    return;
+  }
   const int L = (int)S.fwd_off.size() - 1;
   for (int l = 0; l < L; ++l) {
     const int64_t nt = S.fwd_off[l + 1] - S.fwd_off[l];
@@ -714,6 +868,19 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
     if (S.d == 2) k_backward<2><<<grid, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], nw, S.nodes, S.rows, S.blocks, S.z, S.x);
     else k_backward<3><<<grid, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], nw, S.nodes, S.rows, S.blocks, S.z, S.x);
   }
+}
+
+int persistent_grid(int d, bool forward) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  if (forward) e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_forward_persistent<2>, 256, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_forward_persistent<3>, 256, 0);
+  else e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward_persistent<2>, 256, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward_persistent<3>, 256, 0);
+  if (e != cudaSuccess || per < 1) per = 1;
+  return sms * per;
 }
 
 void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, const double* val,

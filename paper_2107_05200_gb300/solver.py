@@ -43,7 +43,7 @@ class Solver:
     def __init__(self, V, T, pins=None, pin_pos=None, energy: str = "sd", rho: float = 1.0,
                  eps_abs: float = 1e-6, eps_rel: float = 1e-5, check_every: int = 10,
                  precision: str = "fp32", refine_sweeps: int = 2, leaf_size: int = 64,
-                 require_flip_free: bool = True, host_threads: int = 0, stream=None):
+                 require_flip_free: bool = True, host_threads: int = 0, schedule: int = 1, stream=None):
         self._lib = N.load()
         self._ctx = None
         Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
@@ -66,6 +66,7 @@ class Solver:
         prm.refine_sweeps = int(refine_sweeps)
         prm.nd_leaf_size = int(leaf_size)
         prm.host_threads = int(host_threads)
+        prm.solve_schedule = int(schedule)
         n_pin = 0 if pins is None else int(len(pins))
         self.n_pin = max(n_pin, 1)
         pP, self._pins = _ptr(pins, np.int32) if n_pin else (None, None)
