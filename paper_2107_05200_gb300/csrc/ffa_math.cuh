@@ -17,6 +17,8 @@ template <> struct Tr<float> {
   static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
   static __device__ __forceinline__ float tiny() { return 1e-30f; }
   static __device__ __forceinline__ float eps() { return 1.1920929e-07f; }
+  // quotient for rotation angles only (c and s are then formed consistently from it)
+  static __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
   static constexpr int jacobi_sweeps = 6;
   static constexpr int newton_iters = 24;
 };
@@ -28,6 +30,7 @@ template <> struct Tr<double> {
   static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
   static __device__ __forceinline__ double tiny() { return 1e-300; }
   static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
+  static __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
   static constexpr int jacobi_sweeps = 10;
   static constexpr int newton_iters = 48;
 };
@@ -123,10 +126,11 @@ __device__ __forceinline__ R f_of_eigs_en(const R p[D], int en) {
 template <typename R>
 __device__ __forceinline__ void jacobi_rotate(R& app, R& aqq, R& apq, R& arp, R& arq, R V[3][3],
                                               int p, int q) {
-  if (apq == R(0)) return;
-  const R theta = (aqq - app) / (R(2) * apq);
+  // already diagonal to working precision for this pair: nothing to rotate
+  if (!(apq * apq > Tr<R>::eps() * Tr<R>::eps() * Tr<R>::abs_(app * aqq)) || apq == R(0)) return;
+  const R theta = Tr<R>::fdiv(aqq - app, R(2) * apq);
   const R at = Tr<R>::abs_(theta);
-  R t = R(1) / (at + Tr<R>::sqrt_(at * at + R(1)));
+  R t = Tr<R>::fdiv(R(1), at + Tr<R>::sqrt_(at * at + R(1)));
   if (at * Tr<R>::eps() > R(1)) t = R(0.5) / at;  // theta^2 would overflow
   t = (theta < R(0)) ? -t : t;
   const R c = Tr<R>::rsqrt_(t * t + R(1));
@@ -260,9 +264,9 @@ __device__ __forceinline__ void onesided_rotate(R B[3][3], R V[3][3], int p, int
     ga = fma(B[r][p], B[r][q], ga);
   }
   if (!(Tr<R>::abs_(ga) > Tr<R>::eps() * Tr<R>::sqrt_(al * be)) || ga == R(0)) return;
-  const R zeta = (be - al) / (R(2) * ga);
+  const R zeta = Tr<R>::fdiv(be - al, R(2) * ga);
   const R az = Tr<R>::abs_(zeta);
-  R t = R(1) / (az + Tr<R>::sqrt_(az * az + R(1)));
+  R t = Tr<R>::fdiv(R(1), az + Tr<R>::sqrt_(az * az + R(1)));
   if (az * Tr<R>::eps() > R(1)) t = R(0.5) / az;
   t = (zeta < R(0)) ? -t : t;
   const R c = Tr<R>::rsqrt_(t * t + R(1));
