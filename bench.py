@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--check-every", type=int, default=50)
+    ap.add_argument("--schedule", type=int, default=1, choices=[0, 1],
+                    help="supernodal solves: 0 one launch per tree level, 1 dynamic ready queue")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -235,7 +237,7 @@ def main():
     stream = torch.cuda.current_stream()
     wl = wk.cube_deform(cells=args.cells)
     sol = Solver.from_workload(wl, precision=args.precision, refine_sweeps=args.sweeps,
-                               check_every=args.check_every, stream=stream.cuda_stream)
+                               check_every=args.check_every, schedule=args.schedule, stream=stream.cuda_stream)
     info = sol.info()
     W0 = torch.tensor(wl.W0, dtype=torch.float64, device="cuda")
     sol.init(W0)
@@ -291,6 +293,7 @@ def main():
         "config": {"workload": f"cube_deform_{args.cells}", "tets": wl.m, "vertices": wl.n,
                    "energy": "sym_dirichlet", "rho": wl.rho, "local_precision": args.precision,
                    "refine_sweeps": args.sweeps, "check_every": args.check_every,
+                   "solve_schedule": "dynamic" if args.schedule == 1 else "per_level",
                    "l2": "working set > L2 (factor + element state), no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": local_gbs, "peak": hbm_peak, "unit": "GB/s",

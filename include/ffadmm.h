@@ -85,8 +85,9 @@ typedef struct {
   int32_t refine_sweeps;   /* W step: residual-correction sweeps per iteration (>= 1) */
   int32_t nd_leaf_size;    /* W step setup: nested-dissection leaf size (8..512) */
   int32_t host_threads;    /* W step setup: host threads for the factorization (0 = all) */
-  int32_t solve_schedule;  /* W step: 0 one launch per elimination-tree level, 1 one persistent
-                              launch per triangular solve (blocks wait for their dependencies) */
+  int32_t solve_schedule;  /* W step: 0 one launch per elimination-tree level, 1 one launch per
+                              triangular solve whose blocks take ready tasks from a queue that
+                              finished supernodes refill (default) */
 } ffa_params;
 
 typedef struct {
@@ -202,8 +203,9 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out);
 /* Launch shapes picked by ffa_autotune (the paper has no counterpart). */
 typedef struct {
   int32_t local_block;  /* threads per block of the local step: 64, 128 or 256 */
-  int32_t narrow_cols;  /* supernodes with at most this many columns take one warp each: 32 or 64 */
-  int32_t schedule;     /* supernodal solves: 0 per-level launches, 1 persistent */
+  int32_t narrow_cols;  /* supernodes with at most this many columns (and at most 1024 rows) run
+                           as one task on one block: 32 or 64 */
+  int32_t schedule;     /* supernodal solves: 0 per-level launches, 1 dynamic ready queue */
   double ms_local[3];   /* measured local step for 64, 128, 256 threads */
   double ms_solve[2];   /* measured supernodal solve (forward + backward) for 32, 64 */
   double ms_schedule[2];/* measured supernodal solve for schedules 0 and 1 */

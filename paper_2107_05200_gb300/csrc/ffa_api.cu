@@ -55,7 +55,7 @@ struct ffa_ctx {
   int32_t* rows = nullptr;
   float* blocks = nullptr;
   Task *fwd_t = nullptr, *bwd_t = nullptr;
-  std::vector<int64_t> fwd_off, bwd_off, fwd_wide, bwd_wide;
+  std::vector<int64_t> fwd_off, bwd_off;
   double* local_partials = nullptr;
   int64_t n_local_blocks = 0;
   double* vert_partials = nullptr;
@@ -95,11 +95,9 @@ struct ffa_ctx {
   // launch shapes chosen by ffa_autotune
   int local_block = 128;
   int narrow_cols = 64;
-  int schedule = 0;             // supernodal solves: 0 one launch per level, 1 persistent
-  int2 *items_f = nullptr, *items_b = nullptr;
-  int n_items_f = 0, n_items_b = 0;
-  int32_t *need_f = nullptr, *need_b = nullptr, *fchild_ptr = nullptr, *fchild = nullptr, *bpar = nullptr;
-  int32_t *sync = nullptr, *err_flag = nullptr;
+  int schedule = 0;             // supernodal solves: 0 one launch per level, 1 dynamic
+  DynPass fdyn, bdyn;           // dynamic schedule of the forward and backward passes
+  int32_t* err_flag = nullptr;
   int grid_f = 0, grid_b = 0;
   std::vector<Supernode> nodes_h;  // host copy of the supernode table (task lists are rebuilt from it)
   int n_levels = 0;
@@ -289,19 +287,9 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.bwd_tasks = ctx->bwd_t;
   S.fwd_off = ctx->fwd_off;
   S.bwd_off = ctx->bwd_off;
-  S.fwd_wide = ctx->fwd_wide;
-  S.bwd_wide = ctx->bwd_wide;
   S.schedule = ctx->schedule;
-  S.items_f = ctx->items_f;
-  S.items_b = ctx->items_b;
-  S.n_items_f = ctx->n_items_f;
-  S.n_items_b = ctx->n_items_b;
-  S.need_f = ctx->need_f;
-  S.need_b = ctx->need_b;
-  S.fchild_ptr = ctx->fchild_ptr;
-  S.fchild = ctx->fchild;
-  S.bpar = ctx->bpar;
-  S.sync = ctx->sync;
+  S.fdyn = ctx->fdyn;
+  S.bdyn = ctx->bdyn;
   S.n_nodes = (int)ctx->nodes_h.size();
   S.err_flag = ctx->err_flag;
   S.grid_f = ctx->grid_f;
@@ -454,58 +442,99 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   return FFA_ERR_INVALID_ARG;
 }
 
-// Supernode table and per-level task lists of the supernodal solves.  Per level:
-// wide tasks (one block each) first, then narrow warp tasks padded to a
-// multiple of 8.  A node is narrow when it has at most narrow_cols columns.
+// kernels one iteration launches: the gather, per refinement sweep the residual,
+// the schedule reset and the solve launches (2 dynamic, or one per non-empty
+// level and pass), the sweeps - 1 corrections, the vertex update and the local step
+int kernels_per_iteration(const ffa_ctx* ctx) {
+  int solve = 2;
+  if (ctx->schedule == 0) {
+    solve = 0;
+    for (size_t l = 0; l + 1 < ctx->fwd_off.size(); ++l)
+      solve += (ctx->fwd_off[l + 1] > ctx->fwd_off[l]) + (ctx->bwd_off[l + 1] > ctx->bwd_off[l]);
+  }
+  const int sweeps = ctx->prm.refine_sweeps;
+  return 1 + sweeps * (2 + solve) + (sweeps - 1) + 1 + 1;
+}
+
+// Supernode table and task lists of the supernodal solves.  A node with at most
+// narrow_cols columns and ld <= kNodeMaxLd is one node task (a whole block on the
+// whole node); larger nodes are cut into wide tasks.  The level-synchronous
+// schedule launches the tasks of one level at a time (fwd_off / bwd_off); the
+// dynamic schedule uses the same task arrays with the per-node dependencies.
+ffa_status upload_dyn(ffa_ctx* ctx, DynPass& P, const Task* tasks, int n_tasks, const std::vector<int32_t>& task0,
+                      const std::vector<int32_t>& ntask, const std::vector<int32_t>& dep_ptr,
+                      const std::vector<int32_t>& dep, const std::vector<int32_t>& pending,
+                      const std::vector<int32_t>& q_init, int n_init) {
+  ffa_status st;
+  int32_t *t0, *nt, *dp, *dd, *qi, *pi, *q, *pe, *dn, *ct;
+  if ((st = upload(ctx, &t0, task0)) != FFA_OK) return st;
+  if ((st = upload(ctx, &nt, ntask)) != FFA_OK) return st;
+  if ((st = upload(ctx, &dp, dep_ptr)) != FFA_OK) return st;
+  if ((st = upload(ctx, &dd, dep)) != FFA_OK) return st;
+  if ((st = upload(ctx, &qi, q_init)) != FFA_OK) return st;
+  if ((st = upload(ctx, &pi, pending)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &q, q_init.size())) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &pe, pending.size())) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &dn, pending.size())) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &ct, 2)) != FFA_OK) return st;
+  P.tasks = tasks;
+  P.n_tasks = n_tasks;
+  P.n_init = n_init;
+  P.task0 = t0;
+  P.ntask = nt;
+  P.dep_ptr = dp;
+  P.dep = dd;
+  P.q_init = qi;
+  P.pending_init = pi;
+  P.queue = q;
+  P.pending = pe;
+  P.done = dn;
+  P.ctr = ct;
+  return FFA_OK;
+}
+
 ffa_status build_tasks(ffa_ctx* ctx) {
   const std::vector<Supernode>& nd_h = ctx->nodes_h;
   const int nl = ctx->n_levels;
-  const int narrow = ctx->narrow_cols;
-  std::vector<NodeDev> nodes(nd_h.size());
-  std::vector<std::vector<Task>> fl(nl), bl(nl), fn(nl), bn(nl);
-  for (size_t s = 0; s < nd_h.size(); ++s) {
+  const int narrow = std::min(ctx->narrow_cols, kNarrowCols);
+  const int nn = (int)nd_h.size();
+  ctx->grid_f = persistent_grid(ctx->d, true);
+  ctx->grid_b = persistent_grid(ctx->d, false);
+  auto is_node_task = [&](const Supernode& sn) { return sn.ncol <= narrow && sn.ld <= kNodeMaxLd; };
+  std::vector<NodeDev> nodes(nn);
+  std::vector<std::vector<Task>> fl(nl), bl(nl);
+  for (int s = 0; s < nn; ++s) {
     const Supernode& sn = nd_h[s];
     nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, sn.ld, sn.row_off, sn.blk_off};
     const int ntot = sn.ncol + sn.nrow;
     if (sn.ncol == 0) continue;
-    if (sn.ncol <= narrow) {
-      for (int r0 = 0; r0 < ntot; r0 += kFwdRows) fn[sn.level].push_back(Task{(int32_t)s, r0, 0, 1});
-    } else {
-      for (int r0 = 0; r0 < ntot; r0 += kFwdRows)
-        for (int c0 = 0; c0 < sn.ncol; c0 += kFwdCols) {
-          const int rmax = std::min(r0 + kFwdRows, ntot) - 1;
-          if (rmax < c0) continue;  // entirely above the diagonal of inv(L_ss)
-          fl[sn.level].push_back(Task{(int32_t)s, r0, c0, 0});
-        }
+    if (is_node_task(sn)) {
+      fl[sn.level].push_back(Task{s, 0, 0, 1});
+      bl[sn.level].push_back(Task{s, 0, 0, 1});
+      continue;
     }
-    if (sn.ncol <= narrow && sn.ld <= 256) {
-      bn[sn.level].push_back(Task{(int32_t)s, 0, 0, 1});
-    } else {
-      for (int c0 = 0; c0 < sn.ncol; c0 += kBwdCols)
-        for (int r0 = 0; r0 < ntot; r0 += kBwdRows) {
-          const int rmax = std::min(r0 + kBwdRows, ntot) - 1;
-          if (rmax < c0) continue;
-          bl[sn.level].push_back(Task{(int32_t)s, r0, c0, 0});
-        }
-    }
+    // (smaller wide tasks on the narrow top levels were measured slower: the
+    // fixed cost of a task outweighs the shorter tail)
+    const int wf = kFwdCols, wb = kBwdRows;
+    for (int r0 = 0; r0 < ntot; r0 += kFwdRows)
+      for (int c0 = 0; c0 < sn.ncol; c0 += wf) {
+        const int rmax = std::min(r0 + kFwdRows, ntot) - 1;
+        if (rmax < c0) continue;  // entirely above the diagonal of inv(L_ss)
+        fl[sn.level].push_back(Task{s, r0, c0, wf});
+      }
+    for (int c0 = 0; c0 < sn.ncol; c0 += kBwdCols)
+      for (int r0 = 0; r0 < ntot; r0 += wb) {
+        const int rmax = std::min(r0 + wb, ntot) - 1;
+        if (rmax < c0) continue;
+        bl[sn.level].push_back(Task{s, r0, c0, wb});
+      }
   }
   std::vector<Task> fwd_all, bwd_all;
   ctx->fwd_off.assign(1, 0);
   ctx->bwd_off.assign(1, 0);
-  ctx->fwd_wide.clear();
-  ctx->bwd_wide.clear();
-  auto pad8 = [](std::vector<Task>& v) {
-    while (v.size() % 8) v.push_back(Task{-1, 0, 0, 1});
-  };
   for (int l = 0; l < nl; ++l) {
-    pad8(fn[l]);
-    pad8(bn[l]);
-    ctx->fwd_wide.push_back((int64_t)fl[l].size());
-    ctx->bwd_wide.push_back((int64_t)bl[l].size());
     fwd_all.insert(fwd_all.end(), fl[l].begin(), fl[l].end());
-    fwd_all.insert(fwd_all.end(), fn[l].begin(), fn[l].end());
     bwd_all.insert(bwd_all.end(), bl[l].begin(), bl[l].end());
-    bwd_all.insert(bwd_all.end(), bn[l].begin(), bn[l].end());
     ctx->fwd_off.push_back((int64_t)fwd_all.size());
     ctx->bwd_off.push_back((int64_t)bwd_all.size());
   }
@@ -514,59 +543,68 @@ ffa_status build_tasks(ffa_ctx* ctx) {
   if ((st = upload(ctx, &ctx->fwd_t, fwd_all)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->bwd_t, bwd_all)) != FFA_OK) return st;
 
-  // persistent schedule: work items in dependency order, task counts per node,
-  // nearest descendants (forward) / ancestor (backward) that have tasks
-  const int nn = (int)nd_h.size();
-  std::vector<int2> items_f, items_b;
-  std::vector<int32_t> need_f(nn, 0), need_b(nn, 0);
-  for (const Task& t : fwd_all)
-    if (t.node >= 0) need_f[t.node]++;
-  for (const Task& t : bwd_all)
-    if (t.node >= 0) need_b[t.node]++;
-  for (int l = 0; l < nl; ++l) {
-    const int64_t a = ctx->fwd_off[l], w = ctx->fwd_wide[l], b = ctx->fwd_off[l + 1];
-    for (int64_t q = a; q < a + w; ++q) items_f.push_back(make_int2((int)q, 0));
-    for (int64_t q = a + w; q < b; q += 8) items_f.push_back(make_int2((int)q, 1));
-  }
-  for (int l = nl - 1; l >= 0; --l) {
-    const int64_t a = ctx->bwd_off[l], w = ctx->bwd_wide[l], b = ctx->bwd_off[l + 1];
-    for (int64_t q = a; q < a + w; ++q) items_b.push_back(make_int2((int)q, 0));
-    for (int64_t q = a + w; q < b; q += 8) items_b.push_back(make_int2((int)q, 1));
-  }
-  std::vector<std::vector<int>> kids(nn);
-  for (int i = 0; i < nn; ++i)
-    if (nd_h[i].parent >= 0) kids[nd_h[i].parent].push_back(i);
-  std::vector<int32_t> fchild_ptr(nn + 1, 0), fchild, bpar(nn, -1);
-  for (int i = 0; i < nn; ++i) {
-    std::vector<int> stack(kids[i].begin(), kids[i].end());
-    while (!stack.empty()) {
-      const int c = stack.back();
-      stack.pop_back();
-      if (need_f[c] > 0) fchild.push_back(c);
-      else stack.insert(stack.end(), kids[c].begin(), kids[c].end());
+  // dynamic schedule: per-node task ranges (a node's tasks are contiguous in
+  // both arrays) and dependencies through the nearest ancestor with tasks
+  auto ranges = [&](const std::vector<Task>& all, std::vector<int32_t>& t0, std::vector<int32_t>& cnt) {
+    t0.assign(nn, 0);
+    cnt.assign(nn, 0);
+    for (size_t i = 0; i < all.size(); ++i) {
+      const int s = all[i].node;
+      if (cnt[s]++ == 0) t0[s] = (int32_t)i;
     }
-    fchild_ptr[i + 1] = (int32_t)fchild.size();
-    int p = nd_h[i].parent;
-    while (p >= 0 && need_b[p] == 0) p = nd_h[p].parent;
-    bpar[i] = p;
+  };
+  std::vector<int32_t> t0f, ntf, t0b, ntb;
+  ranges(fwd_all, t0f, ntf);
+  ranges(bwd_all, t0b, ntb);
+  std::vector<int32_t> up(nn, -1);   // nearest ancestor with tasks
+  for (int s = 0; s < nn; ++s) {
+    int p = nd_h[s].parent;
+    while (p >= 0 && ntf[p] == 0) p = nd_h[p].parent;
+    up[s] = p;
   }
-  if (fchild.empty()) fchild.push_back(0);
-  ctx->n_items_f = (int)items_f.size();
-  ctx->n_items_b = (int)items_b.size();
-  if ((st = upload(ctx, &ctx->items_f, items_f)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->items_b, items_b)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->need_f, need_f)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->need_b, need_b)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->fchild_ptr, fchild_ptr)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->fchild, fchild)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->bpar, bpar)) != FFA_OK) return st;
-  if (!ctx->sync && (st = dalloc(ctx, &ctx->sync, (size_t)2 * nn + 2)) != FFA_OK) return st;
+  // forward: s waits on the nodes whose nearest ancestor with tasks is s
+  std::vector<int32_t> dptr_f(nn + 1, 0), dep_f, pend_f(nn, 0), qf;
+  for (int s = 0; s < nn; ++s) {
+    if (ntf[s] > 0 && up[s] >= 0) {
+      dep_f.push_back(up[s]);
+      pend_f[up[s]]++;
+    }
+    dptr_f[s + 1] = (int32_t)dep_f.size();
+  }
+  for (int s = 0; s < nn; ++s)
+    if (ntf[s] > 0 && pend_f[s] == 0)
+      for (int i = 0; i < ntf[s]; ++i) qf.push_back(t0f[s] + i);
+  const int n_init_f = (int)qf.size();
+  qf.resize(fwd_all.size(), -1);
+  // backward: s waits on its nearest ancestor with tasks
+  std::vector<std::vector<int32_t>> kids(nn);
+  std::vector<int32_t> pend_b(nn, 0), dptr_b(nn + 1, 0), dep_b, qb;
+  for (int s = 0; s < nn; ++s)
+    if (ntb[s] > 0 && up[s] >= 0) {
+      kids[up[s]].push_back(s);
+      pend_b[s] = 1;
+    }
+  for (int s = 0; s < nn; ++s) {
+    dep_b.insert(dep_b.end(), kids[s].begin(), kids[s].end());
+    dptr_b[s + 1] = (int32_t)dep_b.size();
+  }
+  for (int s = nn - 1; s >= 0; --s)
+    if (ntb[s] > 0 && pend_b[s] == 0)
+      for (int i = 0; i < ntb[s]; ++i) qb.push_back(t0b[s] + i);
+  const int n_init_b = (int)qb.size();
+  qb.resize(bwd_all.size(), -1);
+  if ((st = upload_dyn(ctx, ctx->fdyn, ctx->fwd_t, (int)fwd_all.size(), t0f, ntf, dptr_f, dep_f, pend_f, qf,
+                       n_init_f)) != FFA_OK)
+    return st;
+  if ((st = upload_dyn(ctx, ctx->bdyn, ctx->bwd_t, (int)bwd_all.size(), t0b, ntb, dptr_b, dep_b, pend_b, qb,
+                       n_init_b)) != FFA_OK)
+    return st;
   if (!ctx->err_flag) {
     if ((st = dalloc(ctx, &ctx->err_flag, 1)) != FFA_OK) return st;
     FFA_CUDA(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), ctx->stream));
   }
-  ctx->grid_f = std::max(1, std::min(persistent_grid(ctx->d, true), ctx->n_items_f));
-  ctx->grid_b = std::max(1, std::min(persistent_grid(ctx->d, false), ctx->n_items_b));
+  ctx->grid_f = std::max(1, std::min(ctx->grid_f, (int)fwd_all.size()));
+  ctx->grid_b = std::max(1, std::min(ctx->grid_b, (int)bwd_all.size()));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   return FFA_OK;
 }
@@ -892,11 +930,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   ctx->info.d_in = d_in;
   ctx->info.n_pin = n_pin;
   ctx->info.n_free = nF;
-  int lev_launch = 0;
-  for (int l = 0; l < fac.n_levels; ++l)
-    lev_launch += (ctx->fwd_off[l + 1] > ctx->fwd_off[l]) + (ctx->bwd_off[l + 1] > ctx->bwd_off[l]);
-  const int sweeps = ctx->prm.refine_sweeps;
-  ctx->info.kernels_per_iteration = 1 + sweeps * (1 + lev_launch) + (sweeps - 1) + 1 + 1;
+  ctx->info.kernels_per_iteration = kernels_per_iteration(ctx);
   ctx->info.kernels_per_check = 3;
   (void)t_setup0;
   return FFA_OK;
@@ -1244,6 +1278,7 @@ ffa_status ffa_gradient(ffa_ctx* ctx, const double* W, double* dEdW) {
 
 ffa_status ffa_get_info(ffa_ctx* ctx, ffa_info* info) {
   if (!ctx || !info) return FFA_ERR_INVALID_ARG;
+  ctx->info.kernels_per_iteration = kernels_per_iteration(ctx);   // the schedule may have been retuned
   *info = ctx->info;
   return FFA_OK;
 }
@@ -1439,7 +1474,7 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
   }
   ctx->local_block = best_block;
   ctx->n_local_blocks = (ctx->m + best_block - 1) / best_block;
-  // 2) supernodal solves: which nodes take the narrow (warp per node) path
+  // 2) supernodal solves: which small nodes run as one node task
   const int narrows[2] = {32, 64};
   best = 1e300;
   int best_narrow = ctx->narrow_cols;

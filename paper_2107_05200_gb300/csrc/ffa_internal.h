@@ -19,13 +19,37 @@ enum { QV_GTL = 0, QV_NUM, QV_DEN, NQV };
 
 constexpr int kLocalBlock = 128;
 constexpr int kVertexBlock = 256;
-constexpr int kFwdRows = 128;     // forward task rows (4 per lane)
-constexpr int kFwdCols = 256;     // forward task columns (32 per warp, 8 warps)
-constexpr int kBwdCols = 32;      // backward task: output columns (4 per warp, 8 warps)
-constexpr int kBwdRows = 1024;    // backward task: rows reduced per task
+constexpr int kFwdRows = 128;     // forward wide task rows (4 per lane)
+constexpr int kFwdCols = 256;     // forward wide task: at most this many columns (W/8 per warp)
+constexpr int kFwdBatch = 8;      // forward: columns per lane in flight
+constexpr int kBwdCols = 32;      // backward wide task: output columns (4 per warp, 8 warps)
+constexpr int kBwdRows = 1024;    // backward wide task: at most this many rows
+constexpr int kNarrowCols = 64;   // node tasks: at most this many columns ...
+constexpr int kNodeMaxLd = 1024;  // ... and at most this leading dimension
 
+// kind 1: the whole node on one block; kind > 1: a wide task of B_node from
+// (r0, c0) spanning kind columns (forward) or kind rows (backward)
 struct Task {
-  int32_t node, r0, c0, pad;
+  int32_t node, r0, c0, kind;
+};
+
+// One pass (forward or backward) of the dynamic schedule.  Tasks of a node are
+// contiguous: task0[s] .. task0[s] + ntask[s].  dep (CSR by dep_ptr) lists the
+// nodes that wait on s; pending_init[s] counts what s waits on.  q_init holds
+// the tasks of the nodes that wait on nothing (n_init of them) followed by -1.
+struct DynPass {
+  const Task* tasks = nullptr;
+  int n_tasks = 0, n_init = 0;
+  const int32_t* task0 = nullptr;
+  const int32_t* ntask = nullptr;
+  const int32_t* dep_ptr = nullptr;
+  const int32_t* dep = nullptr;
+  const int32_t* q_init = nullptr;
+  const int32_t* pending_init = nullptr;
+  int32_t* queue = nullptr;     // n_tasks slots
+  int32_t* pending = nullptr;   // per node
+  int32_t* done = nullptr;      // per node: tasks finished
+  int32_t* ctr = nullptr;       // [0] next slot to claim, [1] next slot to fill
 };
 
 struct NodeDev {
@@ -113,18 +137,8 @@ struct SolveData {
   const Task* fwd_tasks;
   const Task* bwd_tasks;
   std::vector<int64_t> fwd_off, bwd_off;  // per level task ranges (host)
-  std::vector<int64_t> fwd_wide, bwd_wide; // per level: leading wide tasks (rest: narrow, padded to 8)
-  // persistent schedule (schedule = 1): work items in dependency order and counters
-  int schedule = 0;          // 0: one launch per level, 1: one persistent launch per pass
-  const int2* items_f = nullptr;   // (task index, kind 0 wide / 1 group of 8 narrow)
-  const int2* items_b = nullptr;
-  int n_items_f = 0, n_items_b = 0;
-  const int32_t* need_f = nullptr;  // per node: forward tasks
-  const int32_t* need_b = nullptr;  // per node: backward tasks
-  const int32_t* fchild_ptr = nullptr;  // per node: nearest descendants with tasks (CSR)
-  const int32_t* fchild = nullptr;
-  const int32_t* bpar = nullptr;    // per node: nearest ancestor with tasks (-1: none)
-  int32_t* sync = nullptr;          // [n_nodes done_f][n_nodes done_b][2 claim counters]
+  int schedule = 0;          // 0: one launch per level, 1: one dynamic launch per pass
+  DynPass fdyn, bdyn;
   int n_nodes = 0;
   int32_t* err_flag = nullptr;      // set to 1 if a wait ran out of polls
   int grid_f = 0, grid_b = 0;
@@ -138,7 +152,7 @@ struct SolveData {
 void launch_residual(const SolveData& S, double* partials, int n_blocks, cudaStream_t s);
 void launch_axpy_correction(const SolveData& S, cudaStream_t s);   // X += x
 void launch_supernodal_solve(const SolveData& S, cudaStream_t s);  // x = L_FF^{-1} y (FP32)
-int persistent_grid(int d, bool forward);  // resident blocks of the persistent solve kernels
+int persistent_grid(int d, bool forward);  // resident blocks of the dynamic solve kernels
 
 // constant part of the right-hand side: cst = -L_FC b (eliminated order)
 void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, const double* val,

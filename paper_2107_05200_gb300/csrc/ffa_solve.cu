@@ -5,6 +5,8 @@
 // reductions that evaluate the termination test of eqs. primaldualerror/primaldualthresholds.
 #include <math.h>
 
+#include <algorithm>
+
 #include "ffa_internal.h"
 #include "ffa_math.cuh"
 
@@ -222,77 +224,70 @@ __global__ void k_axpy(int n, double* __restrict__ X, const float* __restrict__ 
 // ---------------------------------------------------------------------------
 // supernodal solves.  B_s is column-major with a leading dimension ld that is a
 // multiple of 4, so every lane reads 4 consecutive rows of a column as one
-// float4 and a warp reads 512 contiguous bytes per column.
+// float4.  Every task below runs on a whole block of 256 threads.
 //
-// Forward task (node, r0, c0): rows [r0, r0+128) of B_s times the slice
-// [c0, c0+256) of f = y[cols(s)]; warp w takes columns c0+32w .. c0+32w+31, the
-// eight partial sums are added in shared memory and the 128 row results go out
-// as one set of atomics: rows < n_s into z, rows >= n_s subtracted from y at the
-// structure rows.
+// Wide task (node, r0, c0) of the forward pass: rows [r0, r0+128) of B_s times
+// the slice [c0, c0+256) of f = y[cols(s)]; warp w takes columns c0+32w ..
+// c0+32w+31, the eight partial sums are added in shared memory and the 128 row
+// results go out as one set of atomics: rows < n_s into z, rows >= n_s
+// subtracted from y at the structure rows.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float4 ldg_stream(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
 
-// Narrow nodes (at most 64 columns, the leaves and small separators) would
-// leave most of a wide task's warps idle, so one warp takes one 128-row slice of
-// such a node over all its columns, eight independent warps per block.  The
-// level's task list holds its wide tasks first, then the narrow warp tasks
-// (padded with node = -1 to a multiple of 8).
-constexpr int kNarrowCols = 64;
-
 template <int D>
 __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
                                              const float* __restrict__ blocks, float* __restrict__ y,
                                              float* __restrict__ z, float* smem) {
-  float (*fs)[D] = reinterpret_cast<float (*)[D]>(smem);                       // [256][D]
+  const int W = t.kind;      // columns of this task: a multiple of 8, at most kFwdCols
+  const int cpw = W >> 3;    // columns per warp
+  float (*fs)[D] = reinterpret_cast<float (*)[D]>(smem);                       // [W][D]
   float (*red)[kFwdRows][D] = reinterpret_cast<float (*)[kFwdRows][D]>(smem + kFwdCols * D);  // [8][128][D]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntot = nd.ncol + nd.nrow;
-  const int nc = min(kFwdCols, nd.ncol - t.c0);
+  const int nc = min(W, nd.ncol - t.c0);
+  const int r = t.r0 + 4 * lane;
+  const int cw0 = cpw * warp;
+  const int ncw = (r < nd.ld) ? max(0, min(cpw, nc - cw0)) : 0;
+  const float* B = blocks + nd.blk_off + (int64_t)(t.c0 + cw0) * nd.ld + r;
+  // the first kFwdBatch columns are in flight while f is staged
+  const int n0 = min(kFwdBatch, ncw);
+  float4 b[kFwdBatch];
+#pragma unroll
+  for (int u = 0; u < kFwdBatch; ++u)
+    b[u] = (u < n0) ? ldg_stream(B + (int64_t)u * nd.ld) : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int q = threadIdx.x; q < nc * D; q += 256) {
     const int c = q / D, k = q - c * D;
     fs[c][k] = __ldcg(y + (int64_t)(nd.col0 + t.c0 + c) * D + k);
   }
   __syncthreads();
-  const int r = t.r0 + 4 * lane;
-  const int cw0 = 32 * warp;
-  const int ncw = max(0, min(32, nc - cw0));
   float acc[4][D];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int k = 0; k < D; ++k) acc[q][k] = 0.f;
-  if (r < nd.ld && ncw > 0) {
-    const float* B = blocks + nd.blk_off + (int64_t)(t.c0 + cw0) * nd.ld + r;
-    int c = 0;
-    for (; c + 16 <= ncw; c += 16) {
-      float4 b[16];
+  auto fma_col = [&](const float4& bv, int c) {
 #pragma unroll
-      for (int u = 0; u < 16; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld);
-#pragma unroll
-      for (int u = 0; u < 16; ++u)
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const float f = fs[cw0 + c + u][k];
-          acc[0][k] = fmaf(b[u].x, f, acc[0][k]);
-          acc[1][k] = fmaf(b[u].y, f, acc[1][k]);
-          acc[2][k] = fmaf(b[u].z, f, acc[2][k]);
-          acc[3][k] = fmaf(b[u].w, f, acc[3][k]);
-        }
+    for (int k = 0; k < D; ++k) {
+      const float f = fs[cw0 + c][k];
+      acc[0][k] = fmaf(bv.x, f, acc[0][k]);
+      acc[1][k] = fmaf(bv.y, f, acc[1][k]);
+      acc[2][k] = fmaf(bv.z, f, acc[2][k]);
+      acc[3][k] = fmaf(bv.w, f, acc[3][k]);
     }
-    for (; c < ncw; ++c) {
-      const float4 bv = ldg_stream(B + (int64_t)c * nd.ld);
+  };
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const float f = fs[cw0 + c][k];
-        acc[0][k] = fmaf(bv.x, f, acc[0][k]);
-        acc[1][k] = fmaf(bv.y, f, acc[1][k]);
-        acc[2][k] = fmaf(bv.z, f, acc[2][k]);
-        acc[3][k] = fmaf(bv.w, f, acc[3][k]);
-      }
-    }
+  for (int u = 0; u < kFwdBatch; ++u)
+    if (u < n0) fma_col(b[u], u);
+  int c = n0;
+  for (; c + kFwdBatch <= ncw; c += kFwdBatch) {
+#pragma unroll
+    for (int u = 0; u < kFwdBatch; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld);
+#pragma unroll
+    for (int u = 0; u < kFwdBatch; ++u) fma_col(b[u], c + u);
   }
+  for (; c < ncw; ++c) fma_col(ldg_stream(B + (int64_t)c * nd.ld), c);
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -321,91 +316,104 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
   }
 }
 
-// one warp: rows [r0, r0+128) of a narrow node times all of f = y[cols(s)].
-// The node's z rows lie in its first slice and only this warp writes them.
+// Node task of the forward pass: a whole small node (at most kNarrowCols columns,
+// ld <= kNodeMaxLd) on one block.  Thread (g, j) owns the 4-row group g of the
+// ld/4 groups and the column slice j (columns j, j + S, j + 2S, ...) with
+// S = floor(256 / (ld/4)) slices, so a small node is streamed in one or two
+// rounds of loads; the S partial sums of each row meet in shared memory.  z_s
+// is stored directly (no other task touches it).
 template <int D>
-__device__ __forceinline__ void forward_narrow(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
-                                               const float* __restrict__ blocks, float* __restrict__ y,
-                                               float* __restrict__ z, float (*fw)[D]) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* __restrict__ rows,
+                                             const float* __restrict__ blocks, float* __restrict__ y,
+                                             float* __restrict__ z, float* smem) {
+  float (*f)[D] = reinterpret_cast<float (*)[D]>(smem);    // [kNarrowCols][D]
+  float* red = smem + kNarrowCols * D;                     // [D][S][ld]
   const int ntot = nd.ncol + nd.nrow;
-  for (int q = lane; q < nd.ncol * D; q += 32) {
+  const int G = nd.ld >> 2;
+  const int S = 256 / G;
+  const int g = threadIdx.x % G, j = threadIdx.x / G;
+  const bool active = j < S;
+  const float* B = blocks + nd.blk_off + 4 * g;
+  // columns j, j + S, ..., j + 7S are in flight while f is staged
+  float4 b[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    b[u] = (active && j + u * S < nd.ncol) ? ldg_stream(B + (int64_t)(j + u * S) * nd.ld) : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int q = threadIdx.x; q < nd.ncol * D; q += 256) {
     const int c = q / D, k = q - c * D;
-    fw[c][k] = __ldcg(y + (int64_t)(nd.col0 + c) * D + k);
+    f[c][k] = __ldcg(y + (int64_t)(nd.col0 + c) * D + k);
   }
-  __syncwarp();
-  const int r = t.r0 + 4 * lane;
-  float acc[4][D];
+  __syncthreads();
+  if (active) {
+    float acc[4][D];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int k = 0; k < D; ++k) acc[q][k] = 0.f;
-  if (r < nd.ld) {
-    const float* B = blocks + nd.blk_off + r;
-    int c = 0;
-    for (; c + 8 <= nd.ncol; c += 8) {
-      float4 b[8];
+      for (int k = 0; k < D; ++k) acc[q][k] = 0.f;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld);
+    for (int u = 0; u < 8; ++u)
+      if (j + u * S < nd.ncol) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float fv = f[j + u * S][k];
+          acc[0][k] = fmaf(b[u].x, fv, acc[0][k]);
+          acc[1][k] = fmaf(b[u].y, fv, acc[1][k]);
+          acc[2][k] = fmaf(b[u].z, fv, acc[2][k]);
+          acc[3][k] = fmaf(b[u].w, fv, acc[3][k]);
+        }
+      }
+    int c = j + 8 * S;
+    for (; c + 7 * S < nd.ncol; c += 8 * S) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) b[u] = ldg_stream(B + (int64_t)(c + u * S) * nd.ld);
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const float f = fw[c + u][k];
-          acc[0][k] = fmaf(b[u].x, f, acc[0][k]);
-          acc[1][k] = fmaf(b[u].y, f, acc[1][k]);
-          acc[2][k] = fmaf(b[u].z, f, acc[2][k]);
-          acc[3][k] = fmaf(b[u].w, f, acc[3][k]);
+          const float fv = f[c + u * S][k];
+          acc[0][k] = fmaf(b[u].x, fv, acc[0][k]);
+          acc[1][k] = fmaf(b[u].y, fv, acc[1][k]);
+          acc[2][k] = fmaf(b[u].z, fv, acc[2][k]);
+          acc[3][k] = fmaf(b[u].w, fv, acc[3][k]);
         }
     }
-    for (; c < nd.ncol; ++c) {
+    for (; c < nd.ncol; c += S) {
       const float4 bv = ldg_stream(B + (int64_t)c * nd.ld);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const float f = fw[c][k];
-        acc[0][k] = fmaf(bv.x, f, acc[0][k]);
-        acc[1][k] = fmaf(bv.y, f, acc[1][k]);
-        acc[2][k] = fmaf(bv.z, f, acc[2][k]);
-        acc[3][k] = fmaf(bv.w, f, acc[3][k]);
+        const float fv = f[c][k];
+        acc[0][k] = fmaf(bv.x, fv, acc[0][k]);
+        acc[1][k] = fmaf(bv.y, fv, acc[1][k]);
+        acc[2][k] = fmaf(bv.z, fv, acc[2][k]);
+        acc[3][k] = fmaf(bv.w, fv, acc[3][k]);
       }
     }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      *reinterpret_cast<float4*>(red + (k * S + j) * nd.ld + 4 * g) =
+          make_float4(acc[0][k], acc[1][k], acc[2][k], acc[3][k]);
   }
+  __syncthreads();
+  for (int r = threadIdx.x; r < ntot; r += 256) {
+    float s[D];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int row = r + q;
-    if (row >= ntot) break;
-    if (row < nd.ncol) {
+    for (int k = 0; k < D; ++k) {
+      float a = 0.f;
+      for (int jj = 0; jj < S; ++jj) a += red[(k * S + jj) * nd.ld + r];
+      s[k] = a;
+    }
+    if (r < nd.ncol) {
 #pragma unroll
-      for (int k = 0; k < D; ++k) z[(int64_t)(nd.col0 + row) * D + k] = acc[q][k];
+      for (int k = 0; k < D; ++k) z[(int64_t)(nd.col0 + r) * D + k] = s[k];
     } else {
-      const int rr = __ldg(rows + nd.row_off + (row - nd.ncol));
+      const int rr = __ldg(rows + nd.row_off + (r - nd.ncol));
 #pragma unroll
-      for (int k = 0; k < D; ++k) atomicAdd(y + (int64_t)rr * D + k, -acc[q][k]);
+      for (int k = 0; k < D; ++k) atomicAdd(y + (int64_t)rr * D + k, -s[k]);
     }
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(256) k_forward(const Task* __restrict__ tasks, int n_wide,
-                                                 const NodeDev* __restrict__ nodes, const int32_t* __restrict__ rows,
-                                                 const float* __restrict__ blocks, float* __restrict__ y,
-                                                 float* __restrict__ z) {
-  __shared__ __align__(16) float smem[kFwdCols * D + 8 * kFwdRows * D];
-  if ((int)blockIdx.x < n_wide) {
-    const Task t = tasks[blockIdx.x];
-    const NodeDev nd = nodes[t.node];
-    forward_wide<D>(t, nd, rows, blocks, y, z, smem);
-    return;
-  }
-  const int warp = threadIdx.x >> 5;
-  const Task t = tasks[n_wide + ((int)blockIdx.x - n_wide) * 8 + warp];
-  if (t.node < 0) return;
-  const NodeDev nd = nodes[t.node];
-  float (*fw)[D] = reinterpret_cast<float (*)[D]>(smem + warp * kNarrowCols * D);
-  forward_narrow<D>(t, nd, rows, blocks, y, z, fw);
-}
-
-// Backward task (node, r0, c0): output columns [c0, c0+32) of x_s against rows
+// Backward wide task (node, r0, c0): output columns [c0, c0+32) of x_s against rows
 // [r0, r0+1024) of B_s, v = [z_s ; -x at the structure rows] staged in shared
 // memory.  Warp w owns columns c0+4w .. c0+4w+3; each lane reads 4 rows of each
 // of them per step; the 4 column dot products are reduced across the warp.
@@ -415,7 +423,20 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
                                               float* __restrict__ x, float* smem) {
   float (*vs)[kBwdRows] = reinterpret_cast<float (*)[kBwdRows]>(smem);   // [D][1024]
   const int ntot = nd.ncol + nd.nrow;
-  const int nr = min(kBwdRows, nd.ld - t.r0);     // a multiple of 4
+  const int nr = min(t.kind, nd.ld - t.r0);     // rows of this task: a multiple of 4
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = t.c0 + 4 * warp;
+  const int ncw = max(0, min(4, nd.ncol - j0));
+  const float* B = blocks + nd.blk_off + (int64_t)min(j0, nd.ncol - 1) * nd.ld + t.r0;
+  // rows above the diagonal of inv(L_ss) are stored zeros: start at the first
+  // 4-row group that can be nonzero for this warp's first column
+  const int rs = max(0, (j0 - t.r0) & ~3);
+  // the first row step is in flight while v is staged
+  const int ra = rs + 4 * lane;
+  float4 pa[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    pa[q] = (q < ncw && ra < nr) ? ldg_stream(B + (int64_t)q * nd.ld + ra) : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int r = threadIdx.x; r < nr; r += 256) {
     const int row = t.r0 + r;
 #pragma unroll
@@ -427,35 +448,32 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
     }
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j0 = t.c0 + 4 * warp;
-  if (j0 >= nd.ncol) return;
-  const int ncw = min(4, nd.ncol - j0);
+  if (ncw == 0) return;
   float acc[4][D];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int k = 0; k < D; ++k) acc[q][k] = 0.f;
-  const float* B = blocks + nd.blk_off + (int64_t)j0 * nd.ld + t.r0;
-  // rows above the diagonal of inv(L_ss) are stored zeros: start at the first
-  // 4-row group that can be nonzero for this warp's first column
-  const int rs = max(0, (j0 - t.r0) & ~3);
-#pragma unroll 4
-  for (int r = rs + 4 * lane; r < nr; r += 128) {
-    float4 b[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) b[q] = (q < ncw) ? ldg_stream(B + (int64_t)q * nd.ld + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+  auto step = [&](const float4 (&bq)[4], int r) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const float4 v = *reinterpret_cast<const float4*>(&vs[k][r]);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        acc[q][k] = fmaf(b[q].x, v.x, acc[q][k]);
-        acc[q][k] = fmaf(b[q].y, v.y, acc[q][k]);
-        acc[q][k] = fmaf(b[q].z, v.z, acc[q][k]);
-        acc[q][k] = fmaf(b[q].w, v.w, acc[q][k]);
+        acc[q][k] = fmaf(bq[q].x, v.x, acc[q][k]);
+        acc[q][k] = fmaf(bq[q].y, v.y, acc[q][k]);
+        acc[q][k] = fmaf(bq[q].z, v.z, acc[q][k]);
+        acc[q][k] = fmaf(bq[q].w, v.w, acc[q][k]);
       }
     }
+  };
+  if (ra < nr) step(pa, ra);
+#pragma unroll 2
+  for (int r = ra + 128; r < nr; r += 128) {
+    float4 bq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bq[q] = (q < ncw) ? ldg_stream(B + (int64_t)q * nd.ld + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+    step(bq, r);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -473,114 +491,160 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
   }
 }
 
-// one warp: a whole narrow node (<= 64 columns, ld <= 256).  v is staged in the
-// warp's shared slice; lane j owns output columns j and j+32 and streams its own
-// column of B_s (rows below the diagonal only), so no cross-lane reduction is
-// needed and x_s is written directly (no other task touches it).
+// Node task of the backward pass: a whole small node on one block.  v is staged
+// in shared memory; each warp takes 4 columns at a time with 8 lanes per column,
+// so a warp-wide load reads 128 contiguous bytes of each of 4 columns, and the
+// 8 partial dot products of a column meet by shuffles.  Rows above the diagonal
+// of inv(L_ss) are stored zeros: a column j starts at row 32 floor(j / 32).
 template <int D>
-__device__ __forceinline__ void backward_narrow(const NodeDev& nd, const int32_t* __restrict__ rows,
-                                                const float* __restrict__ blocks, const float* __restrict__ z,
-                                                float* __restrict__ x, float (*vw)[256]) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* __restrict__ rows,
+                                              const float* __restrict__ blocks, const float* __restrict__ z,
+                                              float* __restrict__ x, float* smem) {
   const int ntot = nd.ncol + nd.nrow;
-  for (int r = lane; r < nd.ld; r += 32) {
+  const int ld = nd.ld;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cg = lane >> 3, rl = lane & 7;
+  // the first 4 row steps of this lane's first column are in flight while v is staged
+  float4 pre[4];
+  {
+    const int j = 4 * warp + cg;
+    const float* B = blocks + nd.blk_off + (int64_t)min(j, nd.ncol - 1) * ld;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      float val = 0.f;
-      if (r < nd.ncol) val = __ldcg(z + (int64_t)(nd.col0 + r) * D + k);
-      else if (r < ntot) val = -__ldcg(x + (int64_t)__ldg(rows + nd.row_off + (r - nd.ncol)) * D + k);
-      vw[k][r] = val;
+    for (int u = 0; u < 4; ++u) {
+      const int r = 4 * rl + 32 * u;
+      pre[u] = (j < nd.ncol && r < ld) ? ldg_stream(B + r) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  __syncwarp();
-  for (int j = lane; j < nd.ncol; j += 32) {
-    const float* B = blocks + nd.blk_off + (int64_t)j * nd.ld;
+  for (int r = threadIdx.x; r < ld; r += 256) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float v = 0.f;
+      if (r < nd.ncol) v = __ldcg(z + (int64_t)(nd.col0 + r) * D + k);
+      else if (r < ntot) v = -__ldcg(x + (int64_t)__ldg(rows + nd.row_off + (r - nd.ncol)) * D + k);
+      smem[k * ld + r] = v;
+    }
+  }
+  __syncthreads();
+  for (int j0 = 4 * warp; j0 < nd.ncol; j0 += 32) {
+    const int j = j0 + cg;
     float acc[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) acc[k] = 0.f;
-    int r = j & ~3;
-    for (; r + 16 <= nd.ld; r += 16) {
-      float4 b[4];
+    if (j < nd.ncol) {
+      const float* B = blocks + nd.blk_off + (int64_t)j * ld;
+      int r = (j0 & ~31) + 4 * rl;
+      if (j0 < 32) {   // the prefetched rows 4 rl + 32 u, u < 4
 #pragma unroll
-      for (int u = 0; u < 4; ++u) b[u] = ldg_stream(B + r + 4 * u);
+        for (int u = 0; u < 4; ++u) {
+          const int rr = 4 * rl + 32 * u;
+          if (rr < ld) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+            for (int k = 0; k < D; ++k) {
+              const float4 v = *reinterpret_cast<const float4*>(smem + k * ld + rr);
+              acc[k] = fmaf(pre[u].x, v.x, acc[k]);
+              acc[k] = fmaf(pre[u].y, v.y, acc[k]);
+              acc[k] = fmaf(pre[u].z, v.z, acc[k]);
+              acc[k] = fmaf(pre[u].w, v.w, acc[k]);
+            }
+          }
+        }
+        r += 128;
+      }
+#pragma unroll 4
+      for (; r < ld; r += 32) {
+        const float4 b = ldg_stream(B + r);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const float4 v = *reinterpret_cast<const float4*>(&vw[k][r + 4 * u]);
-          acc[k] = fmaf(b[u].x, v.x, acc[k]);
-          acc[k] = fmaf(b[u].y, v.y, acc[k]);
-          acc[k] = fmaf(b[u].z, v.z, acc[k]);
-          acc[k] = fmaf(b[u].w, v.w, acc[k]);
+          const float4 v = *reinterpret_cast<const float4*>(smem + k * ld + r);
+          acc[k] = fmaf(b.x, v.x, acc[k]);
+          acc[k] = fmaf(b.y, v.y, acc[k]);
+          acc[k] = fmaf(b.z, v.z, acc[k]);
+          acc[k] = fmaf(b.w, v.w, acc[k]);
         }
-    }
-    for (; r < nd.ld; r += 4) {
-      const float4 bv = ldg_stream(B + r);
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const float4 v = *reinterpret_cast<const float4*>(&vw[k][r]);
-        acc[k] = fmaf(bv.x, v.x, acc[k]);
-        acc[k] = fmaf(bv.y, v.y, acc[k]);
-        acc[k] = fmaf(bv.z, v.z, acc[k]);
-        acc[k] = fmaf(bv.w, v.w, acc[k]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < D; ++k) x[(int64_t)(nd.col0 + j) * D + k] = acc[k];
+    for (int k = 0; k < D; ++k) {
+      float a = acc[k];
+      a += __shfl_xor_sync(0xffffffffu, a, 4);
+      a += __shfl_xor_sync(0xffffffffu, a, 2);
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      acc[k] = a;
+    }
+    if (rl == 0 && j < nd.ncol) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) x[(int64_t)(nd.col0 + j) * D + k] = acc[k];
+    }
   }
+}
+
+// shared memory of one solve block (floats): the larger of the wide and node tasks
+template <int D>
+struct SolveSmem {
+  static constexpr int kFwd = (kFwdCols + 8 * kFwdRows) * D > (kNarrowCols + kNodeMaxLd) * D
+                                  ? (kFwdCols + 8 * kFwdRows) * D : (kNarrowCols + kNodeMaxLd) * D;
+  static constexpr int kBwd = D * (kBwdRows > kNodeMaxLd ? kBwdRows : kNodeMaxLd);
+};
+
+template <int D>
+__device__ __forceinline__ void forward_task(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
+                                             const float* __restrict__ blocks, float* __restrict__ y,
+                                             float* __restrict__ z, float* smem) {
+  if (t.kind != 1) forward_wide<D>(t, nd, rows, blocks, y, z, smem);
+  else forward_node<D>(nd, rows, blocks, y, z, smem);
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_backward(const Task* __restrict__ tasks, int n_wide,
-                                                  const NodeDev* __restrict__ nodes, const int32_t* __restrict__ rows,
-                                                  const float* __restrict__ blocks, const float* __restrict__ z,
-                                                  float* __restrict__ x) {
-  constexpr int kSmem = (D * kBwdRows > 8 * D * 256) ? D * kBwdRows : 8 * D * 256;
-  __shared__ __align__(16) float smem[kSmem];
-  if ((int)blockIdx.x < n_wide) {
-    const Task t = tasks[blockIdx.x];
-    const NodeDev nd = nodes[t.node];
-    backward_wide<D>(t, nd, rows, blocks, z, x, smem);
-    return;
-  }
-  const int warp = threadIdx.x >> 5;
-  const Task t = tasks[n_wide + ((int)blockIdx.x - n_wide) * 8 + warp];
-  if (t.node < 0) return;
-  backward_narrow<D>(nodes[t.node], rows, blocks, z, x, reinterpret_cast<float (*)[256]>(smem + warp * D * 256));
+__device__ __forceinline__ void backward_task(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
+                                              const float* __restrict__ blocks, const float* __restrict__ z,
+                                              float* __restrict__ x, float* smem) {
+  if (t.kind != 1) backward_wide<D>(t, nd, rows, blocks, z, x, smem);
+  else backward_node<D>(nd, rows, blocks, z, x, smem);
+}
+
+// level-synchronous schedule: one launch per level, one task per block
+template <int D>
+__global__ void __launch_bounds__(256, 4) k_forward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+                                                 const int32_t* __restrict__ rows, const float* __restrict__ blocks,
+                                                 float* __restrict__ y, float* __restrict__ z) {
+  __shared__ __align__(16) float smem[SolveSmem<D>::kFwd];
+  const Task t = tasks[blockIdx.x];
+  forward_task<D>(t, nodes[t.node], rows, blocks, y, z, smem);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256, 4) k_backward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+                                                  const int32_t* __restrict__ rows, const float* __restrict__ blocks,
+                                                  const float* __restrict__ z, float* __restrict__ x) {
+  __shared__ __align__(16) float smem[SolveSmem<D>::kBwd];
+  const Task t = tasks[blockIdx.x];
+  backward_task<D>(t, nodes[t.node], rows, blocks, z, x, smem);
 }
 
 // ---------------------------------------------------------------------------
-// Persistent schedule: one launch per pass.  Blocks claim work items in
-// dependency order (forward: leaves first; backward: root first) from a global
-// counter, wait until the tasks their node depends on are done (forward: its
-// nearest descendants with tasks; backward: its nearest ancestor with tasks),
-// run the same per-task code as the level-synchronous kernels, and count the
-// task as done.  Every waited-on task was claimed earlier by a running block,
-// so the waits end; each wait is still bounded and sets err_flag instead of
-// spinning on.
+// Dynamic schedule: one launch per pass over a ready queue.  The queue starts
+// with the tasks of the nodes that depend on nothing (forward: the nodes with no
+// descendant that has tasks; backward: the roots).  Blocks claim queue slots in
+// order and run the task found there.  The block that finishes the last task of
+// a node decrements the pending count of each node waiting on it (forward: its
+// nearest ancestor with tasks; backward: the nodes whose nearest ancestor with
+// tasks it is) and appends the tasks of every node whose count reached zero.
+// A block therefore only ever waits for a slot to be filled, never for a
+// particular node, and no block holds a task whose inputs are incomplete.
+// Every slot is filled exactly once (each node becomes ready once), so the waits
+// end; each is still bounded and sets err_flag instead of spinning on.
 // ---------------------------------------------------------------------------
 constexpr long long kSpinLimit = 1LL << 22;   // polls of ~100 ns (~0.4 s) before giving up
+constexpr int kMaxPush = 16;                  // nodes made ready by one completion handled per round
 
-// the plain-data part of SolveData that the persistent kernels need
-struct PersistView {
-  const Task* fwd_tasks;
-  const Task* bwd_tasks;
+struct DynView {
+  DynPass P;
   const NodeDev* nodes;
   const int32_t* rows;
   const float* blocks;
   float* y;
   float* z;
   float* x;
-  const int2* items_f;
-  const int2* items_b;
-  int n_items_f, n_items_b;
-  const int32_t* need_f;
-  const int32_t* need_b;
-  const int32_t* fchild_ptr;
-  const int32_t* fchild;
-  const int32_t* bpar;
-  int32_t* sync;
-  int n_nodes;
   int32_t* err_flag;
 };
 
@@ -590,102 +654,118 @@ __device__ __forceinline__ int ld_acquire(const int32_t* p) {
   return v;
 }
 
-// Once any wait has given up (err set), every later wait returns at once, so a
-// failure costs one timeout, not one per task.
-__device__ __forceinline__ void wait_count(const int32_t* p, int need, int32_t* err) {
-  long long it = 0;
-  while (ld_acquire(p) < need) {
-    if (++it > kSpinLimit || ld_acquire(err) != 0) {
-      atomicExch(err, 1);
-      return;
-    }
-    __nanosleep(100);
-  }
+__device__ __forceinline__ void st_relaxed(int32_t* p, int v) {
+  asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void wait_children(const PersistView& S, int node) {
-  for (int q = S.fchild_ptr[node]; q < S.fchild_ptr[node + 1]; ++q) {
-    const int c = S.fchild[q];
-    wait_count(S.sync + c, S.need_f[c], S.err_flag);
-  }
-}
-
-template <int D>
-__global__ void __launch_bounds__(256) k_forward_persistent(PersistView S) {
-  __shared__ __align__(16) float smem[kFwdCols * D + 8 * kFwdRows * D];
-  __shared__ int item_s;
-  int32_t* counter = S.sync + 2 * S.n_nodes;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+template <int D, bool FWD>
+__global__ void __launch_bounds__(256, 4) k_solve_dynamic(DynView V) {
+  __shared__ __align__(16) float smem[FWD ? SolveSmem<D>::kFwd : SolveSmem<D>::kBwd];
+  __shared__ int item_s, slot_s, n_push_s, next_s;
+  __shared__ int push_s[kMaxPush][3];   // first task, queue position, count
+  const DynPass& P = V.P;
+  if (threadIdx.x == 0) slot_s = atomicAdd(P.ctr, 1);
   for (;;) {
-    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+    if (threadIdx.x == 0) {
+      int t = -1;
+      const int h = slot_s;
+      if (h < P.n_tasks) {
+        long long it = 0;
+        while ((t = ld_acquire(P.queue + h)) < 0) {
+          if (++it > kSpinLimit || ld_acquire(V.err_flag) != 0) {
+            atomicExch(V.err_flag, 1);
+            t = -1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      item_s = t;
+    }
     __syncthreads();
-    const int item = item_s;
-    if (item >= S.n_items_f) break;
-    const int2 it = S.items_f[item];
-    if (it.y == 0) {
-      const Task t = S.fwd_tasks[it.x];
-      const NodeDev nd = S.nodes[t.node];
-      if (threadIdx.x == 0) wait_children(S, t.node);
-      __syncthreads();
-      forward_wide<D>(t, nd, S.rows, S.blocks, S.y, S.z, smem);
+    const int ti = item_s;
+    if (ti < 0) break;
+    const Task t = P.tasks[ti];
+    const NodeDev nd = V.nodes[t.node];
+    if constexpr (FWD) forward_task<D>(t, nd, V.rows, V.blocks, V.y, V.z, smem);
+    else backward_task<D>(t, nd, V.rows, V.blocks, V.z, V.x, smem);
+    __syncthreads();
+    // the next slot is claimed while the completion below is worked out
+    if (threadIdx.x == 32) slot_s = atomicAdd(P.ctr, 1);
+    // completion: the block's writes are released by one fence after the barrier
+    // (fences are cumulative); the block that ends a node decrements the pending
+    // counts of the nodes waiting on it and reserves queue room for every node
+    // that became ready
+    int q = 0, q_end = 0;
+    if (threadIdx.x == 0) {
       __threadfence();
+      q_end = -1;
+      if (t.kind == 1 || atomicAdd(P.done + t.node, 1) == P.ntask[t.node] - 1) {
+        q = P.dep_ptr[t.node];
+        q_end = P.dep_ptr[t.node + 1];
+      }
+      next_s = q;
+      n_push_s = q_end;
+    }
+    __syncthreads();
+    q = next_s;
+    q_end = n_push_s;
+    while (q < q_end) {   // block-uniform
+      __syncthreads();    // everyone has read next_s / n_push_s / push_s
+      if (threadIdx.x == 0) {
+        int n = 0;
+        int qq = q;
+        for (; qq < q_end && n < kMaxPush; ++qq) {
+          const int p = P.dep[qq];
+          if (atomicSub(P.pending + p, 1) == 1) {
+            const int cnt = P.ntask[p];
+            push_s[n][0] = P.task0[p];
+            push_s[n][1] = atomicAdd(P.ctr + 1, cnt);
+            push_s[n][2] = cnt;
+            ++n;
+          }
+        }
+        if (n > 0) __threadfence();   // acquire the other dependencies' releases
+        n_push_s = n;
+        next_s = qq;
+      }
       __syncthreads();
-      if (threadIdx.x == 0) atomicAdd(S.sync + t.node, 1);
-    } else {
-      const Task t = S.fwd_tasks[it.x + warp];
-      if (t.node >= 0) {
-        if (lane == 0) wait_children(S, t.node);
-        __syncwarp();
-        const NodeDev nd = S.nodes[t.node];
-        forward_narrow<D>(t, nd, S.rows, S.blocks, S.y, S.z,
-                          reinterpret_cast<float (*)[D]>(smem + warp * kNarrowCols * D));
+      const int n = n_push_s;
+      q = next_s;
+      if (n > 0) {
         __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicAdd(S.sync + t.node, 1);
+        for (int e = 0; e < n; ++e)
+          for (int i = threadIdx.x; i < push_s[e][2]; i += 256) st_relaxed(P.queue + push_s[e][1] + i, push_s[e][0] + i);
       }
     }
-    __syncthreads();   // item_s and smem are reused by the next item
+    __syncthreads();   // item_s, slot_s and the push records are reused
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(256) k_backward_persistent(PersistView S) {
-  constexpr int kSmem = (D * kBwdRows > 8 * D * 256) ? D * kBwdRows : 8 * D * 256;
-  __shared__ __align__(16) float smem[kSmem];
-  __shared__ int item_s;
-  int32_t* counter = S.sync + 2 * S.n_nodes + 1;
-  int32_t* done_b = S.sync + S.n_nodes;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (;;) {
-    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
-    __syncthreads();
-    const int item = item_s;
-    if (item >= S.n_items_b) break;
-    const int2 it = S.items_b[item];
-    if (it.y == 0) {
-      const Task t = S.bwd_tasks[it.x];
-      const NodeDev nd = S.nodes[t.node];
-      const int p = S.bpar[t.node];
-      if (threadIdx.x == 0 && p >= 0) wait_count(done_b + p, S.need_b[p], S.err_flag);
-      __syncthreads();
-      backward_wide<D>(t, nd, S.rows, S.blocks, S.z, S.x, smem);
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) atomicAdd(done_b + t.node, 1);
-    } else {
-      const Task t = S.bwd_tasks[it.x + warp];
-      if (t.node >= 0) {
-        const int p = S.bpar[t.node];
-        if (lane == 0 && p >= 0) wait_count(done_b + p, S.need_b[p], S.err_flag);
-        __syncwarp();
-        backward_narrow<D>(S.nodes[t.node], S.rows, S.blocks, S.z, S.x,
-                           reinterpret_cast<float (*)[256]>(smem + warp * D * 256));
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicAdd(done_b + t.node, 1);
-      }
+// restores the ready queues, pending counts and completion counts of both passes
+// and zeroes z and x (both are accumulated with atomics)
+__global__ void k_dyn_reset(DynPass F, DynPass B, int n_nodes, float* __restrict__ z, float* __restrict__ x,
+                            int64_t nzx, int64_t n_all) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_all; i += stride) {
+    if (i < nzx) {
+      z[i] = 0.f;
+      x[i] = 0.f;
     }
-    __syncthreads();
+    if (i < F.n_tasks) F.queue[i] = F.q_init[i];
+    if (i < B.n_tasks) B.queue[i] = B.q_init[i];
+    if (i < n_nodes) {
+      F.pending[i] = F.pending_init[i];
+      B.pending[i] = B.pending_init[i];
+      F.done[i] = 0;
+      B.done[i] = 0;
+    }
+    if (i == 0) {
+      F.ctr[0] = 0;
+      F.ctr[1] = F.n_init;
+      B.ctr[0] = 0;
+      B.ctr[1] = B.n_init;
+    }
   }
 }
 
@@ -834,20 +914,20 @@ void launch_axpy_correction(const SolveData& S, cudaStream_t s) {
 }
 
 void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
-  const size_t bytes = (size_t)S.nF * S.d * sizeof(float);
-  cudaMemsetAsync(S.z, 0, bytes, s);
-  cudaMemsetAsync(S.x, 0, bytes, s);
+  const int64_t nzx = (int64_t)S.nF * S.d;
+  const int64_t n_all = std::max<int64_t>(std::max<int64_t>(nzx, S.n_nodes),
+                                          std::max<int64_t>(S.fdyn.n_tasks, S.bdyn.n_tasks));
+  const int reset_grid = (int)std::min<int64_t>((n_all + 255) / 256, 4096);
+  k_dyn_reset<<<reset_grid, 256, 0, s>>>(S.fdyn, S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
   if (S.schedule == 1) {
-    cudaMemsetAsync(S.sync, 0, (size_t)(2 * S.n_nodes + 2) * sizeof(int32_t), s);
-    PersistView v{S.fwd_tasks, S.bwd_tasks, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.items_f, S.items_b,
-                  S.n_items_f, S.n_items_b, S.need_f, S.need_b, S.fchild_ptr, S.fchild, S.bpar, S.sync,
-                  S.n_nodes, S.err_flag};
+    const DynView vf{S.fdyn, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
+    const DynView vb{S.bdyn, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
     if (S.d == 2) {
-      k_forward_persistent<2><<<S.grid_f, 256, 0, s>>>(v);
-      k_backward_persistent<2><<<S.grid_b, 256, 0, s>>>(v);
+      k_solve_dynamic<2, true><<<S.grid_f, 256, 0, s>>>(vf);
+      k_solve_dynamic<2, false><<<S.grid_b, 256, 0, s>>>(vb);
     } else {
-      k_forward_persistent<3><<<S.grid_f, 256, 0, s>>>(v);
-      k_backward_persistent<3><<<S.grid_b, 256, 0, s>>>(v);
+      k_solve_dynamic<3, true><<<S.grid_f, 256, 0, s>>>(vf);
+      k_solve_dynamic<3, false><<<S.grid_b, 256, 0, s>>>(vb);
     }
     return;
   }
@@ -855,18 +935,14 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   for (int l = 0; l < L; ++l) {
     const int64_t nt = S.fwd_off[l + 1] - S.fwd_off[l];
     if (nt <= 0) continue;
-    const int nw = (int)S.fwd_wide[l];
-    const unsigned grid = (unsigned)(nw + (nt - nw) / 8);
-    if (S.d == 2) k_forward<2><<<grid, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], nw, S.nodes, S.rows, S.blocks, S.y, S.z);
-    else k_forward<3><<<grid, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], nw, S.nodes, S.rows, S.blocks, S.y, S.z);
+    if (S.d == 2) k_forward<2><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+    else k_forward<3><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
   }
   for (int l = L - 1; l >= 0; --l) {
     const int64_t nt = S.bwd_off[l + 1] - S.bwd_off[l];
     if (nt <= 0) continue;
-    const int nw = (int)S.bwd_wide[l];
-    const unsigned grid = (unsigned)(nw + (nt - nw) / 8);
-    if (S.d == 2) k_backward<2><<<grid, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], nw, S.nodes, S.rows, S.blocks, S.z, S.x);
-    else k_backward<3><<<grid, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], nw, S.nodes, S.rows, S.blocks, S.z, S.x);
+    if (S.d == 2) k_backward<2><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
+    else k_backward<3><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
   }
 }
 
@@ -875,10 +951,10 @@ int persistent_grid(int d, bool forward) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
-  if (forward) e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_forward_persistent<2>, 256, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_forward_persistent<3>, 256, 0);
-  else e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward_persistent<2>, 256, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward_persistent<3>, 256, 0);
+  if (forward) e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<2, true>, 256, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<3, true>, 256, 0);
+  else e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<2, false>, 256, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<3, false>, 256, 0);
   if (e != cudaSuccess || per < 1) per = 1;
   return sms * per;
 }
