@@ -16,6 +16,7 @@ a bounded sample of the same workload family instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -65,6 +66,40 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+SOLVE_PROFILE = os.path.join(ROOT, "profiles", "k_solve_dynamic_cube48.md")
+
+
+def solve_fingerprint() -> str:
+    """sha256 of the device code of the supernodal solves (the kernels the ncu
+    traffic figure was taken on) and of the task-shape constants."""
+    csrc = os.path.join(ROOT, "paper_2107_05200_gb300", "csrc")
+    with open(os.path.join(csrc, "ffa_solve.cu")) as f:
+        src = f.read()
+    a = src.index("// supernodal solves.")
+    b = src.index("}  // namespace\n", a)
+    with open(os.path.join(csrc, "ffa_internal.h")) as f:
+        consts = "".join(line for line in f if line.startswith("constexpr"))
+    return hashlib.sha256((src[a:b] + consts).encode()).hexdigest()[:16]
+
+
+def profiled_solve_traffic():
+    """DRAM bytes per full-size forward and backward launch from the committed ncu
+    summary, or None when the solve kernels changed since it was taken."""
+    if not os.path.exists(SOLVE_PROFILE):
+        return None
+    fp, fwd, bwd = None, None, None
+    with open(SOLVE_PROFILE) as f:
+        for line in f:
+            if line.startswith("fingerprint:"):
+                fp = line.split(":", 1)[1].strip().strip("`")
+            elif line.startswith("full-size traffic per launch (bytes):"):
+                parts = dict(x.strip().split(" ") for x in line.split(":", 1)[1].split(","))
+                fwd, bwd = int(parts["forward"]), int(parts["backward"])
+    if fp != solve_fingerprint() or fwd is None:
+        return None
+    return fwd, bwd
 
 
 class ClockSampler:
@@ -269,6 +304,10 @@ def main():
     hbm_peak, peak_kind = measured_peaks()
     local_gbs = info["bytes_local_step"] / (ph["ms_local"] / 1e3) / 1e9
     wstep_gbs = args.sweeps * info["bytes_global_sweep"] / (ph["ms_wstep"] / 1e3) / 1e9
+    # dominant kernel: the triangular passes of the W step (forward + backward per sweep)
+    ms_pass = 0.5 * (ph["ms_solve_forward"] + ph["ms_solve_backward"])
+    solve_gbs = info["bytes_solve_pass"] / (ms_pass / 1e3) / 1e9
+    traffic = profiled_solve_traffic() if args.cells == 64 and args.precision == "fp32" else None
     resid = sol.wstep_residual()
 
     # end to end through the public API with host buffers: init from pinned host W0,
@@ -296,9 +335,20 @@ def main():
                    "solve_schedule": "dynamic" if args.schedule == 1 else "per_level",
                    "l2": "working set > L2 (factor + element state), no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "achieved": local_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": local_gbs / hbm_peak, "traffic": None,
-                     "kernel": "k_local_step", "peak_kind": peak_kind},
+        "roofline": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": solve_gbs / hbm_peak,
+                     "traffic": None if traffic is None else 0.5 * (traffic[0] + traffic[1]),
+                     "kernel": "k_solve_dynamic (W-step triangular passes, forward and backward)",
+                     "bytes_per_launch": info["bytes_solve_pass"], "ms_per_launch": ms_pass,
+                     "launches_per_step": 2 * args.sweeps, "peak_kind": peak_kind},
+        "kernels": {
+            "k_solve_dynamic_forward": {"ms": ph["ms_solve_forward"],
+                                        "gbs": info["bytes_solve_pass"] / ph["ms_solve_forward"] / 1e6},
+            "k_solve_dynamic_backward": {"ms": ph["ms_solve_backward"],
+                                         "gbs": info["bytes_solve_pass"] / ph["ms_solve_backward"] / 1e6},
+            "k_local_step": {"ms": ph["ms_local"], "gbs": local_gbs, "frac": local_gbs / hbm_peak,
+                             "bytes": info["bytes_local_step"]},
+        },
         "phases_ms": {k: v for k, v in ph.items() if k != "reps"},
         "wstep": {"achieved_gbs": wstep_gbs, "frac": wstep_gbs / hbm_peak,
                   "factor_entries": info["factor_entries"], "rel_residual": resid},

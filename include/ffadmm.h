@@ -111,6 +111,9 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the context */
   int64_t bytes_local_step;   /* algorithmic bytes of one local-step launch */
   int64_t bytes_global_sweep; /* algorithmic bytes of one W-step refinement sweep */
+  int64_t bytes_solve_pass;   /* algorithmic bytes of one triangular pass (forward or backward):
+                                 the stored nonzeros of every B_s, its structure indices, and
+                                 the pass's input and output vectors */
   int32_t kernels_per_iteration; /* kernel launches of one iteration without the test */
   int32_t kernels_per_check;     /* extra launches of an iteration that runs the test */
 } ffa_info;
@@ -123,6 +126,8 @@ typedef struct {
   double ms_local;     /* fused local step (U, P, Lambda) */
   double ms_check;     /* termination test of one check iteration */
   double ms_iteration; /* whole iteration, launched one kernel at a time */
+  double ms_solve_forward;   /* one forward triangular pass of the W step (last sweep) */
+  double ms_solve_backward;  /* one backward triangular pass of the W step (last sweep) */
 } ffa_phase_times;
 
 /* Fill *p with the defaults: symmetric Dirichlet, rho 1, eps_abs 1e-6, eps_rel 1e-5,

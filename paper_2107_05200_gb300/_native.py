@@ -57,7 +57,8 @@ class Info(C.Structure):
                 ("factor_flops", C.c_int64), ("n_supernodes", C.c_int32), ("n_levels", C.c_int32),
                 ("setup_seconds_analyze", C.c_double), ("setup_seconds_factor", C.c_double),
                 ("device_bytes", C.c_int64), ("bytes_local_step", C.c_int64),
-                ("bytes_global_sweep", C.c_int64), ("kernels_per_iteration", C.c_int32),
+                ("bytes_global_sweep", C.c_int64), ("bytes_solve_pass", C.c_int64),
+                ("kernels_per_iteration", C.c_int32),
                 ("kernels_per_check", C.c_int32)]
 
     def as_dict(self) -> dict:
@@ -77,7 +78,8 @@ class Tuning(C.Structure):
 class PhaseTimes(C.Structure):
     _fields_ = [("reps", C.c_int32), ("ms_gather", C.c_double), ("ms_wstep", C.c_double),
                 ("ms_vertex", C.c_double), ("ms_local", C.c_double), ("ms_check", C.c_double),
-                ("ms_iteration", C.c_double)]
+                ("ms_iteration", C.c_double), ("ms_solve_forward", C.c_double),
+                ("ms_solve_backward", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -97,6 +97,7 @@ struct ffa_ctx {
   int narrow_cols = 64;
   int schedule = 0;             // supernodal solves: 0 one launch per level, 1 dynamic
   DynPass fdyn, bdyn;           // dynamic schedule of the forward and backward passes
+  cudaEvent_t solve_ev[3] = {nullptr, nullptr, nullptr};  // set only while ffa_profile_phases runs
   int32_t* err_flag = nullptr;
   int grid_f = 0, grid_b = 0;
   std::vector<Supernode> nodes_h;  // host copy of the supernode table (task lists are rebuilt from it)
@@ -290,6 +291,7 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.schedule = ctx->schedule;
   S.fdyn = ctx->fdyn;
   S.bdyn = ctx->bdyn;
+  for (int i = 0; i < 3; ++i) S.ev[i] = ctx->solve_ev[i];
   S.n_nodes = (int)ctx->nodes_h.size();
   S.err_flag = ctx->err_flag;
   S.grid_f = ctx->grid_f;
@@ -922,8 +924,11 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
       (int64_t)n * d * 16;
   int64_t nz = 0;
   for (const Supernode& sn : fac.nodes) nz += (int64_t)sn.ncol * sn.nrow + (int64_t)sn.ncol * (sn.ncol + 1) / 2;
+  int64_t nstruct = 0;
+  for (const Supernode& sn : fac.nodes) nstruct += sn.nrow;
   // (forward and backward each read every nonzero of every B_s once)
   ctx->info.bytes_global_sweep = 2 * nz * 4 + (int64_t)width * nF * 12 + (int64_t)nF * d * (8 * 3 + 4 * 6);
+  ctx->info.bytes_solve_pass = nz * 4 + nstruct * 4 + (int64_t)2 * nF * d * 4;
   ctx->info.n = n;
   ctx->info.m = m;
   ctx->info.d = d;
@@ -1290,12 +1295,19 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out) 
   if (reps < 1) return fail(ctx, FFA_ERR_INVALID_ARG, "reps < 1");
   cudaEvent_t ev[PH_N + 1];
   for (auto& e : ev) FFA_CUDA(cudaEventCreate(&e));
+  for (auto& e : ctx->solve_ev) FFA_CUDA(cudaEventCreate(&e));
   double acc[PH_N + 1] = {0};
+  double acc_f = 0.0, acc_b = 0.0;
   for (int r = 0; r < reps; ++r) {
     FFA_CUDA(cudaEventRecord(ev[PH_N], ctx->stream));
     enqueue_iteration(ctx, r == reps - 1, ev);
     FFA_CUDA(cudaGetLastError());
     FFA_CUDA(cudaEventSynchronize(ev[PH_CHECK]));
+    float tf, tb;
+    FFA_CUDA(cudaEventElapsedTime(&tf, ctx->solve_ev[0], ctx->solve_ev[1]));
+    FFA_CUDA(cudaEventElapsedTime(&tb, ctx->solve_ev[1], ctx->solve_ev[2]));
+    acc_f += tf;
+    acc_b += tb;
     float t[PH_N];
     FFA_CUDA(cudaEventElapsedTime(&t[PH_GATHER], ev[PH_N], ev[PH_GATHER]));
     for (int p = 1; p < PH_N; ++p) FFA_CUDA(cudaEventElapsedTime(&t[p], ev[p - 1], ev[p]));
@@ -1306,8 +1318,14 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out) 
     acc[PH_N] += whole;
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  for (auto& e : ctx->solve_ev) {
+    cudaEventDestroy(e);
+    e = nullptr;
+  }
   ctx->iter_total += reps;
   out->reps = reps;
+  out->ms_solve_forward = acc_f / reps;
+  out->ms_solve_backward = acc_b / reps;
   out->ms_gather = acc[PH_GATHER] / reps;
   out->ms_wstep = acc[PH_WSTEP] / reps;
   out->ms_vertex = acc[PH_VERTEX] / reps;

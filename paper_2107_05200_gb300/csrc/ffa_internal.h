@@ -142,6 +142,7 @@ struct SolveData {
   int n_nodes = 0;
   int32_t* err_flag = nullptr;      // set to 1 if a wait ran out of polls
   int grid_f = 0, grid_b = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional: before forward, between, after backward
   float* y;                  // nF x d residual / forward work vector
   float* z;                  // nF x d forward result
   float* x;                  // nF x d correction

@@ -919,16 +919,16 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
                                           std::max<int64_t>(S.fdyn.n_tasks, S.bdyn.n_tasks));
   const int reset_grid = (int)std::min<int64_t>((n_all + 255) / 256, 4096);
   k_dyn_reset<<<reset_grid, 256, 0, s>>>(S.fdyn, S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
+  if (S.ev[0]) cudaEventRecord(S.ev[0], s);
   if (S.schedule == 1) {
     const DynView vf{S.fdyn, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
     const DynView vb{S.bdyn, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
-    if (S.d == 2) {
-      k_solve_dynamic<2, true><<<S.grid_f, 256, 0, s>>>(vf);
-      k_solve_dynamic<2, false><<<S.grid_b, 256, 0, s>>>(vb);
-    } else {
-      k_solve_dynamic<3, true><<<S.grid_f, 256, 0, s>>>(vf);
-      k_solve_dynamic<3, false><<<S.grid_b, 256, 0, s>>>(vb);
-    }
+    if (S.d == 2) k_solve_dynamic<2, true><<<S.grid_f, 256, 0, s>>>(vf);
+    else k_solve_dynamic<3, true><<<S.grid_f, 256, 0, s>>>(vf);
+    if (S.ev[1]) cudaEventRecord(S.ev[1], s);
+    if (S.d == 2) k_solve_dynamic<2, false><<<S.grid_b, 256, 0, s>>>(vb);
+    else k_solve_dynamic<3, false><<<S.grid_b, 256, 0, s>>>(vb);
+    if (S.ev[2]) cudaEventRecord(S.ev[2], s);
     return;
   }
   const int L = (int)S.fwd_off.size() - 1;
@@ -938,12 +938,14 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
     if (S.d == 2) k_forward<2><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
     else k_forward<3><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
   }
+  if (S.ev[1]) cudaEventRecord(S.ev[1], s);
   for (int l = L - 1; l >= 0; --l) {
     const int64_t nt = S.bwd_off[l + 1] - S.bwd_off[l];
     if (nt <= 0) continue;
     if (S.d == 2) k_backward<2><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
     else k_backward<3><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
   }
+  if (S.ev[2]) cudaEventRecord(S.ev[2], s);
 }
 
 int persistent_grid(int d, bool forward) {
