@@ -211,9 +211,11 @@ typedef struct {
   int32_t narrow_cols;  /* supernodes with at most this many columns (and at most 1024 rows) run
                            as one task on one block: 32 or 64 */
   int32_t schedule;     /* supernodal solves: 0 per-level launches, 1 dynamic ready queue */
+  int32_t bottom_levels;/* schedule 1: lowest tree levels run as one launch per level: 0, 2, 3 or 4 */
   double ms_local[3];   /* measured local step for 64, 128, 256 threads */
   double ms_solve[2];   /* measured supernodal solve (forward + backward) for 32, 64 */
   double ms_schedule[2];/* measured supernodal solve for schedules 0 and 1 */
+  double ms_bottom[4];  /* measured supernodal solve (schedule 1) for bottom_levels 0, 2, 3, 4 */
 } ffa_tuning;
 
 /* Time the candidate launch shapes of the local step, of the supernodal solves and

@@ -67,12 +67,14 @@ class Info(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("local_block", C.c_int32), ("narrow_cols", C.c_int32), ("schedule", C.c_int32),
-                ("ms_local", C.c_double * 3), ("ms_solve", C.c_double * 2), ("ms_schedule", C.c_double * 2)]
+                ("bottom_levels", C.c_int32), ("ms_local", C.c_double * 3), ("ms_solve", C.c_double * 2),
+                ("ms_schedule", C.c_double * 2), ("ms_bottom", C.c_double * 4)]
 
     def as_dict(self) -> dict:
         return {"local_block": self.local_block, "narrow_cols": self.narrow_cols, "schedule": self.schedule,
-                "ms_local": list(self.ms_local), "ms_solve": list(self.ms_solve),
-                "ms_schedule": list(self.ms_schedule)}
+                "bottom_levels": self.bottom_levels, "ms_local": list(self.ms_local),
+                "ms_solve": list(self.ms_solve), "ms_schedule": list(self.ms_schedule),
+                "ms_bottom": list(self.ms_bottom)}
 
 
 class PhaseTimes(C.Structure):

@@ -97,6 +97,8 @@ struct ffa_ctx {
   int narrow_cols = 64;
   int schedule = 0;             // supernodal solves: 0 one launch per level, 1 dynamic
   DynPass fdyn, bdyn;           // dynamic schedule of the forward and backward passes
+  int bottom_levels = 0;        // dynamic schedule: lowest tree levels run as one launch each
+  int bottom_used = 0;          // min(bottom_levels, levels) of the current task lists
   cudaEvent_t solve_ev[3] = {nullptr, nullptr, nullptr};  // set only while ffa_profile_phases runs
   int32_t* err_flag = nullptr;
   int grid_f = 0, grid_b = 0;
@@ -291,6 +293,7 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.schedule = ctx->schedule;
   S.fdyn = ctx->fdyn;
   S.bdyn = ctx->bdyn;
+  S.bottom_levels = ctx->bottom_used;
   for (int i = 0; i < 3; ++i) S.ev[i] = ctx->solve_ev[i];
   S.n_nodes = (int)ctx->nodes_h.size();
   S.err_flag = ctx->err_flag;
@@ -445,10 +448,13 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
 }
 
 // kernels one iteration launches: the gather, per refinement sweep the residual,
-// the schedule reset and the solve launches (2 dynamic, or one per non-empty
-// level and pass), the sweeps - 1 corrections, the vertex update and the local step
+// the schedule reset and the solve launches (2 dynamic plus one per non-empty
+// bottom level and pass, or one per non-empty level and pass), the sweeps - 1
+// corrections, the vertex update and the local step
 int kernels_per_iteration(const ffa_ctx* ctx) {
   int solve = 2;
+  for (int l = 0; l < ctx->bottom_used && ctx->schedule == 1; ++l)
+    solve += (ctx->fwd_off[l + 1] > ctx->fwd_off[l]) + (ctx->bwd_off[l + 1] > ctx->bwd_off[l]);
   if (ctx->schedule == 0) {
     solve = 0;
     for (size_t l = 0; l + 1 < ctx->fwd_off.size(); ++l)
@@ -564,25 +570,31 @@ ffa_status build_tasks(ffa_ctx* ctx) {
     while (p >= 0 && ntf[p] == 0) p = nd_h[p].parent;
     up[s] = p;
   }
+  // The dynamic launches cover the nodes on levels >= nb (closed under
+  // ancestors); the levels below run as one launch each, before the forward
+  // dynamic launch and after the backward one.
+  const int nb = std::min(ctx->bottom_levels, nl);
+  auto top = [&](int s) { return ntf[s] > 0 && nd_h[s].level >= nb; };
   // forward: s waits on the nodes whose nearest ancestor with tasks is s
   std::vector<int32_t> dptr_f(nn + 1, 0), dep_f, pend_f(nn, 0), qf;
   for (int s = 0; s < nn; ++s) {
-    if (ntf[s] > 0 && up[s] >= 0) {
+    if (top(s) && up[s] >= 0) {
       dep_f.push_back(up[s]);
       pend_f[up[s]]++;
     }
     dptr_f[s + 1] = (int32_t)dep_f.size();
   }
   for (int s = 0; s < nn; ++s)
-    if (ntf[s] > 0 && pend_f[s] == 0)
+    if (top(s) && pend_f[s] == 0)
       for (int i = 0; i < ntf[s]; ++i) qf.push_back(t0f[s] + i);
   const int n_init_f = (int)qf.size();
-  qf.resize(fwd_all.size(), -1);
+  const int n_top_f = (int)(fwd_all.size() - ctx->fwd_off[nb]);
+  qf.resize(n_top_f, -1);
   // backward: s waits on its nearest ancestor with tasks
   std::vector<std::vector<int32_t>> kids(nn);
   std::vector<int32_t> pend_b(nn, 0), dptr_b(nn + 1, 0), dep_b, qb;
   for (int s = 0; s < nn; ++s)
-    if (ntb[s] > 0 && up[s] >= 0) {
+    if (top(s) && up[s] >= 0) {
       kids[up[s]].push_back(s);
       pend_b[s] = 1;
     }
@@ -591,22 +603,22 @@ ffa_status build_tasks(ffa_ctx* ctx) {
     dptr_b[s + 1] = (int32_t)dep_b.size();
   }
   for (int s = nn - 1; s >= 0; --s)
-    if (ntb[s] > 0 && pend_b[s] == 0)
+    if (top(s) && pend_b[s] == 0)
       for (int i = 0; i < ntb[s]; ++i) qb.push_back(t0b[s] + i);
   const int n_init_b = (int)qb.size();
-  qb.resize(bwd_all.size(), -1);
-  if ((st = upload_dyn(ctx, ctx->fdyn, ctx->fwd_t, (int)fwd_all.size(), t0f, ntf, dptr_f, dep_f, pend_f, qf,
-                       n_init_f)) != FFA_OK)
+  const int n_top_b = (int)(bwd_all.size() - ctx->bwd_off[nb]);
+  qb.resize(n_top_b, -1);
+  if ((st = upload_dyn(ctx, ctx->fdyn, ctx->fwd_t, n_top_f, t0f, ntf, dptr_f, dep_f, pend_f, qf, n_init_f)) != FFA_OK)
     return st;
-  if ((st = upload_dyn(ctx, ctx->bdyn, ctx->bwd_t, (int)bwd_all.size(), t0b, ntb, dptr_b, dep_b, pend_b, qb,
-                       n_init_b)) != FFA_OK)
+  if ((st = upload_dyn(ctx, ctx->bdyn, ctx->bwd_t, n_top_b, t0b, ntb, dptr_b, dep_b, pend_b, qb, n_init_b)) != FFA_OK)
     return st;
+  ctx->bottom_used = nb;
   if (!ctx->err_flag) {
     if ((st = dalloc(ctx, &ctx->err_flag, 1)) != FFA_OK) return st;
     FFA_CUDA(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), ctx->stream));
   }
-  ctx->grid_f = std::max(1, std::min(ctx->grid_f, (int)fwd_all.size()));
-  ctx->grid_b = std::max(1, std::min(ctx->grid_b, (int)bwd_all.size()));
+  ctx->grid_f = std::max(1, std::min(ctx->grid_f, n_top_f));
+  ctx->grid_b = std::max(1, std::min(ctx->grid_b, n_top_b));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   return FFA_OK;
 }
@@ -1535,6 +1547,31 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
     }
   }
   ctx->schedule = best_sched;
+  // 4) dynamic schedule: how many of the lowest tree levels run as one launch per level
+  if (ctx->schedule == 1) {
+    const int bottoms[4] = {0, 2, 3, 4};
+    best = 1e300;
+    int best_bottom = ctx->bottom_levels;
+    for (int c = 0; c < 4; ++c) {
+      ctx->bottom_levels = bottoms[c];
+      if ((st = build_tasks(ctx)) != FFA_OK) return st;
+      SolveData S = solve_data(ctx);
+      launch_supernodal_solve(S, s);
+      FFA_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < reps; ++r) launch_supernodal_solve(S, s);
+      FFA_CUDA(cudaEventRecord(e1, s));
+      FFA_CUDA(cudaEventSynchronize(e1));
+      float ms;
+      FFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      t.ms_bottom[c] = ms / reps;
+      if (t.ms_bottom[c] < best) {
+        best = t.ms_bottom[c];
+        best_bottom = bottoms[c];
+      }
+    }
+    ctx->bottom_levels = best_bottom;
+    if ((st = build_tasks(ctx)) != FFA_OK) return st;
+  }
   if (device_wait_failed(ctx)) return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait gave up during tuning");
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1547,6 +1584,7 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
   t.local_block = ctx->local_block;
   t.narrow_cols = ctx->narrow_cols;
   t.schedule = ctx->schedule;
+  t.bottom_levels = ctx->bottom_levels;
   if (out) *out = t;
   return FFA_OK;
 }

@@ -19,13 +19,16 @@ enum { QV_GTL = 0, QV_NUM, QV_DEN, NQV };
 
 constexpr int kLocalBlock = 128;
 constexpr int kVertexBlock = 256;
-constexpr int kFwdRows = 128;     // forward wide task rows (4 per lane)
-constexpr int kFwdCols = 256;     // forward wide task: at most this many columns (W/8 per warp)
-constexpr int kFwdBatch = 8;      // forward: columns per lane in flight
-constexpr int kBwdCols = 32;      // backward wide task: output columns (4 per warp, 8 warps)
-constexpr int kBwdRows = 1024;    // backward wide task: at most this many rows
-constexpr int kNarrowCols = 64;   // node tasks: at most this many columns ...
-constexpr int kNodeMaxLd = 1024;  // ... and at most this leading dimension
+constexpr int kSolveThreads = 256;              // threads of a supernodal-solve block
+constexpr int kSolveMinBlocks = 4;              // resident solve blocks per SM the registers allow
+constexpr int kSolveWarps = kSolveThreads / 32;
+constexpr int kFwdRows = 128;                   // forward wide task rows (4 per lane)
+constexpr int kFwdCols = 32 * kSolveWarps;      // forward wide task: at most this many columns (W / warps per warp)
+constexpr int kFwdBatch = 8;                    // forward: columns per lane in flight
+constexpr int kBwdCols = 4 * kSolveWarps;       // backward wide task: output columns (4 per warp)
+constexpr int kBwdRows = 1024;                  // backward wide task: at most this many rows
+constexpr int kNarrowCols = 64;                 // node tasks: at most this many columns ...
+constexpr int kNodeMaxLd = 4 * kSolveThreads;   // ... and at most one 4-row group per thread
 
 // kind 1: the whole node on one block; kind > 1: a wide task of B_node from
 // (r0, c0) spanning kind columns (forward) or kind rows (backward)
@@ -138,7 +141,8 @@ struct SolveData {
   const Task* bwd_tasks;
   std::vector<int64_t> fwd_off, bwd_off;  // per level task ranges (host)
   int schedule = 0;          // 0: one launch per level, 1: one dynamic launch per pass
-  DynPass fdyn, bdyn;
+  DynPass fdyn, bdyn;            // dynamic passes over the levels >= bottom_levels
+  int bottom_levels = 0;         // levels below run as one launch per level (schedule 1)
   int n_nodes = 0;
   int32_t* err_flag = nullptr;      // set to 1 if a wait ran out of polls
   int grid_f = 0, grid_b = 0;

@@ -224,11 +224,11 @@ __global__ void k_axpy(int n, double* __restrict__ X, const float* __restrict__ 
 // ---------------------------------------------------------------------------
 // supernodal solves.  B_s is column-major with a leading dimension ld that is a
 // multiple of 4, so every lane reads 4 consecutive rows of a column as one
-// float4.  Every task below runs on a whole block of 256 threads.
+// float4.  Every task below runs on a whole block of kSolveThreads threads.
 //
 // Wide task (node, r0, c0) of the forward pass: rows [r0, r0+128) of B_s times
-// the slice [c0, c0+256) of f = y[cols(s)]; warp w takes columns c0+32w ..
-// c0+32w+31, the eight partial sums are added in shared memory and the 128 row
+// the slice [c0, c0+W) of f = y[cols(s)] (W = 32 per warp); warp w takes columns
+// c0+32w .. c0+32w+31, the per-warp partial sums are added in shared memory and the 128 row
 // results go out as one set of atomics: rows < n_s into z, rows >= n_s
 // subtracted from y at the structure rows.
 // ---------------------------------------------------------------------------
@@ -241,9 +241,9 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
                                              const float* __restrict__ blocks, float* __restrict__ y,
                                              float* __restrict__ z, float* smem) {
   const int W = t.kind;      // columns of this task: a multiple of 8, at most kFwdCols
-  const int cpw = W >> 3;    // columns per warp
+  const int cpw = W / kSolveWarps;    // columns per warp
   float (*fs)[D] = reinterpret_cast<float (*)[D]>(smem);                       // [W][D]
-  float (*red)[kFwdRows][D] = reinterpret_cast<float (*)[kFwdRows][D]>(smem + kFwdCols * D);  // [8][128][D]
+  float (*red)[kFwdRows][D] = reinterpret_cast<float (*)[kFwdRows][D]>(smem + kFwdCols * D);  // [warps][128][D]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntot = nd.ncol + nd.nrow;
   const int nc = min(W, nd.ncol - t.c0);
@@ -257,7 +257,7 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
 #pragma unroll
   for (int u = 0; u < kFwdBatch; ++u)
     b[u] = (u < n0) ? ldg_stream(B + (int64_t)u * nd.ld) : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int q = threadIdx.x; q < nc * D; q += 256) {
+  for (int q = threadIdx.x; q < nc * D; q += kSolveThreads) {
     const int c = q / D, k = q - c * D;
     fs[c][k] = __ldcg(y + (int64_t)(nd.col0 + t.c0 + c) * D + k);
   }
@@ -301,7 +301,7 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
       for (int k = 0; k < D; ++k) {
         float a = 0.f;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) a += red[w][threadIdx.x][k];
+        for (int w = 0; w < kSolveWarps; ++w) a += red[w][threadIdx.x][k];
         sum[k] = a;
       }
       if (row < nd.ncol) {
@@ -319,7 +319,7 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
 // Node task of the forward pass: a whole small node (at most kNarrowCols columns,
 // ld <= kNodeMaxLd) on one block.  Thread (g, j) owns the 4-row group g of the
 // ld/4 groups and the column slice j (columns j, j + S, j + 2S, ...) with
-// S = floor(256 / (ld/4)) slices, so a small node is streamed in one or two
+// S = floor(kSolveThreads / (ld/4)) slices, so a small node is streamed in one or two
 // rounds of loads; the S partial sums of each row meet in shared memory.  z_s
 // is stored directly (no other task touches it).
 template <int D>
@@ -330,7 +330,7 @@ __device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* _
   float* red = smem + kNarrowCols * D;                     // [D][S][ld]
   const int ntot = nd.ncol + nd.nrow;
   const int G = nd.ld >> 2;
-  const int S = 256 / G;
+  const int S = kSolveThreads / G;
   const int g = threadIdx.x % G, j = threadIdx.x / G;
   const bool active = j < S;
   const float* B = blocks + nd.blk_off + 4 * g;
@@ -339,7 +339,7 @@ __device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* _
 #pragma unroll
   for (int u = 0; u < 8; ++u)
     b[u] = (active && j + u * S < nd.ncol) ? ldg_stream(B + (int64_t)(j + u * S) * nd.ld) : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int q = threadIdx.x; q < nd.ncol * D; q += 256) {
+  for (int q = threadIdx.x; q < nd.ncol * D; q += kSolveThreads) {
     const int c = q / D, k = q - c * D;
     f[c][k] = __ldcg(y + (int64_t)(nd.col0 + c) * D + k);
   }
@@ -394,7 +394,7 @@ __device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* _
           make_float4(acc[0][k], acc[1][k], acc[2][k], acc[3][k]);
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < ntot; r += 256) {
+  for (int r = threadIdx.x; r < ntot; r += kSolveThreads) {
     float s[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -437,7 +437,7 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     pa[q] = (q < ncw && ra < nr) ? ldg_stream(B + (int64_t)q * nd.ld + ra) : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int r = threadIdx.x; r < nr; r += 256) {
+  for (int r = threadIdx.x; r < nr; r += kSolveThreads) {
     const int row = t.r0 + r;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -515,7 +515,7 @@ __device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* 
       pre[u] = (j < nd.ncol && r < ld) ? ldg_stream(B + r) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  for (int r = threadIdx.x; r < ld; r += 256) {
+  for (int r = threadIdx.x; r < ld; r += kSolveThreads) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       float v = 0.f;
@@ -525,7 +525,7 @@ __device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* 
     }
   }
   __syncthreads();
-  for (int j0 = 4 * warp; j0 < nd.ncol; j0 += 32) {
+  for (int j0 = 4 * warp; j0 < nd.ncol; j0 += 4 * kSolveWarps) {
     const int j = j0 + cg;
     float acc[D];
 #pragma unroll
@@ -581,8 +581,8 @@ __device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* 
 // shared memory of one solve block (floats): the larger of the wide and node tasks
 template <int D>
 struct SolveSmem {
-  static constexpr int kFwd = (kFwdCols + 8 * kFwdRows) * D > (kNarrowCols + kNodeMaxLd) * D
-                                  ? (kFwdCols + 8 * kFwdRows) * D : (kNarrowCols + kNodeMaxLd) * D;
+  static constexpr int kFwd = (kFwdCols + kSolveWarps * kFwdRows) * D > (kNarrowCols + kNodeMaxLd) * D
+                                  ? (kFwdCols + kSolveWarps * kFwdRows) * D : (kNarrowCols + kNodeMaxLd) * D;
   static constexpr int kBwd = D * (kBwdRows > kNodeMaxLd ? kBwdRows : kNodeMaxLd);
 };
 
@@ -604,7 +604,7 @@ __device__ __forceinline__ void backward_task(const Task& t, const NodeDev& nd, 
 
 // level-synchronous schedule: one launch per level, one task per block
 template <int D>
-__global__ void __launch_bounds__(256, 4) k_forward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_forward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
                                                  const int32_t* __restrict__ rows, const float* __restrict__ blocks,
                                                  float* __restrict__ y, float* __restrict__ z) {
   __shared__ __align__(16) float smem[SolveSmem<D>::kFwd];
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(256, 4) k_forward(const Task* __restrict__ tas
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, 4) k_backward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_backward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
                                                   const int32_t* __restrict__ rows, const float* __restrict__ blocks,
                                                   const float* __restrict__ z, float* __restrict__ x) {
   __shared__ __align__(16) float smem[SolveSmem<D>::kBwd];
@@ -659,7 +659,7 @@ __device__ __forceinline__ void st_relaxed(int32_t* p, int v) {
 }
 
 template <int D, bool FWD>
-__global__ void __launch_bounds__(256, 4) k_solve_dynamic(DynView V) {
+__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynamic(DynView V) {
   __shared__ __align__(16) float smem[FWD ? SolveSmem<D>::kFwd : SolveSmem<D>::kBwd];
   __shared__ int item_s, slot_s, n_push_s, next_s;
   __shared__ int push_s[kMaxPush][3];   // first task, queue position, count
@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(256, 4) k_solve_dynamic(DynView V) {
       if (n > 0) {
         __threadfence();
         for (int e = 0; e < n; ++e)
-          for (int i = threadIdx.x; i < push_s[e][2]; i += 256) st_relaxed(P.queue + push_s[e][1] + i, push_s[e][0] + i);
+          for (int i = threadIdx.x; i < push_s[e][2]; i += kSolveThreads) st_relaxed(P.queue + push_s[e][1] + i, push_s[e][0] + i);
       }
     }
     __syncthreads();   // item_s, slot_s and the push records are reused
@@ -913,6 +913,8 @@ void launch_axpy_correction(const SolveData& S, cudaStream_t s) {
   k_axpy<<<blocks_for(n, 256), 256, 0, s>>>((int)n, S.X, S.x);
 }
 
+void launch_levels(const SolveData& S, int l0, int l1, bool forward, cudaStream_t s);
+
 void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   const int64_t nzx = (int64_t)S.nF * S.d;
   const int64_t n_all = std::max<int64_t>(std::max<int64_t>(nzx, S.n_nodes),
@@ -920,32 +922,44 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   const int reset_grid = (int)std::min<int64_t>((n_all + 255) / 256, 4096);
   k_dyn_reset<<<reset_grid, 256, 0, s>>>(S.fdyn, S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
   if (S.ev[0]) cudaEventRecord(S.ev[0], s);
+  const int L = (int)S.fwd_off.size() - 1;
   if (S.schedule == 1) {
     const DynView vf{S.fdyn, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
     const DynView vb{S.bdyn, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
-    if (S.d == 2) k_solve_dynamic<2, true><<<S.grid_f, 256, 0, s>>>(vf);
-    else k_solve_dynamic<3, true><<<S.grid_f, 256, 0, s>>>(vf);
+    const int nb = std::min(S.bottom_levels, L);
+    launch_levels(S, 0, nb, true, s);
+    if (S.d == 2) k_solve_dynamic<2, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);
+    else k_solve_dynamic<3, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);
     if (S.ev[1]) cudaEventRecord(S.ev[1], s);
-    if (S.d == 2) k_solve_dynamic<2, false><<<S.grid_b, 256, 0, s>>>(vb);
-    else k_solve_dynamic<3, false><<<S.grid_b, 256, 0, s>>>(vb);
+    if (S.d == 2) k_solve_dynamic<2, false><<<S.grid_b, kSolveThreads, 0, s>>>(vb);
+    else k_solve_dynamic<3, false><<<S.grid_b, kSolveThreads, 0, s>>>(vb);
+    launch_levels(S, 0, nb, false, s);
     if (S.ev[2]) cudaEventRecord(S.ev[2], s);
     return;
   }
-  const int L = (int)S.fwd_off.size() - 1;
-  for (int l = 0; l < L; ++l) {
-    const int64_t nt = S.fwd_off[l + 1] - S.fwd_off[l];
-    if (nt <= 0) continue;
-    if (S.d == 2) k_forward<2><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
-    else k_forward<3><<<(unsigned)nt, 256, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
-  }
+  launch_levels(S, 0, L, true, s);
   if (S.ev[1]) cudaEventRecord(S.ev[1], s);
-  for (int l = L - 1; l >= 0; --l) {
+  launch_levels(S, 0, L, false, s);
+  if (S.ev[2]) cudaEventRecord(S.ev[2], s);
+}
+
+// one launch per level: forward over levels [l0, l1) bottom up, backward top down
+void launch_levels(const SolveData& S, int l0, int l1, bool forward, cudaStream_t s) {
+  if (forward) {
+    for (int l = l0; l < l1; ++l) {
+      const int64_t nt = S.fwd_off[l + 1] - S.fwd_off[l];
+      if (nt <= 0) continue;
+      if (S.d == 2) k_forward<2><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+      else k_forward<3><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+    }
+    return;
+  }
+  for (int l = l1 - 1; l >= l0; --l) {
     const int64_t nt = S.bwd_off[l + 1] - S.bwd_off[l];
     if (nt <= 0) continue;
-    if (S.d == 2) k_backward<2><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
-    else k_backward<3><<<(unsigned)nt, 256, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
+    if (S.d == 2) k_backward<2><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
+    else k_backward<3><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
   }
-  if (S.ev[2]) cudaEventRecord(S.ev[2], s);
 }
 
 int persistent_grid(int d, bool forward) {
@@ -953,10 +967,10 @@ int persistent_grid(int d, bool forward) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
-  if (forward) e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<2, true>, 256, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<3, true>, 256, 0);
-  else e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<2, false>, 256, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<3, false>, 256, 0);
+  if (forward) e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<2, true>, kSolveThreads, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<3, true>, kSolveThreads, 0);
+  else e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<2, false>, kSolveThreads, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<3, false>, kSolveThreads, 0);
   if (e != cudaSuccess || per < 1) per = 1;
   return sms * per;
 }
