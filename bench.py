@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="cube_deform", choices=["cube_deform", "batch256"])
+    ap.add_argument("--workload", default="cube_deform",
+                    choices=["cube_deform", "batch256", "uv_disk", "uv_heightfield", "cube_handles"],
+                    help="cube_deform: the throughput benchmark; the others report time to tolerance "
+                         "(uv_disk, uv_heightfield), batched meshes, or forward + adjoint (cube_handles)")
     ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
@@ -247,6 +250,106 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def run_to_tolerance(args, local):
+    """A 2D workload solved to its tolerance: wall time (setup excluded), iterations,
+    flips, final energy; on the 48^2 disk also the maximum difference of W from the
+    FP64 oracle run for the same number of iterations."""
+    import numpy as np
+    import torch
+
+    from paper_2107_05200_gb300 import workloads as wk
+    from paper_2107_05200_gb300.solver import Solver
+
+    torch.cuda.set_device(local)
+    wl = wk.uv_disk() if args.workload == "uv_disk" else wk.uv_heightfield()
+    t0 = time.perf_counter()
+    sol = Solver.from_workload(wl, precision=args.precision, check_every=10, refine_sweeps=args.sweeps)
+    t_setup = time.perf_counter() - t0
+    sol.init(wl.W0)
+    sol.iterate(10, stop_at_tol=False)          # warm-up (graph capture)
+    sol.init(wl.W0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = sol.iterate(wl.max_iter, stop_at_tol=True)
+    torch.cuda.synchronize()
+    t_tol = time.perf_counter() - t0
+    W = sol.W()
+    E = sol.energy()
+    dE = sol.gradient() if st["n_flipped"] == 0 else None
+    sol.close()
+    line = {"metric": "time to tolerance", "unit": "s", "value": t_tol, "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "elements": wl.m, "vertices": wl.n, "energy": wl.energy,
+                       "rho": wl.rho, "eps_abs": wl.eps_abs, "eps_rel": wl.eps_rel, "max_iter": wl.max_iter,
+                       "check_every": 10},
+            "iterations": st["iters"], "converged": st["converged"], "n_flipped": st["n_flipped"],
+            "iter_per_s": st["iters"] / t_tol, "elem_updates_per_s": st["iters"] * wl.m / t_tol,
+            "energy": E, "e_prim": st["e_prim"], "e_dual": st["e_dual"], "setup_s": t_setup}
+    if args.workload == "uv_disk":
+        from oracle import admm
+        o = admm.Oracle.from_workload(wl)
+        s_o = o.init(wl.W0)
+        for _ in range(st["iters"]):
+            s_o, _ = o.step(s_o)
+        line["oracle_W_max_rel_diff"] = float(np.abs(W - s_o.W).max() / np.abs(s_o.W).max())
+        line["oracle_energy_rel_diff"] = float(abs(E - o.energy(s_o.W)) / abs(o.energy(s_o.W)))
+        if dE is not None:
+            g_o = o.energy_gradient(s_o.W)
+            line["oracle_gradient_rel_diff"] = float(np.linalg.norm(dE - g_o) / np.linalg.norm(g_o))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_handles(args, local):
+    """The handle workload: 200 unrolled iterations with checkpoints every 20, then
+    dL/db of the target loss; times both passes, and compares the FP32 gradient with
+    the FP64 one."""
+    import numpy as np
+    import torch
+
+    from paper_2107_05200_gb300 import workloads as wk
+    from paper_2107_05200_gb300.solver import Solver
+
+    torch.cuda.set_device(local)
+    wl = wk.cube_handles()
+    idx, tgt = wl.meta["target_idx"], wl.meta["targets"]
+    out = {}
+    for prec in ("fp32", "fp64"):
+        with Solver.from_workload(wl, precision=prec) as sol:
+            sol.set_handles(wl.pin_pos)
+            sol.init(wl.W0)
+            sol.forward_unrolled(20, 20)      # warm-up
+            sol.init(wl.W0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol.forward_unrolled(200, 20)
+            torch.cuda.synchronize()
+            t_f = time.perf_counter() - t0
+            W = sol.W()
+            diff = W[idx] - tgt
+            G = np.zeros_like(W)
+            G[idx] = 2.0 * diff / len(idx)
+            t0 = time.perf_counter()
+            g = sol.backward_unrolled(G)
+            torch.cuda.synchronize()
+            t_b = time.perf_counter() - t0
+            out[prec] = {"forward_s": t_f, "backward_s": t_b, "loss": float(np.mean(np.sum(diff * diff, 1))),
+                         "grad": g}
+    nb = wl.meta["n_bottom"]
+    g32, g64 = out["fp32"]["grad"][nb:], out["fp64"]["grad"][nb:]
+    line = {"metric": "forward + adjoint of 200 unrolled iterations", "unit": "s",
+            "value": out[args.precision]["forward_s"] + out[args.precision]["backward_s"], "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32+f64" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "elements": wl.m, "vertices": wl.n, "handles": len(wl.pin_pos) - nb,
+                       "iterations": 200, "checkpoint_every": 20},
+            "fp32": {k: v for k, v in out["fp32"].items() if k != "grad"},
+            "fp64": {k: v for k, v in out["fp64"].items() if k != "grad"},
+            "grad_fp32_vs_fp64_rel": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -254,6 +357,10 @@ def main():
         return run_reference(args, rank)
     if args.workload == "batch256":
         return run_batch(args, rank, world, local)
+    if args.workload in ("uv_disk", "uv_heightfield"):
+        return run_to_tolerance(args, local) if rank == 0 else 0
+    if args.workload == "cube_handles":
+        return run_handles(args, local) if rank == 0 else 0
 
     import numpy as np
     import torch
