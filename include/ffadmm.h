@@ -88,6 +88,17 @@ typedef struct {
   int32_t solve_schedule;  /* W step: 0 one launch per elimination-tree level, 1 one launch per
                               triangular solve whose blocks take ready tasks from a queue that
                               finished supernodes refill (default) */
+  int32_t penalty_schedule;/* 0: mu_i = rho * w_i, fixed (default; L is decomposed once).
+                              1: the paper's Algorithm 2 (Sec. 6, "Rescaling mu_i and Lambda"):
+                              mu_i = max(mu_min,i, w_i) at ffa_init (mu_min of Prop. 1 with the
+                              gradient bound B_i = sqrt(5 (1 + |grad f(P_i)|^2)) of Sec. 6), then
+                              after iterations 1..5 and every floor(5 (3/2)^p) iterations (p =
+                              events so far) each mu_i is multiplied (divided) by rescale_rho/2
+                              when e_prim_i > rescale_rho e_dual_i (e_dual_i > rescale_rho
+                              e_prim_i), never below mu_min,i/2, Lambda_i keeps mu_i Lambda_i, and L
+                              is decomposed again on the host.  rho is ignored.  Single meshes of
+                              one energy only; not with ffa_forward_unrolled. */
+  double rescale_rho;      /* the paper's rho of the rescaling rule (default 5) */
 } ffa_params;
 
 typedef struct {
@@ -99,6 +110,7 @@ typedef struct {
   double thr_prim, thr_dual; /* eq. primaldualthresholds */
   double energy_P;         /* sum_i w_i f(P_i) */
   double norm_GW, norm_P, norm_GtLambda;
+  int32_t rescales;        /* penalty rescaling events since ffa_init (penalty_schedule 1) */
 } ffa_stats;
 
 typedef struct {
@@ -116,6 +128,7 @@ typedef struct {
                                  the pass's input and output vectors */
   int32_t kernels_per_iteration; /* kernel launches of one iteration without the test */
   int32_t kernels_per_check;     /* extra launches of an iteration that runs the test */
+  double seconds_refactor;       /* host time spent decomposing L again (penalty_schedule 1) */
 } ffa_info;
 
 typedef struct {
@@ -132,7 +145,8 @@ typedef struct {
 
 /* Fill *p with the defaults: symmetric Dirichlet, rho 1, eps_abs 1e-6, eps_rel 1e-5,
  * check_every 10, require_flip_free 1, FP32 local step, 2 refine sweeps,
- * leaf size 64, all host threads, solve schedule 1. */
+ * leaf size 64, all host threads, solve schedule 1, fixed penalties (penalty
+ * schedule 0), rescale_rho 5. */
 ffa_status ffa_default_params(ffa_params* p);
 
 /* Prepare a solver for one mesh: element gradients and measures w_i (Supplemental,
@@ -187,6 +201,12 @@ ffa_status ffa_get_W(ffa_ctx* ctx, double* W_out);
 /* Copy the per-element state out as doubles (m x d x d each, host or device;
  * any pointer may be NULL to skip it). */
 ffa_status ffa_get_state(ffa_ctx* ctx, double* U, double* P, double* Lambda);
+
+/* The current penalties mu_i (m values, host or device buffer): rho * w_i with
+ * fixed penalties, the schedule's values with penalty_schedule 1 (eq.
+ * augmentedlagrangian; Sec. 6, "Rescaling mu_i and Lambda").  With fixed
+ * penalties and the FP32 local step they are read back from float. */
+ffa_status ffa_get_penalties(ffa_ctx* ctx, double* mu);
 
 /* Energy of eq. genericdeformationenergy at W (n x d, host or device; NULL = the current iterate):
  * sum_i w_i f((G W)_i), or +infinity (with FFA_OK) if some det (G W)_i <= 0. */

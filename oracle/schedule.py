@@ -24,8 +24,13 @@ Readings (also in the design notes): C^L = (-B + sqrt(4 + B^2))/2 is evaluated a
 the equal 2 / (B + sqrt(4 + B^2)), which does not cancel for large B; the
 Lambda factor is mu_old/mu_new, which
 is the printed "divide/multiply by rho/2" whenever the lower bound does not
-bind; the termination test of an event iteration is evaluated after the
-rescaling, in the order of Algorithm 2; h_i = 0 as in the fixed-penalty loop.
+bind; the termination test of an event iteration is evaluated on that
+iteration's iterate before its rescaling (Algorithm 2 lists the test after the
+rescaling; testing first lets a converged iterate stop without a needless
+decomposition of L); an element error below 2^-40 (1 + |J_i|) (times mu_i for
+e_dual) counts as zero, so that elements that have stopped moving are not
+rescaled on rounding noise (the paper's rule leaves both errors exactly zero
+alone); h_i = 0 as in the fixed-penalty loop.
 """
 from __future__ import annotations
 
@@ -101,11 +106,19 @@ def rescale_iterations(max_iter: int) -> list[int]:
         p += 1
 
 
+ROUNDING_FLOOR = 2.0 ** -40
+
+
 def element_errors(o: admm.Oracle, s0: admm.State, s1: admm.State):
-    """e_prim_i and e_dual_i of eq. primaldualerror for every element."""
+    """e_prim_i and e_dual_i of eq. primaldualerror for every element; an error
+    below the rounding floor of its element (2^-40 (1 + |J_i|), times mu_i for
+    e_dual) counts as zero."""
     R = s1.J - s1.U @ s1.P
     D = s1.J - s0.J
-    return np.sqrt(np.einsum("mij,mij->m", R, R)), o.mu * np.sqrt(np.einsum("mij,mij->m", D, D))
+    ep = np.sqrt(np.einsum("mij,mij->m", R, R))
+    ed = o.mu * np.sqrt(np.einsum("mij,mij->m", D, D))
+    floor = ROUNDING_FLOOR * (1.0 + np.sqrt(np.einsum("mij,mij->m", s1.J, s1.J)))
+    return np.where(ep > floor, ep, 0.0), np.where(ed > o.mu * floor, ed, 0.0)
 
 
 def set_penalties(o: admm.Oracle, mu: np.ndarray) -> None:
@@ -124,15 +137,15 @@ def run(o: admm.Oracle, W0, max_iter: int, stop_at_tol: bool = True, callback=No
     for k in range(1, max_iter + 1):
         W = o.w_step(s)
         s1 = o.local_steps(s, W)
+        st = o.stats(s, s1, k)
+        if callback is not None:
+            callback(k, s, s1, st)
+        if stop_at_tol and st.converged:
+            return s1, st, n_events
         if k in events:
             ep, ed = element_errors(o, s, s1)
             mu_new, s1.Lam = rescale(o.mu, s1.Lam, ep, ed, 0.5 * mu_min(s1.P, o.w, o.energy_name))
             set_penalties(o, mu_new)
             n_events += 1
-        st = o.stats(s, s1, k)
-        if callback is not None:
-            callback(k, s, s1, st)
         s = s1
-        if stop_at_tol and st.converged:
-            break
     return s, st, n_events

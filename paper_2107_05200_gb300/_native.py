@@ -20,7 +20,7 @@ STATUS_NAMES = {
 
 EXPORTED = [
     "ffa_default_params", "ffa_create", "ffa_destroy", "ffa_last_error", "ffa_set_handles",
-    "ffa_init", "ffa_iterate", "ffa_get_W", "ffa_get_state", "ffa_energy", "ffa_gradient",
+    "ffa_init", "ffa_iterate", "ffa_get_W", "ffa_get_state", "ffa_get_penalties", "ffa_energy", "ffa_gradient",
     "ffa_get_info", "ffa_last_wstep_residual", "ffa_profile_phases", "ffa_energy_noalloc",
     "ffa_forward_unrolled", "ffa_backward_unrolled",
     "ffa_batch_create", "ffa_batch_destroy", "ffa_batch_last_error", "ffa_batch_init", "ffa_batch_iterate",
@@ -38,14 +38,16 @@ class Params(C.Structure):
                 ("eps_rel", C.c_double), ("check_every", C.c_int32),
                 ("require_flip_free", C.c_int32), ("local_precision", C.c_int),
                 ("refine_sweeps", C.c_int32), ("nd_leaf_size", C.c_int32),
-                ("host_threads", C.c_int32), ("solve_schedule", C.c_int32)]
+                ("host_threads", C.c_int32), ("solve_schedule", C.c_int32),
+                ("penalty_schedule", C.c_int32), ("rescale_rho", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("n_flipped", C.c_int32),
                 ("checked_iter", C.c_int32), ("e_prim", C.c_double), ("e_dual", C.c_double),
                 ("thr_prim", C.c_double), ("thr_dual", C.c_double), ("energy_P", C.c_double),
-                ("norm_GW", C.c_double), ("norm_P", C.c_double), ("norm_GtLambda", C.c_double)]
+                ("norm_GW", C.c_double), ("norm_P", C.c_double), ("norm_GtLambda", C.c_double),
+                ("rescales", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -59,7 +61,7 @@ class Info(C.Structure):
                 ("device_bytes", C.c_int64), ("bytes_local_step", C.c_int64),
                 ("bytes_global_sweep", C.c_int64), ("bytes_solve_pass", C.c_int64),
                 ("kernels_per_iteration", C.c_int32),
-                ("kernels_per_check", C.c_int32)]
+                ("kernels_per_check", C.c_int32), ("seconds_refactor", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -110,6 +112,7 @@ def load() -> C.CDLL:
         "ffa_iterate": ([vp, i32, i32, C.POINTER(Stats)], C.c_int),
         "ffa_get_W": ([vp, vp], C.c_int),
         "ffa_get_state": ([vp, vp, vp, vp], C.c_int),
+        "ffa_get_penalties": ([vp, vp], C.c_int),
         "ffa_energy": ([vp, vp, C.POINTER(dbl)], C.c_int),
         "ffa_gradient": ([vp, vp, vp], C.c_int),
         "ffa_get_info": ([vp, C.POINTER(Info)], C.c_int),

@@ -27,6 +27,20 @@ struct BatchSpec {
   std::vector<double> mesh_eps;        // per mesh: eps_abs, eps_rel
 };
 
+// What the host keeps to assemble L = sum mu_i G_i^T G_i again for new penalties
+// (the paper's penalty schedule).
+struct OperatorHost {
+  int n = 0, m = 0, d = 0, nF = 0, n_pin = 0;
+  std::vector<double> g;            // m x d x d hat gradients of local vertices 1..d
+  std::vector<int32_t> T;           // m x (d+1)
+  std::vector<int64_t> inc_ptr;     // incidences per vertex (CSR over all vertices)
+  std::vector<int32_t> inc;         // element * (d+1) + slot
+  std::vector<int32_t> free_of, free_vertex, v2pin;
+  std::vector<double> coords;       // nF x 3 source positions of the free vertices
+  ffa::Factor fac;                  // ordering and supernode structure (blocks released after upload)
+  std::vector<double> mu;           // the current penalties
+};
+
 struct ffa_ctx {
   int n = 0, m = 0, d = 0, d_in = 0, n_pin = 0, nF = 0;
   ffa_params prm{};
@@ -97,6 +111,12 @@ struct ffa_ctx {
   int narrow_cols = 64;
   int schedule = 0;             // supernodal solves: 0 one launch per level, 1 dynamic
   DynPass fdyn, bdyn;           // dynamic schedule of the forward and backward passes
+  // the paper's penalty schedule (penalty_schedule = 1)
+  OperatorHost op;
+  double* mu64 = nullptr;       // device: the penalties in double
+  int32_t n_rescales = 0;
+  int64_t last_event_iter = 0;
+  double seconds_refactor = 0.0;
   int bottom_levels = 0;        // dynamic schedule: lowest tree levels run as one launch each
   int bottom_used = 0;          // min(bottom_levels, levels) of the current task lists
   cudaEvent_t solve_ev[3] = {nullptr, nullptr, nullptr};  // set only while ffa_profile_phases runs
@@ -443,6 +463,9 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   else if (p.nd_leaf_size < 8 || p.nd_leaf_size > 512) msg = "nd_leaf_size must be in [8, 512]";
   else if (p.host_threads < 0) msg = "host_threads must be >= 0";
   else if (p.solve_schedule != 0 && p.solve_schedule != 1) msg = "solve_schedule must be 0 or 1";
+  else if (p.penalty_schedule != 0 && p.penalty_schedule != 1) msg = "penalty_schedule must be 0 or 1";
+  else if (p.penalty_schedule == 1 && !(p.rescale_rho > 2.0 && std::isfinite(p.rescale_rho)))
+    msg = "rescale_rho must be finite and > 2";
   else return FFA_OK;
   return FFA_ERR_INVALID_ARG;
 }
@@ -623,6 +646,122 @@ ffa_status build_tasks(ffa_ctx* ctx) {
   return FFA_OK;
 }
 
+// Rows of L = sum_i mu_i G_i^T G_i (eq. solvinginw) for the free vertices: the
+// free-free block in free numbering with sorted columns (Ap, Ai, Ax) and the
+// free-pinned block by pin slot (Cp, Ci, Cx).  The pattern depends on the mesh
+// only, so new penalties give new values in the same positions.
+void assemble_operator(const OperatorHost& H, const double* mu, std::vector<int64_t>& Ap, std::vector<int32_t>& Ai,
+                       std::vector<double>& Ax, std::vector<int64_t>& Cp, std::vector<int32_t>& Ci,
+                       std::vector<double>& Cx) {
+  const int d = H.d, nF = H.nF;
+  auto grad_of = [&](int i, int j, double out[3]) {  // hat gradient of local vertex j
+    for (int a = 0; a < d; ++a) {
+      if (j > 0) out[a] = H.g[(int64_t)i * d * d + (j - 1) * d + a];
+      else {
+        double sum = 0;
+        for (int jj = 0; jj < d; ++jj) sum += H.g[(int64_t)i * d * d + jj * d + a];
+        out[a] = -sum;
+      }
+    }
+  };
+  Ap.assign(nF + 1, 0);
+  Cp.assign(nF + 1, 0);
+  Ai.clear(); Ax.clear(); Ci.clear(); Cx.clear();
+  std::vector<int32_t> pos(H.n, -1), touched;
+  std::vector<double> acc;
+  std::vector<std::pair<int32_t, double>> fr, cr;
+  for (int f = 0; f < nF; ++f) {
+    const int v = H.free_vertex[f];
+    touched.clear();
+    acc.clear();
+    for (int64_t q = H.inc_ptr[v]; q < H.inc_ptr[v + 1]; ++q) {
+      const int i = H.inc[q] / (d + 1), j = H.inc[q] % (d + 1);
+      double gj[3], gl[3];
+      grad_of(i, j, gj);
+      for (int l = 0; l <= d; ++l) {
+        grad_of(i, l, gl);
+        double dotv = 0;
+        for (int a = 0; a < d; ++a) dotv += gj[a] * gl[a];
+        const int u = H.T[(int64_t)i * (d + 1) + l];
+        if (pos[u] < 0) {
+          pos[u] = (int32_t)touched.size();
+          touched.push_back(u);
+          acc.push_back(0.0);
+        }
+        acc[pos[u]] += mu[i] * dotv;
+      }
+    }
+    fr.clear();
+    cr.clear();
+    for (size_t k = 0; k < touched.size(); ++k) {
+      const int u = touched[k];
+      if (H.free_of[u] >= 0) fr.push_back({H.free_of[u], acc[k]});
+      else cr.push_back({H.v2pin[u], acc[k]});
+      pos[u] = -1;
+    }
+    std::sort(fr.begin(), fr.end());
+    std::sort(cr.begin(), cr.end());
+    for (auto& pr : fr) { Ai.push_back(pr.first); Ax.push_back(pr.second); }
+    for (auto& pr : cr) { Ci.push_back(pr.first); Cx.push_back(pr.second); }
+    Ap[f + 1] = (int64_t)Ai.size();
+    Cp[f + 1] = (int64_t)Ci.size();
+  }
+}
+
+// The device forms of the operator in elimination order: L_FF as column-major ELL
+// (the double residual), L_FC as CSR by free row (the pin right-hand side) and
+// L_CF as CSR by pin (the adjoint's pin term).
+struct OperatorArrays {
+  int width = 1;
+  std::vector<int32_t> ell_col;
+  std::vector<double> ell_val;
+  std::vector<int64_t> fc_ptr;
+  std::vector<int32_t> fc_col;
+  std::vector<double> fc_val;
+  std::vector<int64_t> cf_ptr;
+  std::vector<int32_t> cf_row;
+  std::vector<double> cf_val;
+};
+
+void operator_arrays(const Factor& fac, int nF, int n_pin, const std::vector<int64_t>& Ap,
+                     const std::vector<int32_t>& Ai, const std::vector<double>& Ax, const std::vector<int64_t>& Cp,
+                     const std::vector<int32_t>& Ci, const std::vector<double>& Cx, OperatorArrays& A) {
+  int width = 1;
+  for (int f = 0; f < nF; ++f) width = std::max<int>(width, (int)(Ap[f + 1] - Ap[f]));
+  A.width = width;
+  A.ell_col.assign((size_t)width * nF, 0);
+  A.ell_val.assign((size_t)width * nF, 0.0);
+  A.fc_ptr.assign(nF + 1, 0);
+  A.fc_col.clear();
+  A.fc_val.clear();
+  for (int c = 0; c < nF; ++c) {
+    const int f = fac.perm[c];
+    int q = 0;
+    for (int64_t k = Ap[f]; k < Ap[f + 1]; ++k, ++q) {
+      A.ell_col[(size_t)q * nF + c] = fac.iperm[Ai[k]];
+      A.ell_val[(size_t)q * nF + c] = Ax[k];
+    }
+    for (; q < width; ++q) A.ell_col[(size_t)q * nF + c] = c;
+    for (int64_t k = Cp[f]; k < Cp[f + 1]; ++k) {
+      A.fc_col.push_back(Ci[k]);
+      A.fc_val.push_back(Cx[k]);
+    }
+    A.fc_ptr[c + 1] = (int64_t)A.fc_col.size();
+  }
+  A.cf_ptr.assign(n_pin + 1, 0);
+  for (int32_t p : A.fc_col) A.cf_ptr[p + 1]++;
+  for (int p = 0; p < n_pin; ++p) A.cf_ptr[p + 1] += A.cf_ptr[p];
+  A.cf_row.assign(A.fc_col.size(), 0);
+  A.cf_val.assign(A.fc_col.size(), 0.0);
+  std::vector<int64_t> fill(A.cf_ptr.begin(), A.cf_ptr.end() - 1);
+  for (int c = 0; c < nF; ++c)
+    for (int64_t q = A.fc_ptr[c]; q < A.fc_ptr[c + 1]; ++q) {
+      const int64_t dst = fill[A.fc_col[q]]++;
+      A.cf_row[dst] = c;
+      A.cf_val[dst] = A.fc_val[q];
+    }
+}
+
 ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_idx, int32_t n_pin,
                        const double* pin_pos_in, const ffa_params* params, void* stream,
                        const BatchSpec* batch = nullptr) {
@@ -634,6 +773,8 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     if (validate_params(ctx->prm, msg) != FFA_OK) return fail(ctx, FFA_ERR_INVALID_ARG, msg);
   }
   const int n = mesh->n, m = mesh->m, d = mesh->d, d_in = mesh->d_in;
+  if (batch && ctx->prm.penalty_schedule != 0)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "the penalty schedule is for single-mesh contexts");
   if (d != 2 && d != 3) return fail(ctx, FFA_ERR_INVALID_ARG, "d must be 2 or 3");
   if (d_in < d || d_in > 3) return fail(ctx, FFA_ERR_INVALID_ARG, "d_in must be in [d, 3]");
   if (n < d + 1 || m < 1) return fail(ctx, FFA_ERR_INVALID_ARG, "need n >= d+1 and m >= 1");
@@ -695,81 +836,46 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   const double rho = ctx->prm.rho;
 
   // ---- free vertices and the operator L = sum mu_i G_i^T G_i
-  std::vector<int32_t> free_of(n, -1), free_vertex;
+  OperatorHost H;
+  H.n = n;
+  H.m = m;
+  H.d = d;
+  H.n_pin = n_pin;
+  H.v2pin = v2pin;
+  H.free_of.assign(n, -1);
   for (int v = 0; v < n; ++v)
     if (v2pin[v] < 0) {
-      free_of[v] = (int32_t)free_vertex.size();
-      free_vertex.push_back(v);
+      H.free_of[v] = (int32_t)H.free_vertex.size();
+      H.free_vertex.push_back(v);
     }
-  const int nF = (int)free_vertex.size();
+  const int nF = (int)H.free_vertex.size();
+  H.nF = nF;
   ctx->nF = nF;
   // incidence CSR over all vertices
-  std::vector<int64_t> inc_ptr(n + 1, 0);
-  for (int64_t q = 0; q < (int64_t)m * (d + 1); ++q) inc_ptr[T[q] + 1]++;
-  for (int v = 0; v < n; ++v) inc_ptr[v + 1] += inc_ptr[v];
-  std::vector<int32_t> inc(inc_ptr[n]);
+  H.inc_ptr.assign(n + 1, 0);
+  for (int64_t q = 0; q < (int64_t)m * (d + 1); ++q) H.inc_ptr[T[q] + 1]++;
+  for (int v = 0; v < n; ++v) H.inc_ptr[v + 1] += H.inc_ptr[v];
+  H.inc.resize(H.inc_ptr[n]);
   {
-    std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+    std::vector<int64_t> fill(H.inc_ptr.begin(), H.inc_ptr.end() - 1);
     for (int i = 0; i < m; ++i)
-      for (int j = 0; j <= d; ++j) inc[fill[T[(int64_t)i * (d + 1) + j]]++] = i * (d + 1) + j;
+      for (int j = 0; j <= d; ++j) H.inc[fill[T[(int64_t)i * (d + 1) + j]]++] = i * (d + 1) + j;
   }
-  auto grad_of = [&](int i, int j, double out[3]) {  // hat gradient of local vertex j
-    for (int a = 0; a < d; ++a) {
-      if (j > 0) out[a] = g[(int64_t)i * d * d + (j - 1) * d + a];
-      else {
-        double s = 0;
-        for (int jj = 0; jj < d; ++jj) s += g[(int64_t)i * d * d + jj * d + a];
-        out[a] = -s;
-      }
-    }
-  };
-  // rows of L for free vertices: free-free (free numbering) and free-pinned parts
-  std::vector<int64_t> Ap(nF + 1, 0), Cp(nF + 1, 0);
+  H.g = g;
+  H.T = T;
+  H.mu.resize(m);
+  for (int i = 0; i < m; ++i) H.mu[i] = (batch ? batch->rho_of[i] : rho) * w[i];
+  std::vector<int64_t> Ap, Cp;
   std::vector<int32_t> Ai, Ci;
   std::vector<double> Ax, Cx;
-  {
-    std::vector<int32_t> pos(n, -1), touched;
-    std::vector<double> acc;
-    for (int f = 0; f < nF; ++f) {
-      const int v = free_vertex[f];
-      touched.clear();
-      acc.clear();
-      for (int64_t q = inc_ptr[v]; q < inc_ptr[v + 1]; ++q) {
-        const int i = inc[q] / (d + 1), j = inc[q] % (d + 1);
-        double gj[3], gl[3];
-        grad_of(i, j, gj);
-        const double mu = (batch ? batch->rho_of[i] : rho) * w[i];
-        for (int l = 0; l <= d; ++l) {
-          grad_of(i, l, gl);
-          double dotv = 0;
-          for (int a = 0; a < d; ++a) dotv += gj[a] * gl[a];
-          const int u = T[(int64_t)i * (d + 1) + l];
-          if (pos[u] < 0) {
-            pos[u] = (int32_t)touched.size();
-            touched.push_back(u);
-            acc.push_back(0.0);
-          }
-          acc[pos[u]] += mu * dotv;
-        }
-      }
-      std::vector<std::pair<int32_t, double>> fr, cr;
-      for (size_t k = 0; k < touched.size(); ++k) {
-        const int u = touched[k];
-        if (free_of[u] >= 0) fr.push_back({free_of[u], acc[k]});
-        else cr.push_back({v2pin[u], acc[k]});
-        pos[u] = -1;
-      }
-      std::sort(fr.begin(), fr.end());
-      std::sort(cr.begin(), cr.end());
-      for (auto& pr : fr) { Ai.push_back(pr.first); Ax.push_back(pr.second); }
-      for (auto& pr : cr) { Ci.push_back(pr.first); Cx.push_back(pr.second); }
-      Ap[f + 1] = (int64_t)Ai.size();
-      Cp[f + 1] = (int64_t)Ci.size();
-    }
-  }
-  std::vector<double> coords((size_t)nF * 3, 0.0);
+  assemble_operator(H, H.mu.data(), Ap, Ai, Ax, Cp, Ci, Cx);
+  const std::vector<int32_t>& free_vertex = H.free_vertex;
+  const std::vector<int64_t>& inc_ptr = H.inc_ptr;
+  const std::vector<int32_t>& inc = H.inc;
+  H.coords.assign((size_t)nF * 3, 0.0);
   for (int f = 0; f < nF; ++f)
-    for (int a = 0; a < d_in; ++a) coords[(size_t)f * 3 + a] = V[(int64_t)free_vertex[f] * d_in + a];
+    for (int a = 0; a < d_in; ++a) H.coords[(size_t)f * 3 + a] = V[(int64_t)free_vertex[f] * d_in + a];
+  const std::vector<double>& coords = H.coords;
 
   // ---- factorization (once per mesh and rho)
   Factor fac;
@@ -800,43 +906,18 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     row_vertex[c] = free_vertex[fac.perm[c]];
     v2e[row_vertex[c]] = c;
   }
-  int width = 1;
-  for (int f = 0; f < nF; ++f) width = std::max<int>(width, (int)(Ap[f + 1] - Ap[f]));
-  std::vector<int32_t> ell_col((size_t)width * nF);
-  std::vector<double> ell_val((size_t)width * nF, 0.0);
-  std::vector<int64_t> fc_ptr(nF + 1, 0);
-  std::vector<int32_t> fc_col;
-  std::vector<double> fc_val;
-  for (int c = 0; c < nF; ++c) {
-    const int f = fac.perm[c];
-    int q = 0;
-    for (int64_t k = Ap[f]; k < Ap[f + 1]; ++k, ++q) {
-      ell_col[(size_t)q * nF + c] = fac.iperm[Ai[k]];
-      ell_val[(size_t)q * nF + c] = Ax[k];
-    }
-    for (; q < width; ++q) ell_col[(size_t)q * nF + c] = c;
-    for (int64_t k = Cp[f]; k < Cp[f + 1]; ++k) {
-      fc_col.push_back(Ci[k]);
-      fc_val.push_back(Cx[k]);
-    }
-    fc_ptr[c + 1] = (int64_t)fc_col.size();
-  }
+  OperatorArrays OA;
+  operator_arrays(fac, nF, n_pin, Ap, Ai, Ax, Cp, Ci, Cx, OA);
+  const int width = OA.width;
   ctx->ell_width = width;
-  // transpose of L_FC: for every pin, its (eliminated row, value) entries
-  std::vector<int64_t> cf_ptr(n_pin + 1, 0);
-  for (int32_t p : fc_col) cf_ptr[p + 1]++;
-  for (int p = 0; p < n_pin; ++p) cf_ptr[p + 1] += cf_ptr[p];
-  std::vector<int32_t> cf_row(fc_col.size());
-  std::vector<double> cf_val(fc_col.size());
-  {
-    std::vector<int64_t> fill(cf_ptr.begin(), cf_ptr.end() - 1);
-    for (int c = 0; c < nF; ++c)
-      for (int64_t q = fc_ptr[c]; q < fc_ptr[c + 1]; ++q) {
-        const int64_t dst = fill[fc_col[q]]++;
-        cf_row[dst] = c;
-        cf_val[dst] = fc_val[q];
-      }
-  }
+  const std::vector<int32_t>& ell_col = OA.ell_col;
+  const std::vector<double>& ell_val = OA.ell_val;
+  const std::vector<int64_t>& fc_ptr = OA.fc_ptr;
+  const std::vector<int32_t>& fc_col = OA.fc_col;
+  const std::vector<double>& fc_val = OA.fc_val;
+  const std::vector<int64_t>& cf_ptr = OA.cf_ptr;
+  const std::vector<int32_t>& cf_row = OA.cf_row;
+  const std::vector<double>& cf_val = OA.cf_val;
 
   ctx->nodes_h = fac.nodes;
   ctx->n_levels = fac.n_levels;
@@ -949,8 +1030,67 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   ctx->info.n_free = nF;
   ctx->info.kernels_per_iteration = kernels_per_iteration(ctx);
   ctx->info.kernels_per_check = 3;
+  if (ctx->prm.penalty_schedule == 1) {
+    if ((st = upload(ctx, &ctx->mu64, H.mu)) != FFA_OK) return st;
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::vector<float>().swap(fac.blocks);
+    std::vector<double>().swap(fac.blocks64);
+    ctx->op = std::move(H);
+    ctx->op.fac = std::move(fac);
+  }
   (void)t_setup0;
   return FFA_OK;
+}
+
+// New penalties from ctx->mu64 (the paper's schedule): assemble L again on the
+// host, decompose it on the same ordering and supernodes (Algorithm 2,
+// decompose(L)), and refresh every device form of L and the W-step
+// right-hand-side terms of the current state.
+ffa_status apply_penalties(ffa_ctx* ctx) {
+  OperatorHost& H = ctx->op;
+  cudaStream_t s = ctx->stream;
+  FFA_CUDA(cudaMemcpyAsync(H.mu.data(), ctx->mu64, (size_t)H.m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FFA_CUDA(cudaStreamSynchronize(s));
+  const double t0 = now_s();
+  std::vector<int64_t> Ap, Cp;
+  std::vector<int32_t> Ai, Ci;
+  std::vector<double> Ax, Cx;
+  assemble_operator(H, H.mu.data(), Ap, Ai, Ax, Cp, Ci, Cx);
+  FactorInput in;
+  in.nF = H.nF;
+  in.Ap = Ap.data();
+  in.Ai = Ai.data();
+  in.Ax = Ax.data();
+  in.coords = H.coords.data();
+  in.leaf_size = ctx->prm.nd_leaf_size;
+  in.threads = ctx->prm.host_threads;
+  std::string msg;
+  const int rc = refactor(in, H.fac, msg);
+  if (rc == 3) return fail(ctx, FFA_ERR_SINGULAR_SYSTEM, msg);
+  if (rc != 0) return fail(ctx, FFA_ERR_INVALID_ARG, msg);
+  FFA_CUDA(cudaMemcpy(ctx->blocks, H.fac.blocks.data(), H.fac.blocks.size() * sizeof(float), cudaMemcpyHostToDevice));
+  std::vector<float>().swap(H.fac.blocks);
+  OperatorArrays OA;
+  operator_arrays(H.fac, H.nF, H.n_pin, Ap, Ai, Ax, Cp, Ci, Cx, OA);
+  FFA_CUDA(cudaMemcpy(ctx->ell_val, OA.ell_val.data(), OA.ell_val.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (!OA.fc_val.empty()) {
+    FFA_CUDA(cudaMemcpy(ctx->fc_val, OA.fc_val.data(), OA.fc_val.size() * sizeof(double), cudaMemcpyHostToDevice));
+    FFA_CUDA(cudaMemcpy(ctx->cf_val, OA.cf_val.data(), OA.cf_val.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  launch_pin_rhs(ctx->d, ctx->nF, ctx->fc_ptr, ctx->fc_col, ctx->fc_val, ctx->pin_pos, ctx->cst, s);
+  launch_rhs_terms(local_launch(ctx, false, ctx->vrec), s);
+  FFA_CUDA(cudaGetLastError());
+  FFA_CUDA(cudaStreamSynchronize(s));
+  ctx->seconds_refactor += now_s() - t0;
+  return FFA_OK;
+}
+
+// iteration (counted from ffa_init) after which the next rescaling happens:
+// 1..5, then every floor(5 (3/2)^p) iterations, p = events so far (Sec. 6)
+int64_t next_rescale_iter(const ffa_ctx* ctx) {
+  const int p = ctx->n_rescales;
+  if (p < 5) return p + 1;
+  return ctx->last_event_iter + (int64_t)std::floor(5.0 * std::pow(1.5, (double)p));
 }
 
 void destroy_impl(ffa_ctx* ctx) {
@@ -1083,6 +1223,8 @@ ffa_status ffa_default_params(ffa_params* p) {
   p->nd_leaf_size = 64;
   p->host_threads = 0;
   p->solve_schedule = 1;
+  p->penalty_schedule = 0;
+  p->rescale_rho = 5.0;
   return FFA_OK;
 }
 
@@ -1142,6 +1284,14 @@ ffa_status ffa_init(ffa_ctx* ctx, const double* W0) {
   if (st != FFA_OK) return st;
   launch_init_polar(local_launch(ctx, false, ctx->vrec), ctx->stream);
   FFA_CUDA(cudaGetLastError());
+  if (ctx->prm.penalty_schedule == 1) {
+    // Algorithm 2: mu_i = max(mu_min,i, w_i) from P^0, then decompose(L)
+    launch_penalty(local_launch(ctx, false, ctx->vrec), 0, ctx->mu64, ctx->prm.rescale_rho, ctx->stream);
+    FFA_CUDA(cudaGetLastError());
+    if ((st = apply_penalties(ctx)) != FFA_OK) return st;
+    ctx->n_rescales = 0;
+    ctx->last_event_iter = 0;
+  }
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->initialized = true;
   ctx->iter_total = 0;
@@ -1156,19 +1306,27 @@ ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_
   ffa_status st = ensure_graphs(ctx);
   if (st != FFA_OK) return st;
   const int ce = ctx->prm.check_every;
+  const bool sched = ctx->prm.penalty_schedule == 1;
   int done = 0;
   bool have = false;
   while (done < max_iter) {
-    const int left = max_iter - done;
-    if (left >= ce) {
-      FFA_CUDA(cudaGraphLaunch(ctx->g_batch, ctx->stream));
-      done += ce;
-    } else {
-      for (int k = 0; k < left - 1; ++k) FFA_CUDA(cudaGraphLaunch(ctx->g_one, ctx->stream));
-      FFA_CUDA(cudaGraphLaunch(ctx->g_one_check, ctx->stream));
-      done += left;
+    int step = std::min(max_iter - done, ce);
+    bool at_event = false;
+    if (sched) {
+      const int64_t ev = next_rescale_iter(ctx) - (ctx->iter_total + done);
+      if (ev <= step) {
+        step = (int)std::max<int64_t>(ev, 1);
+        at_event = true;
+      }
     }
-    if (stop_at_tol || done == max_iter) {
+    if (step == ce) {
+      FFA_CUDA(cudaGraphLaunch(ctx->g_batch, ctx->stream));
+    } else {
+      for (int k = 0; k < step - 1; ++k) FFA_CUDA(cudaGraphLaunch(ctx->g_one, ctx->stream));
+      FFA_CUDA(cudaGraphLaunch(ctx->g_one_check, ctx->stream));
+    }
+    done += step;
+    if (stop_at_tol || done == max_iter || at_event) {
       FFA_CUDA(cudaMemcpyAsync(ctx->stats_h, ctx->stats_d, sizeof(ffa_stats), cudaMemcpyDeviceToHost, ctx->stream));
       FFA_CUDA(cudaStreamSynchronize(ctx->stream));
       if (device_wait_failed(ctx)) {
@@ -1187,12 +1345,24 @@ ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_
       }
       if (stop_at_tol && ctx->last.converged) break;
     }
+    if (at_event) {
+      // the test of an event iteration is taken before its rescaling
+      launch_penalty(local_launch(ctx, false, ctx->vrec), 1, ctx->mu64, ctx->prm.rescale_rho, ctx->stream);
+      FFA_CUDA(cudaGetLastError());
+      if ((st = apply_penalties(ctx)) != FFA_OK) {
+        ctx->iter_total += done;
+        return st;
+      }
+      ctx->n_rescales++;
+      ctx->last_event_iter = ctx->iter_total + done;
+    }
   }
   ctx->iter_total += done;
   if (!have) {
     ctx->last = ffa_stats{};
   }
   ctx->last.iters = done;
+  ctx->last.rescales = ctx->n_rescales;
   if (stats) *stats = ctx->last;
   return FFA_OK;
 }
@@ -1204,6 +1374,27 @@ ffa_status ffa_get_W(ffa_ctx* ctx, double* W_out) {
   ctx->err.clear();
   FFA_CUDA(cudaMemcpyAsync(W_out, ctx->W, (size_t)ctx->n * ctx->d * 8, cudaMemcpyDefault, ctx->stream));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  return FFA_OK;
+}
+
+ffa_status ffa_get_penalties(ffa_ctx* ctx, double* mu) {
+  if (!ctx || !mu) return FFA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  const int m = ctx->m;
+  std::vector<double> h(m);
+  if (ctx->mu64) {
+    FFA_CUDA(cudaMemcpyAsync(h.data(), ctx->mu64, (size_t)m * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  } else if (ctx->fp64) {
+    FFA_CUDA(cudaMemcpyAsync(h.data(), ctx->e.mu, (size_t)m * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::vector<float> f(m);
+    FFA_CUDA(cudaMemcpyAsync(f.data(), ctx->e.mu, (size_t)m * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < m; ++i) h[i] = f[i];
+  }
+  FFA_CUDA(cudaMemcpy(mu, h.data(), (size_t)m * 8, cudaMemcpyDefault));
   return FFA_OK;
 }
 
@@ -1296,6 +1487,7 @@ ffa_status ffa_gradient(ffa_ctx* ctx, const double* W, double* dEdW) {
 ffa_status ffa_get_info(ffa_ctx* ctx, ffa_info* info) {
   if (!ctx || !info) return FFA_ERR_INVALID_ARG;
   ctx->info.kernels_per_iteration = kernels_per_iteration(ctx);   // the schedule may have been retuned
+  ctx->info.seconds_refactor = ctx->seconds_refactor;
   *info = ctx->info;
   return FFA_OK;
 }
@@ -1352,6 +1544,8 @@ ffa_status ffa_forward_unrolled(ffa_ctx* ctx, int32_t K, int32_t ckpt_every) {
   ctx->err.clear();
   if (!ctx->initialized) return fail(ctx, FFA_ERR_NOT_INITIALIZED, "ffa_init has not been called");
   if (K < 1 || ckpt_every < 1) return fail(ctx, FFA_ERR_INVALID_ARG, "K and ckpt_every must be >= 1");
+  if (ctx->prm.penalty_schedule != 0)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation needs fixed penalties (penalty_schedule 0)");
   ffa_status st = ensure_graphs(ctx);
   if (st != FFA_OK) return st;
   const int C = std::min(ckpt_every, K);

@@ -259,90 +259,15 @@ struct NumericWork {
   explicit NumericWork(int nF) : pos(nF, -1) {}
 };
 
-}  // namespace
-
-// ---------------------------------------------------------------------------
-int build_factor(const FactorInput& in, Factor& f, std::string& err) {
-  const double t0 = now_s();
-  const int threads = resolve_threads(in.threads);
-  if (in.nF <= 0) {
-    err = "no free vertices";
-    return 1;
-  }
-  f = Factor();
-  f.nF = in.nF;
-
-  // ---- ordering: one dissection per connected piece is not needed; the split
-  // handles disconnected sets through empty separators.
-  Dissection nd(in);
-  std::vector<int32_t> all(in.nF);
-  for (int32_t v = 0; v < in.nF; ++v) all[v] = v;
-  int root_tree = nd.build(all);
-  std::vector<int> tree2node(nd.tree.size(), -1);
-  f.perm.reserve(in.nF);
-  number_tree(nd.tree, root_tree, f, tree2node);
-  if ((int)f.perm.size() != in.nF) {
-    err = "nested dissection lost vertices";
-    return 1;
-  }
-  f.iperm.assign(in.nF, -1);
-  for (int32_t c = 0; c < in.nF; ++c) f.iperm[f.perm[c]] = c;
+// numeric multifrontal factorization into the blocks of an analyzed Factor
+int numeric(const FactorInput& in, Factor& f, std::string& err, int threads) {
+  const double t1 = now_s();
   const int nn = static_cast<int>(f.nodes.size());
   std::vector<std::vector<int32_t>> children(nn);
   for (int s = 0; s < nn; ++s)
     if (f.nodes[s].parent >= 0) children[f.nodes[s].parent].push_back(s);
-  int maxlev = 0;
-  for (auto& s : f.nodes) maxlev = std::max(maxlev, s.level);
-  f.n_levels = maxlev + 1;
-
-  // ---- symbolic: structure of every supernode
-  {
-    std::vector<int32_t> mark(in.nF, -1);
-    std::vector<int32_t> tmp;
-    for (int s = 0; s < nn; ++s) {
-      Supernode& sn = f.nodes[s];
-      const int32_t c1 = sn.col0 + sn.ncol;
-      tmp.clear();
-      for (int32_t c = sn.col0; c < c1; ++c) {
-        int32_t old = f.perm[c];
-        for (int64_t k = in.Ap[old]; k < in.Ap[old + 1]; ++k) {
-          int32_t r = f.iperm[in.Ai[k]];
-          if (r >= c1 && mark[r] != s) {
-            mark[r] = s;
-            tmp.push_back(r);
-          }
-        }
-      }
-      for (int ch : children[s]) {
-        const Supernode& cn = f.nodes[ch];
-        for (int64_t q = 0; q < cn.nrow; ++q) {
-          int32_t r = f.rows[cn.row_off + q];
-          if (r >= c1 && mark[r] != s) {
-            mark[r] = s;
-            tmp.push_back(r);
-          }
-        }
-      }
-      std::sort(tmp.begin(), tmp.end());
-      sn.row_off = static_cast<int64_t>(f.rows.size());
-      sn.nrow = static_cast<int32_t>(tmp.size());
-      f.rows.insert(f.rows.end(), tmp.begin(), tmp.end());
-    }
-  }
-  int64_t total = 0, flops = 0;
-  for (auto& sn : f.nodes) {
-    sn.ld = (sn.ncol + sn.nrow + 3) / 4 * 4;
-    sn.blk_off = total;
-    total += (int64_t)sn.ld * sn.ncol;
-    const double ns = sn.ncol, ms = sn.nrow;
-    // partial Cholesky + explicit inverse + M = L21 inv(L11), FMA = 2 flops
-    flops += (int64_t)(ns * ns * ns / 3.0 + ns * ns * ms + ns * ms * ms + ns * ns * ns / 3.0 + ms * ns * ns);
-  }
-  f.flops = flops;
-  const double t1 = now_s();
-  f.t_analyze = t1 - t0;
-
-  // ---- numeric multifrontal factorization
+  int64_t total = 0;
+  for (auto& sn : f.nodes) total = std::max<int64_t>(total, sn.blk_off + (int64_t)sn.ld * sn.ncol);
   f.blocks.assign(total, 0.0f);
   if (in.keep_double) f.blocks64.assign(total, 0.0);
   std::vector<std::vector<double>> upd(nn);
@@ -489,6 +414,101 @@ int build_factor(const FactorInput& in, Factor& f, std::string& err) {
   }
   f.t_factor = now_s() - t1;
   return 0;
+}
+
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int build_factor(const FactorInput& in, Factor& f, std::string& err) {
+  const double t0 = now_s();
+  const int threads = resolve_threads(in.threads);
+  if (in.nF <= 0) {
+    err = "no free vertices";
+    return 1;
+  }
+  f = Factor();
+  f.nF = in.nF;
+
+  // ---- ordering: one dissection per connected piece is not needed; the split
+  // handles disconnected sets through empty separators.
+  Dissection nd(in);
+  std::vector<int32_t> all(in.nF);
+  for (int32_t v = 0; v < in.nF; ++v) all[v] = v;
+  int root_tree = nd.build(all);
+  std::vector<int> tree2node(nd.tree.size(), -1);
+  f.perm.reserve(in.nF);
+  number_tree(nd.tree, root_tree, f, tree2node);
+  if ((int)f.perm.size() != in.nF) {
+    err = "nested dissection lost vertices";
+    return 1;
+  }
+  f.iperm.assign(in.nF, -1);
+  for (int32_t c = 0; c < in.nF; ++c) f.iperm[f.perm[c]] = c;
+  const int nn = static_cast<int>(f.nodes.size());
+  std::vector<std::vector<int32_t>> children(nn);
+  for (int s = 0; s < nn; ++s)
+    if (f.nodes[s].parent >= 0) children[f.nodes[s].parent].push_back(s);
+  int maxlev = 0;
+  for (auto& s : f.nodes) maxlev = std::max(maxlev, s.level);
+  f.n_levels = maxlev + 1;
+
+  // ---- symbolic: structure of every supernode
+  {
+    std::vector<int32_t> mark(in.nF, -1);
+    std::vector<int32_t> tmp;
+    for (int s = 0; s < nn; ++s) {
+      Supernode& sn = f.nodes[s];
+      const int32_t c1 = sn.col0 + sn.ncol;
+      tmp.clear();
+      for (int32_t c = sn.col0; c < c1; ++c) {
+        int32_t old = f.perm[c];
+        for (int64_t k = in.Ap[old]; k < in.Ap[old + 1]; ++k) {
+          int32_t r = f.iperm[in.Ai[k]];
+          if (r >= c1 && mark[r] != s) {
+            mark[r] = s;
+            tmp.push_back(r);
+          }
+        }
+      }
+      for (int ch : children[s]) {
+        const Supernode& cn = f.nodes[ch];
+        for (int64_t q = 0; q < cn.nrow; ++q) {
+          int32_t r = f.rows[cn.row_off + q];
+          if (r >= c1 && mark[r] != s) {
+            mark[r] = s;
+            tmp.push_back(r);
+          }
+        }
+      }
+      std::sort(tmp.begin(), tmp.end());
+      sn.row_off = static_cast<int64_t>(f.rows.size());
+      sn.nrow = static_cast<int32_t>(tmp.size());
+      f.rows.insert(f.rows.end(), tmp.begin(), tmp.end());
+    }
+  }
+  int64_t total = 0, flops = 0;
+  for (auto& sn : f.nodes) {
+    sn.ld = (sn.ncol + sn.nrow + 3) / 4 * 4;
+    sn.blk_off = total;
+    total += (int64_t)sn.ld * sn.ncol;
+    const double ns = sn.ncol, ms = sn.nrow;
+    // partial Cholesky + explicit inverse + M = L21 inv(L11), FMA = 2 flops
+    flops += (int64_t)(ns * ns * ns / 3.0 + ns * ns * ms + ns * ms * ms + ns * ns * ns / 3.0 + ms * ns * ns);
+  }
+  f.flops = flops;
+  const double t1 = now_s();
+  f.t_analyze = t1 - t0;
+
+  return numeric(in, f, err, threads);
+}
+
+int refactor(const FactorInput& in, Factor& f, std::string& err) {
+  if (in.nF != f.nF || f.nodes.empty()) {
+    err = "refactor: the operator's pattern does not match the analyzed factor";
+    return 1;
+  }
+  return numeric(in, f, err, resolve_threads(in.threads));
 }
 
 void host_solve(const Factor& f, const double* b, double* x, int nrhs) {

@@ -56,6 +56,11 @@ struct FactorInput {
 // Returns 0 on success, 3 if L_FF is not positive definite, 1 on bad input.
 int build_factor(const FactorInput& in, Factor& f, std::string& err);
 
+// New values on the same pattern (the penalties changed, the mesh did not): the
+// ordering and the supernode structure of f are kept and only the blocks are
+// recomputed.  Same return codes.
+int refactor(const FactorInput& in, Factor& f, std::string& err);
+
 // Double-precision host application of the factor (setup diagnostics only):
 // x = L_FF^{-1} b for nrhs interleaved right-hand sides, eliminated numbering
 // handled internally (b and x in free numbering).  Needs keep_double.

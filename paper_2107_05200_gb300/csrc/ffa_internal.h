@@ -93,6 +93,10 @@ void launch_local_step(const LocalLaunch& L, cudaStream_t s);
 void launch_init_polar(const LocalLaunch& L, cudaStream_t s);
 // W-step right-hand-side terms from the stored U, P, Lambda (after a state restore)
 void launch_rhs_terms(const LocalLaunch& L, cudaStream_t s);
+// the paper's penalty schedule: mode 0 mu = max(mu_min(P), w) after the polar
+// initialization, mode 1 the rescaling after an iteration (mu and Lambda updated,
+// mu64 = the penalties in double); single-energy contexts only
+void launch_penalty(const LocalLaunch& L, int mode, double* mu64, double rho, cudaStream_t s);
 // energy (mode 0: sum w f(J) + flips into partials) or gradient terms (mode 1: contrib2)
 void launch_energy_terms(const LocalLaunch& L, int mode, cudaStream_t s);
 

@@ -614,6 +614,104 @@ __global__ void __launch_bounds__(kLocalBlock) k_rhs_terms(ElemBufs e, int m) {
   store_terms<D, R>(e.contrib, i, g, Rhs);
 }
 
+// ---------------------------------------------------------------------------
+// The paper's penalty schedule (Algorithm 2; Sec. 6, "Rescaling mu_i and
+// Lambda"), per element, in double: MODE 0 sets mu_i = max(mu_min,i(P_i), w_i)
+// (after the polar initialization); MODE 1 rescales after an iteration: with
+// e_prim_i = |J_i - U_i P_i| and e_dual_i = mu_i |J_i - J_i^prev| (eq.
+// primaldualerror; an error below 2^-40 (1 + |J_i|), times mu_i for e_dual, counts
+// as zero), mu_i is multiplied by rho/2 if e_prim_i > rho e_dual_i and
+// divided by rho/2 if e_dual_i > rho e_prim_i, never below mu_min,i(P_i)/2, and the
+// scaled multiplier is multiplied by mu_old/mu_new (mu_i Lambda_i is unchanged).
+// mu64 holds the penalties in double (the host refactors L from it); e.mu gets
+// the local step's precision.
+// ---------------------------------------------------------------------------
+template <int D, typename R, int EN, int MODE>
+__global__ void __launch_bounds__(kLocalBlock) k_penalty(ElemBufs e, int m, const void* __restrict__ vrec,
+                                                        double* __restrict__ mu64, double rho) {
+  const int i = blockIdx.x * kLocalBlock + threadIdx.x;
+  if (i >= m) return;
+  const R* Pp = reinterpret_cast<const R*>(e.P);
+  double P[D][D];
+  if constexpr (D == 2) {
+    P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[1][1] = Pp[2 * (int64_t)m + i];
+  } else {
+    P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[0][2] = P[2][0] = Pp[2 * (int64_t)m + i];
+    P[1][1] = Pp[3 * (int64_t)m + i]; P[1][2] = P[2][1] = Pp[4 * (int64_t)m + i]; P[2][2] = Pp[5 * (int64_t)m + i];
+  }
+  // eigenvalues of P; |grad f(P)|^2 = sum (p - p^-3)^2 (SD) or sum (p - 1/p)^2 (SG)
+  double ev[3];
+  if constexpr (D == 2) {
+    const double h = 0.5 * (P[0][0] + P[1][1]), dd = 0.5 * (P[0][0] - P[1][1]);
+    const double r = sqrt(dd * dd + P[0][1] * P[0][1]);
+    ev[0] = h + r;
+    ev[1] = h - r;
+  } else {
+    double V[3][3];
+    sym3_eig<double>(P[0][0], P[0][1], P[0][2], P[1][1], P[1][2], P[2][2], ev, V);
+  }
+  const bool sg = EN == 1;
+  double gn2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double p = ev[k];
+    const double gk = sg ? p - 1.0 / p : p - 1.0 / (p * p * p);
+    gn2 += gk * gk;
+  }
+  const double w = (double)reinterpret_cast<const R*>(e.w)[i];
+  const double mmin = penalty_mu_min<D>(gn2, w, sg);
+  double mu_new;
+  if constexpr (MODE == 0) {
+    mu_new = fmax(mmin, w);
+  } else {
+    const double mu_old = mu64[i];
+    int vid[D + 1];
+    R g[D][D], wr, mur;
+    load_element<D, R>(e, m, i, vid, g, wr, mur);
+    R J[D][D], dJ[D][D];
+    element_jacobians<D, R>(vid, g, vrec, J, dJ);
+    const R* Up = reinterpret_cast<const R*>(e.U);
+    double U[D][D];
+    if constexpr (D == 2) {
+      const double c = Up[i], sn = Up[(int64_t)m + i];
+      U[0][0] = c; U[0][1] = -sn; U[1][0] = sn; U[1][1] = c;
+    } else {
+      double qt[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) qt[k] = Up[(int64_t)k * m + i];
+      quat_to_rot<double>(qt, U);
+    }
+    double rp = 0.0, rd = 0.0, rj = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        double up = 0.0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) up += U[a][l] * P[l][k];
+        const double r = (double)J[a][k] - up;
+        rp += r * r;
+        rd += (double)dJ[a][k] * (double)dJ[a][k];
+        rj += (double)J[a][k] * (double)J[a][k];
+      }
+    // an error below the rounding floor of the element counts as zero
+    const double floor_e = 0x1p-40 * (1.0 + sqrt(rj));
+    double ep = sqrt(rp), ed = mu_old * sqrt(rd);
+    if (!(ep > floor_e)) ep = 0.0;
+    if (!(ed > mu_old * floor_e)) ed = 0.0;
+    mu_new = mu_old;
+    if (ep > rho * ed) mu_new = mu_old * (0.5 * rho);
+    else if (ed > rho * ep) mu_new = mu_old / (0.5 * rho);
+    mu_new = fmax(mu_new, 0.5 * mmin);
+    const double f = mu_old / mu_new;
+    R* Lp = reinterpret_cast<R*>(e.Lam);
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) Lp[(int64_t)q * m + i] = (R)((double)Lp[(int64_t)q * m + i] * f);
+  }
+  mu64[i] = mu_new;
+  reinterpret_cast<R*>(e.mu)[i] = (R)mu_new;
+}
+
 template <int D, typename R, int EN>
 void dispatch_local(const LocalLaunch& L, cudaStream_t s) {
   const int bs = L.block > 0 ? L.block : kLocalBlock;
@@ -642,6 +740,20 @@ void launch_rhs_terms(const LocalLaunch& L, cudaStream_t s) {
     if (L.fp64) k_rhs_terms<3, double><<<grid, kLocalBlock, 0, s>>>(L.e, L.m);
     else k_rhs_terms<3, float><<<grid, kLocalBlock, 0, s>>>(L.e, L.m);
   }
+}
+
+void launch_penalty(const LocalLaunch& L, int mode, double* mu64, double rho, cudaStream_t s) {
+  const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
+#define FFA_PEN(D, R, EN)                                                                                   \
+  do {                                                                                                      \
+    if (mode == 0) k_penalty<D, R, EN, 0><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, mu64, rho);        \
+    else k_penalty<D, R, EN, 1><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, mu64, rho);                  \
+  } while (0)
+#define FFA_PEN2(D, R) do { if (L.energy == 1) FFA_PEN(D, R, 1); else FFA_PEN(D, R, 0); } while (0)
+  if (L.d == 2) { if (L.fp64) FFA_PEN2(2, double); else FFA_PEN2(2, float); }
+  else { if (L.fp64) FFA_PEN2(3, double); else FFA_PEN2(3, float); }
+#undef FFA_PEN2
+#undef FFA_PEN
 }
 
 void launch_init_polar(const LocalLaunch& L, cudaStream_t s) {

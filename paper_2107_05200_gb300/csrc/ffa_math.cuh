@@ -173,6 +173,40 @@ __device__ __forceinline__ void sym3_eig(R a00, R a01, R a02, R a11, R a12, R a2
 }
 
 // ---------------------------------------------------------------------------
+// The penalty bound of the paper's schedule (Lemma 1, Proposition 1, Sec. 6), in
+// double.  gnorm2 = |grad f(P)|^2; B = sqrt(5 (1 + gnorm2)); C^L (SG) is the
+// positive root of x^2 + B x - 1 (written as 2 / (B + sqrt(B^2 + 4)) to avoid
+// cancellation), C^LG (SD) the positive root of x^4 + B x^3 - 1, which is
+// increasing and convex on [0, 1] with value B >= 0 at 1, so Newton from 1 falls
+// monotonically onto it; F = 1 + sqrt(d)/(C^L)^2 (SG) or 1 + 3 sqrt(d)/(C^LG)^4
+// (SD), F^2 capped at eps_m^(-1/4); mu_min = (-w + sqrt(w^2 + 16 w^2 F^2)) / 2
+// (gamma = 1, eps = 0).
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ double penalty_mu_min(double gnorm2, double w, bool sg) {
+  const double B = sqrt(5.0 * (1.0 + gnorm2));
+  double F;
+  if (sg) {
+    const double C = 2.0 / (B + sqrt(B * B + 4.0));
+    F = 1.0 + sqrt((double)D) / (C * C);
+  } else {
+    double x = 1.0;
+#pragma unroll 1
+    for (int it = 0; it < 200; ++it) {
+      const double g = x * x * x * (x + B) - 1.0;
+      const double dg = x * x * (4.0 * x + 3.0 * B);
+      const double xn = x - g / dg;
+      if (!(xn < x)) break;
+      x = xn;
+    }
+    const double x2 = x * x;
+    F = 1.0 + 3.0 * sqrt((double)D) / (x2 * x2);
+  }
+  F = fmin(F, sqrt(8192.0));   // F^2 <= eps_m^(-1/4) = 2^13
+  return 0.5 * (-w + sqrt(w * w + 16.0 * w * w * F * F));
+}
+
+// ---------------------------------------------------------------------------
 // signed 3x3 SVD: Q = U diag(s) V^T with U, V in SO(3), |s0| >= |s1| >= |s2|,
 // s0, s1 >= 0 and sign(s2) = sign(det Q).  Jacobi on Q^T Q gives V; Givens QR
 // of Q V gives U and the signed diagonal.

@@ -38,12 +38,17 @@ def _ptr(a, dtype):
 
 
 class Solver:
-    """One mesh, one energy, fixed penalties: setup once, then init / iterate."""
+    """One mesh, one energy: setup once, then init / iterate.
+
+    penalties="fixed": mu_i = rho w_i, L decomposed once; penalties="paper": the
+    paper's schedule (initial mu_i = max(mu_min,i, w_i) and per-element rescaling by
+    rescale_rho/2 at the paper's events, L decomposed again after each event)."""
 
     def __init__(self, V, T, pins=None, pin_pos=None, energy: str = "sd", rho: float = 1.0,
                  eps_abs: float = 1e-6, eps_rel: float = 1e-5, check_every: int = 10,
                  precision: str = "fp32", refine_sweeps: int = 2, leaf_size: int = 64,
-                 require_flip_free: bool = True, host_threads: int = 0, schedule: int = 1, stream=None):
+                 require_flip_free: bool = True, host_threads: int = 0, schedule: int = 1,
+                 penalties: str = "fixed", rescale_rho: float = 5.0, stream=None):
         self._lib = N.load()
         self._ctx = None
         Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
@@ -67,6 +72,10 @@ class Solver:
         prm.nd_leaf_size = int(leaf_size)
         prm.host_threads = int(host_threads)
         prm.solve_schedule = int(schedule)
+        if penalties not in ("fixed", "paper"):
+            raise ValueError("penalties must be 'fixed' or 'paper'")
+        prm.penalty_schedule = 1 if penalties == "paper" else 0
+        prm.rescale_rho = float(rescale_rho)
         n_pin = 0 if pins is None else int(len(pins))
         self.n_pin = max(n_pin, 1)
         pP, self._pins = _ptr(pins, np.int32) if n_pin else (None, None)
@@ -128,6 +137,13 @@ class Solver:
         self._check(self._lib.ffa_get_state(self._ctx, C.c_void_p(U.ctypes.data), C.c_void_p(P.ctypes.data),
                                             C.c_void_p(L.ctypes.data)))
         return U, P, L
+
+    def penalties(self) -> np.ndarray:
+        """The current penalties mu_i (m values)."""
+        out = np.empty(self.m, np.float64)
+        po, _ = _ptr(out, np.float64)
+        self._check(self._lib.ffa_get_penalties(self._ctx, po))
+        return out
 
     def energy(self, W=None) -> float:
         p, keep = _ptr(W, np.float64)

@@ -87,3 +87,16 @@ def test_paper_schedule_reaches_the_tolerance_flip_free_on_the_disk():
     lhs = o.w[:, None, None] * admm.grad_f(s.P, wl.energy)
     rhs = o.mu[:, None, None] * admm.symm(np.transpose(s.U, (0, 2, 1)) @ s.Lam)
     assert np.abs(lhs - rhs).max() < 1e-8 * (1.0 + np.abs(lhs).max())
+
+
+def test_elements_at_rest_are_not_rescaled_on_rounding_noise():
+    # J = U P up to rounding and J = J_prev: both element errors count as zero, so
+    # neither branch of the rule fires and mu keeps its value
+    wl = wk.cube_deform(cells=2, seed=35)
+    o = admm.Oracle.from_workload(wl)
+    s0 = o.init(wl.V)                      # the rest pose: J = I
+    s1 = o.local_steps(s0, wl.V.copy())
+    ep, ed = schedule.element_errors(o, s0, s1)
+    assert np.all(ep == 0.0) and np.all(ed == 0.0)
+    new, L2 = schedule.rescale(o.mu, s1.Lam, ep, ed, 0.0 * o.mu)
+    np.testing.assert_array_equal(new, o.mu)
