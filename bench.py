@@ -84,8 +84,9 @@ def solve_fingerprint() -> str:
         src = f.read()
     a = src.index("// supernodal solves.")
     b = src.index("}  // namespace\n", a)
+    keys = ("kSolve", "kFwd", "kBwd", "kNarrow", "kNodeMax")
     with open(os.path.join(csrc, "ffa_internal.h")) as f:
-        consts = "".join(line for line in f if line.startswith("constexpr"))
+        consts = "".join(line for line in f if line.startswith("constexpr") and any(k in line for k in keys))
     return hashlib.sha256((src[a:b] + consts).encode()).hexdigest()[:16]
 
 

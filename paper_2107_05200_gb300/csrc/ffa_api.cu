@@ -993,7 +993,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   if ((st = dalloc_bytes(ctx, &ctx->vrec, rec_bytes)) != FFA_OK) return st;
   if ((st = dalloc_bytes(ctx, &ctx->vrec_scratch, rec_bytes)) != FFA_OK) return st;
   ctx->n_local_blocks = (m + ctx->local_block - 1) / ctx->local_block;
-  ctx->n_vert_blocks = (n + kVertexBlock - 1) / kVertexBlock;
+  ctx->n_vert_blocks = ((int64_t)n * kGatherLanes + kVertexBlock - 1) / kVertexBlock;
   ctx->n_res_blocks = (nF + kVertexBlock - 1) / kVertexBlock;
   // sized for the smallest local-step block (64 threads) the autotuner may pick
   if ((st = dalloc(ctx, &ctx->local_partials, (size_t)((m + 63) / 64) * NQ)) != FFA_OK) return st;

@@ -19,6 +19,7 @@ enum { QV_GTL = 0, QV_NUM, QV_DEN, NQV };
 
 constexpr int kLocalBlock = 128;
 constexpr int kVertexBlock = 256;
+constexpr int kGatherLanes = 4;   // lanes sharing one row of the vertex gathers
 constexpr int kSolveThreads = 256;              // threads of a supernodal-solve block
 constexpr int kSolveMinBlocks = 4;              // resident solve blocks per SM the registers allow
 constexpr int kSolveWarps = kSolveThreads / 32;

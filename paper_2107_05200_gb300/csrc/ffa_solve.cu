@@ -83,59 +83,88 @@ __global__ void __launch_bounds__(kVertexBlock) k_vertex_update(VertexLaunch V) 
 
 // ---------------------------------------------------------------------------
 // gather of per-element vertex terms: out_row = sum over the incidences of the
-// row's vertex (+ add_row); float terms are summed in double-float
+// row's vertex (+ add_row); float terms are summed in double-float.  kGatherLanes
+// consecutive lanes share a row, each taking every kGatherLanes-th incidence with
+// its loads issued together, and the lane sums meet by shuffles, so a row costs a
+// few dependent load latencies instead of one per incidence.
 // ---------------------------------------------------------------------------
 template <int D, bool FP64>
 __global__ void __launch_bounds__(kVertexBlock) k_gather(GatherLaunch G) {
-  const int row = blockIdx.x * kVertexBlock + threadIdx.x;
+  const int t = blockIdx.x * kVertexBlock + threadIdx.x;
+  const int row = t / kGatherLanes, sub = t % kGatherLanes;
+  const bool active = row < G.rows;
   double outv[D];
   double sq = 0.0;
-  if (row < G.rows) {
+  int64_t q0 = 0, q1 = 0;
+  if (active) {
     const int v = G.row_vertex ? G.row_vertex[row] : row;
-    const int64_t q0 = G.inc_ptr[v], q1 = G.inc_ptr[v + 1];
-    if constexpr (FP64) {
-      const double* c = reinterpret_cast<const double*>(G.contrib);
-      double acc[D];
+    q0 = G.inc_ptr[v] + sub;
+    q1 = G.inc_ptr[v + 1];
+  }
+  if constexpr (FP64) {
+    const double* c = reinterpret_cast<const double*>(G.contrib);
+    double acc[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) acc[k] = 0.0;
-      for (int64_t q = q0; q < q1; ++q) {
-        const int64_t base = (int64_t)__ldg(G.inc + q) * D;
+    for (int k = 0; k < D; ++k) acc[k] = 0.0;
+    int64_t q = q0;
+    for (; q + 3 * kGatherLanes < q1; q += 4 * kGatherLanes) {
+      int64_t base[4];
 #pragma unroll
-        for (int k = 0; k < D; ++k) acc[k] += __ldg(c + base + k);
-      }
+      for (int u = 0; u < 4; ++u) base[u] = (int64_t)__ldg(G.inc + q + u * kGatherLanes) * D;
 #pragma unroll
-      for (int k = 0; k < D; ++k) outv[k] = acc[k];
-    } else {
-      const float* c = reinterpret_cast<const float*>(G.contrib);
-      FF acc[2][D];
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int k = 0; k < D; ++k) acc[0][k] = acc[1][k] = FF{0.f, 0.f};
-      int64_t q = q0;
-      for (; q + 4 <= q1; q += 4) {
-        int64_t base[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) base[u] = (int64_t)__ldg(G.inc + q + u) * D;
-        float v[4][D];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int k = 0; k < D; ++k) v[u][k] = __ldg(c + base[u] + k);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int k = 0; k < D; ++k) acc[u & 1][k] = ff_addf(acc[u & 1][k], v[u][k]);
-      }
-      for (; q < q1; ++q) {
-        const int64_t base = (int64_t)__ldg(G.inc + q) * D;
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc[0][k] = ff_addf(acc[0][k], __ldg(c + base + k));
-      }
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const FF a = ff_add(acc[0][k], acc[1][k]);
-        outv[k] = (double)a.hi + (double)a.lo;
-      }
+        for (int k = 0; k < D; ++k) acc[k] += __ldg(c + base[u] + k);
     }
+    for (; q < q1; q += kGatherLanes) {
+      const int64_t base = (int64_t)__ldg(G.inc + q) * D;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] += __ldg(c + base + k);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      double a = acc[k];
+#pragma unroll
+      for (int o = 1; o < kGatherLanes; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      outv[k] = a;
+    }
+  } else {
+    const float* c = reinterpret_cast<const float*>(G.contrib);
+    FF acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = FF{0.f, 0.f};
+    int64_t q = q0;
+    for (; q + 3 * kGatherLanes < q1; q += 4 * kGatherLanes) {
+      int64_t base[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) base[u] = (int64_t)__ldg(G.inc + q + u * kGatherLanes) * D;
+      float v[4][D];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[u][k] = __ldg(c + base[u] + k);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] = ff_addf(acc[k], v[u][k]);
+    }
+    for (; q < q1; q += kGatherLanes) {
+      const int64_t base = (int64_t)__ldg(G.inc + q) * D;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = ff_addf(acc[k], __ldg(c + base + k));
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      FF a = acc[k];
+#pragma unroll
+      for (int o = 1; o < kGatherLanes; o <<= 1) {
+        const FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        a = ff_add(a, b);
+      }
+      outv[k] = (double)a.hi + (double)a.lo;
+    }
+  }
+  if (active && sub == 0) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       if (G.add) outv[k] += G.add[(int64_t)row * D + k];
@@ -145,13 +174,13 @@ __global__ void __launch_bounds__(kVertexBlock) k_gather(GatherLaunch G) {
   }
   if (G.mesh_of) {
     // batched meshes: per-mesh sum of squares, warp-aggregated when the warp is uniform
-    const int mesh = (row < G.rows) ? G.mesh_of[G.row_vertex ? G.row_vertex[row] : row] : -1;
+    const int mesh = active ? G.mesh_of[G.row_vertex ? G.row_vertex[row] : row] : -1;
     const int m0 = __shfl_sync(0xffffffffu, mesh, 0);
     if (__all_sync(0xffffffffu, mesh == m0)) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
       if ((threadIdx.x & 31) == 0 && m0 >= 0) atomicAdd(G.mesh_acc + (int64_t)m0 * (NQ + 1) + NQ, sq);
-    } else if (mesh >= 0) {
+    } else if (mesh >= 0 && sub == 0) {
       atomicAdd(G.mesh_acc + (int64_t)mesh * (NQ + 1) + NQ, sq);
     }
   } else if (G.partials) {
@@ -182,11 +211,26 @@ __global__ void __launch_bounds__(kVertexBlock) k_residual(const int32_t* __rest
     double acc[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) acc[k] = b[(int64_t)i * D + k];
-    for (int q = 0; q < width; ++q) {
+    // the index and value loads of 4 entries go out together, then their X gathers
+    int q = 0;
+    for (; q + 4 <= width; q += 4) {
+      int j[4];
+      double a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        j[u] = __ldg(col + (int64_t)(q + u) * nF + i);
+        a[u] = __ldg(val + (int64_t)(q + u) * nF + i);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] = fma(-a[u], __ldg(X + (int64_t)j[u] * D + k), acc[k]);
+    }
+    for (; q < width; ++q) {
       const int j = __ldg(col + (int64_t)q * nF + i);
       const double a = __ldg(val + (int64_t)q * nF + i);
 #pragma unroll
-      for (int k = 0; k < D; ++k) acc[k] = fma(-a, X[(int64_t)j * D + k], acc[k]);
+      for (int k = 0; k < D; ++k) acc[k] = fma(-a, __ldg(X + (int64_t)j * D + k), acc[k]);
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -891,7 +935,7 @@ void launch_vertex_update(const VertexLaunch& V, cudaStream_t s) {
 }
 
 void launch_gather(const GatherLaunch& G, cudaStream_t s) {
-  const int g = blocks_for(G.rows, kVertexBlock);
+  const int g = blocks_for((int64_t)G.rows * kGatherLanes, kVertexBlock);
   if (G.d == 2) {
     if (G.fp64) k_gather<2, true><<<g, kVertexBlock, 0, s>>>(G);
     else k_gather<2, false><<<g, kVertexBlock, 0, s>>>(G);
