@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="cube_deform",
-                    choices=["cube_deform", "batch256", "uv_disk", "uv_heightfield", "cube_handles"],
+                    choices=["cube_deform", "batch256", "uv_disk", "uv_heightfield", "cube_handles", "tutte"],
                     help="cube_deform: the throughput benchmark; the others report time to tolerance "
                          "(uv_disk, uv_heightfield), batched meshes, or forward + adjoint (cube_handles)")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -359,6 +359,45 @@ def run_handles(args, local):
     return 0
 
 
+def run_tutte(args, local):
+    """The Tutte initializer on a 1024^2-vertex disk (2.1M triangles): one ffa_tutte
+    call (host ordering and factorization, GPU solve), against the oracle's sparse
+    LU on the host."""
+    import numpy as np
+    import torch
+
+    from oracle import tutte as ot
+    from paper_2107_05200_gb300 import workloads as wk
+    from paper_2107_05200_gb300.solver import tutte
+
+    torch.cuda.set_device(local)
+    grid = 1024
+    V, T = wk.grid_triangles(grid, grid, no_ears=True)
+    bnd = wk._grid_boundary_cycle(grid, grid)
+    t = np.linspace(0.0, 2.0 * math.pi, len(bnd), endpoint=False)
+    circ = np.stack([np.cos(t), np.sin(t)], 1)
+    V4, T4 = wk.grid_triangles(4, 4, no_ears=True)
+    b4 = wk._grid_boundary_cycle(4, 4)
+    t4 = np.linspace(0.0, 2.0 * math.pi, len(b4), endpoint=False)
+    tutte(V4, T4, b4, np.stack([np.cos(t4), np.sin(t4)], 1))   # load the library, touch the device
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W, rel = tutte(V, T, bnd, circ)
+    t_gpu = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Wo = ot.tutte(V, T, bnd, circ)
+    t_cpu = time.perf_counter() - t0
+    line = {"metric": "Tutte initializer wall time", "unit": "s", "value": t_gpu, "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"tutte_disk_{grid}", "vertices": int(V.shape[0]), "triangles": int(T.shape[0])},
+            "rel_residual": rel, "max_diff_vs_oracle": float(np.abs(W - Wo).max()),
+            "flipped": float(wk.flipped_fraction(W, T)),
+            "cpu_baseline": {"value": t_cpu, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": "scipy sparse LU of the same system"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -370,6 +409,8 @@ def main():
         return run_to_tolerance(args, local) if rank == 0 else 0
     if args.workload == "cube_handles":
         return run_handles(args, local) if rank == 0 else 0
+    if args.workload == "tutte":
+        return run_tutte(args, local) if rank == 0 else 0
 
     import numpy as np
     import torch

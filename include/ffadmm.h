@@ -143,6 +143,28 @@ typedef struct {
   double ms_solve_backward;  /* one backward triangular pass of the W step (last sweep) */
 } ffa_phase_times;
 
+/* Initial map (the paper has no GPU counterpart; App. A, "Tutte's Energy"): the
+ * minimizer of E_T(W) = sum over the mesh edges (i, j) of |W_i - W_j|^2 / |V_i - V_j|
+ * with the boundary vertices held at boundary_pos.  Flip-free in 2D when the
+ * boundary is convex (Tutte's theorem); the paper initializes with it.  One
+ * sparse SPD solve: ordering and factorization on the host as for the W step,
+ * FP32 supernodal passes with FP64 residual correction on the GPU until the
+ * relative residual reaches 1e-13 or stops falling (at most 10 sweeps).
+ *   mesh         : source mesh (V n x d_in, T); d = the target dimension (2 or 3)
+ *   boundary     : n_boundary distinct vertex indices (host or device), >= 1
+ *   boundary_pos : n_boundary x d positions (host or device)
+ *   params       : nd_leaf_size, host_threads, solve_schedule are used (NULL = defaults)
+ *   stream       : cudaStream_t or NULL (a private stream)
+ *   W_out        : n x d result (host or device)
+ *   rel_residual : optional: |b - L_II W_I| / |b| at the end
+ * Errors: FFA_ERR_INVALID_ARG (sizes, indices, repeated boundary index, a zero-length
+ * edge), FFA_ERR_SINGULAR_SYSTEM (an interior part with no boundary vertex), CUDA
+ * errors; the message is in ffa_last_error(NULL).  Allocates and frees its own
+ * device memory. */
+ffa_status ffa_tutte(const ffa_mesh* mesh, const int32_t* boundary, int32_t n_boundary,
+                     const double* boundary_pos, const ffa_params* params, void* stream,
+                     double* W_out, double* rel_residual);
+
 /* Fill *p with the defaults: symmetric Dirichlet, rho 1, eps_abs 1e-6, eps_rel 1e-5,
  * check_every 10, require_flip_free 1, FP32 local step, 2 refine sweeps,
  * leaf size 64, all host threads, solve schedule 1, fixed penalties (penalty

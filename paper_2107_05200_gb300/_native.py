@@ -24,7 +24,7 @@ EXPORTED = [
     "ffa_get_info", "ffa_last_wstep_residual", "ffa_profile_phases", "ffa_energy_noalloc",
     "ffa_forward_unrolled", "ffa_backward_unrolled",
     "ffa_batch_create", "ffa_batch_destroy", "ffa_batch_last_error", "ffa_batch_init", "ffa_batch_iterate",
-    "ffa_batch_get_W", "ffa_autotune", "ffa_batch_autotune", "ffa_batch_groups",
+    "ffa_batch_get_W", "ffa_autotune", "ffa_batch_autotune", "ffa_batch_groups", "ffa_tutte",
 ]
 
 
@@ -131,6 +131,7 @@ def load() -> C.CDLL:
         "ffa_autotune": ([vp, i32, C.POINTER(Tuning)], C.c_int),
         "ffa_batch_autotune": ([vp, i32, C.POINTER(Tuning)], C.c_int),
         "ffa_batch_groups": ([vp], C.c_int32),
+        "ffa_tutte": ([C.POINTER(Mesh), vp, i32, vp, C.POINTER(Params), vp, vp, C.POINTER(dbl)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

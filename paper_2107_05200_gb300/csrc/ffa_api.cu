@@ -1093,6 +1093,217 @@ int64_t next_rescale_iter(const ffa_ctx* ctx) {
   return ctx->last_event_iter + (int64_t)std::floor(5.0 * std::pow(1.5, (double)p));
 }
 
+bool device_wait_failed(ffa_ctx* ctx);
+
+// The Tutte initializer (App. A, "Tutte's Energy"): the minimizer of
+// E_T(W) = sum over edges (i, j) of |W_i - W_j|^2 / |V_i - V_j| with the boundary
+// held.  Its interior rows are the weighted graph Laplacian L_II W_I = -L_IB W_B,
+// solved once with the W step's machinery: host ordering and factorization,
+// FP32 supernodal passes with FP64 residual correction on the GPU.
+ffa_status tutte_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* bnd_in, int32_t nb, const double* bpos_in,
+                      const ffa_params* params, void* stream, double* W_out, double* rel_out) {
+  if (!mesh || !W_out) return fail(ctx, FFA_ERR_INVALID_ARG, "mesh or W_out is NULL");
+  ffa_default_params(&ctx->prm);
+  if (params) ctx->prm = *params;
+  ctx->prm.penalty_schedule = 0;
+  {
+    std::string msg;
+    if (validate_params(ctx->prm, msg) != FFA_OK) return fail(ctx, FFA_ERR_INVALID_ARG, msg);
+  }
+  const int n = mesh->n, m = mesh->m, d = mesh->d, d_in = mesh->d_in;
+  if (d != 2 && d != 3) return fail(ctx, FFA_ERR_INVALID_ARG, "d must be 2 or 3");
+  if (d_in < d || d_in > 3) return fail(ctx, FFA_ERR_INVALID_ARG, "d_in must be in [d, 3]");
+  if (n < 1 || m < 1) return fail(ctx, FFA_ERR_INVALID_ARG, "need n >= 1 and m >= 1");
+  if ((int64_t)m * (d + 1) >= (int64_t)1 << 31) return fail(ctx, FFA_ERR_INVALID_ARG, "mesh too large");
+  if (!mesh->V || !mesh->T) return fail(ctx, FFA_ERR_INVALID_ARG, "V or T is NULL");
+  if (nb < 1 || nb > n || !bnd_in || !bpos_in) return fail(ctx, FFA_ERR_INVALID_ARG, "need 1 <= n_boundary <= n and boundary arrays");
+  if (stream) {
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  } else {
+    FFA_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  ffa_status st;
+  std::vector<double> V, bpos;
+  std::vector<int32_t> T, bnd;
+  if ((st = copy_in(ctx, V, mesh->V, (size_t)n * d_in)) != FFA_OK) return st;
+  if ((st = copy_in(ctx, T, mesh->T, (size_t)m * (d + 1))) != FFA_OK) return st;
+  if ((st = copy_in(ctx, bnd, bnd_in, (size_t)nb)) != FFA_OK) return st;
+  if ((st = copy_in(ctx, bpos, bpos_in, (size_t)nb * d)) != FFA_OK) return st;
+  for (int32_t v : T)
+    if (v < 0 || v >= n) return fail(ctx, FFA_ERR_INVALID_ARG, "element index out of range");
+  std::vector<int32_t> v2pin(n, -1);
+  for (int p = 0; p < nb; ++p) {
+    if (bnd[p] < 0 || bnd[p] >= n) return fail(ctx, FFA_ERR_INVALID_ARG, "boundary index out of range");
+    if (v2pin[bnd[p]] >= 0) return fail(ctx, FFA_ERR_INVALID_ARG, "repeated boundary index");
+    v2pin[bnd[p]] = p;
+  }
+  for (double c : bpos)
+    if (!std::isfinite(c)) return fail(ctx, FFA_ERR_INVALID_ARG, "non-finite boundary position");
+  // neighbours of every vertex (each edge once per endpoint)
+  std::vector<int64_t> nptr(n + 1, 0);
+  for (int i = 0; i < m; ++i)
+    for (int a = 0; a <= d; ++a) nptr[T[(int64_t)i * (d + 1) + a] + 1] += d;
+  for (int v = 0; v < n; ++v) nptr[v + 1] += nptr[v];
+  std::vector<int32_t> nbr(nptr[n]);
+  {
+    std::vector<int64_t> fill(nptr.begin(), nptr.end() - 1);
+    for (int i = 0; i < m; ++i)
+      for (int a = 0; a <= d; ++a)
+        for (int b = 0; b <= d; ++b)
+          if (a != b) {
+            const int u = T[(int64_t)i * (d + 1) + a];
+            nbr[fill[u]++] = T[(int64_t)i * (d + 1) + b];
+          }
+  }
+  std::vector<int32_t> free_of(n, -1), free_vertex;
+  for (int v = 0; v < n; ++v)
+    if (v2pin[v] < 0) {
+      free_of[v] = (int32_t)free_vertex.size();
+      free_vertex.push_back(v);
+    }
+  const int nF = (int)free_vertex.size();
+  std::vector<double> Wh((size_t)n * d, 0.0);
+  for (int p = 0; p < nb; ++p)
+    for (int k = 0; k < d; ++k) Wh[(size_t)bnd[p] * d + k] = bpos[(size_t)p * d + k];
+  if (nF == 0) {
+    FFA_CUDA(cudaMemcpy(W_out, Wh.data(), Wh.size() * 8, cudaMemcpyDefault));
+    if (rel_out) *rel_out = 0.0;
+    return FFA_OK;
+  }
+  // rows of the interior vertices: L_II (free numbering) and L_IB (boundary slots)
+  std::vector<int64_t> Ap(nF + 1, 0), Cp(nF + 1, 0);
+  std::vector<int32_t> Ai, Ci;
+  std::vector<double> Ax, Cx;
+  for (int f = 0; f < nF; ++f) {
+    const int v = free_vertex[f];
+    std::vector<int32_t> js(nbr.begin() + nptr[v], nbr.begin() + nptr[v + 1]);
+    std::sort(js.begin(), js.end());
+    js.erase(std::unique(js.begin(), js.end()), js.end());
+    double diag = 0.0;
+    std::vector<std::pair<int32_t, double>> fr, cr;
+    for (int j : js) {
+      double l2 = 0.0;
+      for (int a = 0; a < d_in; ++a) {
+        const double t = V[(size_t)v * d_in + a] - V[(size_t)j * d_in + a];
+        l2 += t * t;
+      }
+      if (!(l2 > 0.0)) return fail(ctx, FFA_ERR_INVALID_ARG, "zero-length edge at vertex " + std::to_string(v));
+      const double c = 1.0 / std::sqrt(l2);
+      diag += c;
+      if (free_of[j] >= 0) fr.push_back({free_of[j], -c});
+      else cr.push_back({v2pin[j], -c});
+    }
+    fr.push_back({f, diag});
+    std::sort(fr.begin(), fr.end());
+    std::sort(cr.begin(), cr.end());
+    for (auto& pr : fr) { Ai.push_back(pr.first); Ax.push_back(pr.second); }
+    for (auto& pr : cr) { Ci.push_back(pr.first); Cx.push_back(pr.second); }
+    Ap[f + 1] = (int64_t)Ai.size();
+    Cp[f + 1] = (int64_t)Ci.size();
+  }
+  std::vector<double> coords((size_t)nF * 3, 0.0);
+  for (int f = 0; f < nF; ++f)
+    for (int a = 0; a < d_in; ++a) coords[(size_t)f * 3 + a] = V[(size_t)free_vertex[f] * d_in + a];
+  Factor fac;
+  {
+    FactorInput in;
+    in.nF = nF;
+    in.Ap = Ap.data();
+    in.Ai = Ai.data();
+    in.Ax = Ax.data();
+    in.coords = coords.data();
+    in.leaf_size = ctx->prm.nd_leaf_size;
+    in.threads = ctx->prm.host_threads;
+    std::string msg;
+    const int rc = build_factor(in, fac, msg);
+    if (rc == 3) return fail(ctx, FFA_ERR_SINGULAR_SYSTEM, "Tutte system: " + msg + " (an interior part without a boundary vertex?)");
+    if (rc != 0) return fail(ctx, FFA_ERR_INVALID_ARG, msg);
+  }
+  OperatorArrays OA;
+  operator_arrays(fac, nF, nb, Ap, Ai, Ax, Cp, Ci, Cx, OA);
+  ctx->n = n;
+  ctx->m = m;
+  ctx->d = d;
+  ctx->d_in = d_in;
+  ctx->nF = nF;
+  ctx->n_pin = nb;
+  ctx->fp64 = 1;
+  ctx->rsz = 8;
+  ctx->schedule = ctx->prm.solve_schedule;
+  ctx->ell_width = OA.width;
+  ctx->nodes_h = fac.nodes;
+  ctx->n_levels = fac.n_levels;
+  std::vector<int32_t> v2e(n, -1);
+  for (int c = 0; c < nF; ++c) v2e[free_vertex[fac.perm[c]]] = c;
+  if ((st = upload(ctx, &ctx->rows, fac.rows)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->blocks, fac.blocks)) != FFA_OK) return st;
+  if ((st = build_tasks(ctx)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->ell_col, OA.ell_col)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->ell_val, OA.ell_val)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->fc_ptr, OA.fc_ptr)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->fc_col, OA.fc_col)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->fc_val, OA.fc_val)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->pin_pos, bpos)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->v2e, v2e)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->v2pin, v2pin)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &ctx->W, (size_t)n * d)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &ctx->X, (size_t)nF * d)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &ctx->b, (size_t)nF * d)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &ctx->y, (size_t)nF * d)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &ctx->z, (size_t)nF * d)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &ctx->x, (size_t)nF * d)) != FFA_OK) return st;
+  if ((st = dalloc_bytes(ctx, &ctx->vrec, (size_t)n * d * 16)) != FFA_OK) return st;
+  ctx->n_res_blocks = (nF + kVertexBlock - 1) / kVertexBlock;
+  if ((st = dalloc(ctx, &ctx->res_partials, (size_t)ctx->n_res_blocks * 2)) != FFA_OK) return st;
+  cudaStream_t s = ctx->stream;
+  // b = -L_IB W_B, X = 0
+  launch_pin_rhs(d, nF, ctx->fc_ptr, ctx->fc_col, ctx->fc_val, ctx->pin_pos, ctx->b, s);
+  FFA_CUDA(cudaMemsetAsync(ctx->X, 0, (size_t)nF * d * 8, s));
+  FFA_CUDA(cudaMemsetAsync(ctx->W, 0, (size_t)n * d * 8, s));
+  // residual-correction sweeps until the relative residual stops improving or is
+  // at double rounding level
+  SolveData S = solve_data(ctx);
+  std::vector<double> part((size_t)ctx->n_res_blocks * 2);
+  double rel = 1.0, prev = 2.0;
+  for (int sw = 0; sw < 10; ++sw) {
+    launch_residual(S, ctx->res_partials, (int)ctx->n_res_blocks, s);
+    FFA_CUDA(cudaMemcpyAsync(part.data(), ctx->res_partials, part.size() * 8, cudaMemcpyDeviceToHost, s));
+    FFA_CUDA(cudaStreamSynchronize(s));
+    double rr = 0.0, bb = 0.0;
+    for (int64_t q = 0; q < ctx->n_res_blocks; ++q) {
+      rr += part[2 * q];
+      bb += part[2 * q + 1];
+    }
+    rel = bb > 0.0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+    if (rel < 1e-13 || rel > 0.5 * prev || sw == 9) break;
+    prev = rel;
+    launch_supernodal_solve(S, s);
+    launch_axpy_correction(S, s);
+  }
+  if (device_wait_failed(ctx)) return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait of the supernodal solve gave up");
+  VertexLaunch Vl{};
+  Vl.d = d;
+  Vl.fp64 = 1;
+  Vl.n = n;
+  Vl.Wnew_free = ctx->X;
+  Vl.corr = nullptr;
+  Vl.v2e = ctx->v2e;
+  Vl.v2pin = ctx->v2pin;
+  Vl.pin_pos = ctx->pin_pos;
+  Vl.W_in = nullptr;
+  Vl.W = ctx->W;
+  Vl.X = nullptr;
+  Vl.vrec = ctx->vrec;
+  Vl.write_dw = 0;
+  launch_vertex_update(Vl, s);
+  FFA_CUDA(cudaGetLastError());
+  FFA_CUDA(cudaMemcpyAsync(W_out, ctx->W, (size_t)n * d * 8, cudaMemcpyDefault, s));
+  FFA_CUDA(cudaStreamSynchronize(s));
+  if (rel_out) *rel_out = rel;
+  return FFA_OK;
+}
+
 void destroy_impl(ffa_ctx* ctx) {
   if (ctx->g_batch) cudaGraphExecDestroy(ctx->g_batch);
   if (ctx->g_one) cudaGraphExecDestroy(ctx->g_one);
@@ -1226,6 +1437,28 @@ ffa_status ffa_default_params(ffa_params* p) {
   p->penalty_schedule = 0;
   p->rescale_rho = 5.0;
   return FFA_OK;
+}
+
+ffa_status ffa_tutte(const ffa_mesh* mesh, const int32_t* boundary, int32_t n_boundary, const double* boundary_pos,
+                     const ffa_params* params, void* stream, double* W_out, double* rel_residual) {
+  ffa_ctx* ctx = nullptr;
+  try {
+    ctx = new ffa_ctx();
+  } catch (...) {
+    return FFA_ERR_OOM;
+  }
+  ffa_status st;
+  try {
+    st = tutte_impl(ctx, mesh, boundary, n_boundary, boundary_pos, params, stream, W_out, rel_residual);
+  } catch (const std::bad_alloc&) {
+    st = FFA_ERR_OOM;
+  } catch (...) {
+    st = FFA_ERR_INVALID_ARG;
+  }
+  if (st != FFA_OK) g_create_error = ctx->err.empty() ? "ffa_tutte failed" : ctx->err;
+  destroy_impl(ctx);
+  delete ctx;
+  return st;
 }
 
 ffa_status ffa_create(const ffa_mesh* mesh, const int32_t* pin_idx, int32_t n_pin, const double* pin_pos,

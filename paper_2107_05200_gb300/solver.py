@@ -201,6 +201,40 @@ class Solver:
         return cls(wl.V, wl.T, wl.pins, wl.pin_pos, **kw)
 
 
+def tutte(V, T, boundary, boundary_pos, leaf_size: int = 64, host_threads: int = 0, schedule: int = 1,
+          stream=None, out=None):
+    """The minimizer of Tutte's energy with the boundary held (ffa_tutte).
+
+    Returns (W, relative residual); W is a new (n, d) float64 array unless `out`
+    (host array or device tensor) is given."""
+    lib = N.load()
+    Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
+    Tn = np.asarray(T) if isinstance(T, (list, tuple)) else T
+    n, d_in = int(Vn.shape[0]), int(Vn.shape[1])
+    m, d_t = int(Tn.shape[0]), int(Tn.shape[1])
+    bp = np.asarray(boundary_pos) if isinstance(boundary_pos, (list, tuple)) else boundary_pos
+    d = int(bp.shape[1])
+    if d_t != d + 1:
+        raise ValueError("boundary_pos has d columns and T must have d + 1")
+    pV, kV = _ptr(Vn, np.float64)
+    pT, kT = _ptr(Tn, np.int32)
+    pb, kb = _ptr(boundary, np.int32)
+    pp, kp = _ptr(bp, np.float64)
+    mesh = N.Mesh(n, m, d, d_in, pV, pT)
+    prm = N.Params()
+    N.check(lib, None, lib.ffa_default_params(C.byref(prm)))
+    prm.nd_leaf_size = int(leaf_size)
+    prm.host_threads = int(host_threads)
+    prm.solve_schedule = int(schedule)
+    if out is None:
+        out = np.empty((n, d), np.float64)
+    po, ko = _ptr(out, np.float64)
+    rel = C.c_double()
+    N.check(lib, None, lib.ffa_tutte(C.byref(mesh), pb, int(len(kb)), pp, C.byref(prm),
+                                     C.c_void_p(stream) if stream else None, po, C.byref(rel)))
+    return out, rel.value
+
+
 class BatchSolver:
     """Many independent meshes solved together (one graph launch for all of them)."""
 
