@@ -329,7 +329,7 @@ class Oracle:
     """The FP64 reference solver for one mesh, one energy, fixed penalties."""
 
     def __init__(self, V, T, pins, pin_pos, energy_name: str, rho: float = 1.0,
-                 eps_abs: float = 1e-6, eps_rel: float = 1e-5, h=None):
+                 eps_abs: float = 1e-6, eps_rel: float = 1e-5, h=None, local_variant: str = "paper"):
         self.V = np.asarray(V, np.float64)
         self.T = np.asarray(T, np.int64)
         self.energy_name = energy_name
@@ -341,6 +341,9 @@ class Oracle:
         self.mu = rho * self.w
         self.h = np.zeros(self.m) if h is None else np.broadcast_to(h, (self.m,)).astype(float)
         self.eps_abs, self.eps_rel = eps_abs, eps_rel
+        if local_variant not in ("paper", "joint"):
+            raise ValueError("local_variant must be 'paper' or 'joint'")
+        self.local_variant = local_variant
         self.wstep = WStep(self.g, self.T, self.mu, self.n, np.asarray(pins), np.asarray(pin_pos))
 
     @classmethod
@@ -361,10 +364,21 @@ class Oracle:
         return self.wstep.solve(gradient_adjoint(self.g, self.T, r, self.n))
 
     def local_steps(self, s: State, W: np.ndarray) -> State:
-        """U, P and Lambda updates for a given W^{(k)} (Sec. 4)."""
+        """U, P and Lambda updates for a given W^{(k)} (Sec. 4).
+
+        local_variant "paper": the U step uses P^{k-1} (Algorithm 1).
+        local_variant "joint" (not the paper's scheme): (U, P) minimize
+        w f(P) + mu/2 |U P - A|^2 together.  For a rotation-invariant f the
+        minimizer is U = the rotation nearest to A itself and P = the prox of
+        symm(U^T A) (von Neumann's trace inequality: |U P - A|^2 is smallest when
+        P shares A's right singular vectors, and then the P problem separates per
+        signed singular value), so only Q changes; h is not used."""
         J = jacobians(self.g, self.T, W)
         A = J + s.Lam
-        Q = A @ s.P + (self.h / self.mu)[:, None, None] * s.U
+        if self.local_variant == "joint":
+            Q = A
+        else:
+            Q = A @ s.P + (self.h / self.mu)[:, None, None] * s.U
         U = procrustes(Q, s.U)
         S = symm(np.transpose(U, (0, 2, 1)) @ A)
         P = p_step(S, self.w, self.mu, self.energy_name)
