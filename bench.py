@@ -52,6 +52,8 @@ def parse():
                     help="cube_deform: the throughput benchmark; the others report time to tolerance "
                          "(uv_disk, uv_heightfield), batched meshes, or forward + adjoint (cube_handles)")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--local-variant", default="paper", choices=["paper", "joint"],
+                    help="uv_disk / uv_heightfield: the paper's local step or the joint (U, P) prox variant")
     ap.add_argument("--penalties", default="fixed", choices=["fixed", "paper"],
                     help="uv_disk / uv_heightfield: mu = rho w fixed, or the paper's rescaling schedule")
     return ap.parse_args()
@@ -267,7 +269,7 @@ def run_to_tolerance(args, local):
     wl = wk.uv_disk() if args.workload == "uv_disk" else wk.uv_heightfield()
     t0 = time.perf_counter()
     sol = Solver.from_workload(wl, precision=args.precision, check_every=10, refine_sweeps=args.sweeps,
-                               penalties=args.penalties)
+                               penalties=args.penalties, local_variant=args.local_variant)
     t_setup = time.perf_counter() - t0
     sol.init(wl.W0)
     sol.iterate(10, stop_at_tol=False)          # warm-up (graph capture)
@@ -287,13 +289,14 @@ def run_to_tolerance(args, local):
             "config": {"workload": wl.name, "elements": wl.m, "vertices": wl.n, "energy": wl.energy,
                        "rho": wl.rho, "eps_abs": wl.eps_abs, "eps_rel": wl.eps_rel, "max_iter": wl.max_iter,
                        "check_every": 10},
-            "penalties": args.penalties, "rescales": st["rescales"], "refactor_s_total": t_refactor,
+            "penalties": args.penalties, "local_variant": args.local_variant,
+            "rescales": st["rescales"], "refactor_s_total": t_refactor,
             "iterations": st["iters"], "converged": st["converged"], "n_flipped": st["n_flipped"],
             "iter_per_s": st["iters"] / t_tol, "elem_updates_per_s": st["iters"] * wl.m / t_tol,
             "energy": E, "e_prim": st["e_prim"], "e_dual": st["e_dual"], "setup_s": t_setup}
     if args.workload == "uv_disk":
         from oracle import admm, schedule
-        o = admm.Oracle.from_workload(wl)
+        o = admm.Oracle.from_workload(wl, local_variant=args.local_variant)
         if args.penalties == "paper":
             s_o, _, _ = schedule.run(o, wl.W0, st["iters"], stop_at_tol=False)
         else:

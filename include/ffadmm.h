@@ -99,6 +99,11 @@ typedef struct {
                               is decomposed again on the host.  rho is ignored.  Single meshes of
                               one energy only; not with ffa_forward_unrolled. */
   double rescale_rho;      /* the paper's rho of the rescaling rule (default 5) */
+  int32_t local_variant;   /* 0: the paper's local step (Algorithm 1: U from (J + Lambda) P^{k-1}, then P;
+                              default).  1: a joint (U, P) prox (not the paper's scheme): U is the
+                              rotation nearest to J + Lambda and P the prox of symm(U^T (J + Lambda)),
+                              the joint minimizer of w f(P) + mu/2 |U P - J - Lambda|^2 for the
+                              rotation-invariant energies.  Not with ffa_forward_unrolled. */
 } ffa_params;
 
 typedef struct {

@@ -39,7 +39,8 @@ class Params(C.Structure):
                 ("require_flip_free", C.c_int32), ("local_precision", C.c_int),
                 ("refine_sweeps", C.c_int32), ("nd_leaf_size", C.c_int32),
                 ("host_threads", C.c_int32), ("solve_schedule", C.c_int32),
-                ("penalty_schedule", C.c_int32), ("rescale_rho", C.c_double)]
+                ("penalty_schedule", C.c_int32), ("rescale_rho", C.c_double),
+                ("local_variant", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -464,6 +464,7 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   else if (p.host_threads < 0) msg = "host_threads must be >= 0";
   else if (p.solve_schedule != 0 && p.solve_schedule != 1) msg = "solve_schedule must be 0 or 1";
   else if (p.penalty_schedule != 0 && p.penalty_schedule != 1) msg = "penalty_schedule must be 0 or 1";
+  else if (p.local_variant != 0 && p.local_variant != 1) msg = "local_variant must be 0 or 1";
   else if (p.penalty_schedule == 1 && !(p.rescale_rho > 2.0 && std::isfinite(p.rescale_rho)))
     msg = "rescale_rho must be finite and > 2";
   else return FFA_OK;
@@ -973,6 +974,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     ctx->e.mesh_of = ctx->mesh_of_elem;
     ctx->e.mesh_acc = ctx->mesh_acc;
   }
+  ctx->e.joint = ctx->prm.local_variant == 1 ? 1 : 0;
   const size_t R = ctx->rsz;
   if ((st = dalloc_bytes(ctx, &ctx->e.P, (size_t)m * (d == 2 ? 3 : 6) * R)) != FFA_OK) return st;
   if ((st = dalloc_bytes(ctx, &ctx->e.Lam, (size_t)m * d * d * R)) != FFA_OK) return st;
@@ -1436,6 +1438,7 @@ ffa_status ffa_default_params(ffa_params* p) {
   p->solve_schedule = 1;
   p->penalty_schedule = 0;
   p->rescale_rho = 5.0;
+  p->local_variant = 0;
   return FFA_OK;
 }
 
@@ -1779,6 +1782,8 @@ ffa_status ffa_forward_unrolled(ffa_ctx* ctx, int32_t K, int32_t ckpt_every) {
   if (K < 1 || ckpt_every < 1) return fail(ctx, FFA_ERR_INVALID_ARG, "K and ckpt_every must be >= 1");
   if (ctx->prm.penalty_schedule != 0)
     return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation needs fixed penalties (penalty_schedule 0)");
+  if (ctx->prm.local_variant != 0)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation is implemented for the paper's local step (local_variant 0)");
   ffa_status st = ensure_graphs(ctx);
   if (st != FFA_OK) return st;
   const int C = std::min(ckpt_every, K);

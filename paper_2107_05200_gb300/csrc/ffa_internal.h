@@ -78,6 +78,7 @@ struct ElemBufs {
   const int8_t* energy_of = nullptr;   // m: 0 = SD, 1 = SG (kernels instantiated with EN = 2)
   const int32_t* mesh_of = nullptr;    // m: mesh of each element
   double* mesh_acc = nullptr;          // n_mesh x (NQ + 1) per-mesh sums of the check quantities
+  int32_t joint = 0;                   // 1: the joint (U, P) prox variant of the local step
 };
 
 struct LocalLaunch {

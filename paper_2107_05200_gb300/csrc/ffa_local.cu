@@ -191,7 +191,7 @@ __device__ __forceinline__ void mesh_reduce(const R v[NQ], const ElemBufs& e, in
 // ---------------------------------------------------------------------------
 // the fused local step
 // ---------------------------------------------------------------------------
-template <int D, typename R, int EN, bool CHECK>
+template <int D, typename R, int EN, bool CHECK, bool JOINT>
 __global__ void __launch_bounds__(256) k_local_step(ElemBufs e, int m, const void* __restrict__ vrec,
                                                     double* __restrict__ partials) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,17 +222,27 @@ __global__ void __launch_bounds__(256) k_local_step(ElemBufs e, int m, const voi
       P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[0][2] = P[2][0] = Pp[2 * (int64_t)m + i];
       P[1][1] = Pp[3 * (int64_t)m + i]; P[1][2] = P[2][1] = Pp[4 * (int64_t)m + i]; P[2][2] = Pp[5 * (int64_t)m + i];
     }
-    // ---- U step: nearest rotation to Q = (J + Lambda) P (eqs. rawoptimizationinudecoupled/optimizationinudecoupled, h = 0)
+    // ---- U step: nearest rotation to Q = (J + Lambda) P (eqs. rawoptimizationinudecoupled/optimizationinudecoupled, h = 0);
+    // the joint (U, P) prox variant (not the paper's scheme) takes Q = J + Lambda:
+    // for a rotation-invariant f the joint minimizer of w f(P) + mu/2 |U P - A|^2 is
+    // the rotation nearest to A with P the prox of symm(U^T A)
     R Q[D][D], U[D][D];
+    if constexpr (JOINT) {
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+      for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        R s = R(0);
+        for (int k = 0; k < D; ++k) Q[a][k] = A[a][k];
+    } else {
 #pragma unroll
-        for (int l = 0; l < D; ++l) s = fma(A[a][l], P[l][k], s);
-        Q[a][k] = s;
-      }
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          R s = R(0);
+#pragma unroll
+          for (int l = 0; l < D; ++l) s = fma(A[a][l], P[l][k], s);
+          Q[a][k] = s;
+        }
+    }
     if constexpr (D == 2) {
       // maximize U(phi) . Q: (cos, sin) along (q00 + q11, q10 - q01); tie keeps U^{k-1}
       const R ca = Q[0][0] + Q[1][1], sa = Q[1][0] - Q[0][1];
@@ -716,8 +726,13 @@ template <int D, typename R, int EN>
 void dispatch_local(const LocalLaunch& L, cudaStream_t s) {
   const int bs = L.block > 0 ? L.block : kLocalBlock;
   const int grid = (L.m + bs - 1) / bs;
-  if (L.check) k_local_step<D, R, EN, true><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
-  else k_local_step<D, R, EN, false><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+  if (L.e.joint) {
+    if (L.check) k_local_step<D, R, EN, true, true><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+    else k_local_step<D, R, EN, false, true><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+  } else {
+    if (L.check) k_local_step<D, R, EN, true, false><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+    else k_local_step<D, R, EN, false, false><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+  }
 }
 
 }  // namespace

@@ -48,7 +48,8 @@ class Solver:
                  eps_abs: float = 1e-6, eps_rel: float = 1e-5, check_every: int = 10,
                  precision: str = "fp32", refine_sweeps: int = 2, leaf_size: int = 64,
                  require_flip_free: bool = True, host_threads: int = 0, schedule: int = 1,
-                 penalties: str = "fixed", rescale_rho: float = 5.0, stream=None):
+                 penalties: str = "fixed", rescale_rho: float = 5.0, local_variant: str = "paper",
+                 stream=None):
         self._lib = N.load()
         self._ctx = None
         Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
@@ -76,6 +77,9 @@ class Solver:
             raise ValueError("penalties must be 'fixed' or 'paper'")
         prm.penalty_schedule = 1 if penalties == "paper" else 0
         prm.rescale_rho = float(rescale_rho)
+        if local_variant not in ("paper", "joint"):
+            raise ValueError("local_variant must be 'paper' or 'joint'")
+        prm.local_variant = 1 if local_variant == "joint" else 0
         n_pin = 0 if pins is None else int(len(pins))
         self.n_pin = max(n_pin, 1)
         pP, self._pins = _ptr(pins, np.int32) if n_pin else (None, None)
