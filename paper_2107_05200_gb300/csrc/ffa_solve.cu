@@ -457,6 +457,49 @@ __device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* _
   }
 }
 
+// v = [z_s ; -x at the structure rows] for rows [r0, r0 + nr) of a node into
+// dst[k * dst_ld + r]: every thread first issues the index loads of all its rows,
+// then all their z / x loads, so staging costs two load latencies, not two per row.
+template <int D>
+__device__ __forceinline__ void stage_v(const NodeDev& nd, int r0, int nr, const int32_t* __restrict__ rows,
+                                        const float* __restrict__ z, const float* __restrict__ x, float* dst,
+                                        int dst_ld) {
+  constexpr int kIt = (kBwdRows > kNodeMaxLd ? kBwdRows : kNodeMaxLd) / kSolveThreads;
+  const int ntot = nd.ncol + nd.nrow;
+  int src[kIt];
+  bool from_z[kIt];
+#pragma unroll
+  for (int u = 0; u < kIt; ++u) {
+    const int r = threadIdx.x + u * kSolveThreads;
+    const int row = r0 + r;
+    src[u] = -1;
+    from_z[u] = false;
+    if (r < nr) {
+      if (row < nd.ncol) {
+        src[u] = nd.col0 + row;
+        from_z[u] = true;
+      } else if (row < ntot) {
+        src[u] = __ldg(rows + nd.row_off + (row - nd.ncol));
+      }
+    }
+  }
+  float v[kIt][D];
+#pragma unroll
+  for (int u = 0; u < kIt; ++u)
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      v[u][k] = src[u] < 0 ? 0.f
+                           : (from_z[u] ? __ldcg(z + (int64_t)src[u] * D + k) : -__ldcg(x + (int64_t)src[u] * D + k));
+#pragma unroll
+  for (int u = 0; u < kIt; ++u) {
+    const int r = threadIdx.x + u * kSolveThreads;
+    if (r < nr) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) dst[k * dst_ld + r] = v[u][k];
+    }
+  }
+}
+
 // Backward wide task (node, r0, c0): output columns [c0, c0+32) of x_s against rows
 // [r0, r0+1024) of B_s, v = [z_s ; -x at the structure rows] staged in shared
 // memory.  Warp w owns columns c0+4w .. c0+4w+3; each lane reads 4 rows of each
@@ -466,7 +509,6 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
                                               const float* __restrict__ blocks, const float* __restrict__ z,
                                               float* __restrict__ x, float* smem) {
   float (*vs)[kBwdRows] = reinterpret_cast<float (*)[kBwdRows]>(smem);   // [D][1024]
-  const int ntot = nd.ncol + nd.nrow;
   const int nr = min(t.kind, nd.ld - t.r0);     // rows of this task: a multiple of 4
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j0 = t.c0 + 4 * warp;
@@ -481,16 +523,7 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     pa[q] = (q < ncw && ra < nr) ? ldg_stream(B + (int64_t)q * nd.ld + ra) : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int r = threadIdx.x; r < nr; r += kSolveThreads) {
-    const int row = t.r0 + r;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      float v = 0.f;
-      if (row < nd.ncol) v = __ldcg(z + (int64_t)(nd.col0 + row) * D + k);
-      else if (row < ntot) v = -__ldcg(x + (int64_t)__ldg(rows + nd.row_off + (row - nd.ncol)) * D + k);
-      vs[k][r] = v;
-    }
-  }
+  stage_v<D>(nd, t.r0, nr, rows, z, x, &vs[0][0], kBwdRows);
   __syncthreads();
   if (ncw == 0) return;
   float acc[4][D];
@@ -544,7 +577,6 @@ template <int D>
 __device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* __restrict__ rows,
                                               const float* __restrict__ blocks, const float* __restrict__ z,
                                               float* __restrict__ x, float* smem) {
-  const int ntot = nd.ncol + nd.nrow;
   const int ld = nd.ld;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cg = lane >> 3, rl = lane & 7;
@@ -559,15 +591,7 @@ __device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* 
       pre[u] = (j < nd.ncol && r < ld) ? ldg_stream(B + r) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  for (int r = threadIdx.x; r < ld; r += kSolveThreads) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      float v = 0.f;
-      if (r < nd.ncol) v = __ldcg(z + (int64_t)(nd.col0 + r) * D + k);
-      else if (r < ntot) v = -__ldcg(x + (int64_t)__ldg(rows + nd.row_off + (r - nd.ncol)) * D + k);
-      smem[k * ld + r] = v;
-    }
-  }
+  stage_v<D>(nd, 0, ld, rows, z, x, smem, ld);
   __syncthreads();
   for (int j0 = 4 * warp; j0 < nd.ncol; j0 += 4 * kSolveWarps) {
     const int j = j0 + cg;
