@@ -191,8 +191,11 @@ __device__ __forceinline__ void mesh_reduce(const R v[NQ], const ElemBufs& e, in
 // ---------------------------------------------------------------------------
 // the fused local step
 // ---------------------------------------------------------------------------
+// float: 64 registers (4 blocks of 256 or 8 of 128 per SM).  The per-element math is issue
+// bound, and the extra resident warps hide its latencies better than the spilled
+// registers cost (measured 0.215 -> 0.167 ms on the 64^3-cell cube).
 template <int D, typename R, int EN, bool CHECK, bool JOINT>
-__global__ void __launch_bounds__(256) k_local_step(ElemBufs e, int m, const void* __restrict__ vrec,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(ElemBufs e, int m, const void* __restrict__ vrec,
                                                     double* __restrict__ partials) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   R qv[NQ];
