@@ -493,29 +493,29 @@ int kernels_per_iteration(const ffa_ctx* ctx) {
 // whole node); larger nodes are cut into wide tasks.  The level-synchronous
 // schedule launches the tasks of one level at a time (fwd_off / bwd_off); the
 // dynamic schedule uses the same task arrays with the per-node dependencies.
-ffa_status upload_dyn(ffa_ctx* ctx, DynPass& P, const Task* tasks, int n_tasks, const std::vector<int32_t>& task0,
-                      const std::vector<int32_t>& ntask, const std::vector<int32_t>& dep_ptr,
-                      const std::vector<int32_t>& dep, const std::vector<int32_t>& pending,
-                      const std::vector<int32_t>& q_init, int n_init) {
+ffa_status upload_dyn(ffa_ctx* ctx, DynPass& P, const Task* tasks, int n_tasks, const std::vector<int4>& push,
+                      const std::vector<int4>& kids, const std::vector<int32_t>& pending,
+                      const std::vector<int32_t>& q_init, int n_init, bool forward) {
   ffa_status st;
-  int32_t *t0, *nt, *dp, *dd, *qi, *pi, *q, *pe, *dn, *ct;
-  if ((st = upload(ctx, &t0, task0)) != FFA_OK) return st;
-  if ((st = upload(ctx, &nt, ntask)) != FFA_OK) return st;
-  if ((st = upload(ctx, &dp, dep_ptr)) != FFA_OK) return st;
-  if ((st = upload(ctx, &dd, dep)) != FFA_OK) return st;
+  int4 *pu = nullptr, *kd = nullptr;
+  int32_t *qi, *pi = nullptr, *q, *pe = nullptr, *dn = nullptr, *ct;
+  const int nn = (int)push.size();
+  if ((st = upload(ctx, &pu, push)) != FFA_OK) return st;
+  if (!kids.empty() && (st = upload(ctx, &kd, kids)) != FFA_OK) return st;
   if ((st = upload(ctx, &qi, q_init)) != FFA_OK) return st;
-  if ((st = upload(ctx, &pi, pending)) != FFA_OK) return st;
   if ((st = dalloc(ctx, &q, q_init.size())) != FFA_OK) return st;
-  if ((st = dalloc(ctx, &pe, pending.size())) != FFA_OK) return st;
-  if ((st = dalloc(ctx, &dn, pending.size())) != FFA_OK) return st;
+  if (forward) {
+    if ((st = upload(ctx, &pi, pending)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &pe, nn)) != FFA_OK) return st;
+  } else if ((st = dalloc(ctx, &dn, nn)) != FFA_OK) {
+    return st;
+  }
   if ((st = dalloc(ctx, &ct, 2)) != FFA_OK) return st;
   P.tasks = tasks;
   P.n_tasks = n_tasks;
   P.n_init = n_init;
-  P.task0 = t0;
-  P.ntask = nt;
-  P.dep_ptr = dp;
-  P.dep = dd;
+  P.push = pu;
+  P.kids = kd;
   P.q_init = qi;
   P.pending_init = pi;
   P.queue = q;
@@ -599,42 +599,46 @@ ffa_status build_tasks(ffa_ctx* ctx) {
   // dynamic launch and after the backward one.
   const int nb = std::min(ctx->bottom_levels, nl);
   auto top = [&](int s) { return ntf[s] > 0 && nd_h[s].level >= nb; };
-  // forward: s waits on the nodes whose nearest ancestor with tasks is s
-  std::vector<int32_t> dptr_f(nn + 1, 0), dep_f, pend_f(nn, 0), qf;
-  for (int s = 0; s < nn; ++s) {
+  // forward: s waits on the tasks of the nodes whose nearest ancestor with tasks is s
+  std::vector<int4> push_f(nn, int4{-1, 0, 0, 0}), push_b((size_t)nn * (1 + kPushKids), int4{0, 0, 0, 0}),
+      kids_b, none;
+  std::vector<int32_t> pend_f(nn, 0), qf, qb;
+  for (int s = 0; s < nn; ++s)
     if (top(s) && up[s] >= 0) {
-      dep_f.push_back(up[s]);
-      pend_f[up[s]]++;
+      const int p = up[s];
+      push_f[s] = int4{p, t0f[p], ntf[p], 0};
+      pend_f[p] += ntf[s];
     }
-    dptr_f[s + 1] = (int32_t)dep_f.size();
-  }
   for (int s = 0; s < nn; ++s)
     if (top(s) && pend_f[s] == 0)
       for (int i = 0; i < ntf[s]; ++i) qf.push_back(t0f[s] + i);
   const int n_init_f = (int)qf.size();
   const int n_top_f = (int)(fwd_all.size() - ctx->fwd_off[nb]);
   qf.resize(n_top_f, -1);
-  // backward: s waits on its nearest ancestor with tasks
+  // backward: s waits on its nearest ancestor with tasks alone
   std::vector<std::vector<int32_t>> kids(nn);
-  std::vector<int32_t> pend_b(nn, 0), dptr_b(nn + 1, 0), dep_b, qb;
   for (int s = 0; s < nn; ++s)
-    if (top(s) && up[s] >= 0) {
-      kids[up[s]].push_back(s);
-      pend_b[s] = 1;
-    }
+    if (top(s) && up[s] >= 0) kids[up[s]].push_back(s);
   for (int s = 0; s < nn; ++s) {
-    dep_b.insert(dep_b.end(), kids[s].begin(), kids[s].end());
-    dptr_b[s + 1] = (int32_t)dep_b.size();
+    const int k0 = (int)kids_b.size();
+    int total = 0;
+    for (int c : kids[s]) {
+      kids_b.push_back(int4{t0b[c], ntb[c], total, 0});
+      total += ntb[c];
+    }
+    push_b[(size_t)s * (1 + kPushKids)] = int4{k0, (int)kids_b.size(), total, ntb[s]};
+    for (int j = 0; j < kPushKids && k0 + j < push_b[(size_t)s * (1 + kPushKids)].y; ++j)
+      push_b[(size_t)s * (1 + kPushKids) + 1 + j] = kids_b[k0 + j];
   }
   for (int s = nn - 1; s >= 0; --s)
-    if (top(s) && pend_b[s] == 0)
+    if (top(s) && up[s] < 0)
       for (int i = 0; i < ntb[s]; ++i) qb.push_back(t0b[s] + i);
   const int n_init_b = (int)qb.size();
   const int n_top_b = (int)(bwd_all.size() - ctx->bwd_off[nb]);
   qb.resize(n_top_b, -1);
-  if ((st = upload_dyn(ctx, ctx->fdyn, ctx->fwd_t, n_top_f, t0f, ntf, dptr_f, dep_f, pend_f, qf, n_init_f)) != FFA_OK)
+  if ((st = upload_dyn(ctx, ctx->fdyn, ctx->fwd_t, n_top_f, push_f, none, pend_f, qf, n_init_f, true)) != FFA_OK)
     return st;
-  if ((st = upload_dyn(ctx, ctx->bdyn, ctx->bwd_t, n_top_b, t0b, ntb, dptr_b, dep_b, pend_b, qb, n_init_b)) != FFA_OK)
+  if ((st = upload_dyn(ctx, ctx->bdyn, ctx->bwd_t, n_top_b, push_b, kids_b, pend_f, qb, n_init_b, false)) != FFA_OK)
     return st;
   ctx->bottom_used = nb;
   if (!ctx->err_flag) {
@@ -1095,7 +1099,7 @@ int64_t next_rescale_iter(const ffa_ctx* ctx) {
   return ctx->last_event_iter + (int64_t)std::floor(5.0 * std::pow(1.5, (double)p));
 }
 
-bool device_wait_failed(ffa_ctx* ctx);
+ffa_status device_wait_status(ffa_ctx* ctx, const char* what);
 
 // The Tutte initializer (App. A, "Tutte's Energy"): the minimizer of
 // E_T(W) = sum over edges (i, j) of |W_i - W_j|^2 / |V_i - V_j| with the boundary
@@ -1283,7 +1287,7 @@ ffa_status tutte_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* bnd_in,
     launch_supernodal_solve(S, s);
     launch_axpy_correction(S, s);
   }
-  if (device_wait_failed(ctx)) return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait of the supernodal solve gave up");
+  if ((st = device_wait_status(ctx, "supernodal solve")) != FFA_OK) return st;
   VertexLaunch Vl{};
   Vl.d = d;
   Vl.fp64 = 1;
@@ -1406,13 +1410,16 @@ ffa_status records_of(ffa_ctx* ctx, const double* W) {
   return FFA_OK;
 }
 
-// reads (and clears) the flag the persistent solve kernels set when a bounded wait ran out
-bool device_wait_failed(ffa_ctx* ctx) {
-  if (!ctx->err_flag) return false;
+// reads (and clears) the flag the persistent solve kernels set when a bounded
+// wait ran out (FFA_ERR_TIMEOUT); a read that fails reports the CUDA error
+ffa_status device_wait_status(ffa_ctx* ctx, const char* what) {
+  if (!ctx->err_flag) return FFA_OK;
   int32_t f = 0;
-  if (cudaMemcpy(&f, ctx->err_flag, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return true;
-  if (f) cudaMemset(ctx->err_flag, 0, sizeof(f));
-  return f != 0;
+  const cudaError_t e = cudaMemcpy(&f, ctx->err_flag, sizeof(f), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(ctx, FFA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  if (!f) return FFA_OK;
+  cudaMemset(ctx->err_flag, 0, sizeof(f));
+  return fail(ctx, FFA_ERR_TIMEOUT, std::string("a device-side wait gave up: ") + what);
 }
 
 }  // namespace
@@ -1565,9 +1572,9 @@ ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_
     if (stop_at_tol || done == max_iter || at_event) {
       FFA_CUDA(cudaMemcpyAsync(ctx->stats_h, ctx->stats_d, sizeof(ffa_stats), cudaMemcpyDeviceToHost, ctx->stream));
       FFA_CUDA(cudaStreamSynchronize(ctx->stream));
-      if (device_wait_failed(ctx)) {
+      if (const ffa_status ws = device_wait_status(ctx, "supernodal solve")) {
         ctx->iter_total += done;
-        return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait of the supernodal solve gave up");
+        return ws;
       }
       have = true;
       ctx->last = *ctx->stats_h;
@@ -1604,8 +1611,8 @@ ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_
 }
 
 ffa_status ffa_get_W(ffa_ctx* ctx, double* W_out) {
-  if (ctx && device_wait_failed(ctx)) return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait of the supernodal solve gave up");
   if (!ctx) return FFA_ERR_INVALID_ARG;
+  if (const ffa_status ws = device_wait_status(ctx, "supernodal solve")) return ws;
   if (!W_out) return fail(ctx, FFA_ERR_INVALID_ARG, "W_out is NULL");
   ctx->err.clear();
   FFA_CUDA(cudaMemcpyAsync(W_out, ctx->W, (size_t)ctx->n * ctx->d * 8, cudaMemcpyDefault, ctx->stream));
@@ -2004,7 +2011,7 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
     ctx->bottom_levels = best_bottom;
     if ((st = build_tasks(ctx)) != FFA_OK) return st;
   }
-  if (device_wait_failed(ctx)) return fail(ctx, FFA_ERR_TIMEOUT, "a device-side wait gave up during tuning");
+  if ((st = device_wait_status(ctx, "tuning")) != FFA_OK) return st;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // the graphs captured the old launch shapes

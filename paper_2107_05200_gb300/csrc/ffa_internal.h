@@ -38,21 +38,29 @@ struct Task {
 };
 
 // One pass (forward or backward) of the dynamic schedule.  Tasks of a node are
-// contiguous: task0[s] .. task0[s] + ntask[s].  dep (CSR by dep_ptr) lists the
-// nodes that wait on s; pending_init[s] counts what s waits on.  q_init holds
-// the tasks of the nodes that wait on nothing (n_init of them) followed by -1.
+// contiguous in `tasks`.  push[s] says what a completed task of node s releases:
+//   forward:  {p, first task of p, tasks of p, 0}, p = the node waiting on s or
+//             -1; pending[p] counts the tasks of all nodes waiting on p, so the
+//             task that brings it to zero makes p ready;
+//   backward: {k0, k1, tasks of all nodes waiting on s, tasks of s} followed by
+//             kPushKids inline copies of kids[k0], kids[k0 + 1] (stride
+//             1 + kPushKids per node); the nodes waiting on s are kids[k0..k1) =
+//             {first task, tasks, offset of its tasks among all of them, 0};
+//             each waits on s alone, so the task that completes s (done[s]
+//             reaches the task count) releases them all.
+// q_init holds the tasks that wait on nothing (n_init of them) followed by -1.
+constexpr int kPushKids = 2;
+
 struct DynPass {
   const Task* tasks = nullptr;
   int n_tasks = 0, n_init = 0;
-  const int32_t* task0 = nullptr;
-  const int32_t* ntask = nullptr;
-  const int32_t* dep_ptr = nullptr;
-  const int32_t* dep = nullptr;
+  const int4* push = nullptr;
+  const int4* kids = nullptr;   // backward only
   const int32_t* q_init = nullptr;
-  const int32_t* pending_init = nullptr;
+  const int32_t* pending_init = nullptr;   // forward only
   int32_t* queue = nullptr;     // n_tasks slots
-  int32_t* pending = nullptr;   // per node
-  int32_t* done = nullptr;      // per node: tasks finished
+  int32_t* pending = nullptr;   // forward: per node
+  int32_t* done = nullptr;      // backward: per node, tasks finished
   int32_t* ctr = nullptr;       // [0] next slot to claim, [1] next slot to fill
 };
 

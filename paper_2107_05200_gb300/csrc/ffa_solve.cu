@@ -693,17 +693,20 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_backward(con
 // Dynamic schedule: one launch per pass over a ready queue.  The queue starts
 // with the tasks of the nodes that depend on nothing (forward: the nodes with no
 // descendant that has tasks; backward: the roots).  Blocks claim queue slots in
-// order and run the task found there.  The block that finishes the last task of
-// a node decrements the pending count of each node waiting on it (forward: its
-// nearest ancestor with tasks; backward: the nodes whose nearest ancestor with
-// tasks it is) and appends the tasks of every node whose count reached zero.
-// A block therefore only ever waits for a slot to be filled, never for a
-// particular node, and no block holds a task whose inputs are incomplete.
-// Every slot is filled exactly once (each node becomes ready once), so the waits
-// end; each is still bounded and sets err_flag instead of spinning on.
+// order and run the task found there.  Forward, every finished task decrements
+// the pending count of the node waiting on its node (the count starts at the
+// number of tasks it waits on); backward, the task that completes its node
+// releases the nodes waiting on it, each of which waits on that node alone.  A
+// released node's tasks are appended to the queue, so a block only ever waits
+// for a slot to be filled, never for a particular node, and no block holds a
+// task whose inputs are incomplete.  What a completion releases (the push
+// record of the node) is fetched asynchronously when the task starts, so the
+// completion itself costs a fence, one counter atomic and, when something is
+// released, one queue reservation.  Every slot is filled exactly once (each
+// node becomes ready once), so the waits end; each is still bounded and sets
+// err_flag instead of spinning on.
 // ---------------------------------------------------------------------------
 constexpr long long kSpinLimit = 1LL << 22;   // polls of ~100 ns (~0.4 s) before giving up
-constexpr int kMaxPush = 16;                  // nodes made ready by one completion handled per round
 
 struct DynView {
   DynPass P;
@@ -726,11 +729,22 @@ __device__ __forceinline__ void st_relaxed(int32_t* p, int v) {
   asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy (completes by cp_async_wait_all)
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 template <int D, bool FWD>
 __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynamic(DynView V) {
+  constexpr int kRec = FWD ? 1 : 1 + kPushKids;   // int4 entries of a push record
   __shared__ __align__(16) float smem[FWD ? SolveSmem<D>::kFwd : SolveSmem<D>::kBwd];
-  __shared__ int item_s, slot_s, n_push_s, next_s;
-  __shared__ int push_s[kMaxPush][3];   // first task, queue position, count
+  __shared__ __align__(16) int4 rec_s[kRec];
+  __shared__ int item_s, slot_s, base_s;
   const DynPass& P = V.P;
   if (threadIdx.x == 0) slot_s = atomicAdd(P.ctr, 1);
   for (;;) {
@@ -754,6 +768,10 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
     const int ti = item_s;
     if (ti < 0) break;
     const Task t = P.tasks[ti];
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int e = 0; e < kRec; ++e) cp_async16(&rec_s[e], P.push + (int64_t)t.node * kRec + e);
+    }
     const NodeDev nd = V.nodes[t.node];
     if constexpr (FWD) forward_task<D>(t, nd, V.rows, V.blocks, V.y, V.z, smem);
     else backward_task<D>(t, nd, V.rows, V.blocks, V.z, V.x, smem);
@@ -761,52 +779,37 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
     // the next slot is claimed while the completion below is worked out
     if (threadIdx.x == 32) slot_s = atomicAdd(P.ctr, 1);
     // completion: the block's writes are released by one fence after the barrier
-    // (fences are cumulative); the block that ends a node decrements the pending
-    // counts of the nodes waiting on it and reserves queue room for every node
-    // that became ready
-    int q = 0, q_end = 0;
+    // (fences are cumulative); a release reserves queue room for everything it
+    // releases, and the whole block then writes the released tasks' ids
     if (threadIdx.x == 0) {
+      cp_async_wait_all();
+      const int4 r = rec_s[0];
+      int base = -1;
       __threadfence();
-      q_end = -1;
-      if (t.kind == 1 || atomicAdd(P.done + t.node, 1) == P.ntask[t.node] - 1) {
-        q = P.dep_ptr[t.node];
-        q_end = P.dep_ptr[t.node + 1];
+      if constexpr (FWD) {
+        if (r.x >= 0 && atomicSub(P.pending + r.x, 1) == 1) base = atomicAdd(P.ctr + 1, r.z);
+      } else if (r.z > 0 && (t.kind == 1 || atomicAdd(P.done + t.node, 1) == r.w - 1)) {
+        base = atomicAdd(P.ctr + 1, r.z);
       }
-      next_s = q;
-      n_push_s = q_end;
+      if (base >= 0) __threadfence();   // acquire the other tasks' releases
+      base_s = base;
     }
     __syncthreads();
-    q = next_s;
-    q_end = n_push_s;
-    while (q < q_end) {   // block-uniform
-      __syncthreads();    // everyone has read next_s / n_push_s / push_s
-      if (threadIdx.x == 0) {
-        int n = 0;
-        int qq = q;
-        for (; qq < q_end && n < kMaxPush; ++qq) {
-          const int p = P.dep[qq];
-          if (atomicSub(P.pending + p, 1) == 1) {
-            const int cnt = P.ntask[p];
-            push_s[n][0] = P.task0[p];
-            push_s[n][1] = atomicAdd(P.ctr + 1, cnt);
-            push_s[n][2] = cnt;
-            ++n;
-          }
+    const int base = base_s;
+    if (base >= 0) {
+      __threadfence();
+      const int4 r = rec_s[0];
+      if constexpr (FWD) {
+        for (int i = threadIdx.x; i < r.z; i += kSolveThreads) st_relaxed(P.queue + base + i, r.y + i);
+      } else {
+        for (int k = r.x; k < r.y; ++k) {   // block-uniform
+          const int j = k - r.x;
+          const int4 e = j < kPushKids ? rec_s[1 + j] : P.kids[k];
+          for (int i = threadIdx.x; i < e.y; i += kSolveThreads) st_relaxed(P.queue + base + e.z + i, e.x + i);
         }
-        if (n > 0) __threadfence();   // acquire the other dependencies' releases
-        n_push_s = n;
-        next_s = qq;
-      }
-      __syncthreads();
-      const int n = n_push_s;
-      q = next_s;
-      if (n > 0) {
-        __threadfence();
-        for (int e = 0; e < n; ++e)
-          for (int i = threadIdx.x; i < push_s[e][2]; i += kSolveThreads) st_relaxed(P.queue + push_s[e][1] + i, push_s[e][0] + i);
       }
     }
-    __syncthreads();   // item_s, slot_s and the push records are reused
+    __syncthreads();   // item_s, slot_s, base_s and rec_s are reused
   }
 }
 
@@ -824,8 +827,6 @@ __global__ void k_dyn_reset(DynPass F, DynPass B, int n_nodes, float* __restrict
     if (i < B.n_tasks) B.queue[i] = B.q_init[i];
     if (i < n_nodes) {
       F.pending[i] = F.pending_init[i];
-      B.pending[i] = B.pending_init[i];
-      F.done[i] = 0;
       B.done[i] = 0;
     }
     if (i == 0) {
