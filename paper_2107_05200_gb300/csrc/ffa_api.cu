@@ -65,7 +65,6 @@ struct ffa_ctx {
   int64_t* fc_ptr = nullptr;
   int32_t* fc_col = nullptr;
   double* fc_val = nullptr;
-  NodeDev* nodes = nullptr;
   int32_t* rows = nullptr;
   float* blocks = nullptr;
   Task *fwd_t = nullptr, *bwd_t = nullptr;
@@ -303,7 +302,6 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.ell_width = ctx->ell_width;
   S.ell_col = ctx->ell_col;
   S.ell_val = ctx->ell_val;
-  S.nodes = ctx->nodes;
   S.rows = ctx->rows;
   S.blocks = ctx->blocks;
   S.fwd_tasks = ctx->fwd_t;
@@ -541,8 +539,8 @@ ffa_status build_tasks(ffa_ctx* ctx) {
     const int ntot = sn.ncol + sn.nrow;
     if (sn.ncol == 0) continue;
     if (is_node_task(sn)) {
-      fl[sn.level].push_back(Task{s, 0, 0, 1});
-      bl[sn.level].push_back(Task{s, 0, 0, 1});
+      fl[sn.level].push_back(Task{s, 0, 0, 1, nodes[s]});
+      bl[sn.level].push_back(Task{s, 0, 0, 1, nodes[s]});
       continue;
     }
     // (smaller wide tasks on the narrow top levels were measured slower: the
@@ -552,13 +550,13 @@ ffa_status build_tasks(ffa_ctx* ctx) {
       for (int c0 = 0; c0 < sn.ncol; c0 += wf) {
         const int rmax = std::min(r0 + kFwdRows, ntot) - 1;
         if (rmax < c0) continue;  // entirely above the diagonal of inv(L_ss)
-        fl[sn.level].push_back(Task{s, r0, c0, wf});
+        fl[sn.level].push_back(Task{s, r0, c0, wf, nodes[s]});
       }
     for (int c0 = 0; c0 < sn.ncol; c0 += kBwdCols)
       for (int r0 = 0; r0 < ntot; r0 += wb) {
         const int rmax = std::min(r0 + wb, ntot) - 1;
         if (rmax < c0) continue;
-        bl[sn.level].push_back(Task{s, r0, c0, wb});
+        bl[sn.level].push_back(Task{s, r0, c0, wb, nodes[s]});
       }
   }
   std::vector<Task> fwd_all, bwd_all;
@@ -571,7 +569,6 @@ ffa_status build_tasks(ffa_ctx* ctx) {
     ctx->bwd_off.push_back((int64_t)bwd_all.size());
   }
   ffa_status st;
-  if (!ctx->nodes && (st = upload(ctx, &ctx->nodes, nodes)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->fwd_t, fwd_all)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->bwd_t, bwd_all)) != FFA_OK) return st;
 

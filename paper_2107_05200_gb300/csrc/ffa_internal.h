@@ -31,10 +31,17 @@ constexpr int kBwdRows = 1024;                  // backward wide task: at most t
 constexpr int kNarrowCols = 64;                 // node tasks: at most this many columns ...
 constexpr int kNodeMaxLd = 4 * kSolveThreads;   // ... and at most one 4-row group per thread
 
+struct NodeDev {
+  int32_t col0, ncol, nrow, ld;   // ld: leading dimension of B_s (multiple of 4)
+  int64_t row_off, blk_off;
+};
+
 // kind 1: the whole node on one block; kind > 1: a wide task of B_node from
-// (r0, c0) spanning kind columns (forward) or kind rows (backward)
-struct Task {
+// (r0, c0) spanning kind columns (forward) or kind rows (backward).  The node's
+// descriptor travels with the task, so one 48-byte load brings both.
+struct __align__(16) Task {
   int32_t node, r0, c0, kind;
+  NodeDev nd;
 };
 
 // One pass (forward or backward) of the dynamic schedule.  Tasks of a node are
@@ -64,10 +71,6 @@ struct DynPass {
   int32_t* ctr = nullptr;       // [0] next slot to claim, [1] next slot to fill
 };
 
-struct NodeDev {
-  int32_t col0, ncol, nrow, ld;   // ld: leading dimension of B_s (multiple of 4)
-  int64_t row_off, blk_off;
-};
 
 // Element state.  Real-typed arrays are float or double depending on the
 // precision of the local step; all are structure-of-arrays with stride m,
@@ -148,7 +151,6 @@ struct SolveData {
   int ell_width;
   const int32_t* ell_col;    // width x nF (eliminated numbering)
   const double* ell_val;     // width x nF
-  const NodeDev* nodes;
   const int32_t* rows;
   const float* blocks;
   const Task* fwd_tasks;

@@ -672,21 +672,21 @@ __device__ __forceinline__ void backward_task(const Task& t, const NodeDev& nd, 
 
 // level-synchronous schedule: one launch per level, one task per block
 template <int D>
-__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_forward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_forward(const Task* __restrict__ tasks,
                                                  const int32_t* __restrict__ rows, const float* __restrict__ blocks,
                                                  float* __restrict__ y, float* __restrict__ z) {
   __shared__ __align__(16) float smem[SolveSmem<D>::kFwd];
-  const Task t = tasks[blockIdx.x];
-  forward_task<D>(t, nodes[t.node], rows, blocks, y, z, smem);
+  const Task& t = tasks[blockIdx.x];
+  forward_task<D>(t, t.nd, rows, blocks, y, z, smem);
 }
 
 template <int D>
-__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_backward(const Task* __restrict__ tasks, const NodeDev* __restrict__ nodes,
+__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_backward(const Task* __restrict__ tasks,
                                                   const int32_t* __restrict__ rows, const float* __restrict__ blocks,
                                                   const float* __restrict__ z, float* __restrict__ x) {
   __shared__ __align__(16) float smem[SolveSmem<D>::kBwd];
-  const Task t = tasks[blockIdx.x];
-  backward_task<D>(t, nodes[t.node], rows, blocks, z, x, smem);
+  const Task& t = tasks[blockIdx.x];
+  backward_task<D>(t, t.nd, rows, blocks, z, x, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -710,7 +710,6 @@ constexpr long long kSpinLimit = 1LL << 22;   // polls of ~100 ns (~0.4 s) befor
 
 struct DynView {
   DynPass P;
-  const NodeDev* nodes;
   const int32_t* rows;
   const float* blocks;
   float* y;
@@ -744,22 +743,30 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
   constexpr int kRec = FWD ? 1 : 1 + kPushKids;   // int4 entries of a push record
   __shared__ __align__(16) float smem[FWD ? SolveSmem<D>::kFwd : SolveSmem<D>::kBwd];
   __shared__ __align__(16) int4 rec_s[kRec];
-  __shared__ int item_s, slot_s, base_s;
+  __shared__ __align__(16) Task task_s;   // the task to run next
+  __shared__ int item_s, slot_s, next_s, base_s;
   const DynPass& P = V.P;
-  if (threadIdx.x == 0) slot_s = atomicAdd(P.ctr, 1);
+  if (threadIdx.x == 0) {
+    slot_s = atomicAdd(P.ctr, 1);
+    next_s = -1;
+  }
   for (;;) {
     if (threadIdx.x == 0) {
       int t = -1;
       const int h = slot_s;
       if (h < P.n_tasks) {
-        long long it = 0;
-        while ((t = ld_acquire(P.queue + h)) < 0) {
-          if (++it > kSpinLimit || ld_acquire(V.err_flag) != 0) {
-            atomicExch(V.err_flag, 1);
-            t = -1;
-            break;
+        t = next_s;   // >= 0: the slot was already filled and task_s holds its task
+        if (t < 0) {
+          long long it = 0;
+          while ((t = ld_acquire(P.queue + h)) < 0) {
+            if (++it > kSpinLimit || ld_acquire(V.err_flag) != 0) {
+              atomicExch(V.err_flag, 1);
+              t = -1;
+              break;
+            }
+            __nanosleep(64);
           }
-          __nanosleep(64);
+          if (t >= 0) task_s = P.tasks[t];
         }
       }
       item_s = t;
@@ -767,17 +774,22 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
     __syncthreads();
     const int ti = item_s;
     if (ti < 0) break;
-    const Task t = P.tasks[ti];
+    const Task& t = task_s;   // read in place: task_s is rewritten only after the completion
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int e = 0; e < kRec; ++e) cp_async16(&rec_s[e], P.push + (int64_t)t.node * kRec + e);
     }
-    const NodeDev nd = V.nodes[t.node];
+    const NodeDev& nd = task_s.nd;
     if constexpr (FWD) forward_task<D>(t, nd, V.rows, V.blocks, V.y, V.z, smem);
     else backward_task<D>(t, nd, V.rows, V.blocks, V.z, V.x, smem);
     __syncthreads();
-    // the next slot is claimed while the completion below is worked out
-    if (threadIdx.x == 32) slot_s = atomicAdd(P.ctr, 1);
+    // the next slot is claimed, and read once, while the completion below is
+    // worked out
+    if (threadIdx.x == 32) {
+      const int h = atomicAdd(P.ctr, 1);
+      slot_s = h;
+      next_s = h < P.n_tasks ? ld_acquire(P.queue + h) : -1;
+    }
     // completion: the block's writes are released by one fence after the barrier
     // (fences are cumulative); a release reserves queue room for everything it
     // releases, and the whole block then writes the released tasks' ids
@@ -809,7 +821,13 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
         }
       }
     }
-    __syncthreads();   // item_s, slot_s, base_s and rec_s are reused
+    // the next task, when its slot was already filled, is fetched before the
+    // block goes round
+    if (threadIdx.x >= 32 && threadIdx.x < 35) {
+      const int nt = next_s;
+      if (nt >= 0) reinterpret_cast<int4*>(&task_s)[threadIdx.x - 32] = reinterpret_cast<const int4*>(P.tasks + nt)[threadIdx.x - 32];
+    }
+    __syncthreads();   // item_s, slot_s, next_s, task_s, base_s and rec_s are reused
   }
 }
 
@@ -993,8 +1011,8 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   if (S.ev[0]) cudaEventRecord(S.ev[0], s);
   const int L = (int)S.fwd_off.size() - 1;
   if (S.schedule == 1) {
-    const DynView vf{S.fdyn, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
-    const DynView vb{S.bdyn, S.nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
+    const DynView vf{S.fdyn, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
+    const DynView vb{S.bdyn, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
     const int nb = std::min(S.bottom_levels, L);
     launch_levels(S, 0, nb, true, s);
     if (S.d == 2) k_solve_dynamic<2, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);
@@ -1018,16 +1036,16 @@ void launch_levels(const SolveData& S, int l0, int l1, bool forward, cudaStream_
     for (int l = l0; l < l1; ++l) {
       const int64_t nt = S.fwd_off[l + 1] - S.fwd_off[l];
       if (nt <= 0) continue;
-      if (S.d == 2) k_forward<2><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
-      else k_forward<3><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.nodes, S.rows, S.blocks, S.y, S.z);
+      if (S.d == 2) k_forward<2><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.rows, S.blocks, S.y, S.z);
+      else k_forward<3><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.fwd_tasks + S.fwd_off[l], S.rows, S.blocks, S.y, S.z);
     }
     return;
   }
   for (int l = l1 - 1; l >= l0; --l) {
     const int64_t nt = S.bwd_off[l + 1] - S.bwd_off[l];
     if (nt <= 0) continue;
-    if (S.d == 2) k_backward<2><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
-    else k_backward<3><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.nodes, S.rows, S.blocks, S.z, S.x);
+    if (S.d == 2) k_backward<2><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.rows, S.blocks, S.z, S.x);
+    else k_backward<3><<<(unsigned)nt, kSolveThreads, 0, s>>>(S.bwd_tasks + S.bwd_off[l], S.rows, S.blocks, S.z, S.x);
   }
 }
 
