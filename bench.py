@@ -80,16 +80,18 @@ SOLVE_PROFILE = os.path.join(ROOT, "profiles", "k_solve_dynamic_cube48.md")
 
 def solve_fingerprint() -> str:
     """sha256 of the device code of the supernodal solves (the kernels the ncu
-    traffic figure was taken on) and of the task-shape constants."""
+    traffic figure was taken on), of the task-shape constants and of the code
+    that builds the task lists."""
     csrc = os.path.join(ROOT, "paper_2107_05200_gb300", "csrc")
     with open(os.path.join(csrc, "ffa_solve.cu")) as f:
         src = f.read()
     a = src.index("// supernodal solves.")
     b = src.index("}  // namespace\n", a)
-    keys = ("kSolve", "kFwd", "kBwd", "kNarrow", "kNodeMax")
-    with open(os.path.join(csrc, "ffa_internal.h")) as f:
-        consts = "".join(line for line in f if line.startswith("constexpr") and any(k in line for k in keys))
-    return hashlib.sha256((src[a:b] + consts).encode()).hexdigest()[:16]
+    with open(os.path.join(csrc, "ffa_schedule.h")) as f:
+        consts = "".join(line for line in f if line.startswith("constexpr"))
+    with open(os.path.join(csrc, "ffa_schedule.cpp")) as f:
+        sched = f.read()
+    return hashlib.sha256((src[a:b] + consts + sched).encode()).hexdigest()[:16]
 
 
 def profiled_solve_traffic():

@@ -104,6 +104,10 @@ typedef struct {
                               rotation nearest to J + Lambda and P the prox of symm(U^T (J + Lambda)),
                               the joint minimizer of w f(P) + mu/2 |U P - J - Lambda|^2 for the
                               rotation-invariant energies.  Not with ffa_forward_unrolled. */
+  int32_t solve_subtree_height[2]; /* solve_schedule 1: bottom subtrees of the elimination tree of
+                              at most this height whose supernodes are all small run as one task
+                              of the forward / backward pass (one block, supernodes in order);
+                              0 off, -1 the library's choice (default), at most 8 */
 } ffa_params;
 
 typedef struct {
@@ -255,14 +259,17 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out);
 /* Launch shapes picked by ffa_autotune (the paper has no counterpart). */
 typedef struct {
   int32_t local_block;  /* threads per block of the local step: 64, 128 or 256 */
-  int32_t narrow_cols;  /* supernodes with at most this many columns (and at most 1024 rows) run
-                           as one task on one block: 32 or 64 */
+  int32_t narrow_cols;  /* supernodes with at most this many columns (and at most 1024 rows and
+                           64 KB of factor) run as one task on one block: 32 or 64 */
   int32_t schedule;     /* supernodal solves: 0 per-level launches, 1 dynamic ready queue */
   int32_t bottom_levels;/* schedule 1: lowest tree levels run as one launch per level: 0, 2, 3 or 4 */
   double ms_local[3];   /* measured local step for 64, 128, 256 threads */
   double ms_solve[2];   /* measured supernodal solve (forward + backward) for 32, 64 */
   double ms_schedule[2];/* measured supernodal solve for schedules 0 and 1 */
   double ms_bottom[4];  /* measured supernodal solve (schedule 1) for bottom_levels 0, 2, 3, 4 */
+  int32_t subtree_height[2]; /* schedule 1 with bottom_levels 0: bottom subtrees of at most this
+                           height run as one task, forward and backward pass: 0 (off) .. 3 */
+  double ms_subtree[2][4];   /* measured forward / backward pass for heights 0 .. 3 */
 } ffa_tuning;
 
 /* Time the candidate launch shapes of the local step, of the supernodal solves and

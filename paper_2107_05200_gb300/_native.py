@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("refine_sweeps", C.c_int32), ("nd_leaf_size", C.c_int32),
                 ("host_threads", C.c_int32), ("solve_schedule", C.c_int32),
                 ("penalty_schedule", C.c_int32), ("rescale_rho", C.c_double),
-                ("local_variant", C.c_int32)]
+                ("local_variant", C.c_int32), ("solve_subtree_height", C.c_int32 * 2)]
 
 
 class Stats(C.Structure):
@@ -71,13 +71,15 @@ class Info(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("local_block", C.c_int32), ("narrow_cols", C.c_int32), ("schedule", C.c_int32),
                 ("bottom_levels", C.c_int32), ("ms_local", C.c_double * 3), ("ms_solve", C.c_double * 2),
-                ("ms_schedule", C.c_double * 2), ("ms_bottom", C.c_double * 4)]
+                ("ms_schedule", C.c_double * 2), ("ms_bottom", C.c_double * 4),
+                ("subtree_height", C.c_int32 * 2), ("ms_subtree", (C.c_double * 4) * 2)]
 
     def as_dict(self) -> dict:
         return {"local_block": self.local_block, "narrow_cols": self.narrow_cols, "schedule": self.schedule,
                 "bottom_levels": self.bottom_levels, "ms_local": list(self.ms_local),
                 "ms_solve": list(self.ms_solve), "ms_schedule": list(self.ms_schedule),
-                "ms_bottom": list(self.ms_bottom)}
+                "ms_bottom": list(self.ms_bottom), "subtree_height": list(self.subtree_height),
+                "ms_subtree": [list(r) for r in self.ms_subtree]}
 
 
 class PhaseTimes(C.Structure):

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libffadmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["ffa_api.cu", "ffa_local.cu", "ffa_solve.cu", "ffa_adjoint.cu", "ffa_noalloc.cu"]
-CXX_SOURCES = ["ffa_factor.cpp"]
+CXX_SOURCES = ["ffa_factor.cpp", "ffa_schedule.cpp"]
 
 
 def _nvcc() -> str:

@@ -68,6 +68,8 @@ struct ffa_ctx {
   int32_t* rows = nullptr;
   float* blocks = nullptr;
   Task *fwd_t = nullptr, *bwd_t = nullptr;
+  Task *fdyn_t = nullptr, *bdyn_t = nullptr;   // task lists of the dynamic passes
+  NodeDev* sub_nodes = nullptr;                 // their merged subtrees' nodes
   std::vector<int64_t> fwd_off, bwd_off;
   double* local_partials = nullptr;
   int64_t n_local_blocks = 0;
@@ -118,6 +120,8 @@ struct ffa_ctx {
   double seconds_refactor = 0.0;
   int bottom_levels = 0;        // dynamic schedule: lowest tree levels run as one launch each
   int bottom_used = 0;          // min(bottom_levels, levels) of the current task lists
+  int subtree_height_f = 2;     // dynamic schedule: bottom subtrees up to this height run as one task
+  int subtree_height_b = 1;     // (forward / backward pass; measured best on the benchmark cube)
   cudaEvent_t solve_ev[3] = {nullptr, nullptr, nullptr};  // set only while ffa_profile_phases runs
   int32_t* err_flag = nullptr;
   int grid_f = 0, grid_b = 0;
@@ -306,6 +310,7 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.blocks = ctx->blocks;
   S.fwd_tasks = ctx->fwd_t;
   S.bwd_tasks = ctx->bwd_t;
+  S.sub_nodes = ctx->sub_nodes;
   S.fwd_off = ctx->fwd_off;
   S.bwd_off = ctx->bwd_off;
   S.schedule = ctx->schedule;
@@ -465,6 +470,9 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   else if (p.local_variant != 0 && p.local_variant != 1) msg = "local_variant must be 0 or 1";
   else if (p.penalty_schedule == 1 && !(p.rescale_rho > 2.0 && std::isfinite(p.rescale_rho)))
     msg = "rescale_rho must be finite and > 2";
+  else if (p.solve_subtree_height[0] < -1 || p.solve_subtree_height[0] > 8 || p.solve_subtree_height[1] < -1 ||
+           p.solve_subtree_height[1] > 8)
+    msg = "solve_subtree_height must be in [-1, 8]";
   else return FFA_OK;
   return FFA_ERR_INVALID_ARG;
 }
@@ -491,29 +499,27 @@ int kernels_per_iteration(const ffa_ctx* ctx) {
 // whole node); larger nodes are cut into wide tasks.  The level-synchronous
 // schedule launches the tasks of one level at a time (fwd_off / bwd_off); the
 // dynamic schedule uses the same task arrays with the per-node dependencies.
-ffa_status upload_dyn(ffa_ctx* ctx, DynPass& P, const Task* tasks, int n_tasks, const std::vector<int4>& push,
-                      const std::vector<int4>& kids, const std::vector<int32_t>& pending,
-                      const std::vector<int32_t>& q_init, int n_init, bool forward) {
+ffa_status upload_dyn(ffa_ctx* ctx, DynPass& P, const Task* tasks, const PassSchedule& sch, bool forward) {
   ffa_status st;
-  int4 *pu = nullptr, *kd = nullptr;
+  PushRec *pu = nullptr, *kd = nullptr;
   int32_t *qi, *pi = nullptr, *q, *pe = nullptr, *dn = nullptr, *ct;
-  const int nn = (int)push.size();
-  if ((st = upload(ctx, &pu, push)) != FFA_OK) return st;
-  if (!kids.empty() && (st = upload(ctx, &kd, kids)) != FFA_OK) return st;
-  if ((st = upload(ctx, &qi, q_init)) != FFA_OK) return st;
-  if ((st = dalloc(ctx, &q, q_init.size())) != FFA_OK) return st;
+  const int nn = (int)(forward ? sch.push.size() : sch.push.size() / (1 + kPushKids));
+  if ((st = upload(ctx, &pu, sch.push)) != FFA_OK) return st;
+  if (!sch.kids.empty() && (st = upload(ctx, &kd, sch.kids)) != FFA_OK) return st;
+  if ((st = upload(ctx, &qi, sch.queue)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &q, sch.queue.size())) != FFA_OK) return st;
   if (forward) {
-    if ((st = upload(ctx, &pi, pending)) != FFA_OK) return st;
+    if ((st = upload(ctx, &pi, sch.pending)) != FFA_OK) return st;
     if ((st = dalloc(ctx, &pe, nn)) != FFA_OK) return st;
   } else if ((st = dalloc(ctx, &dn, nn)) != FFA_OK) {
     return st;
   }
   if ((st = dalloc(ctx, &ct, 2)) != FFA_OK) return st;
   P.tasks = tasks;
-  P.n_tasks = n_tasks;
-  P.n_init = n_init;
-  P.push = pu;
-  P.kids = kd;
+  P.n_tasks = (int)sch.tasks.size();
+  P.n_init = sch.n_init;
+  P.push = reinterpret_cast<const int4*>(pu);
+  P.kids = reinterpret_cast<const int4*>(kd);
   P.q_init = qi;
   P.pending_init = pi;
   P.queue = q;
@@ -524,124 +530,31 @@ ffa_status upload_dyn(ffa_ctx* ctx, DynPass& P, const Task* tasks, int n_tasks, 
 }
 
 ffa_status build_tasks(ffa_ctx* ctx) {
-  const std::vector<Supernode>& nd_h = ctx->nodes_h;
-  const int nl = ctx->n_levels;
-  const int narrow = std::min(ctx->narrow_cols, kNarrowCols);
-  const int nn = (int)nd_h.size();
+  ScheduleOptions opt;
+  opt.narrow_cols = ctx->narrow_cols;
+  opt.bottom_levels = ctx->bottom_levels;
+  opt.subtree_height_f = ctx->subtree_height_f;
+  opt.subtree_height_b = ctx->subtree_height_b;
+  Schedule sch;
+  build_schedule(ctx->nodes_h, ctx->n_levels, opt, sch);
   ctx->grid_f = persistent_grid(ctx->d, true);
   ctx->grid_b = persistent_grid(ctx->d, false);
-  auto is_node_task = [&](const Supernode& sn) { return sn.ncol <= narrow && sn.ld <= kNodeMaxLd; };
-  std::vector<NodeDev> nodes(nn);
-  std::vector<std::vector<Task>> fl(nl), bl(nl);
-  for (int s = 0; s < nn; ++s) {
-    const Supernode& sn = nd_h[s];
-    nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, sn.ld, sn.row_off, sn.blk_off};
-    const int ntot = sn.ncol + sn.nrow;
-    if (sn.ncol == 0) continue;
-    if (is_node_task(sn)) {
-      fl[sn.level].push_back(Task{s, 0, 0, 1, nodes[s]});
-      bl[sn.level].push_back(Task{s, 0, 0, 1, nodes[s]});
-      continue;
-    }
-    // (smaller wide tasks on the narrow top levels were measured slower: the
-    // fixed cost of a task outweighs the shorter tail)
-    const int wf = kFwdCols, wb = kBwdRows;
-    for (int r0 = 0; r0 < ntot; r0 += kFwdRows)
-      for (int c0 = 0; c0 < sn.ncol; c0 += wf) {
-        const int rmax = std::min(r0 + kFwdRows, ntot) - 1;
-        if (rmax < c0) continue;  // entirely above the diagonal of inv(L_ss)
-        fl[sn.level].push_back(Task{s, r0, c0, wf, nodes[s]});
-      }
-    for (int c0 = 0; c0 < sn.ncol; c0 += kBwdCols)
-      for (int r0 = 0; r0 < ntot; r0 += wb) {
-        const int rmax = std::min(r0 + wb, ntot) - 1;
-        if (rmax < c0) continue;
-        bl[sn.level].push_back(Task{s, r0, c0, wb, nodes[s]});
-      }
-  }
-  std::vector<Task> fwd_all, bwd_all;
-  ctx->fwd_off.assign(1, 0);
-  ctx->bwd_off.assign(1, 0);
-  for (int l = 0; l < nl; ++l) {
-    fwd_all.insert(fwd_all.end(), fl[l].begin(), fl[l].end());
-    bwd_all.insert(bwd_all.end(), bl[l].begin(), bl[l].end());
-    ctx->fwd_off.push_back((int64_t)fwd_all.size());
-    ctx->bwd_off.push_back((int64_t)bwd_all.size());
-  }
+  ctx->fwd_off = sch.fwd_off;
+  ctx->bwd_off = sch.bwd_off;
   ffa_status st;
-  if ((st = upload(ctx, &ctx->fwd_t, fwd_all)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->bwd_t, bwd_all)) != FFA_OK) return st;
-
-  // dynamic schedule: per-node task ranges (a node's tasks are contiguous in
-  // both arrays) and dependencies through the nearest ancestor with tasks
-  auto ranges = [&](const std::vector<Task>& all, std::vector<int32_t>& t0, std::vector<int32_t>& cnt) {
-    t0.assign(nn, 0);
-    cnt.assign(nn, 0);
-    for (size_t i = 0; i < all.size(); ++i) {
-      const int s = all[i].node;
-      if (cnt[s]++ == 0) t0[s] = (int32_t)i;
-    }
-  };
-  std::vector<int32_t> t0f, ntf, t0b, ntb;
-  ranges(fwd_all, t0f, ntf);
-  ranges(bwd_all, t0b, ntb);
-  std::vector<int32_t> up(nn, -1);   // nearest ancestor with tasks
-  for (int s = 0; s < nn; ++s) {
-    int p = nd_h[s].parent;
-    while (p >= 0 && ntf[p] == 0) p = nd_h[p].parent;
-    up[s] = p;
-  }
-  // The dynamic launches cover the nodes on levels >= nb (closed under
-  // ancestors); the levels below run as one launch each, before the forward
-  // dynamic launch and after the backward one.
-  const int nb = std::min(ctx->bottom_levels, nl);
-  auto top = [&](int s) { return ntf[s] > 0 && nd_h[s].level >= nb; };
-  // forward: s waits on the tasks of the nodes whose nearest ancestor with tasks is s
-  std::vector<int4> push_f(nn, int4{-1, 0, 0, 0}), push_b((size_t)nn * (1 + kPushKids), int4{0, 0, 0, 0}),
-      kids_b, none;
-  std::vector<int32_t> pend_f(nn, 0), qf, qb;
-  for (int s = 0; s < nn; ++s)
-    if (top(s) && up[s] >= 0) {
-      const int p = up[s];
-      push_f[s] = int4{p, t0f[p], ntf[p], 0};
-      pend_f[p] += ntf[s];
-    }
-  for (int s = 0; s < nn; ++s)
-    if (top(s) && pend_f[s] == 0)
-      for (int i = 0; i < ntf[s]; ++i) qf.push_back(t0f[s] + i);
-  const int n_init_f = (int)qf.size();
-  const int n_top_f = (int)(fwd_all.size() - ctx->fwd_off[nb]);
-  qf.resize(n_top_f, -1);
-  // backward: s waits on its nearest ancestor with tasks alone
-  std::vector<std::vector<int32_t>> kids(nn);
-  for (int s = 0; s < nn; ++s)
-    if (top(s) && up[s] >= 0) kids[up[s]].push_back(s);
-  for (int s = 0; s < nn; ++s) {
-    const int k0 = (int)kids_b.size();
-    int total = 0;
-    for (int c : kids[s]) {
-      kids_b.push_back(int4{t0b[c], ntb[c], total, 0});
-      total += ntb[c];
-    }
-    push_b[(size_t)s * (1 + kPushKids)] = int4{k0, (int)kids_b.size(), total, ntb[s]};
-    for (int j = 0; j < kPushKids && k0 + j < push_b[(size_t)s * (1 + kPushKids)].y; ++j)
-      push_b[(size_t)s * (1 + kPushKids) + 1 + j] = kids_b[k0 + j];
-  }
-  for (int s = nn - 1; s >= 0; --s)
-    if (top(s) && up[s] < 0)
-      for (int i = 0; i < ntb[s]; ++i) qb.push_back(t0b[s] + i);
-  const int n_init_b = (int)qb.size();
-  const int n_top_b = (int)(bwd_all.size() - ctx->bwd_off[nb]);
-  qb.resize(n_top_b, -1);
-  if ((st = upload_dyn(ctx, ctx->fdyn, ctx->fwd_t, n_top_f, push_f, none, pend_f, qf, n_init_f, true)) != FFA_OK)
-    return st;
-  if ((st = upload_dyn(ctx, ctx->bdyn, ctx->bwd_t, n_top_b, push_b, kids_b, pend_f, qb, n_init_b, false)) != FFA_OK)
-    return st;
-  ctx->bottom_used = nb;
+  if ((st = upload(ctx, &ctx->fwd_t, sch.fwd_levels)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->bwd_t, sch.bwd_levels)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->fdyn_t, sch.fwd.tasks)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->bdyn_t, sch.bwd.tasks)) != FFA_OK) return st;
+  if ((st = upload(ctx, &ctx->sub_nodes, sch.sub_nodes)) != FFA_OK) return st;
+  if ((st = upload_dyn(ctx, ctx->fdyn, ctx->fdyn_t, sch.fwd, true)) != FFA_OK) return st;
+  if ((st = upload_dyn(ctx, ctx->bdyn, ctx->bdyn_t, sch.bwd, false)) != FFA_OK) return st;
+  ctx->bottom_used = sch.bottom_used;
   if (!ctx->err_flag) {
     if ((st = dalloc(ctx, &ctx->err_flag, 1)) != FFA_OK) return st;
     FFA_CUDA(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), ctx->stream));
   }
+  const int n_top_f = (int)sch.fwd.tasks.size(), n_top_b = (int)sch.bwd.tasks.size();
   ctx->grid_f = std::max(1, std::min(ctx->grid_f, n_top_f));
   ctx->grid_b = std::max(1, std::min(ctx->grid_b, n_top_b));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -791,6 +704,8 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   ctx->fp64 = ctx->prm.local_precision == FFA_LOCAL_FP64;
   ctx->rsz = ctx->fp64 ? 8 : 4;
   ctx->schedule = ctx->prm.solve_schedule;
+  if (ctx->prm.solve_subtree_height[0] >= 0) ctx->subtree_height_f = ctx->prm.solve_subtree_height[0];
+  if (ctx->prm.solve_subtree_height[1] >= 0) ctx->subtree_height_b = ctx->prm.solve_subtree_height[1];
   if (stream) {
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
   } else {
@@ -1234,6 +1149,8 @@ ffa_status tutte_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* bnd_in,
   ctx->fp64 = 1;
   ctx->rsz = 8;
   ctx->schedule = ctx->prm.solve_schedule;
+  if (ctx->prm.solve_subtree_height[0] >= 0) ctx->subtree_height_f = ctx->prm.solve_subtree_height[0];
+  if (ctx->prm.solve_subtree_height[1] >= 0) ctx->subtree_height_b = ctx->prm.solve_subtree_height[1];
   ctx->ell_width = OA.width;
   ctx->nodes_h = fac.nodes;
   ctx->n_levels = fac.n_levels;
@@ -1443,6 +1360,7 @@ ffa_status ffa_default_params(ffa_params* p) {
   p->penalty_schedule = 0;
   p->rescale_rho = 5.0;
   p->local_variant = 0;
+  p->solve_subtree_height[0] = p->solve_subtree_height[1] = -1;
   return FFA_OK;
 }
 
@@ -2006,6 +1924,52 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
       }
     }
     ctx->bottom_levels = best_bottom;
+    if ((st = build_tasks(ctx)) != FFA_OK) return st;
+  }
+  // 5) dynamic schedule without bottom launches: the height of the merged bottom
+  // subtrees, per pass (each pass timed on its own)
+  t.subtree_height[0] = ctx->subtree_height_f;
+  t.subtree_height[1] = ctx->subtree_height_b;
+  for (int c = 0; c < 4; ++c) t.ms_subtree[0][c] = t.ms_subtree[1][c] = 0.0;
+  if (ctx->schedule == 1 && ctx->bottom_levels == 0) {
+    for (auto& e : ctx->solve_ev) FFA_CUDA(cudaEventCreate(&e));
+    double best_f = 1e300, best_b = 1e300;
+    int hf = ctx->subtree_height_f, hb = ctx->subtree_height_b;
+    for (int c = 0; c < 4; ++c) {
+      ctx->subtree_height_f = ctx->subtree_height_b = c;
+      if ((st = build_tasks(ctx)) != FFA_OK) return st;
+      SolveData S = solve_data(ctx);
+      double af = 0.0, ab = 0.0;
+      for (int r = 0; r <= reps; ++r) {   // the first launch warms up
+        launch_supernodal_solve(S, s);
+        FFA_CUDA(cudaEventSynchronize(ctx->solve_ev[2]));
+        float tf, tb;
+        FFA_CUDA(cudaEventElapsedTime(&tf, ctx->solve_ev[0], ctx->solve_ev[1]));
+        FFA_CUDA(cudaEventElapsedTime(&tb, ctx->solve_ev[1], ctx->solve_ev[2]));
+        if (r > 0) {
+          af += tf;
+          ab += tb;
+        }
+      }
+      t.ms_subtree[0][c] = af / reps;
+      t.ms_subtree[1][c] = ab / reps;
+      if (t.ms_subtree[0][c] < best_f) {
+        best_f = t.ms_subtree[0][c];
+        hf = c;
+      }
+      if (t.ms_subtree[1][c] < best_b) {
+        best_b = t.ms_subtree[1][c];
+        hb = c;
+      }
+    }
+    for (auto& e : ctx->solve_ev) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+    ctx->subtree_height_f = hf;
+    ctx->subtree_height_b = hb;
+    t.subtree_height[0] = hf;
+    t.subtree_height[1] = hb;
     if ((st = build_tasks(ctx)) != FFA_OK) return st;
   }
   if ((st = device_wait_status(ctx, "tuning")) != FFA_OK) return st;

@@ -9,6 +9,7 @@
 
 #include "../../include/ffadmm.h"
 #include "ffa_factor.h"
+#include "ffa_schedule.h"
 
 namespace ffa {
 
@@ -20,44 +21,11 @@ enum { QV_GTL = 0, QV_NUM, QV_DEN, NQV };
 constexpr int kLocalBlock = 128;
 constexpr int kVertexBlock = 256;
 constexpr int kGatherLanes = 4;   // lanes sharing one row of the vertex gathers
-constexpr int kSolveThreads = 256;              // threads of a supernodal-solve block
-constexpr int kSolveMinBlocks = 4;              // resident solve blocks per SM the registers allow
-constexpr int kSolveWarps = kSolveThreads / 32;
-constexpr int kFwdRows = 128;                   // forward wide task rows (4 per lane)
-constexpr int kFwdCols = 32 * kSolveWarps;      // forward wide task: at most this many columns (W / warps per warp)
-constexpr int kFwdBatch = 8;                    // forward: columns per lane in flight
-constexpr int kBwdCols = 4 * kSolveWarps;       // backward wide task: output columns (4 per warp)
-constexpr int kBwdRows = 1024;                  // backward wide task: at most this many rows
-constexpr int kNarrowCols = 64;                 // node tasks: at most this many columns ...
-constexpr int kNodeMaxLd = 4 * kSolveThreads;   // ... and at most one 4-row group per thread
+// (the supernodal-solve task shapes, Task, NodeDev and the schedule records
+// are in ffa_schedule.h)
 
-struct NodeDev {
-  int32_t col0, ncol, nrow, ld;   // ld: leading dimension of B_s (multiple of 4)
-  int64_t row_off, blk_off;
-};
-
-// kind 1: the whole node on one block; kind > 1: a wide task of B_node from
-// (r0, c0) spanning kind columns (forward) or kind rows (backward).  The node's
-// descriptor travels with the task, so one 48-byte load brings both.
-struct __align__(16) Task {
-  int32_t node, r0, c0, kind;
-  NodeDev nd;
-};
-
-// One pass (forward or backward) of the dynamic schedule.  Tasks of a node are
-// contiguous in `tasks`.  push[s] says what a completed task of node s releases:
-//   forward:  {p, first task of p, tasks of p, 0}, p = the node waiting on s or
-//             -1; pending[p] counts the tasks of all nodes waiting on p, so the
-//             task that brings it to zero makes p ready;
-//   backward: {k0, k1, tasks of all nodes waiting on s, tasks of s} followed by
-//             kPushKids inline copies of kids[k0], kids[k0 + 1] (stride
-//             1 + kPushKids per node); the nodes waiting on s are kids[k0..k1) =
-//             {first task, tasks, offset of its tasks among all of them, 0};
-//             each waits on s alone, so the task that completes s (done[s]
-//             reaches the task count) releases them all.
-// q_init holds the tasks that wait on nothing (n_init of them) followed by -1.
-constexpr int kPushKids = 2;
-
+// A dynamic pass as the device sees it: the PassSchedule arrays of
+// ffa_schedule.h (push and kids as 16-byte vectors) plus its working state.
 struct DynPass {
   const Task* tasks = nullptr;
   int n_tasks = 0, n_init = 0;
@@ -155,6 +123,7 @@ struct SolveData {
   const float* blocks;
   const Task* fwd_tasks;
   const Task* bwd_tasks;
+  const NodeDev* sub_nodes;  // merged subtrees of the dynamic passes
   std::vector<int64_t> fwd_off, bwd_off;  // per level task ranges (host)
   int schedule = 0;          // 0: one launch per level, 1: one dynamic launch per pass
   DynPass fdyn, bdyn;            // dynamic passes over the levels >= bottom_levels

@@ -361,7 +361,7 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
 }
 
 // Node task of the forward pass: a whole small node (at most kNarrowCols columns,
-// ld <= kNodeMaxLd) on one block.  Thread (g, j) owns the 4-row group g of the
+// ld <= kNodeMaxLd, at most kNodeMaxBytes of B_s) on one block.  Thread (g, j) owns the 4-row group g of the
 // ld/4 groups and the column slice j (columns j, j + S, j + 2S, ...) with
 // S = floor(kSolveThreads / (ld/4)) slices, so a small node is streamed in one or two
 // rounds of loads; the S partial sums of each row meet in shared memory.  z_s
@@ -710,6 +710,7 @@ constexpr long long kSpinLimit = 1LL << 22;   // polls of ~100 ns (~0.4 s) befor
 
 struct DynView {
   DynPass P;
+  const NodeDev* sub;   // merged subtrees' nodes
   const int32_t* rows;
   const float* blocks;
   float* y;
@@ -744,6 +745,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
   __shared__ __align__(16) float smem[FWD ? SolveSmem<D>::kFwd : SolveSmem<D>::kBwd];
   __shared__ __align__(16) int4 rec_s[kRec];
   __shared__ __align__(16) Task task_s;   // the task to run next
+  __shared__ __align__(16) NodeDev sub_s[kSubtreeMaxNodes];   // a merged subtree's nodes
   __shared__ int item_s, slot_s, next_s, base_s;
   const DynPass& P = V.P;
   if (threadIdx.x == 0) {
@@ -780,9 +782,24 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
       for (int e = 0; e < kRec; ++e) cp_async16(&rec_s[e], P.push + (int64_t)t.node * kRec + e);
     }
     const NodeDev& nd = task_s.nd;
-    if constexpr (FWD) forward_task<D>(t, nd, V.rows, V.blocks, V.y, V.z, smem);
-    else backward_task<D>(t, nd, V.rows, V.blocks, V.z, V.x, smem);
-    __syncthreads();
+    if (t.kind == 0) {
+      // a merged bottom subtree: its nodes in order (forward children first,
+      // backward parents first), each on the whole block; a barrier makes one
+      // node's results visible to the next
+      const int n_sub = t.c0;
+      for (int i = threadIdx.x; i < n_sub * (int)(sizeof(NodeDev) / 4); i += kSolveThreads)
+        reinterpret_cast<int32_t*>(sub_s)[i] = reinterpret_cast<const int32_t*>(V.sub + t.r0)[i];
+      __syncthreads();
+      for (int q = 0; q < n_sub; ++q) {
+        if constexpr (FWD) forward_node<D>(sub_s[q], V.rows, V.blocks, V.y, V.z, smem);
+        else backward_node<D>(sub_s[n_sub - 1 - q], V.rows, V.blocks, V.z, V.x, smem);
+        __syncthreads();
+      }
+    } else {
+      if constexpr (FWD) forward_task<D>(t, nd, V.rows, V.blocks, V.y, V.z, smem);
+      else backward_task<D>(t, nd, V.rows, V.blocks, V.z, V.x, smem);
+      __syncthreads();
+    }
     // the next slot is claimed, and read once, while the completion below is
     // worked out
     if (threadIdx.x == 32) {
@@ -800,7 +817,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
       __threadfence();
       if constexpr (FWD) {
         if (r.x >= 0 && atomicSub(P.pending + r.x, 1) == 1) base = atomicAdd(P.ctr + 1, r.z);
-      } else if (r.z > 0 && (t.kind == 1 || atomicAdd(P.done + t.node, 1) == r.w - 1)) {
+      } else if (r.z > 0 && (t.kind <= 1 || atomicAdd(P.done + t.node, 1) == r.w - 1)) {
         base = atomicAdd(P.ctr + 1, r.z);
       }
       if (base >= 0) __threadfence();   // acquire the other tasks' releases
@@ -1011,8 +1028,8 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   if (S.ev[0]) cudaEventRecord(S.ev[0], s);
   const int L = (int)S.fwd_off.size() - 1;
   if (S.schedule == 1) {
-    const DynView vf{S.fdyn, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
-    const DynView vb{S.bdyn, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
+    const DynView vf{S.fdyn, S.sub_nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
+    const DynView vb{S.bdyn, S.sub_nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
     const int nb = std::min(S.bottom_levels, L);
     launch_levels(S, 0, nb, true, s);
     if (S.d == 2) k_solve_dynamic<2, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);

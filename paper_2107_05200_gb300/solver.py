@@ -49,7 +49,7 @@ class Solver:
                  precision: str = "fp32", refine_sweeps: int = 2, leaf_size: int = 64,
                  require_flip_free: bool = True, host_threads: int = 0, schedule: int = 1,
                  penalties: str = "fixed", rescale_rho: float = 5.0, local_variant: str = "paper",
-                 stream=None):
+                 subtree_height=None, stream=None):
         self._lib = N.load()
         self._ctx = None
         Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
@@ -80,6 +80,8 @@ class Solver:
         if local_variant not in ("paper", "joint"):
             raise ValueError("local_variant must be 'paper' or 'joint'")
         prm.local_variant = 1 if local_variant == "joint" else 0
+        if subtree_height is not None:   # (forward, backward) merged bottom subtree heights
+            prm.solve_subtree_height[0], prm.solve_subtree_height[1] = (int(h) for h in subtree_height)
         n_pin = 0 if pins is None else int(len(pins))
         self.n_pin = max(n_pin, 1)
         pP, self._pins = _ptr(pins, np.int32) if n_pin else (None, None)

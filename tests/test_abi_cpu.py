@@ -44,6 +44,7 @@ def test_default_params_and_struct_layout():
     assert p.energy == 0 and p.rho == 1.0 and p.eps_abs == 1e-6 and p.eps_rel == 1e-5
     assert p.check_every == 10 and p.require_flip_free == 1 and p.refine_sweeps == 2
     assert p.nd_leaf_size == 64
+    assert list(p.solve_subtree_height) == [-1, -1]
     assert lib.ffa_default_params(None) == 1
     assert isinstance(lib.ffa_last_error(None), bytes)
 
@@ -69,6 +70,10 @@ def test_bad_parameters_are_rejected_before_any_device_work():
     out = C.c_void_p()
     assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
     assert b"refine_sweeps" in lib.ffa_last_error(None)
+    lib.ffa_default_params(C.byref(p))
+    p.solve_subtree_height[1] = 9
+    assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
+    assert b"solve_subtree_height" in lib.ffa_last_error(None)
     lib.ffa_default_params(C.byref(p))
     mesh.d = 4
     assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
