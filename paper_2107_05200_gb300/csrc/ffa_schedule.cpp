@@ -15,7 +15,7 @@ namespace {
 std::vector<Task> dynamic_list(const std::vector<Supernode>& nd, const std::vector<NodeDev>& nodes,
                                const std::vector<char>& all_node_tasks, const std::vector<int32_t>& size,
                                const std::vector<Task>& all, const std::vector<int64_t>& off, int nb, int H,
-                               std::vector<NodeDev>& sub_nodes) {
+                               const std::vector<char>& keep, std::vector<NodeDev>& sub_nodes) {
   const int nn = (int)nd.size();
   if (nb > 0) H = 0;
   auto mergeable = [&](int s) {
@@ -38,7 +38,10 @@ std::vector<Task> dynamic_list(const std::vector<Supernode>& nd, const std::vect
     if (members[r].empty()) continue;
     first[r] = (int32_t)sub_nodes.size();
     count[r] = (int32_t)members[r].size();
-    for (int m : members[r]) sub_nodes.push_back(nodes[m]);
+    for (int m : members[r]) {
+      sub_nodes.push_back(nodes[m]);
+      sub_nodes.back().l2_keep = keep[m];
+    }
   }
   std::vector<Task> out;
   for (int64_t i = off[nb]; i < (int64_t)all.size(); ++i) {
@@ -46,6 +49,8 @@ std::vector<Task> dynamic_list(const std::vector<Supernode>& nd, const std::vect
     const int r = root[s];
     if (r < 0) out.push_back(all[i]);
     else if (r == s) out.push_back(Task{s, first[s], count[s], 0, nodes[s]});
+    else continue;
+    out.back().nd.l2_keep = keep[s];
   }
   return out;
 }
@@ -85,7 +90,7 @@ void build_schedule(const std::vector<Supernode>& nd, int n_levels, const Schedu
   std::vector<std::vector<Task>> fl(nl), bl(nl);
   for (int s = 0; s < nn; ++s) {
     const Supernode& sn = nd[s];
-    nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, sn.ld, sn.row_off, sn.blk_off};
+    nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, sn.ld, 0, 0, sn.row_off, sn.blk_off};
     const int ntot = sn.ncol + sn.nrow;
     if (sn.ncol == 0) continue;
     if (is_node_task(sn)) {
@@ -140,10 +145,15 @@ void build_schedule(const std::vector<Supernode>& nd, int n_levels, const Schedu
       size[sn.parent] += size[s];
     }
   }
+  std::vector<char> keep_f(nn, 0), keep_b(nn, 0);
+  for (int s = 0; s < nn; ++s) {
+    keep_f[s] = nd[s].level >= nl - opt.l2_keep_top;
+    keep_b[s] = nd[s].level < opt.l2_keep_bottom;
+  }
   out.fwd.tasks = dynamic_list(nd, nodes, all_node_tasks, size, out.fwd_levels, out.fwd_off, nb, opt.subtree_height_f,
-                               out.sub_nodes);
+                               keep_f, out.sub_nodes);
   out.bwd.tasks = dynamic_list(nd, nodes, all_node_tasks, size, out.bwd_levels, out.bwd_off, nb, opt.subtree_height_b,
-                               out.sub_nodes);
+                               keep_b, out.sub_nodes);
   // the two lists merge different subtrees, so a node can have tasks in one
   // pass only: each pass has its own dependencies
   std::vector<int32_t> t0f, ntf, t0b, ntb;

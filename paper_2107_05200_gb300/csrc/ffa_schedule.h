@@ -29,6 +29,7 @@ constexpr int kPushKids = 2;                    // backward push records: releas
 
 struct NodeDev {
   int32_t col0, ncol, nrow, ld;   // ld: leading dimension of B_s (multiple of 4)
+  int32_t l2_keep, pad;           // 1: stream B_s with the L2 keep-resident hint (the next pass reads it first)
   int64_t row_off, blk_off;
 };
 
@@ -37,7 +38,7 @@ struct NodeDev {
 // dynamic passes only): a merged bottom subtree rooted at node, whose c0 nodes
 // (node tasks, children before parents) start at entry r0 of the subtree node
 // list and run in order on one block.  The node's descriptor travels with the
-// task, so one 48-byte load brings both.
+// task, so one 64-byte load brings both.
 struct alignas(16) Task {
   int32_t node, r0, c0, kind;
   NodeDev nd;
@@ -73,6 +74,12 @@ struct ScheduleOptions {
   int bottom_levels = 0;           // lowest levels run as one launch per level, outside the dynamic passes
   int subtree_height_f = 2;        // nb = 0: merged bottom subtrees of at most this height, forward pass
   int subtree_height_b = 1;        // ... backward pass (0: none)
+  // L2 residency between passes: the forward pass reads the top levels last and
+  // the backward pass reads them first (and the other way round for the bottom
+  // levels and the next sweep's forward pass), so those blocks are streamed with
+  // a keep-resident hint and all others with an evict-first hint
+  int l2_keep_top = 2;             // forward: the top this-many levels (0: none)
+  int l2_keep_bottom = 2;          // backward: levels below this one (0: none)
 };
 
 struct Schedule {

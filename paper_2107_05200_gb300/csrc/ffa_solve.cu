@@ -276,14 +276,28 @@ __global__ void k_axpy(int n, double* __restrict__ X, const float* __restrict__ 
 // results go out as one set of atomics: rows < n_s into z, rows >= n_s
 // subtracted from y at the structure rows.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float4 ldg_stream(const float* p) {
-  return __ldg(reinterpret_cast<const float4*>(p));
+// Factor data is read once per pass: no L1 allocation, and in L2 either
+// evict-first or, for the blocks the next pass reads first, evict-last.
+__device__ __forceinline__ uint64_t l2_policy(int keep) {
+  uint64_t pol;
+  if (keep) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  else asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ float4 ldg_stream(const float* p, uint64_t pol) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
 }
 
 template <int D>
 __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
                                              const float* __restrict__ blocks, float* __restrict__ y,
                                              float* __restrict__ z, float* smem) {
+  const uint64_t pol = l2_policy(nd.l2_keep);
   const int W = t.kind;      // columns of this task: a multiple of 8, at most kFwdCols
   const int cpw = W / kSolveWarps;    // columns per warp
   float (*fs)[D] = reinterpret_cast<float (*)[D]>(smem);                       // [W][D]
@@ -300,7 +314,7 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
   float4 b[kFwdBatch];
 #pragma unroll
   for (int u = 0; u < kFwdBatch; ++u)
-    b[u] = (u < n0) ? ldg_stream(B + (int64_t)u * nd.ld) : make_float4(0.f, 0.f, 0.f, 0.f);
+    b[u] = (u < n0) ? ldg_stream(B + (int64_t)u * nd.ld, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int q = threadIdx.x; q < nc * D; q += kSolveThreads) {
     const int c = q / D, k = q - c * D;
     fs[c][k] = __ldcg(y + (int64_t)(nd.col0 + t.c0 + c) * D + k);
@@ -327,11 +341,11 @@ __device__ __forceinline__ void forward_wide(const Task& t, const NodeDev& nd, c
   int c = n0;
   for (; c + kFwdBatch <= ncw; c += kFwdBatch) {
 #pragma unroll
-    for (int u = 0; u < kFwdBatch; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld);
+    for (int u = 0; u < kFwdBatch; ++u) b[u] = ldg_stream(B + (int64_t)(c + u) * nd.ld, pol);
 #pragma unroll
     for (int u = 0; u < kFwdBatch; ++u) fma_col(b[u], c + u);
   }
-  for (; c < ncw; ++c) fma_col(ldg_stream(B + (int64_t)c * nd.ld), c);
+  for (; c < ncw; ++c) fma_col(ldg_stream(B + (int64_t)c * nd.ld, pol), c);
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -370,6 +384,7 @@ template <int D>
 __device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* __restrict__ rows,
                                              const float* __restrict__ blocks, float* __restrict__ y,
                                              float* __restrict__ z, float* smem) {
+  const uint64_t pol = l2_policy(nd.l2_keep);
   float (*f)[D] = reinterpret_cast<float (*)[D]>(smem);    // [kNarrowCols][D]
   float* red = smem + kNarrowCols * D;                     // [D][S][ld]
   const int ntot = nd.ncol + nd.nrow;
@@ -382,7 +397,7 @@ __device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* _
   float4 b[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u)
-    b[u] = (active && j + u * S < nd.ncol) ? ldg_stream(B + (int64_t)(j + u * S) * nd.ld) : make_float4(0.f, 0.f, 0.f, 0.f);
+    b[u] = (active && j + u * S < nd.ncol) ? ldg_stream(B + (int64_t)(j + u * S) * nd.ld, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int q = threadIdx.x; q < nd.ncol * D; q += kSolveThreads) {
     const int c = q / D, k = q - c * D;
     f[c][k] = __ldcg(y + (int64_t)(nd.col0 + c) * D + k);
@@ -409,7 +424,7 @@ __device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* _
     int c = j + 8 * S;
     for (; c + 7 * S < nd.ncol; c += 8 * S) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) b[u] = ldg_stream(B + (int64_t)(c + u * S) * nd.ld);
+      for (int u = 0; u < 8; ++u) b[u] = ldg_stream(B + (int64_t)(c + u * S) * nd.ld, pol);
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -422,7 +437,7 @@ __device__ __forceinline__ void forward_node(const NodeDev& nd, const int32_t* _
         }
     }
     for (; c < nd.ncol; c += S) {
-      const float4 bv = ldg_stream(B + (int64_t)c * nd.ld);
+      const float4 bv = ldg_stream(B + (int64_t)c * nd.ld, pol);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const float fv = f[c][k];
@@ -508,6 +523,7 @@ template <int D>
 __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, const int32_t* __restrict__ rows,
                                               const float* __restrict__ blocks, const float* __restrict__ z,
                                               float* __restrict__ x, float* smem) {
+  const uint64_t pol = l2_policy(nd.l2_keep);
   float (*vs)[kBwdRows] = reinterpret_cast<float (*)[kBwdRows]>(smem);   // [D][1024]
   const int nr = min(t.kind, nd.ld - t.r0);     // rows of this task: a multiple of 4
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -522,7 +538,7 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
   float4 pa[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    pa[q] = (q < ncw && ra < nr) ? ldg_stream(B + (int64_t)q * nd.ld + ra) : make_float4(0.f, 0.f, 0.f, 0.f);
+    pa[q] = (q < ncw && ra < nr) ? ldg_stream(B + (int64_t)q * nd.ld + ra, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
   stage_v<D>(nd, t.r0, nr, rows, z, x, &vs[0][0], kBwdRows);
   __syncthreads();
   if (ncw == 0) return;
@@ -549,7 +565,7 @@ __device__ __forceinline__ void backward_wide(const Task& t, const NodeDev& nd, 
   for (int r = ra + 128; r < nr; r += 128) {
     float4 bq[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) bq[q] = (q < ncw) ? ldg_stream(B + (int64_t)q * nd.ld + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < 4; ++q) bq[q] = (q < ncw) ? ldg_stream(B + (int64_t)q * nd.ld + r, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
     step(bq, r);
   }
 #pragma unroll
@@ -577,6 +593,7 @@ template <int D>
 __device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* __restrict__ rows,
                                               const float* __restrict__ blocks, const float* __restrict__ z,
                                               float* __restrict__ x, float* smem) {
+  const uint64_t pol = l2_policy(nd.l2_keep);
   const int ld = nd.ld;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cg = lane >> 3, rl = lane & 7;
@@ -588,7 +605,7 @@ __device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int r = 4 * rl + 32 * u;
-      pre[u] = (j < nd.ncol && r < ld) ? ldg_stream(B + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+      pre[u] = (j < nd.ncol && r < ld) ? ldg_stream(B + r, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   stage_v<D>(nd, 0, ld, rows, z, x, smem, ld);
@@ -620,7 +637,7 @@ __device__ __forceinline__ void backward_node(const NodeDev& nd, const int32_t* 
       }
 #pragma unroll 4
       for (; r < ld; r += 32) {
-        const float4 b = ldg_stream(B + r);
+        const float4 b = ldg_stream(B + r, pol);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           const float4 v = *reinterpret_cast<const float4*>(smem + k * ld + r);
@@ -840,7 +857,8 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
     }
     // the next task, when its slot was already filled, is fetched before the
     // block goes round
-    if (threadIdx.x >= 32 && threadIdx.x < 35) {
+    constexpr int kTaskVecs = (int)(sizeof(Task) / sizeof(int4));
+    if (threadIdx.x >= 32 && threadIdx.x < 32 + kTaskVecs) {
       const int nt = next_s;
       if (nt >= 0) reinterpret_cast<int4*>(&task_s)[threadIdx.x - 32] = reinterpret_cast<const int4*>(P.tasks + nt)[threadIdx.x - 32];
     }
