@@ -108,10 +108,23 @@ __device__ __forceinline__ void store_terms(void* dst, int i, const R g[D][D], c
       c[0][k] -= s;
     }
   R* out = reinterpret_cast<R*>(dst) + (int64_t)i * (D + 1) * D;
+  constexpr int kBytes = (D + 1) * D * (int)sizeof(R);
+  if constexpr (kBytes % 16 == 0) {
+    // 16-byte stores: the element's terms start on a 16-byte boundary
+    const R* f = &c[0][0];
 #pragma unroll
-  for (int j = 0; j <= D; ++j)
+    for (int q = 0; q < kBytes / 16; ++q) {
+      if constexpr (sizeof(R) == 4)
+        reinterpret_cast<float4*>(out)[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+      else
+        reinterpret_cast<double2*>(out)[q] = make_double2(f[2 * q], f[2 * q + 1]);
+    }
+  } else {
 #pragma unroll
-    for (int k = 0; k < D; ++k) out[j * D + k] = c[j][k];
+    for (int j = 0; j <= D; ++j)
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[j * D + k] = c[j][k];
+  }
 }
 
 // ---------------------------------------------------------------------------
