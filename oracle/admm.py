@@ -111,17 +111,37 @@ def assemble_L(g: np.ndarray, T: np.ndarray, mu: np.ndarray, n: int) -> sp.csr_m
 # defining functions and gradients (eqs. symmetricgradientdefiningfunction/symmetricgradientdefininggrad, eqs. symmetricdirichletdefiningfunction/symmetricdirichletdefininggrad)
 # ----------------------------------------------------------------------------
 
+def rotation_part(X: np.ndarray) -> np.ndarray:
+    """R(X): the rotation of the polar decomposition X = R S (det X > 0), U V^T of the SVD."""
+    U, _, Vt = np.linalg.svd(X)
+    return U @ Vt
+
+
 def f_energy(X: np.ndarray, energy: str) -> np.ndarray:
-    """f_SD(X) = (|X|^2 + |X^-1|^2)/2 ;  f_SG(X) = |X|^2/2 - log det X."""
+    """f_SD(X) = (|X|^2 + |X^-1|^2)/2 ;  f_SG(X) = |X|^2/2 - log det X ;
+    f_SA(X) = (|X - R|^2 + |X^-1 - R^-1|^2)/2 with R the rotation of X (the
+    symmetric ARAP energy, one more rotation-invariant choice of the defining
+    function, Sec. 3: other energies plug into the same scheme)."""
     fro2 = np.einsum("mij,mij->m", X, X)
     if energy == "sd":
         Xi = np.linalg.inv(X)
         return 0.5 * (fro2 + np.einsum("mij,mij->m", Xi, Xi))
+    if energy == "sa":
+        R = rotation_part(X)
+        D1 = X - R
+        D2 = np.linalg.inv(X) - np.transpose(R, (0, 2, 1))
+        return 0.5 * (np.einsum("mij,mij->m", D1, D1) + np.einsum("mij,mij->m", D2, D2))
     return 0.5 * fro2 - np.log(np.linalg.det(X))
 
 
 def grad_f(X: np.ndarray, energy: str) -> np.ndarray:
-    """grad f_SD = X - X^-T X^-1 X^-T ;  grad f_SG = X - X^-T."""
+    """grad f_SD = X - X^-T X^-1 X^-T ;  grad f_SG = X - X^-T ;
+    grad f_SA = U diag(phi'(s)) V^T for X = U diag(s) V^T, phi'(s) = s - 1 - s^-3 + s^-2
+    (f_SA = sum phi(s_k), phi(s) = ((s - 1)^2 + (1/s - 1)^2)/2)."""
+    if energy == "sa":
+        U, sv, Vt = np.linalg.svd(X)
+        dphi = sv - 1.0 - sv ** -3 + sv ** -2
+        return np.einsum("mij,mj,mjk->mik", U, dphi, Vt)
     XiT = np.transpose(np.linalg.inv(X), (0, 2, 1))
     if energy == "sd":
         Xi = np.linalg.inv(X)
@@ -222,6 +242,38 @@ def root_sd(q: np.ndarray, w: np.ndarray, mu: np.ndarray) -> np.ndarray:
     return np.where((pn >= lo) & (pn <= hi), pn, p)
 
 
+def root_sa(q: np.ndarray, w: np.ndarray, mu: np.ndarray) -> np.ndarray:
+    """Unique positive root of (w+mu) p^4 - (w + mu q) p^3 + w p - w = 0: the
+    stationarity condition w phi'(p) + mu (p - q) = 0 of the symmetric ARAP
+    scalar prox, multiplied by p^3.
+
+    With a = (w + mu q)/(w+mu) and c = w/(w+mu) it reads g(p) = p^3 (p - a) +
+    c (p - 1) = 0; g(0) = -c < 0 and g(max(1, a)) >= 0, so the root lies in
+    (0, max(1, a)] (the objective w phi(p) + mu/2 (p - q)^2 is strictly convex on
+    p > 0, so there is one).  Bisection to adjacent doubles, then one Newton step.
+    """
+    a = (w + mu * q) / (w + mu)
+    c = w / (w + mu)
+    lo = np.zeros_like(q)
+    hi = np.maximum(a, 1.0)
+
+    def g(p):
+        return p ** 3 * (p - a) + c * (p - 1.0)
+
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        neg = g(mid) < 0.0
+        lo = np.where(neg, mid, lo)
+        hi = np.where(neg, hi, mid)
+        if np.all(np.nextafter(lo, np.inf) >= hi):
+            break
+    p = 0.5 * (lo + hi)
+    dg = p * p * (4.0 * p - 3.0 * a) + c
+    step = np.where(dg > 0, g(p) / np.where(dg > 0, dg, 1.0), 0.0)
+    pn = p - step
+    return np.where((pn >= lo) & (pn <= hi), pn, p)
+
+
 def p_step(S: np.ndarray, w: np.ndarray, mu: np.ndarray, energy_name: str) -> np.ndarray:
     """argmin_{P SPD} w f(P) + mu/2 |P - S|^2 for symmetric S (eqs. optimizinginp/rootfindinginp, Supplemental).
 
@@ -232,7 +284,8 @@ def p_step(S: np.ndarray, w: np.ndarray, mu: np.ndarray, energy_name: str) -> np
     q, E = np.linalg.eigh(S)
     ww = w[:, None] * np.ones_like(q)
     mm = mu[:, None] * np.ones_like(q)
-    p = root_sg(q, ww, mm) if energy_name == "sg" else root_sd(q, ww, mm)
+    roots = {"sg": root_sg, "sd": root_sd, "sa": root_sa}
+    p = roots[energy_name](q, ww, mm)
     small = (np.prod(p, axis=1) < SQRT_EPS_M) | (np.sum(p, axis=1) < SQRT_EPS_M)
     p[small] = np.maximum(p[small], SQRT_EPS_M)
     return np.einsum("mij,mj,mkj->mik", E, p, E)
@@ -246,7 +299,8 @@ def polar_init(J0: np.ndarray, energy_name: str) -> tuple[np.ndarray, np.ndarray
     """U0, P0 from the polar decomposition of GW0 (eqs. initialpolardecomposition/polardecompositionapplied.
 
     J0 = R1 S R2^T, U0 = R1 R2^T, P0 = R2 S R2^T; singular values below eps are
-    raised to eps, eps = eps_m^{1/4} (SG) or eps_m^{1/8} (SD).  A flipped J0
+    raised to eps, eps = eps_m^{1/4} (SG) or eps_m^{1/8} (SD, and SA, which grows
+    like SD as a singular value goes to 0).  A flipped J0
     (det <= 0) gets S = eps I and, when R1 R2^T is a reflection, its last column
     negated.
     """

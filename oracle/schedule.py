@@ -52,6 +52,8 @@ def grad_f_norm(P: np.ndarray, energy_name: str) -> np.ndarray:
 
 def c_lipschitz(B: np.ndarray, energy_name: str) -> np.ndarray:
     """C^L (SG, closed form) or C^LG (SD, bisection to adjacent doubles) of Lemma 1."""
+    if energy_name not in ("sd", "sg"):
+        raise ValueError("Lemma 1 bounds the Lipschitz constant for the SD and SG energies only")
     if energy_name == "sg":
         # (-B + sqrt(4 + B^2)) / 2, written without the cancellation for large B
         return 2.0 / (B + np.sqrt(4.0 + B * B))

@@ -118,7 +118,7 @@ def test_energy_closed_forms_and_rotation_invariance(d):
         np.testing.assert_allclose(admm.f_energy(Rm @ A, e), admm.f_energy(A, e), rtol=1e-12)
 
 
-@pytest.mark.parametrize("energy", ["sd", "sg"])
+@pytest.mark.parametrize("energy", ["sd", "sg", "sa"])
 def test_grad_f_matches_finite_differences(energy):
     """eq. symmetricgradientdefininggrad / eq. symmetricdirichletdefininggrad against central differences of f."""
     rng = np.random.default_rng(5)
@@ -142,13 +142,15 @@ WM = [(1.0, 1.0), (1e-4, 1e-4), (1e-4, 3e-4), (2.0, 0.1), (0.1, 20.0)]
 
 
 def _scalar_f(p, energy):
+    if energy == "sa":
+        return 0.5 * ((p - 1) ** 2 + (1 / p - 1) ** 2)
     return 0.5 * (p * p + 1 / (p * p)) if energy == "sd" else 0.5 * p * p - math.log(p)
 
 
-@pytest.mark.parametrize("energy", ["sd", "sg"])
+@pytest.mark.parametrize("energy", ["sd", "sg", "sa"])
 def test_scalar_prox_is_the_1d_minimizer(energy):
     """Each eigenvalue solves min_p w f(p) + mu/2 (p - q)^2 over p > 0 (brute force)."""
-    root = admm.root_sd if energy == "sd" else admm.root_sg
+    root = {"sd": admm.root_sd, "sg": admm.root_sg, "sa": admm.root_sa}[energy]
     for (w, mu) in WM:
         q = np.array(QS)
         p = root(q, np.full_like(q, w), np.full_like(q, mu))
@@ -164,9 +166,10 @@ def test_scalar_prox_is_the_1d_minimizer(energy):
             assert obj(pi) <= obj(res.x) + 1e-12 * max(1.0, abs(obj(pi)))
 
 
-@pytest.mark.parametrize("energy", ["sd", "sg"])
+@pytest.mark.parametrize("energy", ["sd", "sg", "sa"])
 def test_scalar_prox_polynomial_residual(energy):
-    """The root satisfies (w+mu)p^2 - mu q p - w = 0 (SG) or (w+mu)p^4 - mu q p^3 - w = 0 (SD)."""
+    """The root satisfies (w+mu)p^2 - mu q p - w = 0 (SG), (w+mu)p^4 - mu q p^3 - w = 0 (SD) or
+    (w+mu)p^4 - (w + mu q)p^3 + w p - w = 0 (SA)."""
     rng = np.random.default_rng(6)
     q = rng.normal(scale=5, size=2000)
     w = rng.uniform(1e-5, 1.0, size=2000)
@@ -175,6 +178,11 @@ def test_scalar_prox_polynomial_residual(energy):
         p = admm.root_sd(q, w, mu)
         res = (w + mu) * p ** 4 - mu * q * p ** 3 - w
         scale = (w + mu) * p ** 4 + np.abs(mu * q * p ** 3) + w
+    elif energy == "sa":
+        # w phi'(p) + mu (p - q) = 0 with phi'(p) = p - 1 - p^-3 + p^-2, times p^3
+        p = admm.root_sa(q, w, mu)
+        res = (w + mu) * p ** 4 - (w + mu * q) * p ** 3 + w * p - w
+        scale = (w + mu) * p ** 4 + np.abs((w + mu * q) * p ** 3) + w * p + w
     else:
         p = admm.root_sg(q, w, mu)
         res = (w + mu) * p ** 2 - mu * q * p - w
@@ -190,7 +198,7 @@ def _spd_from_params(x, d):
     return Lc @ Lc.T
 
 
-@pytest.mark.parametrize("energy", ["sd", "sg"])
+@pytest.mark.parametrize("energy", ["sd", "sg", "sa"])
 @pytest.mark.parametrize("d", [2, 3])
 def test_matrix_prox_brute_force(energy, d):
     """P = argmin_{SPD} w f(P) + mu/2 |P - S|^2, found independently by BFGS over SPD matrices."""
@@ -345,7 +353,7 @@ def test_w_step_without_pins_fixes_vertex_zero():
 # whole iterations
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("energy", ["sd", "sg"])
+@pytest.mark.parametrize("energy", ["sd", "sg", "sa"])
 @pytest.mark.parametrize("k", [0, 1])
 def test_rigid_motion_is_a_fixed_point(energy, k):
     """J in SO(d) gives q = 1 -> p = 1 for both energies: one iteration changes nothing,
@@ -361,8 +369,8 @@ def test_rigid_motion_is_a_fixed_point(energy, k):
     np.testing.assert_allclose(s1.W, W0, atol=1e-12)
     np.testing.assert_allclose(s1.P, np.broadcast_to(np.eye(d), s1.P.shape), atol=1e-12)
     assert st.e_prim < 1e-11 and st.e_dual < 1e-11 and st.n_flipped == 0
-    fI = d if energy == "sd" else d / 2
-    assert math.isclose(o.energy(s1.W), fI * o.w.sum(), rel_tol=1e-12)
+    fI = {"sd": d, "sg": d / 2, "sa": 0.0}[energy]
+    assert math.isclose(o.energy(s1.W), fI * o.w.sum(), rel_tol=1e-12, abs_tol=1e-20)
 
 
 def _c1_small(rho=1.0):
