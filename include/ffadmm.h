@@ -57,7 +57,13 @@ typedef enum {
 
 typedef enum {
   FFA_SYM_DIRICHLET = 0, /* f(X) = (|X|^2 + |X^-1|^2) / 2          (eq. symmetricdirichletdefiningfunction) */
-  FFA_SYM_GRADIENT = 1   /* f(X) = |X|^2 / 2 - log det X            (eq. symmetricgradientdefiningfunction) */
+  FFA_SYM_GRADIENT = 1,  /* f(X) = |X|^2 / 2 - log det X            (eq. symmetricgradientdefiningfunction) */
+  FFA_SYM_ARAP = 2       /* f(X) = (|X - R|^2 + |X^-1 - R^-1|^2) / 2, R the rotation of X: the
+                            symmetric ARAP energy, one more rotation-invariant defining function
+                            plugged into the same scheme (Sec. 3 leaves the choice of f open);
+                            its P step solves (w+mu) p^4 - (w + mu q) p^3 + w p - w = 0 per
+                            eigenvalue.  Not with penalty_schedule 1 (Lemma 1 bounds SD and SG
+                            only) nor with ffa_energy_noalloc. */
 } ffa_energy_kind;
 
 typedef enum {
@@ -97,7 +103,7 @@ typedef struct {
                               when e_prim_i > rescale_rho e_dual_i (e_dual_i > rescale_rho
                               e_prim_i), never below mu_min,i/2, Lambda_i keeps mu_i Lambda_i, and L
                               is decomposed again on the host.  rho is ignored.  Single meshes of
-                              one energy only; not with ffa_forward_unrolled. */
+                              one energy, SD or SG, only; not with ffa_forward_unrolled. */
   double rescale_rho;      /* the paper's rho of the rescaling rule (default 5) */
   int32_t local_variant;   /* 0: the paper's local step (Algorithm 1: U from (J + Lambda) P^{k-1}, then P;
                               default).  1: a joint (U, P) prox (not the paper's scheme): U is the
@@ -341,7 +347,7 @@ ffa_status ffa_batch_get_W(ffa_batch* b, int32_t mesh, double* W_out);
  *                   (larger m is rejected with FFA_ERR_INVALID_ARG).
  *   V, T, W       : device pointers (n x d_in doubles, m x (d+1) int32,
  *                   n x d doubles), read only.
- *   energy        : which defining function f.
+ *   energy        : which defining function f (FFA_SYM_DIRICHLET or FFA_SYM_GRADIENT).
  *   E             : device pointer to one double, written by the call.
  *   stream        : cudaStream_t to run on (NULL = the legacy default stream).
  * The call only enqueues two kernels on the stream and returns; E is valid once

@@ -47,11 +47,13 @@ __device__ __forceinline__ void load_vertex_a(const void* rec, int v, R hi[D], R
 }
 
 // derivative of the scalar prox root p(q): implicit differentiation of
-// (w+mu) p^2 - mu q p - w = 0 (SG) or (w+mu) p^4 - mu q p^3 - w = 0 (SD)
+// (w+mu) p^2 - mu q p - w = 0 (SG), (w+mu) p^4 - mu q p^3 - w = 0 (SD) or
+// (w+mu) p^4 - (w + mu q) p^3 + w p - w = 0 (SA)
 template <typename R, int EN>
 __device__ __forceinline__ R prox_root_deriv(R p, R q, R w, R mu) {
-  if (EN == 0) return mu * p / (R(4) * (w + mu) * p - R(3) * mu * q);
-  return mu * p / (R(2) * (w + mu) * p - mu * q);
+  if constexpr (EN == kEnSD) return mu * p / (R(4) * (w + mu) * p - R(3) * mu * q);
+  else if constexpr (EN == kEnSG) return mu * p / (R(2) * (w + mu) * p - mu * q);
+  else return mu * p * p * p / ((R(4) * (w + mu) * p - R(3) * (w + mu * q)) * p * p + w);
 }
 
 template <int D, typename R, int EN>
@@ -491,15 +493,25 @@ __global__ void k_adj_pins(int n_pin, int d, const int64_t* __restrict__ ptr, co
 }  // namespace
 
 void launch_adjoint_local(const AdjointLaunch& a, cudaStream_t s) {
-  if (a.energy != 0 && a.energy != 1) return;  // mixed-energy (batched) contexts have no adjoint
+  if (a.energy == kEnMixed) return;  // mixed-energy (batched) contexts have no adjoint
   const int grid = (a.m + 127) / 128;
 #define FFA_ADJ(D, R, EN) k_adjoint_local<D, R, EN><<<grid, 128, 0, s>>>(a)
   if (a.d == 2) {
-    if (a.fp64) { if (a.energy == 0) FFA_ADJ(2, double, 0); else FFA_ADJ(2, double, 1); }
-    else { if (a.energy == 0) FFA_ADJ(2, float, 0); else FFA_ADJ(2, float, 1); }
+    if (a.fp64) {
+      if (a.energy == kEnSD) FFA_ADJ(2, double, kEnSD); else if (a.energy == kEnSG) FFA_ADJ(2, double, kEnSG);
+      else FFA_ADJ(2, double, kEnSA);
+    } else {
+      if (a.energy == kEnSD) FFA_ADJ(2, float, kEnSD); else if (a.energy == kEnSG) FFA_ADJ(2, float, kEnSG);
+      else FFA_ADJ(2, float, kEnSA);
+    }
   } else {
-    if (a.fp64) { if (a.energy == 0) FFA_ADJ(3, double, 0); else FFA_ADJ(3, double, 1); }
-    else { if (a.energy == 0) FFA_ADJ(3, float, 0); else FFA_ADJ(3, float, 1); }
+    if (a.fp64) {
+      if (a.energy == kEnSD) FFA_ADJ(3, double, kEnSD); else if (a.energy == kEnSG) FFA_ADJ(3, double, kEnSG);
+      else FFA_ADJ(3, double, kEnSA);
+    } else {
+      if (a.energy == kEnSD) FFA_ADJ(3, float, kEnSD); else if (a.energy == kEnSG) FFA_ADJ(3, float, kEnSG);
+      else FFA_ADJ(3, float, kEnSA);
+    }
   }
 #undef FFA_ADJ
 }

@@ -19,7 +19,7 @@ using namespace ffa;
 // Per-element and per-mesh data of a group of batched meshes concatenated into
 // one context (disjoint vertex sets, so L_FF is block diagonal).
 struct BatchSpec {
-  std::vector<int8_t> energy_of;       // per element: 0 SD, 1 SG
+  std::vector<int8_t> energy_of;       // per element: 0 SD, 1 SG, 2 SA
   std::vector<double> rho_of;          // per element penalty scale
   std::vector<int32_t> mesh_of_elem;   // per element
   std::vector<int32_t> mesh_of_vertex; // per vertex
@@ -457,7 +457,7 @@ ffa_status ensure_graphs(ffa_ctx* ctx) {
 }
 
 ffa_status validate_params(const ffa_params& p, std::string& msg) {
-  if (p.energy != FFA_SYM_DIRICHLET && p.energy != FFA_SYM_GRADIENT) msg = "unknown energy";
+  if (p.energy != FFA_SYM_DIRICHLET && p.energy != FFA_SYM_GRADIENT && p.energy != FFA_SYM_ARAP) msg = "unknown energy";
   else if (!(p.rho > 0) || !std::isfinite(p.rho)) msg = "rho must be positive";
   else if (!(p.eps_abs >= 0) || !(p.eps_rel >= 0)) msg = "eps_abs/eps_rel must be >= 0";
   else if (p.check_every < 1 || p.check_every > 100000) msg = "check_every must be in [1, 100000]";
@@ -470,6 +470,8 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   else if (p.local_variant != 0 && p.local_variant != 1) msg = "local_variant must be 0 or 1";
   else if (p.penalty_schedule == 1 && !(p.rescale_rho > 2.0 && std::isfinite(p.rescale_rho)))
     msg = "rescale_rho must be finite and > 2";
+  else if (p.penalty_schedule == 1 && p.energy == FFA_SYM_ARAP)
+    msg = "penalty_schedule 1 needs the penalty bound of Lemma 1, derived for SD and SG only";
   else if (p.solve_subtree_height[0] < -1 || p.solve_subtree_height[0] > 8 || p.solve_subtree_height[1] < -1 ||
            p.solve_subtree_height[1] > 8)
     msg = "solve_subtree_height must be in [-1, 8]";
@@ -876,7 +878,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     ctx->n_mesh = (int)batch->mesh_m.size();
     bool mixed = false;
     for (int8_t en : batch->energy_of) mixed |= (en != batch->energy_of[0]);
-    ctx->prm.energy = mixed ? (ffa_energy_kind)2 : (ffa_energy_kind)batch->energy_of[0];
+    ctx->prm.energy = mixed ? (ffa_energy_kind)kEnMixed : (ffa_energy_kind)batch->energy_of[0];
     if ((st = upload(ctx, &ctx->energy_of, batch->energy_of)) != FFA_OK) return st;
     if ((st = upload(ctx, &ctx->mesh_of_elem, batch->mesh_of_elem)) != FFA_OK) return st;
     if ((st = upload(ctx, &ctx->mesh_of_vertex, batch->mesh_of_vertex)) != FFA_OK) return st;
@@ -2142,7 +2144,12 @@ ffa_status batch_create_impl(ffa_batch* b, int32_t n_meshes, const ffa_mesh* mes
         pins.push_back((int32_t)n_tot);       // vertex 0 of this mesh at the origin
         for (int c = 0; c < d; ++c) pos.push_back(0.0);
       }
-      const int8_t en = energies ? (int8_t)energies[k] : (int8_t)prm.energy;
+      const int en_k = energies ? (int)energies[k] : (int)prm.energy;
+      if (en_k != FFA_SYM_DIRICHLET && en_k != FFA_SYM_GRADIENT && en_k != FFA_SYM_ARAP) {
+        b->err = "mesh " + std::to_string(k) + ": unknown energy";
+        return FFA_ERR_INVALID_ARG;
+      }
+      const int8_t en = (int8_t)en_k;
       const double rk = rho ? rho[k] : prm.rho;
       for (int i = 0; i < mk.m; ++i) {
         spec.energy_of.push_back(en);

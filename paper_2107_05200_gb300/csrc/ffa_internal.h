@@ -18,6 +18,13 @@ enum { Q_EPRIM = 0, Q_EDUAL, Q_GW, Q_P, Q_ENERGY, Q_FLIPS, Q_NONFINITE, NQ };
 // Quantities reduced by the vertex gathers.
 enum { QV_GTL = 0, QV_NUM, QV_DEN, NQV };
 
+// defining functions (the values of ffa_energy_kind) and, for batches, the
+// per-element choice
+constexpr int kEnSD = 0;      // symmetric Dirichlet
+constexpr int kEnSG = 1;      // symmetric gradient
+constexpr int kEnSA = 2;      // symmetric ARAP
+constexpr int kEnMixed = 3;   // per element, from energy_of[i]
+
 constexpr int kLocalBlock = 128;
 constexpr int kVertexBlock = 256;
 constexpr int kGatherLanes = 4;   // lanes sharing one row of the vertex gathers

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
     int vid[D + 1];
     R g[D][D], w, mu;
     load_element<D, R>(e, m, i, vid, g, w, mu);
-    const int en = (EN == 2) ? (int)e.energy_of[i] : EN;
+    const int en = (EN == kEnMixed) ? (int)e.energy_of[i] : EN;
     R J[D][D], dJ[D][D];
     element_jacobians<D, R>(vid, g, vrec, J, dJ);
     R* Pp = reinterpret_cast<R*>(e.P);
@@ -416,8 +416,9 @@ __global__ void __launch_bounds__(kLocalBlock) k_init_polar(ElemBufs e, int m, c
   load_element<D, R>(e, m, i, vid, g, w, mu);
   R J[D][D], dJ[D][D];
   element_jacobians<D, R>(vid, g, vrec, J, dJ);
-  const int en = (EN == 2) ? (int)e.energy_of[i] : EN;
-  const R eps = (en == 0) ? R(kEpsInitSD) : R(kEpsInitSG);
+  const int en = (EN == kEnMixed) ? (int)e.energy_of[i] : EN;
+  // the clamp of eq. polardecompositionapplied: SG's, or SD's for SD and SA (both grow like p^-2 at 0)
+  const R eps = (en == kEnSG) ? R(kEpsInitSG) : R(kEpsInitSD);
   R U[D][D], P[D][D];
   R* Up = reinterpret_cast<R*>(e.U);
   if constexpr (D == 2) {
@@ -559,15 +560,45 @@ __global__ void __launch_bounds__(kLocalBlock) k_energy_terms(ElemBufs e, int m,
           fro = fma(J[a][k], J[a][k], fro);
           fri = fma(Ji[a][k], Ji[a][k], fri);
         }
-      const int en = (EN == 2) ? (int)e.energy_of[i] : EN;
-      const R f = (en == 0) ? R(0.5) * (fro + fri) : R(0.5) * fro - Tr<R>::log_(det);
+      const int en = (EN == kEnMixed) ? (int)e.energy_of[i] : EN;
+      R f;
+      if (en == kEnSD) {
+        f = R(0.5) * (fro + fri);
+      } else if (en == kEnSG) {
+        f = R(0.5) * fro - Tr<R>::log_(det);
+      } else {
+        // SA: sum over the singular values s of ((s - 1)^2 + (1/s - 1)^2)/2, the s
+        // from the eigenvalues of J^T J
+        R s2[D];
+        if constexpr (D == 2) {
+          const R a = J[0][0] * J[0][0] + J[1][0] * J[1][0], b = J[0][1] * J[0][1] + J[1][1] * J[1][1];
+          const R c = J[0][0] * J[0][1] + J[1][0] * J[1][1];
+          const R h = R(0.5) * (a + b), dd = R(0.5) * (a - b);
+          const R r = Tr<R>::sqrt_(dd * dd + c * c);
+          s2[0] = h + r;
+          s2[1] = h - r;
+        } else {
+          R C[3][3], V[3][3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) C[a][k] = J[0][a] * J[0][k] + J[1][a] * J[1][k] + J[2][a] * J[2][k];
+          sym3_eig<R>(C[0][0], C[0][1], C[0][2], C[1][1], C[1][2], C[2][2], s2, V);
+        }
+        R sv[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) sv[k] = Tr<R>::sqrt_(fmax(s2[k], R(0)));
+        f = f_of_eigs<R, kEnSA, D>(sv);
+      }
       qv[Q_ENERGY] = flipped ? R(0) : w * f;
       qv[Q_FLIPS] = flipped ? R(1) : R(0);
     } else {
-      // grad f_SG = J - J^-T ; grad f_SD = J - J^-T J^-1 J^-T
+      // grad f_SG = J - J^-T ; grad f_SD = J - J^-T J^-1 J^-T ;
+      // grad f_SA = J - R - J^-T J^-1 J^-T + J^-T J^-1 R, R the rotation of J
+      // (U diag(phi'(s)) V^T with phi'(s) = s - 1 - s^-3 + s^-2 in matrix form)
       R Gr[D][D];
-      const int en = (EN == 2) ? (int)e.energy_of[i] : EN;
-      if (en == 1) {
+      const int en = (EN == kEnMixed) ? (int)e.energy_of[i] : EN;
+      if (en == kEnSG) {
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -583,6 +614,17 @@ __global__ void __launch_bounds__(kLocalBlock) k_energy_terms(ElemBufs e, int m,
             for (int l = 0; l < D; ++l) s = fma(Ji[l][a], Ji[l][k], s);
             T1[a][k] = s;
           }
+        R Rt[D][D];   // the rotation of J (SA only)
+        if (en == kEnSA && !flipped) {
+          if constexpr (D == 2) {
+            const R ca = J[0][0] + J[1][1], sa = J[1][0] - J[0][1];
+            const R ir = Tr<R>::rsqrt_(ca * ca + sa * sa);
+            Rt[0][0] = ca * ir; Rt[0][1] = -sa * ir; Rt[1][0] = sa * ir; Rt[1][1] = ca * ir;
+          } else {
+            R cond;
+            nearest_rotation3<R>(J, Rt, cond);
+          }
+        }
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -590,6 +632,12 @@ __global__ void __launch_bounds__(kLocalBlock) k_energy_terms(ElemBufs e, int m,
             R s = R(0);
 #pragma unroll
             for (int l = 0; l < D; ++l) s = fma(T1[a][l], Ji[k][l], s);
+            if (en == kEnSA && !flipped) {
+              R t = R(0);
+#pragma unroll
+              for (int l = 0; l < D; ++l) t = fma(T1[a][l], Rt[l][k], t);
+              s += Rt[a][k] - t;
+            }
             Gr[a][k] = w * (J[a][k] - s);
           }
       }
@@ -755,8 +803,8 @@ void dispatch_local(const LocalLaunch& L, cudaStream_t s) {
 
 void launch_local_step(const LocalLaunch& L, cudaStream_t s) {
 #define FFA_LS(D, R) \
-  do { if (L.energy == 0) dispatch_local<D, R, 0>(L, s); else if (L.energy == 1) dispatch_local<D, R, 1>(L, s); \
-       else dispatch_local<D, R, 2>(L, s); } while (0)
+  do { if (L.energy == kEnSD) dispatch_local<D, R, kEnSD>(L, s); else if (L.energy == kEnSG) dispatch_local<D, R, kEnSG>(L, s); \
+       else if (L.energy == kEnSA) dispatch_local<D, R, kEnSA>(L, s); else dispatch_local<D, R, kEnMixed>(L, s); } while (0)
   if (L.d == 2) { if (L.fp64) FFA_LS(2, double); else FFA_LS(2, float); }
   else { if (L.fp64) FFA_LS(3, double); else FFA_LS(3, float); }
 #undef FFA_LS
@@ -790,9 +838,10 @@ void launch_penalty(const LocalLaunch& L, int mode, double* mu64, double rho, cu
 void launch_init_polar(const LocalLaunch& L, cudaStream_t s) {
   const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
 #define FFA_INIT(D, R) \
-  do { if (L.energy == 0) k_init_polar<D, R, 0><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); \
-       else if (L.energy == 1) k_init_polar<D, R, 1><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); \
-       else k_init_polar<D, R, 2><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); } while (0)
+  do { if (L.energy == kEnSD) k_init_polar<D, R, kEnSD><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); \
+       else if (L.energy == kEnSG) k_init_polar<D, R, kEnSG><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); \
+       else if (L.energy == kEnSA) k_init_polar<D, R, kEnSA><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); \
+       else k_init_polar<D, R, kEnMixed><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec); } while (0)
   if (L.d == 2) { if (L.fp64) FFA_INIT(2, double); else FFA_INIT(2, float); }
   else { if (L.fp64) FFA_INIT(3, double); else FFA_INIT(3, float); }
 #undef FFA_INIT
@@ -806,7 +855,8 @@ void launch_energy_terms(const LocalLaunch& L, int mode, cudaStream_t s) {
     else k_energy_terms<D, R, EN, 1><<<grid, kLocalBlock, 0, s>>>(L.e, L.m, L.vrec, L.partials);           \
   } while (0)
 #define FFA_EN3(D, R) \
-  do { if (L.energy == 0) FFA_EN(D, R, 0); else if (L.energy == 1) FFA_EN(D, R, 1); else FFA_EN(D, R, 2); } while (0)
+  do { if (L.energy == kEnSD) FFA_EN(D, R, kEnSD); else if (L.energy == kEnSG) FFA_EN(D, R, kEnSG); \
+       else if (L.energy == kEnSA) FFA_EN(D, R, kEnSA); else FFA_EN(D, R, kEnMixed); } while (0)
   if (L.d == 2) { if (L.fp64) FFA_EN3(2, double); else FFA_EN3(2, float); }
   else { if (L.fp64) FFA_EN3(3, double); else FFA_EN3(3, float); }
 #undef FFA_EN3

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "ffa_internal.h"
+
 namespace ffa {
 
 template <typename R> struct Tr;
@@ -90,34 +92,77 @@ __device__ __forceinline__ R prox_root_sd(R q, R w, R mu) {
   return p;
 }
 
+// Symmetric ARAP, phi(p) = ((p - 1)^2 + (1/p - 1)^2)/2: w phi'(p) + mu (p - q) = 0
+// times p^3 is (w + mu) p^4 - (w + mu q) p^3 + w p - w = 0, i.e. g(p) = p^3 (p - a)
+// + c (p - 1) with a = (w + mu q)/(w + mu), c = w/(w + mu).  g(0) = -c < 0 and the
+// objective is strictly convex on p > 0, so the positive root is unique; it lies
+// below max(1, a) (g(1) = 1 - a, g(a) = c (a - 1)), and for a < 0 also below
+// (c/|a|)^(1/3) (g there is p^4 + c p > 0).  The root exceeds a/2, so g is convex
+// and increasing to its right and Newton from the bound decreases monotonically
+// onto it.
+template <typename R>
+__device__ __forceinline__ R prox_root_sa(R q, R w, R mu) {
+  const R inv = R(1) / (w + mu);
+  const R a = (w + mu * q) * inv, c = w * inv;
+  R p = a >= R(1) ? a : R(1);
+  if (a < R(0)) p = fmin(p, Tr<R>::cbrt_(c / (-a)));
+#pragma unroll 1
+  for (int it = 0; it < Tr<R>::newton_iters; ++it) {
+    const R p2 = p * p;
+    const R g = p2 * p * (p - a) + c * (p - R(1));
+    const R dg = p2 * (R(4) * p - R(3) * a) + c;
+    if (!(dg > R(0))) break;
+    const R step = g / dg;
+    p -= step;
+    if (Tr<R>::abs_(step) <= R(2) * Tr<R>::eps() * p) break;
+  }
+  return p;
+}
+
 template <typename R, int ENERGY>
 __device__ __forceinline__ R prox_root(R q, R w, R mu) {
-  return ENERGY == 0 ? prox_root_sd<R>(q, w, mu) : prox_root_sg<R>(q, w, mu);
+  if constexpr (ENERGY == kEnSD) return prox_root_sd<R>(q, w, mu);
+  else if constexpr (ENERGY == kEnSG) return prox_root_sg<R>(q, w, mu);
+  else return prox_root_sa<R>(q, w, mu);
 }
 
-// EN = 0 / 1: one energy for all elements; EN = 2: per element (en = 0 SD, 1 SG)
+// EN = kEnSD / kEnSG / kEnSA: one energy for all elements; EN = kEnMixed: per
+// element, en = that element's energy
 template <typename R, int EN>
 __device__ __forceinline__ R prox_root_en(R q, R w, R mu, int en) {
-  if constexpr (EN == 2) return en == 0 ? prox_root_sd<R>(q, w, mu) : prox_root_sg<R>(q, w, mu);
-  else return prox_root<R, EN>(q, w, mu);
+  if constexpr (EN == kEnMixed) {
+    return en == kEnSD ? prox_root_sd<R>(q, w, mu) : (en == kEnSG ? prox_root_sg<R>(q, w, mu) : prox_root_sa<R>(q, w, mu));
+  } else {
+    return prox_root<R, EN>(q, w, mu);
+  }
 }
 
-// f on an SPD matrix with eigenvalues p: SD (sum p^2 + sum p^-2)/2, SG sum p^2/2 - log p.
+// f on an SPD matrix with eigenvalues p: SD (sum p^2 + sum p^-2)/2, SG sum p^2/2 - log p,
+// SA sum ((p - 1)^2 + (1/p - 1)^2)/2.
 template <typename R, int ENERGY, int D>
 __device__ __forceinline__ R f_of_eigs(const R p[D]) {
   R s = 0;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    if (ENERGY == 0) s += R(0.5) * (p[j] * p[j] + R(1) / (p[j] * p[j]));
-    else s += R(0.5) * p[j] * p[j] - Tr<R>::log_(p[j]);
+    if constexpr (ENERGY == kEnSD) {
+      s += R(0.5) * (p[j] * p[j] + R(1) / (p[j] * p[j]));
+    } else if constexpr (ENERGY == kEnSG) {
+      s += R(0.5) * p[j] * p[j] - Tr<R>::log_(p[j]);
+    } else {
+      const R u = p[j] - R(1), v = R(1) / p[j] - R(1);
+      s += R(0.5) * (u * u + v * v);
+    }
   }
   return s;
 }
 
 template <typename R, int EN, int D>
 __device__ __forceinline__ R f_of_eigs_en(const R p[D], int en) {
-  if constexpr (EN == 2) return en == 0 ? f_of_eigs<R, 0, D>(p) : f_of_eigs<R, 1, D>(p);
-  else return f_of_eigs<R, EN, D>(p);
+  if constexpr (EN == kEnMixed) {
+    return en == kEnSD ? f_of_eigs<R, kEnSD, D>(p) : (en == kEnSG ? f_of_eigs<R, kEnSG, D>(p) : f_of_eigs<R, kEnSA, D>(p));
+  } else {
+    return f_of_eigs<R, EN, D>(p);
+  }
 }
 
 // ---------------------------------------------------------------------------

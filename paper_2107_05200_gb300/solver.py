@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _native as N
 
-ENERGIES = {"sd": 0, "sg": 1}
+ENERGIES = {"sd": 0, "sg": 1, "sa": 2}
 PRECISIONS = {"fp32": 0, "fp64": 1}
 
 

@@ -23,6 +23,7 @@ import numpy as np
 
 SYM_DIRICHLET = "sd"
 SYM_GRADIENT = "sg"
+SYM_ARAP = "sa"
 
 
 @dataclasses.dataclass
@@ -33,7 +34,7 @@ class Workload:
     pins: np.ndarray       # (n_pin,) int32 constrained vertices
     pin_pos: np.ndarray    # (n_pin, d_out) float64 constraint values b
     W0: np.ndarray         # (n, d_out) float64 initial map
-    energy: str            # "sd" or "sg"
+    energy: str            # "sd", "sg" or "sa"
     rho: float = 1.0       # penalty scale, mu_i = rho * w_i
     eps_abs: float = 1e-6
     eps_rel: float = 1e-5
