@@ -28,6 +28,9 @@ design notes):
   * 2D Procrustes tie (Q with q11+q22 = q21-q12 = 0): keep the previous U.
   * Flipped init: R1 R2^T gets its last column negated when its determinant is
     negative, and Sigma = eps I whenever det J0 <= 0.
+  * General constraints A W = b (Sec. 4, W update): A is c x n and acts on every
+    coordinate column alike, b is c x d (the paper's notation); constraints that
+    mix coordinates are not covered.  Pinned vertices are rows of the identity.
 """
 from __future__ import annotations
 
@@ -354,6 +357,55 @@ class WStep:
         return W
 
 
+class WStepKKT:
+    """Exact minimizer of Phi over W subject to general linear constraints
+    A W = b (Sec. 4, W update: any feasible A W = b; A is c x n and acts on every
+    coordinate column alike, b is c x d).  The KKT system
+
+        [ L  A^T ] [ W   ]   [ G^T r ]
+        [ A  0   ] [ nu  ] = [ b     ]
+
+    is indefinite; it is factored once by sparse LU (the paper's UMFPACK role)
+    and back-substituted every iteration.  Pinned vertices are rows of the
+    identity in A.  Raises ValueError when the system is singular (the
+    constraints do not fix the translations that G annihilates).
+    """
+
+    def __init__(self, g, T, mu, n, A, b):
+        A = sp.csr_matrix(A, dtype=np.float64)
+        if A.shape[1] != n:
+            raise ValueError("A must have n columns")
+        self.n = n
+        self.A = A
+        self.b = np.asarray(b, dtype=np.float64)
+        L = assemble_L(g, T, mu, n)
+        self.L = L
+        # L annihilates the constant vectors (a connected mesh), so the system is
+        # regular only if some constraint row has a nonzero sum, and only if the
+        # rows are independent (checked on the pivots of the factorization)
+        if np.abs(A @ np.ones(n)).max() <= 1e-12 * max(1.0, abs(A).max()):
+            raise ValueError("singular constrained W step: the constraints fix no translation")
+        K = sp.bmat([[L, A.T], [A, None]], format="csc")
+        try:
+            self.lu = sla.splu(K, permc_spec="MMD_AT_PLUS_A")
+        except RuntimeError as e:   # exactly singular
+            raise ValueError(f"singular constrained W step: dependent constraints ({e})") from e
+        piv = np.abs(self.lu.U.diagonal())
+        if not np.all(np.isfinite(piv)) or piv.min() <= 1e-13 * piv.max():
+            raise ValueError("singular constrained W step: dependent constraints")
+
+    def solve(self, rhs: np.ndarray) -> np.ndarray:
+        top = np.vstack([rhs, self.b])
+        sol = self.lu.solve(np.ascontiguousarray(top))
+        return sol[: self.n]
+
+
+def pin_rows(pins, n: int) -> sp.csr_matrix:
+    """The constraint rows of pinned vertices: one row of the identity per pin."""
+    pins = np.asarray(pins, dtype=np.int64)
+    return sp.csr_matrix((np.ones(len(pins)), (np.arange(len(pins)), pins)), shape=(len(pins), n))
+
+
 # ----------------------------------------------------------------------------
 # the loop (Algorithm 1; Algorithm 2 without rescaling)
 # ----------------------------------------------------------------------------
@@ -383,7 +435,8 @@ class Oracle:
     """The FP64 reference solver for one mesh, one energy, fixed penalties."""
 
     def __init__(self, V, T, pins, pin_pos, energy_name: str, rho: float = 1.0,
-                 eps_abs: float = 1e-6, eps_rel: float = 1e-5, h=None, local_variant: str = "paper"):
+                 eps_abs: float = 1e-6, eps_rel: float = 1e-5, h=None, local_variant: str = "paper",
+                 constraints=None):
         self.V = np.asarray(V, np.float64)
         self.T = np.asarray(T, np.int64)
         self.energy_name = energy_name
@@ -398,7 +451,17 @@ class Oracle:
         if local_variant not in ("paper", "joint"):
             raise ValueError("local_variant must be 'paper' or 'joint'")
         self.local_variant = local_variant
-        self.wstep = WStep(self.g, self.T, self.mu, self.n, np.asarray(pins), np.asarray(pin_pos))
+        if constraints is None:
+            self.wstep = WStep(self.g, self.T, self.mu, self.n, np.asarray(pins), np.asarray(pin_pos))
+        else:
+            # general A W = b (the pins, if any, become rows of the identity in A)
+            A, b = constraints
+            A = sp.csr_matrix(A, dtype=np.float64)
+            b = np.asarray(b, dtype=np.float64)
+            if len(pins):
+                A = sp.vstack([pin_rows(pins, self.n), A]).tocsr()
+                b = np.vstack([np.asarray(pin_pos, np.float64), b])
+            self.wstep = WStepKKT(self.g, self.T, self.mu, self.n, A, b)
 
     @classmethod
     def from_workload(cls, wl, **kw):
