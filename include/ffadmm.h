@@ -216,6 +216,26 @@ const char* ffa_last_error(const ffa_ctx* ctx);
  * unchanged, so no refactorization happens; the next W step uses the new b. */
 ffa_status ffa_set_handles(ffa_ctx* ctx, const double* pin_pos);
 
+/* General linear constraints A W = b on the vertex positions, on top of the
+ * pinned vertices (Sec. 4, W update: any feasible A W = b).  A is c x n in CSR
+ * (row_ptr: c + 1 int64, col: int32 vertex indices, val: double), acting on every
+ * coordinate column alike; b is c x d (row-major).  All arrays host or device,
+ * copied.  Entries on pinned vertices move to the right-hand side (and follow
+ * ffa_set_handles).  The W step stays the pinned one, L_FF W_F = G^T r - L_FC b_pins,
+ * corrected by a Schur complement on the c rows: with Z = L_FF^-1 A_F^T (c
+ * refined solves at this call) and S = A_F Z (c x c, Cholesky on the host), each
+ * iteration projects W_F <- W_F - Z S^-1 (A_F W_F - b'), the exact constrained
+ * minimizer.  Z is stored c x nF in double (8 c nF bytes on the device).  Call
+ * after ffa_create (with at least one pinned vertex) and before ffa_init, once;
+ * 1 <= c <= 256.  Not with penalty_schedule 1 nor with ffa_forward_unrolled.
+ * Errors: FFA_ERR_INVALID_ARG (sizes, indices, non-finite values, c out of
+ * range, after ffa_init or a second call, no pins, rows that are dependent once
+ * the pinned vertices are eliminated: a Cholesky pivot of S below 1e-10 of its
+ * diagonal), FFA_ERR_SINGULAR_SYSTEM (a column solve that does not converge),
+ * FFA_ERR_TIMEOUT, FFA_ERR_CUDA, FFA_ERR_OOM. */
+ffa_status ffa_set_constraints(ffa_ctx* ctx, int32_t c, const int64_t* row_ptr, const int32_t* col,
+                               const double* val, const double* b);
+
 /* Start a solve from W0 (n x d, host or device): U0, P0 from the polar
  * decomposition of G W0 with singular values clamped to eps and the flipped case
  * of eq. polardecompositionapplied (eps = eps_m^(1/4) for SG, eps_m^(1/8) for SD, eps_m = 2^-52);
@@ -300,7 +320,9 @@ ffa_status ffa_forward_unrolled(ffa_ctx* ctx, int32_t K, int32_t ckpt_every);
 ffa_status ffa_backward_unrolled(ffa_ctx* ctx, const double* dL_dW, double* dL_db);
 
 /* Relative residual |L_FF W_F - b_F| / |b_F| of the last W step, measured in
- * double on the device (a diagnostic of the refinement sweeps; eq. solvinginw. */
+ * double on the device (a diagnostic of the refinement sweeps; eq. solvinginw).
+ * FFA_ERR_INVALID_ARG on a context with general constraints, whose W step
+ * leaves the multiplier term A_F^T nu in that residual. */
 ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel_residual);
 
 /* Many independent meshes solved together (the paper solves one mesh at a time;

@@ -19,7 +19,7 @@ STATUS_NAMES = {
 }
 
 EXPORTED = [
-    "ffa_default_params", "ffa_create", "ffa_destroy", "ffa_last_error", "ffa_set_handles",
+    "ffa_default_params", "ffa_create", "ffa_destroy", "ffa_last_error", "ffa_set_handles", "ffa_set_constraints",
     "ffa_init", "ffa_iterate", "ffa_get_W", "ffa_get_state", "ffa_get_penalties", "ffa_energy", "ffa_gradient",
     "ffa_get_info", "ffa_last_wstep_residual", "ffa_profile_phases", "ffa_energy_noalloc",
     "ffa_forward_unrolled", "ffa_backward_unrolled",
@@ -111,6 +111,7 @@ def load() -> C.CDLL:
         "ffa_destroy": ([vp], None),
         "ffa_last_error": ([vp], C.c_char_p),
         "ffa_set_handles": ([vp, vp], C.c_int),
+        "ffa_set_constraints": ([vp, i32, vp, vp, vp, vp], C.c_int),
         "ffa_init": ([vp, vp], C.c_int),
         "ffa_iterate": ([vp, i32, i32, C.POINTER(Stats)], C.c_int),
         "ffa_get_W": ([vp, vp], C.c_int),

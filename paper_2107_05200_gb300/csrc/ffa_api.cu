@@ -88,6 +88,17 @@ struct ffa_ctx {
   ffa_stats last{};
   ffa_info info{};
   std::vector<int32_t> pins_h;
+  std::vector<int32_t> v2e_h;   // vertex -> eliminated index (-1 pinned), host copy
+  bool pins_user = true;        // false: made without pins, vertex 0 held at the origin
+  // general constraints A W = b (ffa_set_constraints): the device arrays of the
+  // projection, and on the host the entries on pinned vertices and b, from which
+  // b' = b - (entries on pins) pin_pos is rebuilt when the pins move
+  int n_con = 0;
+  ConstraintLaunch con;
+  struct ConPin { int32_t row, slot; double val; };
+  std::vector<ConPin> con_pin;
+  std::vector<double> con_b;
+  double* con_bprime = nullptr;
 
   // differentiation through unrolled iterations (ffa_forward_unrolled / ffa_backward_unrolled)
   struct Slot {
@@ -356,13 +367,18 @@ void enqueue_iteration(ffa_ctx* ctx, bool check, cudaEvent_t* ev = nullptr) {
     launch_residual(S, nullptr, 0, s);
     launch_supernodal_solve(S, s);
   }
+  if (ctx->n_con > 0) {
+    // general constraints: the last correction joins X, which is then projected
+    launch_axpy_correction(S, s);
+    launch_constraint_projection(ctx->con, s);
+  }
   if (ev) cudaEventRecord(ev[PH_WSTEP], s);
   VertexLaunch V{};
   V.d = ctx->d;
   V.fp64 = ctx->fp64;
   V.n = ctx->n;
   V.Wnew_free = ctx->X;
-  V.corr = ctx->x;
+  V.corr = ctx->n_con > 0 ? nullptr : ctx->x;
   V.v2e = ctx->v2e;
   V.v2pin = ctx->v2pin;
   V.pin_pos = ctx->pin_pos;
@@ -493,7 +509,7 @@ int kernels_per_iteration(const ffa_ctx* ctx) {
       solve += (ctx->fwd_off[l + 1] > ctx->fwd_off[l]) + (ctx->bwd_off[l + 1] > ctx->bwd_off[l]);
   }
   const int sweeps = ctx->prm.refine_sweeps;
-  return 1 + sweeps * (2 + solve) + (sweeps - 1) + 1 + 1;
+  return 1 + sweeps * (2 + solve) + (sweeps - 1) + 1 + 1 + (ctx->n_con > 0 ? 3 : 0);
 }
 
 // Supernode table and task lists of the supernodal solves.  A node with at most
@@ -728,6 +744,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     pins = {0};
     pin_pos.assign(d, 0.0);
     n_pin = 1;
+    ctx->pins_user = false;
   }
   ctx->n_pin = n_pin;
   for (int32_t v : T)
@@ -853,6 +870,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   if ((st = upload(ctx, &ctx->inc, inc)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->row_vertex, row_vertex)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->v2e, v2e)) != FFA_OK) return st;
+  ctx->v2e_h = v2e;
   if ((st = upload(ctx, &ctx->v2pin, v2pin)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->pin_pos, pin_pos)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->pins_d, pins)) != FFA_OK) return st;
@@ -1338,6 +1356,63 @@ ffa_status device_wait_status(ffa_ctx* ctx, const char* what) {
   return fail(ctx, FFA_ERR_TIMEOUT, std::string("a device-side wait gave up: ") + what);
 }
 
+// b' = b - A_C b_pins (c x d): the constraint entries on pinned vertices times
+// the current pinned positions move to the right-hand side
+ffa_status constraint_rhs(ffa_ctx* ctx) {
+  const int d = ctx->d;
+  std::vector<double> pp((size_t)ctx->n_pin * d);
+  FFA_CUDA(cudaMemcpy(pp.data(), ctx->pin_pos, pp.size() * 8, cudaMemcpyDeviceToHost));
+  std::vector<double> bp = ctx->con_b;
+  for (const auto& e : ctx->con_pin)
+    for (int k = 0; k < d; ++k) bp[(size_t)e.row * d + k] -= e.val * pp[(size_t)e.slot * d + k];
+  FFA_CUDA(cudaMemcpy(ctx->con_bprime, bp.data(), bp.size() * 8, cudaMemcpyHostToDevice));
+  return FFA_OK;
+}
+
+// Columns c0 .. c0+count-1 of Z = L_FF^-1 A_F^T: each coordinate column of the
+// solve carries one constraint row (b = that row of A_F, X = 0), refined in FP64
+// until the relative residual reaches double rounding level.
+ffa_status constraint_columns(ffa_ctx* ctx, const std::vector<int64_t>& fptr, const std::vector<int32_t>& fcol,
+                              const std::vector<double>& fval, double* Z, int c, int c0, int count,
+                              std::vector<double>& Xh) {
+  const int d = ctx->d, nF = ctx->nF;
+  cudaStream_t s = ctx->stream;
+  std::vector<double> Bh((size_t)nF * d, 0.0);
+  for (int j = 0; j < count; ++j)
+    for (int64_t q = fptr[c0 + j]; q < fptr[c0 + j + 1]; ++q) Bh[(size_t)fcol[q] * d + j] = fval[q];
+  FFA_CUDA(cudaMemcpyAsync(ctx->b, Bh.data(), Bh.size() * 8, cudaMemcpyHostToDevice, s));
+  FFA_CUDA(cudaMemsetAsync(ctx->X, 0, (size_t)nF * d * 8, s));
+  SolveData S = solve_data(ctx);
+  std::vector<double> part((size_t)ctx->n_res_blocks * 2);
+  double rel = 1.0, prev = 2.0;
+  for (int sw = 0; sw < 12; ++sw) {
+    launch_residual(S, ctx->res_partials, (int)ctx->n_res_blocks, s);
+    FFA_CUDA(cudaMemcpyAsync(part.data(), ctx->res_partials, part.size() * 8, cudaMemcpyDeviceToHost, s));
+    FFA_CUDA(cudaStreamSynchronize(s));
+    double rr = 0.0, bb = 0.0;
+    for (int64_t q = 0; q < ctx->n_res_blocks; ++q) {
+      rr += part[2 * q];
+      bb += part[2 * q + 1];
+    }
+    rel = bb > 0.0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+    if (rel < 1e-13 || rel > 0.5 * prev) break;
+    prev = rel;
+    launch_supernodal_solve(S, s);
+    launch_axpy_correction(S, s);
+  }
+  ffa_status st = device_wait_status(ctx, "constraint solves");
+  if (st != FFA_OK) return st;
+  if (!(rel < 1e-10))
+    return fail(ctx, FFA_ERR_SINGULAR_SYSTEM, "the solves for the constraint columns did not converge (relative residual " +
+                                                  std::to_string(rel) + ")");
+  launch_copy_columns(ctx->X, d, Z, c, c0, count, nF, s);
+  FFA_CUDA(cudaGetLastError());
+  Xh.resize((size_t)nF * d);
+  FFA_CUDA(cudaMemcpyAsync(Xh.data(), ctx->X, Xh.size() * 8, cudaMemcpyDeviceToHost, s));
+  FFA_CUDA(cudaStreamSynchronize(s));
+  return FFA_OK;
+}
+
 }  // namespace
 
 void ffa::set_thread_error(const std::string& msg) { g_create_error = msg; }
@@ -1433,7 +1508,140 @@ ffa_status ffa_set_handles(ffa_ctx* ctx, const double* pin_pos) {
   launch_pin_rhs(ctx->d, ctx->nF, ctx->fc_ptr, ctx->fc_col, ctx->fc_val, ctx->pin_pos, ctx->cst, ctx->stream);
   FFA_CUDA(cudaGetLastError());
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->n_con > 0) return constraint_rhs(ctx);
   return FFA_OK;
+}
+
+ffa_status ffa_set_constraints(ffa_ctx* ctx, int32_t c, const int64_t* row_ptr, const int32_t* col,
+                               const double* val, const double* b) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->initialized) return fail(ctx, FFA_ERR_INVALID_ARG, "constraints are set before ffa_init");
+  if (ctx->n_con > 0) return fail(ctx, FFA_ERR_INVALID_ARG, "constraints are already set");
+  if (c < 1 || c > kMaxConstraints) return fail(ctx, FFA_ERR_INVALID_ARG, "need 1 <= c <= 256 constraint rows");
+  if (!row_ptr || !col || !val || !b) return fail(ctx, FFA_ERR_INVALID_ARG, "constraint arrays are NULL");
+  if (ctx->prm.penalty_schedule != 0)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "constraints do not combine with the penalty schedule (it refactors L)");
+  if (!ctx->pins_user)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "constraints need at least one pinned vertex (L_FF must be definite)");
+  const int d = ctx->d, n = ctx->n, nF = ctx->nF;
+  ffa_status st;
+  try {
+    std::vector<int64_t> ptr;
+    if ((st = copy_in(ctx, ptr, row_ptr, (size_t)c + 1)) != FFA_OK) return st;
+    if (ptr[0] != 0) return fail(ctx, FFA_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+    for (int r = 0; r < c; ++r)
+      if (ptr[r + 1] < ptr[r]) return fail(ctx, FFA_ERR_INVALID_ARG, "row_ptr is not non-decreasing");
+    const int64_t nnz = ptr[c];
+    if (nnz > (int64_t)c * n) return fail(ctx, FFA_ERR_INVALID_ARG, "more constraint entries than c x n");
+    std::vector<int32_t> ci;
+    std::vector<double> cv, bh;
+    if ((st = copy_in(ctx, ci, col, (size_t)nnz)) != FFA_OK) return st;
+    if ((st = copy_in(ctx, cv, val, (size_t)nnz)) != FFA_OK) return st;
+    if ((st = copy_in(ctx, bh, b, (size_t)c * d)) != FFA_OK) return st;
+    for (int64_t q = 0; q < nnz; ++q) {
+      if (ci[q] < 0 || ci[q] >= n) return fail(ctx, FFA_ERR_INVALID_ARG, "constraint column out of range");
+      if (!std::isfinite(cv[q])) return fail(ctx, FFA_ERR_INVALID_ARG, "non-finite constraint entry");
+    }
+    for (double x : bh)
+      if (!std::isfinite(x)) return fail(ctx, FFA_ERR_INVALID_ARG, "non-finite constraint right-hand side");
+    // split A = [A_F A_C]: entries on free vertices by eliminated index (repeated
+    // columns of a row summed), entries on pinned vertices by pin slot
+    std::vector<int32_t> slot_of(n, -1);
+    for (size_t p = 0; p < ctx->pins_h.size(); ++p) slot_of[ctx->pins_h[p]] = (int32_t)p;
+    std::vector<int64_t> fptr(c + 1, 0);
+    std::vector<int32_t> fcol;
+    std::vector<double> fval;
+    ctx->con_pin.clear();
+    for (int r = 0; r < c; ++r) {
+      std::vector<std::pair<int32_t, double>> row;
+      for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
+        const int v = ci[q];
+        if (ctx->v2e_h[v] >= 0) row.push_back({ctx->v2e_h[v], cv[q]});
+        else ctx->con_pin.push_back({r, slot_of[v], cv[q]});
+      }
+      std::sort(row.begin(), row.end());
+      for (size_t k = 0; k < row.size(); ++k) {
+        if (!fcol.empty() && (int64_t)fcol.size() > fptr[r] && fcol.back() == row[k].first) fval.back() += row[k].second;
+        else {
+          fcol.push_back(row[k].first);
+          fval.push_back(row[k].second);
+        }
+      }
+      fptr[r + 1] = (int64_t)fcol.size();
+    }
+    // Z = L_FF^-1 A_F^T, d rows of A_F per refined solve, and S = A_F Z (host)
+    double* Z = nullptr;
+    if ((st = dalloc(ctx, &Z, (size_t)c * nF)) != FFA_OK) return st;
+    std::vector<double> Sm((size_t)c * c, 0.0), Xh;
+    for (int c0 = 0; c0 < c; c0 += d) {
+      const int cnt = std::min(d, c - c0);
+      if ((st = constraint_columns(ctx, fptr, fcol, fval, Z, c, c0, cnt, Xh)) != FFA_OK) return st;
+      for (int r = 0; r < c; ++r)
+        for (int64_t q = fptr[r]; q < fptr[r + 1]; ++q)
+          for (int j = 0; j < cnt; ++j) Sm[(size_t)r * c + c0 + j] += fval[q] * Xh[(size_t)fcol[q] * d + j];
+    }
+    // Cholesky S = L L^T; a pivot that falls to 1e-10 of its row's diagonal means
+    // the row is (numerically) a combination of the rows before it, given the pins
+    std::vector<double> Lc((size_t)c * c, 0.0);
+    for (int i = 0; i < c; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double a = 0.5 * (Sm[(size_t)i * c + j] + Sm[(size_t)j * c + i]);
+        for (int k = 0; k < j; ++k) a -= Lc[(size_t)i * c + k] * Lc[(size_t)j * c + k];
+        if (i == j) {
+          if (!(a > 1e-10 * Sm[(size_t)i * c + i]) || !(Sm[(size_t)i * c + i] > 0.0))
+            return fail(ctx, FFA_ERR_INVALID_ARG, "constraint row " + std::to_string(i) +
+                                                      " depends on the pins or on the rows before it");
+          Lc[(size_t)i * c + i] = std::sqrt(a);
+        } else {
+          Lc[(size_t)i * c + j] = a / Lc[(size_t)j * c + j];
+        }
+      }
+    // S^-1 column by column: L y = e_j, L^T x = y
+    std::vector<double> Sinv((size_t)c * c), y(c);
+    for (int j = 0; j < c; ++j) {
+      for (int i = 0; i < c; ++i) {
+        double a = i == j ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) a -= Lc[(size_t)i * c + k] * y[k];
+        y[i] = a / Lc[(size_t)i * c + i];
+      }
+      for (int i = c - 1; i >= 0; --i) {
+        double a = y[i];
+        for (int k = i + 1; k < c; ++k) a -= Lc[(size_t)k * c + i] * Sinv[(size_t)k * c + j];
+        Sinv[(size_t)i * c + j] = a / Lc[(size_t)i * c + i];
+      }
+    }
+    int64_t* dptr = nullptr;
+    int32_t* dcol = nullptr;
+    double *dval = nullptr, *dSinv = nullptr, *dnu = nullptr;
+    if ((st = upload(ctx, &dptr, fptr)) != FFA_OK) return st;
+    if ((st = upload(ctx, &dcol, fcol)) != FFA_OK) return st;
+    if ((st = upload(ctx, &dval, fval)) != FFA_OK) return st;
+    if ((st = upload(ctx, &dSinv, Sinv)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &dnu, (size_t)c * d)) != FFA_OK) return st;
+    if ((st = dalloc(ctx, &ctx->con_bprime, (size_t)c * d)) != FFA_OK) return st;
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->con_b = bh;
+    ctx->con.d = d;
+    ctx->con.c = c;
+    ctx->con.nF = nF;
+    ctx->con.ptr = dptr;
+    ctx->con.col = dcol;
+    ctx->con.val = dval;
+    ctx->con.bprime = ctx->con_bprime;
+    ctx->con.Sinv = dSinv;
+    ctx->con.Z = Z;
+    ctx->con.nu = dnu;
+    ctx->con.X = ctx->X;
+    ctx->n_con = c;
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, FFA_ERR_OOM, "host allocation failed");
+  }
+  // graphs captured before (none before ffa_init, kept for safety) lack the projection
+  if (ctx->g_batch) { cudaGraphExecDestroy(ctx->g_batch); ctx->g_batch = nullptr; }
+  if (ctx->g_one) { cudaGraphExecDestroy(ctx->g_one); ctx->g_one = nullptr; }
+  if (ctx->g_one_check) { cudaGraphExecDestroy(ctx->g_one_check); ctx->g_one_check = nullptr; }
+  return constraint_rhs(ctx);
 }
 
 ffa_status ffa_init(ffa_ctx* ctx, const double* W0) {
@@ -1708,6 +1916,8 @@ ffa_status ffa_forward_unrolled(ffa_ctx* ctx, int32_t K, int32_t ckpt_every) {
     return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation needs fixed penalties (penalty_schedule 0)");
   if (ctx->prm.local_variant != 0)
     return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation is implemented for the paper's local step (local_variant 0)");
+  if (ctx->n_con > 0)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation is implemented for pinned constraints only");
   ffa_status st = ensure_graphs(ctx);
   if (st != FFA_OK) return st;
   const int C = std::min(ckpt_every, K);
@@ -1994,6 +2204,8 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
 ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel) {
   if (!ctx || !rel) return FFA_ERR_INVALID_ARG;
   ctx->err.clear();
+  if (ctx->n_con > 0)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "with general constraints L_FF W_F - b_F holds the multiplier term A_F^T nu");
   SolveData S = solve_data(ctx);
   launch_residual(S, ctx->res_partials, (int)ctx->n_res_blocks, ctx->stream);
   launch_sum_partials(ctx->res_partials, ctx->n_res_blocks, 2, ctx->sums_d, ctx->stream);

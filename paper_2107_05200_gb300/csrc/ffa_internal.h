@@ -105,6 +105,27 @@ struct VertexLaunch {
 };
 void launch_vertex_update(const VertexLaunch& V, cudaStream_t s);
 
+// General linear constraints on the free vertices after the pinned ones are
+// eliminated: A_F W_F = b' (c rows, CSR over eliminated indices).  With
+// Z = L_FF^-1 A_F^T (nF x c, row-major) and S^-1 = (A_F Z)^-1 (c x c), the W step's
+// unconstrained solution X is projected onto the constraints:
+// X <- X - Z S^-1 (A_F X - b'), the exact constrained minimizer.
+constexpr int kMaxConstraints = 256;
+struct ConstraintLaunch {
+  int d = 0, c = 0, nF = 0;
+  const int64_t* ptr = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+  const double* bprime = nullptr;   // c x d
+  const double* Sinv = nullptr;     // c x c
+  const double* Z = nullptr;        // c x nF (column r of L_FF^-1 A_F^T contiguous)
+  double* nu = nullptr;             // c x d: S^-1 (A_F X - b')
+  double* X = nullptr;              // nF x d, projected in place
+};
+void launch_constraint_projection(const ConstraintLaunch& C, cudaStream_t s);
+// column c0 + k of dst (c x nF, column-major) = column k of src (nF x d) for k < count
+void launch_copy_columns(const double* src, int d, double* dst, int c, int c0, int count, int nF, cudaStream_t s);
+
 struct GatherLaunch {
   int d, fp64;
   int rows;                  // vertices gathered

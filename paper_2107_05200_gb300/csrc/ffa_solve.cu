@@ -260,6 +260,55 @@ __global__ void __launch_bounds__(kVertexBlock) k_residual(const int32_t* __rest
   }
 }
 
+// nu = S^-1 (A_F X - b'), on one block: the c x d residual of the constraints
+// in shared memory, then the small dense product
+template <int D>
+__global__ void __launch_bounds__(256) k_constraint_nu(ConstraintLaunch C) {
+  __shared__ double t[kMaxConstraints * D];
+  for (int q = threadIdx.x; q < C.c * D; q += blockDim.x) {
+    const int r = q / D, k = q - r * D;
+    double a = -C.bprime[q];
+    for (int64_t e = C.ptr[r]; e < C.ptr[r + 1]; ++e) a = fma(C.val[e], C.X[(int64_t)C.col[e] * D + k], a);
+    t[q] = a;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < C.c * D; q += blockDim.x) {
+    const int r = q / D, k = q - r * D;
+    double a = 0.0;
+    for (int j = 0; j < C.c; ++j) a = fma(C.Sinv[(int64_t)r * C.c + j], t[j * D + k], a);
+    C.nu[q] = a;
+  }
+}
+
+// X <- X - Z nu, one thread per free row
+template <int D>
+__global__ void __launch_bounds__(kVertexBlock) k_constraint_project(ConstraintLaunch C) {
+  __shared__ double nu[kMaxConstraints * D];
+  for (int q = threadIdx.x; q < C.c * D; q += blockDim.x) nu[q] = C.nu[q];
+  __syncthreads();
+  const int i = blockIdx.x * kVertexBlock + threadIdx.x;
+  if (i >= C.nF) return;
+  double acc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = 0.0;
+  for (int r = 0; r < C.c; ++r) {
+    const double zr = C.Z[(int64_t)r * C.nF + i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = fma(zr, nu[r * D + k], acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) C.X[(int64_t)i * D + k] -= acc[k];
+}
+
+__global__ void k_copy_columns(const double* __restrict__ src, int d, double* __restrict__ dst, int c, int c0,
+                               int count, int nF) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)nF * count) return;
+  const int64_t i = q / count;
+  const int k = (int)(q - i * count);
+  dst[(int64_t)(c0 + k) * nF + i] = src[i * d + k];
+}
+
 __global__ void k_axpy(int n, double* __restrict__ X, const float* __restrict__ x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) X[i] += (double)x[i];
@@ -1028,6 +1077,24 @@ void launch_residual(const SolveData& S, double* partials, int n_blocks, cudaStr
   const int g = blocks_for(S.nF, kVertexBlock);
   if (S.d == 2) k_residual<2><<<g, kVertexBlock, 0, s>>>(S.ell_col, S.ell_val, S.ell_width, S.nF, S.X, S.b, S.y, partials);
   else k_residual<3><<<g, kVertexBlock, 0, s>>>(S.ell_col, S.ell_val, S.ell_width, S.nF, S.X, S.b, S.y, partials);
+}
+
+void launch_constraint_projection(const ConstraintLaunch& C, cudaStream_t s) {
+  if (C.c <= 0 || C.nF <= 0) return;
+  const int g = blocks_for(C.nF, kVertexBlock);
+  if (C.d == 2) {
+    k_constraint_nu<2><<<1, 256, 0, s>>>(C);
+    k_constraint_project<2><<<g, kVertexBlock, 0, s>>>(C);
+  } else {
+    k_constraint_nu<3><<<1, 256, 0, s>>>(C);
+    k_constraint_project<3><<<g, kVertexBlock, 0, s>>>(C);
+  }
+}
+
+void launch_copy_columns(const double* src, int d, double* dst, int c, int c0, int count, int nF, cudaStream_t s) {
+  const int64_t n = (int64_t)nF * count;
+  if (n <= 0) return;
+  k_copy_columns<<<blocks_for(n, 256), 256, 0, s>>>(src, d, dst, c, c0, count, nF);
 }
 
 void launch_axpy_correction(const SolveData& S, cudaStream_t s) {

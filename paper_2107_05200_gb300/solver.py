@@ -120,6 +120,21 @@ class Solver:
         p, keep = _ptr(pin_pos, np.float64)
         self._check(self._lib.ffa_set_handles(self._ctx, p))
 
+    def set_constraints(self, A, b) -> None:
+        """General linear constraints A W = b on top of the pins (Sec. 4, W update):
+        A is c x n (scipy sparse or dense), b is c x d.  Before init, once."""
+        import scipy.sparse as sp
+        A = sp.csr_matrix(A)
+        A.sum_duplicates()
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(A.shape[0], -1))
+        if A.shape[1] != self.n:
+            raise ValueError(f"A has {A.shape[1]} columns, the mesh {self.n} vertices")
+        ptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        col = np.ascontiguousarray(A.indices, dtype=np.int32)
+        val = np.ascontiguousarray(A.data, dtype=np.float64)
+        self._check(self._lib.ffa_set_constraints(self._ctx, int(A.shape[0]), ptr.ctypes.data, col.ctypes.data,
+                                                  val.ctypes.data, b.ctypes.data))
+
     def init(self, W0) -> None:
         p, keep = _ptr(W0, np.float64)
         self._check(self._lib.ffa_init(self._ctx, p))
