@@ -259,6 +259,20 @@ ffa_status ffa_get_W(ffa_ctx* ctx, double* W_out);
  * any pointer may be NULL to skip it). */
 ffa_status ffa_get_state(ffa_ctx* ctx, double* U, double* P, double* Lambda);
 
+/* Make (W, U, P, Lambda) the current state, in place of ffa_init: the state of
+ * Algorithm 1 between two iterations (W n x d, U, P, Lambda m x d x d each,
+ * row-major, host or device, copied), e.g. from ffa_get_W and ffa_get_state of
+ * an earlier run, to resume it or to restart from a checkpoint.  U must be a
+ * rotation (U^T U = I and det U = 1 to 1e-5 per entry), P is symmetrized; the
+ * free rows of W start the next W step, and r_i = mu_i (U_i P_i - Lambda_i) is
+ * formed for it as the last local step would have.  The iteration counter
+ * restarts at 0 and checkpoints of ffa_forward_unrolled are dropped.  On the
+ * FP32 local step the state is rounded to float.  Not with penalty_schedule 1
+ * (mu and the event counters are part of that state).
+ * Errors: FFA_ERR_INVALID_ARG (NULL pointer, non-finite entry, U not a rotation,
+ * penalty schedule), FFA_ERR_CUDA, FFA_ERR_OOM. */
+ffa_status ffa_set_state(ffa_ctx* ctx, const double* W, const double* U, const double* P, const double* Lambda);
+
 /* The current penalties mu_i (m values, host or device buffer): rho * w_i with
  * fixed penalties, the schedule's values with penalty_schedule 1 (eq.
  * augmentedlagrangian; Sec. 6, "Rescaling mu_i and Lambda").  With fixed

@@ -20,7 +20,7 @@ STATUS_NAMES = {
 
 EXPORTED = [
     "ffa_default_params", "ffa_create", "ffa_destroy", "ffa_last_error", "ffa_set_handles", "ffa_set_constraints",
-    "ffa_init", "ffa_iterate", "ffa_get_W", "ffa_get_state", "ffa_get_penalties", "ffa_energy", "ffa_gradient",
+    "ffa_init", "ffa_iterate", "ffa_get_W", "ffa_get_state", "ffa_set_state", "ffa_get_penalties", "ffa_energy", "ffa_gradient",
     "ffa_get_info", "ffa_last_wstep_residual", "ffa_profile_phases", "ffa_energy_noalloc",
     "ffa_forward_unrolled", "ffa_backward_unrolled",
     "ffa_batch_create", "ffa_batch_destroy", "ffa_batch_last_error", "ffa_batch_init", "ffa_batch_iterate",
@@ -116,6 +116,7 @@ def load() -> C.CDLL:
         "ffa_iterate": ([vp, i32, i32, C.POINTER(Stats)], C.c_int),
         "ffa_get_W": ([vp, vp], C.c_int),
         "ffa_get_state": ([vp, vp, vp, vp], C.c_int),
+        "ffa_set_state": ([vp, vp, vp, vp, vp], C.c_int),
         "ffa_get_penalties": ([vp, vp], C.c_int),
         "ffa_energy": ([vp, vp, C.POINTER(dbl)], C.c_int),
         "ffa_gradient": ([vp, vp, vp], C.c_int),

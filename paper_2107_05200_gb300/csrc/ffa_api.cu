@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ffa_internal.h"
+#include "ffa_state.h"
 
 using namespace ffa;
 
@@ -1771,38 +1772,75 @@ ffa_status ffa_get_state(ffa_ctx* ctx, double* U, double* P, double* Lam) {
   ctx->err.clear();
   const int m = ctx->m, d = ctx->d;
   const size_t R = ctx->rsz;
-  const int ps = d == 2 ? 3 : 6, us = d == 2 ? 2 : 4;
+  const int ps = state_p_size(d), us = state_u_size(d);
   std::vector<unsigned char> hu((size_t)m * us * R), hp((size_t)m * ps * R), hl((size_t)m * d * d * R);
   FFA_CUDA(cudaMemcpyAsync(hu.data(), ctx->e.U, hu.size(), cudaMemcpyDeviceToHost, ctx->stream));
   FFA_CUDA(cudaMemcpyAsync(hp.data(), ctx->e.P, hp.size(), cudaMemcpyDeviceToHost, ctx->stream));
   FFA_CUDA(cudaMemcpyAsync(hl.data(), ctx->e.Lam, hl.size(), cudaMemcpyDeviceToHost, ctx->stream));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
-  auto get = [&](const std::vector<unsigned char>& h, size_t k) -> double {
-    return ctx->fp64 ? reinterpret_cast<const double*>(h.data())[k] : (double)reinterpret_cast<const float*>(h.data())[k];
+  auto as_double = [&](const std::vector<unsigned char>& h) {
+    std::vector<double> v(h.size() / R);
+    for (size_t k = 0; k < v.size(); ++k)
+      v[k] = ctx->fp64 ? reinterpret_cast<const double*>(h.data())[k] : (double)reinterpret_cast<const float*>(h.data())[k];
+    return v;
   };
+  const std::vector<double> u = as_double(hu), p = as_double(hp), l = as_double(hl);
   std::vector<double> oU((size_t)m * d * d), oP((size_t)m * d * d), oL((size_t)m * d * d);
-  for (int i = 0; i < m; ++i) {
-    double* u = oU.data() + (size_t)i * d * d;
-    double* p = oP.data() + (size_t)i * d * d;
-    double* l = oL.data() + (size_t)i * d * d;
-    if (d == 2) {
-      const double c = get(hu, i), s = get(hu, (size_t)m + i);
-      u[0] = c; u[1] = -s; u[2] = s; u[3] = c;
-      p[0] = get(hp, i); p[1] = p[2] = get(hp, (size_t)m + i); p[3] = get(hp, 2 * (size_t)m + i);
-    } else {
-      const double w = get(hu, i), x = get(hu, (size_t)m + i), y = get(hu, 2 * (size_t)m + i), z = get(hu, 3 * (size_t)m + i);
-      u[0] = 1 - 2 * (y * y + z * z); u[1] = 2 * (x * y - z * w); u[2] = 2 * (x * z + y * w);
-      u[3] = 2 * (x * y + z * w); u[4] = 1 - 2 * (x * x + z * z); u[5] = 2 * (y * z - x * w);
-      u[6] = 2 * (x * z - y * w); u[7] = 2 * (y * z + x * w); u[8] = 1 - 2 * (x * x + y * y);
-      p[0] = get(hp, i); p[1] = p[3] = get(hp, (size_t)m + i); p[2] = p[6] = get(hp, 2 * (size_t)m + i);
-      p[4] = get(hp, 3 * (size_t)m + i); p[5] = p[7] = get(hp, 4 * (size_t)m + i); p[8] = get(hp, 5 * (size_t)m + i);
-    }
-    for (int q = 0; q < d * d; ++q) l[q] = get(hl, (size_t)q * m + i);
-  }
+  unpack_state(d, m, u.data(), p.data(), l.data(), oU.data(), oP.data(), oL.data());
   const size_t bytes = (size_t)m * d * d * 8;
   if (U) FFA_CUDA(cudaMemcpy(U, oU.data(), bytes, cudaMemcpyDefault));
   if (P) FFA_CUDA(cudaMemcpy(P, oP.data(), bytes, cudaMemcpyDefault));
   if (Lam) FFA_CUDA(cudaMemcpy(Lam, oL.data(), bytes, cudaMemcpyDefault));
+  return FFA_OK;
+}
+
+ffa_status ffa_set_state(ffa_ctx* ctx, const double* W, const double* U, const double* P, const double* Lam) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!W || !U || !P || !Lam) return fail(ctx, FFA_ERR_INVALID_ARG, "W, U, P and Lambda are all required");
+  if (ctx->prm.penalty_schedule != 0)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "with the penalty schedule the state also holds mu and its event counters");
+  const int m = ctx->m, d = ctx->d;
+  const size_t mdd = (size_t)m * d * d;
+  ffa_status st;
+  try {
+    std::vector<double> hU, hP, hL, hW;
+    if ((st = copy_in(ctx, hU, U, mdd)) != FFA_OK) return st;
+    if ((st = copy_in(ctx, hP, P, mdd)) != FFA_OK) return st;
+    if ((st = copy_in(ctx, hL, Lam, mdd)) != FFA_OK) return st;
+    if ((st = copy_in(ctx, hW, W, (size_t)ctx->n * d)) != FFA_OK) return st;
+    for (double x : hW)
+      if (!std::isfinite(x)) return fail(ctx, FFA_ERR_INVALID_ARG, "non-finite entry in W");
+    std::vector<double> u((size_t)m * state_u_size(d)), p((size_t)m * state_p_size(d)), l(mdd);
+    std::string msg;
+    if (!pack_state(d, m, hU.data(), hP.data(), hL.data(), u.data(), p.data(), l.data(), msg))
+      return fail(ctx, FFA_ERR_INVALID_ARG, msg);
+    auto put = [&](void* dst, const std::vector<double>& h) -> ffa_status {
+      if (ctx->fp64) {
+        FFA_CUDA(cudaMemcpy(dst, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+      } else {
+        std::vector<float> f(h.begin(), h.end());
+        FFA_CUDA(cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+      }
+      return FFA_OK;
+    };
+    // nothing may still read the old state
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+    if ((st = put(ctx->e.U, u)) != FFA_OK) return st;
+    if ((st = put(ctx->e.P, p)) != FFA_OK) return st;
+    if ((st = put(ctx->e.Lam, l)) != FFA_OK) return st;
+    // W, its free rows as the W step's starting point, the vertex records, and the
+    // right-hand-side terms r_i = mu_i (U_i P_i - Lambda_i) the next W step gathers
+    if ((st = load_W_records(ctx, hW.data(), true, ctx->W, ctx->vrec)) != FFA_OK) return st;
+    launch_rhs_terms(local_launch(ctx, false, ctx->vrec), ctx->stream);
+    FFA_CUDA(cudaGetLastError());
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, FFA_ERR_OOM, "host allocation failed");
+  }
+  ctx->initialized = true;
+  ctx->iter_total = 0;
+  ctx->adj_K = 0;
   return FFA_OK;
 }
 

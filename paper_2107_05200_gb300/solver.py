@@ -159,6 +159,11 @@ class Solver:
                                             C.c_void_p(L.ctypes.data)))
         return U, P, L
 
+    def set_state(self, W, U, P, Lam) -> None:
+        """Resume from (W, U, P, Lambda) instead of init (W n x d; U, P, Lambda m x d x d)."""
+        keep = [_ptr(a, np.float64) for a in (W, U, P, Lam)]
+        self._check(self._lib.ffa_set_state(self._ctx, *(k[0] for k in keep)))
+
     def penalties(self) -> np.ndarray:
         """The current penalties mu_i (m values)."""
         out = np.empty(self.m, np.float64)
