@@ -232,7 +232,8 @@ ffa_status ffa_set_handles(ffa_ctx* ctx, const double* pin_pos);
  * range, after ffa_init or a second call, no pins, rows that are dependent once
  * the pinned vertices are eliminated: a Cholesky pivot of S below 1e-10 of its
  * diagonal), FFA_ERR_SINGULAR_SYSTEM (a column solve that does not converge),
- * FFA_ERR_TIMEOUT, FFA_ERR_CUDA, FFA_ERR_OOM. */
+ * FFA_ERR_TIMEOUT, FFA_ERR_CUDA, FFA_ERR_OOM.  A call that fails after the
+ * column solves keeps their device scratch (8 c nF bytes) until ffa_destroy. */
 ffa_status ffa_set_constraints(ffa_ctx* ctx, int32_t c, const int64_t* row_ptr, const int32_t* col,
                                const double* val, const double* b);
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ffa_internal.h"
+#include "ffa_constraint_host.h"
 #include "ffa_state.h"
 
 using namespace ffa;
@@ -96,8 +97,7 @@ struct ffa_ctx {
   // b' = b - (entries on pins) pin_pos is rebuilt when the pins move
   int n_con = 0;
   ConstraintLaunch con;
-  struct ConPin { int32_t row, slot; double val; };
-  std::vector<ConPin> con_pin;
+  std::vector<ConstraintSplit::PinEntry> con_pin;
   std::vector<double> con_b;
   double* con_bprime = nullptr;
 
@@ -1550,27 +1550,12 @@ ffa_status ffa_set_constraints(ffa_ctx* ctx, int32_t c, const int64_t* row_ptr, 
     // columns of a row summed), entries on pinned vertices by pin slot
     std::vector<int32_t> slot_of(n, -1);
     for (size_t p = 0; p < ctx->pins_h.size(); ++p) slot_of[ctx->pins_h[p]] = (int32_t)p;
-    std::vector<int64_t> fptr(c + 1, 0);
-    std::vector<int32_t> fcol;
-    std::vector<double> fval;
-    ctx->con_pin.clear();
-    for (int r = 0; r < c; ++r) {
-      std::vector<std::pair<int32_t, double>> row;
-      for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
-        const int v = ci[q];
-        if (ctx->v2e_h[v] >= 0) row.push_back({ctx->v2e_h[v], cv[q]});
-        else ctx->con_pin.push_back({r, slot_of[v], cv[q]});
-      }
-      std::sort(row.begin(), row.end());
-      for (size_t k = 0; k < row.size(); ++k) {
-        if (!fcol.empty() && (int64_t)fcol.size() > fptr[r] && fcol.back() == row[k].first) fval.back() += row[k].second;
-        else {
-          fcol.push_back(row[k].first);
-          fval.push_back(row[k].second);
-        }
-      }
-      fptr[r + 1] = (int64_t)fcol.size();
-    }
+    ConstraintSplit sp;
+    split_constraints(c, ptr.data(), ci.data(), cv.data(), ctx->v2e_h, slot_of, sp);
+    const std::vector<int64_t>& fptr = sp.fptr;
+    const std::vector<int32_t>& fcol = sp.fcol;
+    const std::vector<double>& fval = sp.fval;
+    ctx->con_pin = sp.pin;
     // Z = L_FF^-1 A_F^T, d rows of A_F per refined solve, and S = A_F Z (host)
     double* Z = nullptr;
     if ((st = dalloc(ctx, &Z, (size_t)c * nF)) != FFA_OK) return st;
@@ -1582,36 +1567,11 @@ ffa_status ffa_set_constraints(ffa_ctx* ctx, int32_t c, const int64_t* row_ptr, 
         for (int64_t q = fptr[r]; q < fptr[r + 1]; ++q)
           for (int j = 0; j < cnt; ++j) Sm[(size_t)r * c + c0 + j] += fval[q] * Xh[(size_t)fcol[q] * d + j];
     }
-    // Cholesky S = L L^T; a pivot that falls to 1e-10 of its row's diagonal means
-    // the row is (numerically) a combination of the rows before it, given the pins
-    std::vector<double> Lc((size_t)c * c, 0.0);
-    for (int i = 0; i < c; ++i)
-      for (int j = 0; j <= i; ++j) {
-        double a = 0.5 * (Sm[(size_t)i * c + j] + Sm[(size_t)j * c + i]);
-        for (int k = 0; k < j; ++k) a -= Lc[(size_t)i * c + k] * Lc[(size_t)j * c + k];
-        if (i == j) {
-          if (!(a > 1e-10 * Sm[(size_t)i * c + i]) || !(Sm[(size_t)i * c + i] > 0.0))
-            return fail(ctx, FFA_ERR_INVALID_ARG, "constraint row " + std::to_string(i) +
-                                                      " depends on the pins or on the rows before it");
-          Lc[(size_t)i * c + i] = std::sqrt(a);
-        } else {
-          Lc[(size_t)i * c + j] = a / Lc[(size_t)j * c + j];
-        }
-      }
-    // S^-1 column by column: L y = e_j, L^T x = y
-    std::vector<double> Sinv((size_t)c * c), y(c);
-    for (int j = 0; j < c; ++j) {
-      for (int i = 0; i < c; ++i) {
-        double a = i == j ? 1.0 : 0.0;
-        for (int k = 0; k < i; ++k) a -= Lc[(size_t)i * c + k] * y[k];
-        y[i] = a / Lc[(size_t)i * c + i];
-      }
-      for (int i = c - 1; i >= 0; --i) {
-        double a = y[i];
-        for (int k = i + 1; k < c; ++k) a -= Lc[(size_t)k * c + i] * Sinv[(size_t)k * c + j];
-        Sinv[(size_t)i * c + j] = a / Lc[(size_t)i * c + i];
-      }
-    }
+    std::vector<double> Sinv;
+    const int dep = schur_inverse(c, Sm, Sinv);
+    if (dep >= 0)
+      return fail(ctx, FFA_ERR_INVALID_ARG, "constraint row " + std::to_string(dep) +
+                                                " depends on the pins or on the rows before it");
     int64_t* dptr = nullptr;
     int32_t* dcol = nullptr;
     double *dval = nullptr, *dSinv = nullptr, *dnu = nullptr;
