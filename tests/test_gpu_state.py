@@ -51,8 +51,9 @@ def test_resumed_run_continues_the_uninterrupted_one(name, precision, tol):
     with Solver.from_workload(wl, precision=precision, check_every=5) as b:
         b.set_state(W, U, P, L)
         U2, P2, L2 = b.state()
-        # U passes through the quaternion (3D) or (cos, sin) (2D) of the device layout
-        assert np.abs(U2 - U).max() <= (1e-13 if precision == "fp64" else 1e-6)
+        # U passes through the quaternion (3D) or (cos, sin) (2D) of the device layout,
+        # renormalized on the way in (a float quaternion is unit only to a few ulp)
+        assert np.abs(U2 - U).max() <= (1e-13 if precision == "fp64" else 1e-5)
         assert np.array_equal(P2, P) and np.array_equal(L2, L)
         assert np.abs(b.W() - W).max() <= 1e-15 * np.abs(W).max()
         b.iterate(10, stop_at_tol=False)
