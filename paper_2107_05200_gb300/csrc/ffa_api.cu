@@ -204,6 +204,16 @@ ffa_status copy_in(ffa_ctx* ctx, std::vector<T>& dst, const T* src, size_t count
   return FFA_OK;
 }
 
+// host data out to a caller's buffer (host or device): on the context stream and
+// complete on return, whichever stream the caller then reads it from (a plain
+// synchronous copy from pageable memory may return before its last transfer lands)
+ffa_status copy_out(ffa_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return FFA_OK;
+  FFA_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+  FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  return FFA_OK;
+}
+
 // upload a double array as the local-step scalar type
 ffa_status upload_real(ffa_ctx* ctx, void** p, const std::vector<double>& h) {
   ffa_status st = dalloc_bytes(ctx, p, h.size() * ctx->rsz);
@@ -817,14 +827,22 @@ ffa_status apply_penalties(ffa_ctx* ctx) {
   const int rc = refactor(in, H.fac, msg);
   if (rc == 3) return fail(ctx, FFA_ERR_SINGULAR_SYSTEM, msg);
   if (rc != 0) return fail(ctx, FFA_ERR_INVALID_ARG, msg);
-  FFA_CUDA(cudaMemcpy(ctx->blocks, H.fac.blocks.data(), H.fac.blocks.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // uploads on the context stream, so that the kernels below and the next
+  // iteration are ordered after them (a synchronous copy from pageable memory may
+  // return before its last transfer lands); each host buffer outlives its copy
+  FFA_CUDA(cudaMemcpyAsync(ctx->blocks, H.fac.blocks.data(), H.fac.blocks.size() * sizeof(float),
+                           cudaMemcpyHostToDevice, s));
+  FFA_CUDA(cudaStreamSynchronize(s));
   std::vector<float>().swap(H.fac.blocks);
   OperatorArrays OA;
   operator_arrays(H.fac, H.nF, H.n_pin, Ap, Ai, Ax, Cp, Ci, Cx, OA);
-  FFA_CUDA(cudaMemcpy(ctx->ell_val, OA.ell_val.data(), OA.ell_val.size() * sizeof(double), cudaMemcpyHostToDevice));
+  FFA_CUDA(cudaMemcpyAsync(ctx->ell_val, OA.ell_val.data(), OA.ell_val.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           s));
   if (!OA.fc_val.empty()) {
-    FFA_CUDA(cudaMemcpy(ctx->fc_val, OA.fc_val.data(), OA.fc_val.size() * sizeof(double), cudaMemcpyHostToDevice));
-    FFA_CUDA(cudaMemcpy(ctx->cf_val, OA.cf_val.data(), OA.cf_val.size() * sizeof(double), cudaMemcpyHostToDevice));
+    FFA_CUDA(cudaMemcpyAsync(ctx->fc_val, OA.fc_val.data(), OA.fc_val.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             s));
+    FFA_CUDA(cudaMemcpyAsync(ctx->cf_val, OA.cf_val.data(), OA.cf_val.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             s));
   }
   launch_pin_rhs(ctx->d, ctx->nF, ctx->fc_ptr, ctx->fc_col, ctx->fc_val, ctx->pin_pos, ctx->cst, s);
   launch_rhs_terms(local_launch(ctx, false, ctx->vrec), s);
@@ -916,7 +934,7 @@ ffa_status tutte_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* bnd_in,
   for (int p = 0; p < nb; ++p)
     for (int k = 0; k < d; ++k) Wh[(size_t)bnd[p] * d + k] = bpos[(size_t)p * d + k];
   if (nF == 0) {
-    FFA_CUDA(cudaMemcpy(W_out, Wh.data(), Wh.size() * 8, cudaMemcpyDefault));
+    if ((st = copy_out(ctx, W_out, Wh.data(), Wh.size() * 8)) != FFA_OK) return st;
     if (rel_out) *rel_out = 0.0;
     return FFA_OK;
   }
@@ -1171,12 +1189,15 @@ ffa_status device_wait_status(ffa_ctx* ctx, const char* what) {
 // the current pinned positions move to the right-hand side
 ffa_status constraint_rhs(ffa_ctx* ctx) {
   const int d = ctx->d;
+  // on the context stream: ordered after the pin upload and before the next W step
   std::vector<double> pp((size_t)ctx->n_pin * d);
-  FFA_CUDA(cudaMemcpy(pp.data(), ctx->pin_pos, pp.size() * 8, cudaMemcpyDeviceToHost));
+  FFA_CUDA(cudaMemcpyAsync(pp.data(), ctx->pin_pos, pp.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   std::vector<double> bp = ctx->con_b;
   for (const auto& e : ctx->con_pin)
     for (int k = 0; k < d; ++k) bp[(size_t)e.row * d + k] -= e.val * pp[(size_t)e.slot * d + k];
-  FFA_CUDA(cudaMemcpy(ctx->con_bprime, bp.data(), bp.size() * 8, cudaMemcpyHostToDevice));
+  FFA_CUDA(cudaMemcpyAsync(ctx->con_bprime, bp.data(), bp.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   return FFA_OK;
 }
 
@@ -1533,8 +1554,7 @@ ffa_status ffa_get_penalties(ffa_ctx* ctx, double* mu) {
     FFA_CUDA(cudaStreamSynchronize(ctx->stream));
     for (int i = 0; i < m; ++i) h[i] = f[i];
   }
-  FFA_CUDA(cudaMemcpy(mu, h.data(), (size_t)m * 8, cudaMemcpyDefault));
-  return FFA_OK;
+  return copy_out(ctx, mu, h.data(), (size_t)m * 8);
 }
 
 ffa_status ffa_get_state(ffa_ctx* ctx, double* U, double* P, double* Lam) {
@@ -1558,9 +1578,10 @@ ffa_status ffa_get_state(ffa_ctx* ctx, double* U, double* P, double* Lam) {
   std::vector<double> oU((size_t)m * d * d), oP((size_t)m * d * d), oL((size_t)m * d * d);
   unpack_state(d, m, u.data(), p.data(), l.data(), oU.data(), oP.data(), oL.data());
   const size_t bytes = (size_t)m * d * d * 8;
-  if (U) FFA_CUDA(cudaMemcpy(U, oU.data(), bytes, cudaMemcpyDefault));
-  if (P) FFA_CUDA(cudaMemcpy(P, oP.data(), bytes, cudaMemcpyDefault));
-  if (Lam) FFA_CUDA(cudaMemcpy(Lam, oL.data(), bytes, cudaMemcpyDefault));
+  ffa_status st;
+  if (U && (st = copy_out(ctx, U, oU.data(), bytes)) != FFA_OK) return st;
+  if (P && (st = copy_out(ctx, P, oP.data(), bytes)) != FFA_OK) return st;
+  if (Lam && (st = copy_out(ctx, Lam, oL.data(), bytes)) != FFA_OK) return st;
   return FFA_OK;
 }
 
@@ -1585,12 +1606,16 @@ ffa_status ffa_set_state(ffa_ctx* ctx, const double* W, const double* U, const d
     std::string msg;
     if (!pack_state(d, m, hU.data(), hP.data(), hL.data(), u.data(), p.data(), l.data(), msg))
       return fail(ctx, FFA_ERR_INVALID_ARG, msg);
+    // copies on the context stream, complete before their host buffers go away,
+    // and ordered before the kernels below
     auto put = [&](void* dst, const std::vector<double>& h) -> ffa_status {
       if (ctx->fp64) {
-        FFA_CUDA(cudaMemcpy(dst, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+        FFA_CUDA(cudaMemcpyAsync(dst, h.data(), h.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        FFA_CUDA(cudaStreamSynchronize(ctx->stream));
       } else {
         std::vector<float> f(h.begin(), h.end());
-        FFA_CUDA(cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+        FFA_CUDA(cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        FFA_CUDA(cudaStreamSynchronize(ctx->stream));
       }
       return FFA_OK;
     };
