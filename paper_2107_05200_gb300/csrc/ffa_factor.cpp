@@ -8,6 +8,7 @@
 #include <cmath>
 #include <functional>
 #include <limits>
+#include <memory>
 #include <thread>
 
 namespace ffa {
@@ -176,82 +177,179 @@ void number_tree(const std::vector<TreeNode>& tree, int t, Factor& f, std::vecto
 // ---------------------------------------------------------------------------
 // dense kernels on a front stored row-major (lower triangle used), ld = N
 // ---------------------------------------------------------------------------
-inline double dot(const double* a, const double* b, int n) {
-  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  int k = 0;
-  for (; k + 4 <= n; k += 4) {
-    s0 += a[k] * b[k];
-    s1 += a[k + 1] * b[k + 1];
-    s2 += a[k + 2] * b[k + 2];
-    s3 += a[k + 3] * b[k + 3];
+// Register tiles of the dense kernels: kMR rows times kNR columns of an update,
+// the kNR columns contiguous in the packed operand so that the compiler's
+// vectorizer keeps kMR x kNR independent accumulators (no reductions, so no
+// reassociation and the same rounding whatever the target's vector width).
+constexpr int kMR = 4, kNR = 8;
+
+// acc[r][c] += sum_k a_r[k] * b[k * kNR + c], a_r the kMR rows of A (k contiguous)
+inline void tile_rows(int64_t K, const double* const a[kMR], const double* b, double acc[kMR][kNR]) {
+  for (int64_t k = 0; k < K; ++k) {
+    const double* bk = b + k * kNR;
+    for (int r = 0; r < kMR; ++r) {
+      const double ar = a[r][k];
+      for (int c = 0; c < kNR; ++c) acc[r][c] += ar * bk[c];
+    }
   }
-  for (; k < n; ++k) s0 += a[k] * b[k];
-  return (s0 + s1) + (s2 + s3);
+}
+
+// acc[r][c] += sum_k a[k * kNR + r0 + r] * b[k * kNR + c]: both operands packed
+inline void tile_packed(int64_t K, const double* a, const double* b, double acc[kMR][kNR]) {
+  for (int64_t k = 0; k < K; ++k) {
+    const double* ak = a + k * kNR;
+    const double* bk = b + k * kNR;
+    for (int r = 0; r < kMR; ++r) {
+      const double ar = ak[r];
+      for (int c = 0; c < kNR; ++c) acc[r][c] += ar * bk[c];
+    }
+  }
 }
 
 // Eliminate the first ns columns of the N x N front F; on return rows/cols
 // [0, ns) hold L11, rows [ns, N) x cols [0, ns) hold L21 and the trailing lower
 // triangle holds F22 - L21 L21^T.  Returns false if a pivot is not positive.
+// Right-looking in panels of kPanel columns: the diagonal block is factored in
+// place, the rows below it are packed kNR at a time (column k of the panel as kNR
+// consecutive values), solved against the diagonal block in that form and
+// written back, and the trailing lower triangle is updated tile by tile from the
+// packed panel.
 bool partial_cholesky(double* F, int N, int ns, int threads) {
-  const int NB = 64;
-  for (int k0 = 0; k0 < ns; k0 += NB) {
-    const int k1 = std::min(ns, k0 + NB);
+  constexpr int kPanel = 96;
+  std::vector<double> pack;
+  for (int k0 = 0; k0 < ns; k0 += kPanel) {
+    const int k1 = std::min(ns, k0 + kPanel);
+    const int w = k1 - k0;
     // diagonal block, left-looking within the panel
     for (int k = k0; k < k1; ++k) {
       double* Fk = F + (int64_t)k * N;
-      double dkk = Fk[k] - dot(Fk + k0, Fk + k0, k - k0);
+      double dkk = Fk[k];
+      for (int l = k0; l < k; ++l) dkk -= Fk[l] * Fk[l];
       if (!(dkk > 0.0) || !std::isfinite(dkk)) return false;
       dkk = std::sqrt(dkk);
       Fk[k] = dkk;
       for (int i = k + 1; i < k1; ++i) {
         double* Fi = F + (int64_t)i * N;
-        Fi[k] = (Fi[k] - dot(Fi + k0, Fk + k0, k - k0)) / dkk;
+        double v = Fi[k];
+        for (int l = k0; l < k; ++l) v -= Fi[l] * Fk[l];
+        Fi[k] = v / dkk;
       }
     }
-    // rows below the panel: row-wise triangular solve against the panel
     const int64_t nrows = N - k1;
-    const int64_t work = nrows * (k1 - k0) * (k1 - k0);
-    parallel_for(nrows, work > (1 << 20) ? threads : 1, 64, [&](int64_t b, int64_t e) {
-      for (int64_t r = b; r < e; ++r) {
-        double* Fi = F + (k1 + r) * N;
-        for (int k = k0; k < k1; ++k) {
-          const double* Fk = F + (int64_t)k * N;
-          Fi[k] = (Fi[k] - dot(Fi + k0, Fk + k0, k - k0)) / Fk[k];
+    if (nrows == 0) continue;
+    const int64_t nblk = (nrows + kNR - 1) / kNR;
+    pack.assign((size_t)nblk * w * kNR, 0.0);
+    // rows below the panel: pack, solve X L11^T = F21 by columns, write back
+    const int64_t tw = nrows * w * w;
+    parallel_for(nblk, tw > (1 << 20) ? threads : 1, 4, [&](int64_t b, int64_t e) {
+      for (int64_t blk = b; blk < e; ++blk) {
+        double* P = pack.data() + blk * w * kNR;
+        const int64_t r0 = blk * kNR;
+        const int nr = (int)std::min<int64_t>(kNR, nrows - r0);
+        for (int c = 0; c < nr; ++c) {
+          const double* Fi = F + (k1 + r0 + c) * N + k0;
+          for (int k = 0; k < w; ++k) P[k * kNR + c] = Fi[k];
+        }
+        for (int k = 0; k < w; ++k) {
+          const double* Lk = F + (int64_t)(k0 + k) * N + k0;
+          double v[kNR];
+          for (int c = 0; c < kNR; ++c) v[c] = P[k * kNR + c];
+          for (int l = 0; l < k; ++l) {
+            const double lkl = Lk[l];
+            for (int c = 0; c < kNR; ++c) v[c] -= P[l * kNR + c] * lkl;
+          }
+          const double dk = Lk[k];
+          for (int c = 0; c < kNR; ++c) P[k * kNR + c] = v[c] / dk;
+        }
+        for (int c = 0; c < nr; ++c) {
+          double* Fi = F + (k1 + r0 + c) * N + k0;
+          for (int k = 0; k < w; ++k) Fi[k] = P[k * kNR + c];
         }
       }
     });
-    // trailing update of the lower triangle below/right of the panel
-    const int w = k1 - k0;
-    const int64_t tw = nrows * nrows / 2 * w;
-    parallel_for(nrows, tw > (1 << 20) ? threads : 1, 16, [&](int64_t b, int64_t e) {
-      for (int64_t r = b; r < e; ++r) {
-        const int64_t i = k1 + r;
-        double* Fi = F + i * N;
-        const double* ai = Fi + k0;
-        int64_t j = k1;
-        for (; j + 4 <= i + 1; j += 4) {
-          const double* b0 = F + j * N + k0;
-          const double* b1 = b0 + N;
-          const double* b2 = b1 + N;
-          const double* b3 = b2 + N;
-          double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-          for (int k = 0; k < w; ++k) {
-            double x = ai[k];
-            s0 += x * b0[k];
-            s1 += x * b1[k];
-            s2 += x * b2[k];
-            s3 += x * b3[k];
+    // trailing update of the lower triangle: rows in tiles of kMR, columns in
+    // tiles of kNR up to the diagonal
+    const int64_t nrt = (nrows + kMR - 1) / kMR;
+    const int64_t uw = nrows * nrows / 2 * w;
+    parallel_for(nrt, uw > (1 << 20) ? threads : 1, 2, [&](int64_t b, int64_t e) {
+      for (int64_t rt = b; rt < e; ++rt) {
+        const int64_t i0 = rt * kMR;
+        const double* a = pack.data() + (i0 / kNR) * w * kNR + (i0 % kNR);
+        const int64_t jb_end = std::min<int64_t>(i0 + kMR - 1, nrows - 1) / kNR;
+        for (int64_t jb = 0; jb <= jb_end; ++jb) {
+          double acc[kMR][kNR] = {};
+          tile_packed(w, a, pack.data() + jb * w * kNR, acc);
+          for (int r = 0; r < kMR; ++r) {
+            const int64_t i = i0 + r;
+            if (i >= nrows) break;
+            double* Fi = F + (k1 + i) * N + k1;
+            for (int c = 0; c < kNR; ++c) {
+              const int64_t j = jb * kNR + c;
+              if (j > i) break;
+              Fi[j] -= acc[r][c];
+            }
           }
-          Fi[j] -= s0;
-          Fi[j + 1] -= s1;
-          Fi[j + 2] -= s2;
-          Fi[j + 3] -= s3;
         }
-        for (; j <= i; ++j) Fi[j] -= dot(ai, F + j * N + k0, w);
       }
     });
   }
   return true;
+}
+
+// B = [inv(L11); L21 inv(L11)] (column-major, leading dimension N, zero above the
+// diagonal of inv(L11); every entry of B is written) from the factored front F (row-major, L11 in rows/cols
+// [0, ns), L21 in rows [ns, N)).  Columns go kNR at a time: the columns of
+// inv(L11) by forward substitution of L11 X = I with the kNR right-hand sides
+// side by side, then the rows of L21 times them kMR at a time.
+void inverse_blocks(const double* F, int N, int ns, int threads, double* B) {
+  const int ms = N - ns;
+  const int64_t ncb = (ns + kNR - 1) / kNR;
+  const int64_t work = (int64_t)ns * ns * (ns + ms);
+  parallel_for(ncb, work > (1 << 21) ? threads : 1, 1, [&](int64_t b, int64_t e) {
+    std::vector<double> X((size_t)ns * kNR);
+    for (int64_t cb = b; cb < e; ++cb) {
+      const int j0 = (int)(cb * kNR);
+      const int nc = std::min(kNR, ns - j0);
+      // rows [j0, ns) of columns j0 .. j0+kNR of inv(L11); rows above are zero.
+      // Rows go kMR at a time: the part of the sum over rows already solved as
+      // one tile, then the small triangle inside the row block in order.
+      double* Xj = X.data() + (int64_t)j0 * kNR;
+      for (int i0 = j0; i0 < ns; i0 += kMR) {
+        const double* rows[kMR];
+        for (int r = 0; r < kMR; ++r) rows[r] = F + (int64_t)std::min(i0 + r, ns - 1) * N + j0;
+        double acc[kMR][kNR] = {};
+        tile_rows(i0 - j0, rows, Xj, acc);
+        for (int r = 0; r < kMR && i0 + r < ns; ++r) {
+          const int i = i0 + r;
+          const double* Li = F + (int64_t)i * N;
+          double v[kNR];
+          for (int c = 0; c < kNR; ++c) v[c] = ((i == j0 + c) ? 1.0 : 0.0) - acc[r][c];
+          for (int k = i0; k < i; ++k) {
+            const double lik = Li[k];
+            const double* xk = X.data() + (int64_t)k * kNR;
+            for (int c = 0; c < kNR; ++c) v[c] -= lik * xk[c];
+          }
+          const double di = Li[i];
+          for (int c = 0; c < kNR; ++c) X[(int64_t)i * kNR + c] = v[c] / di;
+        }
+      }
+      for (int c = 0; c < nc; ++c) {
+        double* col = B + (int64_t)(j0 + c) * N;
+        std::fill(col, col + j0 + c, 0.0);
+        for (int i = j0 + c; i < ns; ++i) col[i] = X[(int64_t)i * kNR + c];
+      }
+      // rows of L21 inv(L11): sum over k >= j0 (inv(L11) is lower triangular)
+      const int64_t K = ns - j0;
+      for (int a0 = 0; a0 < ms; a0 += kMR) {
+        const double* rows[kMR];
+        for (int r = 0; r < kMR; ++r) rows[r] = F + (int64_t)(ns + std::min(a0 + r, ms - 1)) * N + j0;
+        double acc[kMR][kNR] = {};
+        tile_rows(K, rows, Xj, acc);
+        for (int r = 0; r < kMR && a0 + r < ms; ++r)
+          for (int c = 0; c < nc; ++c) B[(int64_t)(j0 + c) * N + ns + a0 + r] = acc[r][c];
+      }
+    }
+  });
 }
 
 struct NumericWork {
@@ -270,7 +368,7 @@ int numeric(const FactorInput& in, Factor& f, std::string& err, int threads) {
   for (auto& sn : f.nodes) total = std::max<int64_t>(total, sn.blk_off + (int64_t)sn.ld * sn.ncol);
   f.blocks.assign(total, 0.0f);
   if (in.keep_double) f.blocks64.assign(total, 0.0);
-  std::vector<std::vector<double>> upd(nn);
+  std::vector<std::unique_ptr<double[]>> upd(nn);  // ms x ms, lower triangle used
   std::atomic<int> failed(-1);
 
   auto factor_node = [&](int s, NumericWork& wk, int dense_threads) {
@@ -278,78 +376,71 @@ int numeric(const FactorInput& in, Factor& f, std::string& err, int threads) {
     const Supernode& sn = f.nodes[s];
     const int ns = sn.ncol, ms = sn.nrow, N = ns + ms;
     const int32_t* R = f.rows.data() + sn.row_off;
-    std::vector<double> F((int64_t)N * N, 0.0);
+    // the front, row-major; only its lower triangle is ever read, so only that is
+    // zeroed (row by row, in parallel on the large fronts at the top of the tree)
+    const int64_t big = (int64_t)N * N > (1 << 22) ? dense_threads : 1;
+    std::unique_ptr<double[]> Fbuf(new double[(size_t)N * N]);
+    double* F = Fbuf.get();
+    parallel_for(N, big, 64, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i) std::fill(F + i * N, F + i * N + i + 1, 0.0);
+    });
     for (int q = 0; q < ns; ++q) wk.pos[sn.col0 + q] = q;
     for (int q = 0; q < ms; ++q) wk.pos[R[q]] = ns + q;
-    // original entries (lower triangle of the front)
-    for (int q = 0; q < ns; ++q) {
-      const int32_t c = sn.col0 + q;
-      const int32_t old = f.perm[c];
-      for (int64_t k = in.Ap[old]; k < in.Ap[old + 1]; ++k) {
-        const int32_t r = f.iperm[in.Ai[k]];
-        if (r < c) continue;
-        F[(int64_t)wk.pos[r] * N + q] += in.Ax[k];
+    // original entries (lower triangle of the front); each column is its own
+    parallel_for(ns, big, 64, [&](int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q) {
+        const int32_t c = sn.col0 + (int32_t)q;
+        const int32_t old = f.perm[c];
+        for (int64_t k = in.Ap[old]; k < in.Ap[old + 1]; ++k) {
+          const int32_t r = f.iperm[in.Ai[k]];
+          if (r < c) continue;
+          F[(int64_t)wk.pos[r] * N + q] += in.Ax[k];
+        }
       }
-    }
-    // extend-add of the children's update matrices
+    });
+    // extend-add of the children's update matrices, child after child; the rows
+    // of one child land on distinct rows of the front
     for (int ch : children[s]) {
       const Supernode& cn = f.nodes[ch];
       const int32_t* Rc = f.rows.data() + cn.row_off;
-      const std::vector<double>& Uc = upd[ch];
-      for (int a = 0; a < cn.nrow; ++a) {
-        const int pa = wk.pos[Rc[a]];
-        double* Fa = F.data() + (int64_t)pa * N;
-        const double* Ua = Uc.data() + (int64_t)a * cn.nrow;
-        for (int b = 0; b <= a; ++b) Fa[wk.pos[Rc[b]]] += Ua[b];
-      }
-      std::vector<double>().swap(upd[ch]);
+      const double* Uc = upd[ch].get();
+      const int64_t cbig = (int64_t)cn.nrow * cn.nrow > (1 << 22) ? dense_threads : 1;
+      parallel_for(cn.nrow, cbig, 32, [&](int64_t b0, int64_t e0) {
+        for (int64_t a = b0; a < e0; ++a) {
+          const int pa = wk.pos[Rc[a]];
+          double* Fa = F + (int64_t)pa * N;
+          const double* Ua = Uc + a * cn.nrow;
+          for (int64_t b = 0; b <= a; ++b) Fa[wk.pos[Rc[b]]] += Ua[b];
+        }
+      });
+      upd[ch].reset();
     }
     for (int q = 0; q < ns; ++q) wk.pos[sn.col0 + q] = -1;
     for (int q = 0; q < ms; ++q) wk.pos[R[q]] = -1;
-    if (!partial_cholesky(F.data(), N, ns, dense_threads)) {
+    if (!partial_cholesky(F, N, ns, dense_threads)) {
       failed.store(s);
       return;
     }
     // update matrix for the parent
     if (ms > 0) {
-      std::vector<double>& U = upd[s];
-      U.assign((int64_t)ms * ms, 0.0);
-      for (int a = 0; a < ms; ++a)
-        for (int b = 0; b <= a; ++b) U[(int64_t)a * ms + b] = F[(int64_t)(ns + a) * N + ns + b];
+      upd[s].reset(new double[(size_t)ms * ms]);
+      double* U = upd[s].get();
+      parallel_for(ms, (int64_t)ms * ms > (1 << 22) ? dense_threads : 1, 64, [&](int64_t b, int64_t e) {
+        for (int64_t a = b; a < e; ++a) std::copy(F + (ns + a) * N + ns, F + (ns + a) * N + ns + a + 1, U + a * ms);
+      });
     }
     if (ns == 0) return;
     // B_s = [inv(L11); L21 inv(L11)], column-major, leading dimension N
-    std::vector<double> B((int64_t)N * ns, 0.0);
-    const int64_t inv_work = (int64_t)ns * ns * ns;
-    parallel_for(ns, inv_work > (1 << 21) ? dense_threads : 1, 8, [&](int64_t b, int64_t e) {
+    std::unique_ptr<double[]> B(new double[(size_t)N * ns]);
+    inverse_blocks(F, N, ns, dense_threads, B.get());
+    parallel_for(ns, (int64_t)N * ns > (1 << 22) ? dense_threads : 1, 64, [&](int64_t b, int64_t e) {
       for (int64_t j = b; j < e; ++j) {
-        double* x = B.data() + j * N;  // column j, rows [0, ns)
-        x[j] = 1.0 / F[j * N + j];
-        for (int64_t i = j + 1; i < ns; ++i) {
-          const double* Li = F.data() + i * N;
-          double sacc = 0.0;
-          for (int64_t k = j; k < i; ++k) sacc += Li[k] * x[k];
-          x[i] = -sacc / Li[i];
-        }
+        float* dst = f.blocks.data() + sn.blk_off + j * sn.ld;
+        const double* src = B.get() + j * N;
+        for (int i = 0; i < N; ++i) dst[i] = static_cast<float>(src[i]);
+        if (in.keep_double) std::copy(src, src + N, f.blocks64.begin() + sn.blk_off + j * sn.ld);
       }
     });
-    const int64_t m_work = (int64_t)ms * ns * ns;
-    parallel_for(ms, m_work > (1 << 21) ? dense_threads : 1, 8, [&](int64_t b, int64_t e) {
-      for (int64_t a = b; a < e; ++a) {
-        const double* La = F.data() + (int64_t)(ns + a) * N;
-        for (int j = 0; j < ns; ++j) {
-          const double* col = B.data() + (int64_t)j * N;
-          B[(int64_t)j * N + ns + a] = dot(La + j, col + j, ns - j);
-        }
-      }
-    });
-    for (int j = 0; j < ns; ++j) {
-      float* dst = f.blocks.data() + sn.blk_off + (int64_t)j * sn.ld;
-      const double* src = B.data() + (int64_t)j * N;
-      for (int i = 0; i < N; ++i) dst[i] = static_cast<float>(src[i]);
-      if (in.keep_double)
-        std::copy(src, src + N, f.blocks64.begin() + sn.blk_off + (int64_t)j * sn.ld);
-    }
   };
 
   // independent subtrees go to a pool; the top of the tree runs with parallel dense kernels
