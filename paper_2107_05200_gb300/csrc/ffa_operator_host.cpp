@@ -2,6 +2,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <utility>
 
 namespace ffa {
@@ -77,47 +78,79 @@ void assemble_operator(const OperatorHost& H, const double* mu, std::vector<int6
       }
     }
   };
+  // Rows are independent: contiguous chunks of rows are assembled by separate
+  // threads into their own arrays, then concatenated in row order, so the result
+  // does not depend on the number of threads.
+  struct Chunk {
+    std::vector<int32_t> ai, ci;
+    std::vector<double> ax, cx;
+    std::vector<int32_t> na, nc;  // entries per row
+  };
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nchunk = std::max(1, std::min<int>(hw ? (int)hw : 1, nF / 4096 + 1));
+  std::vector<Chunk> chunks(nchunk);
+  auto assemble_rows = [&](int ck) {
+    Chunk& C = chunks[ck];
+    const int f0 = (int)((int64_t)nF * ck / nchunk), f1 = (int)((int64_t)nF * (ck + 1) / nchunk);
+    std::vector<int32_t> pos(H.n, -1), touched;
+    std::vector<double> acc;
+    std::vector<std::pair<int32_t, double>> fr, cr;
+    for (int f = f0; f < f1; ++f) {
+      const int v = H.free_vertex[f];
+      touched.clear();
+      acc.clear();
+      for (int64_t q = H.inc_ptr[v]; q < H.inc_ptr[v + 1]; ++q) {
+        const int i = H.inc[q] / (d + 1), j = H.inc[q] % (d + 1);
+        double gj[3], gl[3];
+        grad_of(i, j, gj);
+        for (int l = 0; l <= d; ++l) {
+          grad_of(i, l, gl);
+          double dotv = 0;
+          for (int a = 0; a < d; ++a) dotv += gj[a] * gl[a];
+          const int u = H.T[(int64_t)i * (d + 1) + l];
+          if (pos[u] < 0) {
+            pos[u] = (int32_t)touched.size();
+            touched.push_back(u);
+            acc.push_back(0.0);
+          }
+          acc[pos[u]] += mu[i] * dotv;
+        }
+      }
+      fr.clear();
+      cr.clear();
+      for (size_t k = 0; k < touched.size(); ++k) {
+        const int u = touched[k];
+        if (H.free_of[u] >= 0) fr.push_back({H.free_of[u], acc[k]});
+        else cr.push_back({H.v2pin[u], acc[k]});
+        pos[u] = -1;
+      }
+      std::sort(fr.begin(), fr.end());
+      std::sort(cr.begin(), cr.end());
+      for (auto& pr : fr) { C.ai.push_back(pr.first); C.ax.push_back(pr.second); }
+      for (auto& pr : cr) { C.ci.push_back(pr.first); C.cx.push_back(pr.second); }
+      C.na.push_back((int32_t)fr.size());
+      C.nc.push_back((int32_t)cr.size());
+    }
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int ck = 1; ck < nchunk; ++ck) pool.emplace_back(assemble_rows, ck);
+    assemble_rows(0);
+    for (auto& th : pool) th.join();
+  }
   Ap.assign(nF + 1, 0);
   Cp.assign(nF + 1, 0);
   Ai.clear(); Ax.clear(); Ci.clear(); Cx.clear();
-  std::vector<int32_t> pos(H.n, -1), touched;
-  std::vector<double> acc;
-  std::vector<std::pair<int32_t, double>> fr, cr;
-  for (int f = 0; f < nF; ++f) {
-    const int v = H.free_vertex[f];
-    touched.clear();
-    acc.clear();
-    for (int64_t q = H.inc_ptr[v]; q < H.inc_ptr[v + 1]; ++q) {
-      const int i = H.inc[q] / (d + 1), j = H.inc[q] % (d + 1);
-      double gj[3], gl[3];
-      grad_of(i, j, gj);
-      for (int l = 0; l <= d; ++l) {
-        grad_of(i, l, gl);
-        double dotv = 0;
-        for (int a = 0; a < d; ++a) dotv += gj[a] * gl[a];
-        const int u = H.T[(int64_t)i * (d + 1) + l];
-        if (pos[u] < 0) {
-          pos[u] = (int32_t)touched.size();
-          touched.push_back(u);
-          acc.push_back(0.0);
-        }
-        acc[pos[u]] += mu[i] * dotv;
-      }
+  int f = 0;
+  for (const Chunk& C : chunks) {
+    Ai.insert(Ai.end(), C.ai.begin(), C.ai.end());
+    Ax.insert(Ax.end(), C.ax.begin(), C.ax.end());
+    Ci.insert(Ci.end(), C.ci.begin(), C.ci.end());
+    Cx.insert(Cx.end(), C.cx.begin(), C.cx.end());
+    for (size_t r = 0; r < C.na.size(); ++r, ++f) {
+      Ap[f + 1] = Ap[f] + C.na[r];
+      Cp[f + 1] = Cp[f] + C.nc[r];
     }
-    fr.clear();
-    cr.clear();
-    for (size_t k = 0; k < touched.size(); ++k) {
-      const int u = touched[k];
-      if (H.free_of[u] >= 0) fr.push_back({H.free_of[u], acc[k]});
-      else cr.push_back({H.v2pin[u], acc[k]});
-      pos[u] = -1;
-    }
-    std::sort(fr.begin(), fr.end());
-    std::sort(cr.begin(), cr.end());
-    for (auto& pr : fr) { Ai.push_back(pr.first); Ax.push_back(pr.second); }
-    for (auto& pr : cr) { Ci.push_back(pr.first); Cx.push_back(pr.second); }
-    Ap[f + 1] = (int64_t)Ai.size();
-    Cp[f + 1] = (int64_t)Ci.size();
   }
 }
 

@@ -3,9 +3,10 @@
 //     column k the gradient of coordinate k) on triangles and tetrahedra, an
 //     isometric copy of a planar triangle in R^3 has a rotation as its intrinsic
 //     Jacobian, w is the area / volume, degenerate elements are refused;
-//   * assemble_operator: L_FF is symmetric with ascending columns, L 1 = 0 (rows
-//     of [L_FF L_FC] sum to zero), and the quadratic form and the pin block equal
-//     sum_i mu_i |G_i x|^2 and (G^T M G x)_F computed element by element;
+//   * assemble_operator (one thread and, on the larger grid, several): L_FF is
+//     symmetric with ascending columns, L 1 = 0 (rows of [L_FF L_FC] sum to zero),
+//     and the quadratic form and the pin block equal sum_i mu_i |G_i x|^2 and
+//     (G^T M G x)_F computed element by element;
 //   * operator_arrays: the ELL rows in elimination order hold exactly the CSR row
 //     of perm[c] (padding: own column, value 0), L_FC by elimination row, and L_CF
 //     its transpose.
@@ -130,9 +131,10 @@ static void check_geometry(std::mt19937_64& rng) {
   }
 }
 
-// a jittered nx x ny grid of triangles (two per cell), its left column pinned
-static void check_operator(std::mt19937_64& rng) {
-  const int nx = 9, ny = 7, d = 2, n = nx * ny;
+// a jittered nx x ny grid of triangles (two per cell), its left column pinned;
+// grids above a few thousand free vertices are assembled by several threads
+static void check_operator(std::mt19937_64& rng, int nx, int ny) {
+  const int d = 2, n = nx * ny;
   std::uniform_real_distribution<double> J(-0.2, 0.2), M(0.5, 3.0);
   std::vector<double> V(n * 2);
   for (int j = 0; j < ny; ++j)
@@ -288,7 +290,8 @@ static void check_operator(std::mt19937_64& rng) {
 int main() {
   std::mt19937_64 rng(3);
   check_geometry(rng);
-  check_operator(rng);
+  check_operator(rng, 9, 7);
+  check_operator(rng, 90, 80);
   if (!fails) std::printf("ok\n");
   return fails ? 1 : 0;
 }
