@@ -1,0 +1,54 @@
+"""The benchmark's command-line contract on a machine without a GPU: the oracle
+arm (`--impl reference`, the plain FP64 CPU restatement timed on the host) prints
+one JSON line with the keys the contract names, and the GPU arm refuses to run
+instead of falling back to the CPU."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _cuda_available():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def _run(args, timeout=600):
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, capture_output=True,
+                          text=True, timeout=timeout)
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = _run(["--impl", "reference", "--steps", "2", "--warmup", "0"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout
+    out = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in out, key
+    assert out["impl"] == "reference"
+    assert out["value"] > 0 and out["ms_per_step"] > 0
+    assert out["steps"] == 2 and out["warmup"] == 0 and out["n_gpus"] == 1
+    assert out["higher_is_better"] is True
+    assert "workload" in out["config"]
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == out["value"]
+    e2e = out["e2e"]
+    assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.skipif(_cuda_available(), reason="a CUDA device is present")
+def test_gpu_arm_refuses_without_a_device():
+    r = _run(["--steps", "1", "--warmup", "0"])
+    assert r.returncode != 0
+    assert "CUDA" in (r.stdout + r.stderr)
+    assert not any(ln.strip().startswith("{") for ln in r.stdout.splitlines())
