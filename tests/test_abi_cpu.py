@@ -77,3 +77,26 @@ def test_bad_parameters_are_rejected_before_any_device_work():
     lib.ffa_default_params(C.byref(p))
     mesh.d = 4
     assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
+
+
+def test_no_cpu_fallback_without_a_device():
+    """Valid inputs on a machine without a GPU: creation fails with FFA_ERR_CUDA and
+    a message, rather than running anywhere else; the state and constraint entry
+    points reject a NULL context."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    native, lib = _lib()
+    V = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    T = np.array([[0, 1, 2], [1, 3, 2]], np.int32)
+    pins = np.array([0], np.int32)
+    pos = np.zeros((1, 2))
+    mesh = native.Mesh(4, 2, 2, 2, C.c_void_p(V.ctypes.data), C.c_void_p(T.ctypes.data))
+    out = C.c_void_p()
+    st = lib.ffa_create(C.byref(mesh), C.c_void_p(pins.ctypes.data), 1, C.c_void_p(pos.ctypes.data), None, None,
+                        C.byref(out))
+    assert st == 4 and out.value is None
+    assert lib.ffa_last_error(None)
+    assert lib.ffa_set_state(None, None, None, None, None) == 1
+    assert lib.ffa_set_constraints(None, 1, None, None, None, None) == 1
