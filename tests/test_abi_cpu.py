@@ -100,3 +100,12 @@ def test_no_cpu_fallback_without_a_device():
     assert lib.ffa_last_error(None)
     assert lib.ffa_set_state(None, None, None, None, None) == 1
     assert lib.ffa_set_constraints(None, 1, None, None, None, None) == 1
+
+
+def test_build_compiles_every_source_file():
+    """Every .cu and .cpp under csrc/ is a translation unit of libffadmm.so (the GPU
+    box rebuilds from build.py alone)."""
+    from paper_2107_05200_gb300 import build
+    csrc = os.path.join(os.path.dirname(os.path.abspath(build.__file__)), "csrc")
+    on_disk = {f for f in os.listdir(csrc) if f.endswith((".cu", ".cpp"))}
+    assert on_disk == set(build.CU_SOURCES) | set(build.CXX_SOURCES)
