@@ -141,7 +141,9 @@ static double backward_error(const Sparse& S, const Factor& f, std::mt19937_64& 
 int main() {
   std::mt19937_64 rng(5);
   struct Case { int nx, ny, nz; double spread; int leaf; };
-  const Case cases[] = {{23, 17, 1, 0.5, 16}, {31, 29, 1, 3.0, 64}, {9, 8, 7, 0.5, 16}, {12, 11, 10, 3.0, 64}};
+  // the last case is a larger 3D grid (fronts up to about 1300 rows)
+  const Case cases[] = {{23, 17, 1, 0.5, 16}, {31, 29, 1, 3.0, 64}, {9, 8, 7, 0.5, 16}, {12, 11, 10, 3.0, 64},
+                        {30, 29, 28, 1.0, 64}};
   for (const Case& cs : cases) {
     const std::string tag = std::to_string(cs.nx) + "x" + std::to_string(cs.ny) + "x" + std::to_string(cs.nz) +
                             " spread " + std::to_string(cs.spread);
