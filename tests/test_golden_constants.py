@@ -98,3 +98,21 @@ def test_library_defaults_match():
     assert lib.ffa_default_params(C.byref(p)) == 0
     assert p.rescale_rho == K["rescale_rho"]
     assert p.penalty_schedule == 0
+    assert p.eps_abs == K["eps_abs_default"] and p.eps_rel == K["eps_rel_default"]
+
+
+def test_termination_tolerances():
+    """The oracle's default tolerances are the printed ones for most examples; the 3D deformation
+    workload takes the printed deformation values; the other workloads keep the printed ratio
+    eps_rel / eps_abs = 10 for the tolerance their configuration states."""
+    import inspect
+    from paper_2107_05200_gb300 import workloads as wk
+    sig = inspect.signature(admm.Oracle.__init__).parameters
+    assert sig["eps_abs"].default == K["eps_abs_default"]
+    assert sig["eps_rel"].default == K["eps_rel_default"]
+    cube = wk.cube_deform(cells=2)
+    assert cube.eps_abs == K["eps_abs_deformation"] and cube.eps_rel == K["eps_rel_deformation"]
+    assert K["eps_rel_default"] / K["eps_abs_default"] == pytest.approx(10.0)
+    assert K["eps_rel_deformation"] / K["eps_abs_deformation"] == pytest.approx(10.0)
+    disk = wk.uv_disk(grid=8)
+    assert disk.eps_rel / disk.eps_abs == pytest.approx(10.0)
