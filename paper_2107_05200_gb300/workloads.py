@@ -189,8 +189,17 @@ def tutte_embedding(V: np.ndarray, T: np.ndarray, boundary: np.ndarray,
 # ----------------------------------------------------------------------------
 
 def _noise_scale_for_flips(base: np.ndarray, xi: np.ndarray, T: np.ndarray,
-                           target: float, hi: float) -> float:
-    """Bisection on s so that base + s*xi has the target fraction of flipped elements."""
+                           target: float, hi: float, margin: float = 1e-6) -> float:
+    """Noise scale s such that base + s*xi has the target fraction of flipped
+    elements and no element sits at the flip threshold.
+
+    Bisection finds the smallest s, to rounding, at which the flipped fraction
+    reaches the target.  At that s one element's signed measure is zero up to
+    rounding, so whether it counts as flipped would be decided by the order in
+    which each program forms its determinant.  The scale is therefore moved past
+    the crossing by relative steps of 1e-3 until every element's signed measure
+    is at least `margin` times its measure in `base` away from zero.
+    """
     lo = 0.0
     for _ in range(60):
         mid = 0.5 * (lo + hi)
@@ -198,7 +207,12 @@ def _noise_scale_for_flips(base: np.ndarray, xi: np.ndarray, T: np.ndarray,
             lo = mid
         else:
             hi = mid
-    return 0.5 * (lo + hi)
+    ref = np.abs(_signed_measure(base, T))
+    for k in range(1, 500):
+        s = hi * (1.0 + 1e-3 * k)
+        if np.all(np.abs(_signed_measure(base + s * xi, T)) >= margin * ref):
+            return s
+    raise RuntimeError("no noise scale near the target keeps every element off the flip threshold")
 
 
 def uv_disk(grid: int = 48, seed: int = 1, target_flip: float | None = 0.03,
