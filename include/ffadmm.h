@@ -114,6 +114,14 @@ typedef struct {
                               at most this height whose supernodes are all small run as one task
                               of the forward / backward pass (one block, supernodes in order);
                               0 off, -1 the library's choice (default), at most 8 */
+  int32_t prox_h;          /* proximal U term of eq. proximalfunctionu: 0 h_i = 0 (default; Sec. 6
+                              switches it off when many elements start flipped), 1 h_i at the bound
+                              of Prop. 1, h_i = 4 w_i^2 B_i^2 / mu_i with B_i = sqrt(5 (1 + |grad
+                              f(P_i)|^2)) (gamma = 1, eps = 0 as Sec. 6 sets them), B_i from the P
+                              given by ffa_init (P^0) or ffa_set_state.  The U step then takes
+                              Q_i = (J_i + Lambda_i) P_i + (h_i / mu_i) U_i^{k-1}.  Fixed penalties,
+                              the paper's local step and single meshes only (not with
+                              penalty_schedule 1, local_variant 1, batches or ffa_forward_unrolled). */
 } ffa_params;
 
 typedef struct {
@@ -183,7 +191,7 @@ ffa_status ffa_tutte(const ffa_mesh* mesh, const int32_t* boundary, int32_t n_bo
 /* Fill *p with the defaults: symmetric Dirichlet, rho 1, eps_abs 1e-6, eps_rel 1e-5,
  * check_every 10, require_flip_free 1, FP32 local step, 2 refine sweeps,
  * leaf size 64, all host threads, solve schedule 1, fixed penalties (penalty
- * schedule 0), rescale_rho 5. */
+ * schedule 0), rescale_rho 5, the paper's local step, prox_h 0. */
 ffa_status ffa_default_params(ffa_params* p);
 
 /* Prepare a solver for one mesh: element gradients and measures w_i (Supplemental,
@@ -244,7 +252,7 @@ ffa_status ffa_set_constraints(ffa_ctx* ctx, int32_t c, const int64_t* row_ptr, 
  * pinned positions take effect from the first W step on. */
 ffa_status ffa_init(ffa_ctx* ctx, const double* W0);
 
-/* Run up to max_iter iterations of Algorithm 1 (W, U, P, Lambda steps, h = 0).
+/* Run up to max_iter iterations of Algorithm 1 (W, U, P, Lambda steps; h_i per prox_h).
  * With stop_at_tol = 1 the termination test of eq. primaldualthresholds (plus flip-freeness when
  * require_flip_free) is evaluated every check_every iterations and the call
  * returns as soon as it passes; with stop_at_tol = 0 exactly max_iter iterations
@@ -340,6 +348,19 @@ ffa_status ffa_backward_unrolled(ffa_ctx* ctx, const double* dL_dW, double* dL_d
  * leaves the multiplier term A_F^T nu in that residual. */
 ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel_residual);
 
+/* Failure detection of the W step's device-side waits (the paper has no
+ * counterpart: its back-substitution runs on one CPU thread).  With solve_schedule
+ * 1 each block of a triangular pass polls its queue slot until a finished
+ * supernode fills it; a wait that sees an empty slot for more than `polls` polls
+ * (each about 100 ns; the default is 2^22, about 0.4 s) gives up, sets a device
+ * flag that makes every other wait give up too, and the block exits.  The call
+ * then returns FFA_ERR_TIMEOUT and the iterate is invalid; the context stays
+ * usable (the next W step resets the queues), so a caller may restore the limit
+ * and call ffa_init or ffa_set_state again.  polls = 0 gives up at the first
+ * empty poll.  Takes effect from the next ffa_iterate (captured graphs are
+ * dropped).  Errors: FFA_ERR_INVALID_ARG (NULL context, polls < 0). */
+ffa_status ffa_set_wait_limit(ffa_ctx* ctx, int64_t polls);
+
 /* Many independent meshes solved together (the paper solves one mesh at a time;
  * this batches its Algorithm 1 over independent problems).  Meshes of equal
  * (d, d_in) are concatenated into one block-diagonal problem: one factorization
@@ -388,15 +409,23 @@ ffa_status ffa_batch_get_W(ffa_batch* b, int32_t mesh, double* W_out);
  *   E             : device pointer to one double, written by the call.
  *   stream        : cudaStream_t to run on (NULL = the legacy default stream).
  * The call only enqueues two kernels on the stream and returns; E is valid once
- * the stream has reached that point.  The per-block partial sums live in one
- * fixed static device array (1 MiB, held by every GPU that loads the library
- * until the process exits).  The first call on each device looks up that array's
- * device address (cudaGetSymbolAddress, with that device current), so make the
- * first call on a device before any stream capture.  All calls share the array:
- * each call overwrites the slots it reads, so nothing has to be cleared, but calls
- * that overlap on the GPU (other streams, other host threads) race on it.
+ * the stream has reached that point.  Because it never waits for its kernels, an
+ * invalid mesh is reported in *E: an element with a vertex index outside [0, n)
+ * (skipped before any load through that index) or a source element of zero
+ * measure makes *E a NaN, whereas a valid mesh with some det (G W)_i <= 0 gives
+ * +infinity (ffa_create refuses the same meshes with FFA_ERR_INVALID_ARG and
+ * FFA_ERR_DEGENERATE_ELEMENT).  The per-block partial sums live in one fixed
+ * static device array (1.5 MiB, held by every GPU that loads the library until the
+ * process exits).  Every call looks up that array's device address on the current
+ * device (cudaGetSymbolAddress); the first call on a device also loads the
+ * library's device code there, so make the first call on a device before any
+ * stream capture.  All calls share the array: each call overwrites the slots it
+ * reads, so nothing has to be cleared, but calls that overlap on the GPU (other
+ * streams, other host threads) race on it.
  * Errors: FFA_ERR_INVALID_ARG (sizes, NULL pointers, unknown energy),
- * FFA_ERR_CUDA; the message is returned by ffa_last_error(NULL). */
+ * FFA_ERR_CUDA (also when a CUDA error from earlier work is pending on the calling
+ * thread; it is reported and left pending); the message is returned by
+ * ffa_last_error(NULL). */
 ffa_status ffa_energy_noalloc(int32_t n, int32_t m, int32_t d, int32_t d_in, const double* V,
                               const int32_t* T, const double* W, ffa_energy_kind energy, double* E,
                               void* stream);

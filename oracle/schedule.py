@@ -85,6 +85,14 @@ def mu_min(P: np.ndarray, w: np.ndarray, energy_name: str) -> np.ndarray:
     return 0.5 * (-w + np.sqrt(w * w + 16.0 * w * w * F * F))
 
 
+def h_bound(P: np.ndarray, w: np.ndarray, mu: np.ndarray, energy_name: str) -> np.ndarray:
+    """The proximal weight of eq. proximalfunctionu at the bound of Proposition 1,
+    h_i = 4 gamma w_i^2 B_i^2 / mu_i + 2 eps with gamma = 1, eps = 0 (Sec. 6: "h_i is set to
+    its value from" the convergence section), B_i = sqrt(5 (1 + |grad f(P_i)|^2)) as for mu_min."""
+    B2 = 5.0 * (1.0 + grad_f_norm(P, energy_name) ** 2)
+    return 4.0 * w * w * B2 / mu
+
+
 def rescale(mu, Lam, e_prim_i, e_dual_i, mu_lo, rho: float = RESCALE_RHO):
     """One rescaling of every element's penalty and scaled multiplier (Sec. 6)."""
     new = mu.copy()

@@ -25,6 +25,7 @@ EXPORTED = [
     "ffa_forward_unrolled", "ffa_backward_unrolled",
     "ffa_batch_create", "ffa_batch_destroy", "ffa_batch_last_error", "ffa_batch_init", "ffa_batch_iterate",
     "ffa_batch_get_W", "ffa_autotune", "ffa_batch_autotune", "ffa_batch_groups", "ffa_tutte",
+    "ffa_set_wait_limit",
 ]
 
 
@@ -40,7 +41,8 @@ class Params(C.Structure):
                 ("refine_sweeps", C.c_int32), ("nd_leaf_size", C.c_int32),
                 ("host_threads", C.c_int32), ("solve_schedule", C.c_int32),
                 ("penalty_schedule", C.c_int32), ("rescale_rho", C.c_double),
-                ("local_variant", C.c_int32), ("solve_subtree_height", C.c_int32 * 2)]
+                ("local_variant", C.c_int32), ("solve_subtree_height", C.c_int32 * 2),
+                ("prox_h", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -137,6 +139,7 @@ def load() -> C.CDLL:
         "ffa_batch_autotune": ([vp, i32, C.POINTER(Tuning)], C.c_int),
         "ffa_batch_groups": ([vp], C.c_int32),
         "ffa_tutte": ([C.POINTER(Mesh), vp, i32, vp, C.POINTER(Params), vp, vp, C.POINTER(dbl)], C.c_int),
+        "ffa_set_wait_limit": ([vp, C.c_int64], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

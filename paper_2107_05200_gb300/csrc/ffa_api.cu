@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -123,6 +124,7 @@ struct ffa_ctx {
   int subtree_height_b = 1;     // (forward / backward pass; measured best on the benchmark cube)
   cudaEvent_t solve_ev[3] = {nullptr, nullptr, nullptr};  // set only while ffa_profile_phases runs
   int32_t* err_flag = nullptr;
+  long long spin_limit = kDefaultSpinLimit;  // ffa_set_wait_limit
   int grid_f = 0, grid_b = 0;
   std::vector<Supernode> nodes_h;  // host copy of the supernode table (task lists are rebuilt from it)
   int n_levels = 0;
@@ -268,6 +270,7 @@ SolveData solve_data(ffa_ctx* ctx) {
   for (int i = 0; i < 3; ++i) S.ev[i] = ctx->solve_ev[i];
   S.n_nodes = (int)ctx->nodes_h.size();
   S.err_flag = ctx->err_flag;
+  S.spin_limit = ctx->spin_limit;
   S.grid_f = ctx->grid_f;
   S.grid_b = ctx->grid_b;
   S.y = ctx->y;
@@ -428,6 +431,10 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   else if (p.solve_subtree_height[0] < -1 || p.solve_subtree_height[0] > 8 || p.solve_subtree_height[1] < -1 ||
            p.solve_subtree_height[1] > 8)
     msg = "solve_subtree_height must be in [-1, 8]";
+  else if (p.prox_h != 0 && p.prox_h != 1) msg = "prox_h must be 0 or 1";
+  else if (p.prox_h == 1 && p.penalty_schedule == 1)
+    msg = "prox_h 1 is implemented with fixed penalties (its bound depends on mu_i)";
+  else if (p.prox_h == 1 && p.local_variant == 1) msg = "the joint (U, P) variant has no proximal U term";
   else return FFA_OK;
   return FFA_ERR_INVALID_ARG;
 }
@@ -733,6 +740,10 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   }
   ctx->e.joint = ctx->prm.local_variant == 1 ? 1 : 0;
   const size_t R = ctx->rsz;
+  if (ctx->prm.prox_h == 1) {
+    if (batch) return fail(ctx, FFA_ERR_INVALID_ARG, "prox_h 1 is implemented for single meshes");
+    if ((st = dalloc_bytes(ctx, &ctx->e.hmu, (size_t)m * R)) != FFA_OK) return st;
+  }
   if ((st = dalloc_bytes(ctx, &ctx->e.P, (size_t)m * (d == 2 ? 3 : 6) * R)) != FFA_OK) return st;
   if ((st = dalloc_bytes(ctx, &ctx->e.Lam, (size_t)m * d * d * R)) != FFA_OK) return st;
   if ((st = dalloc_bytes(ctx, &ctx->e.U, (size_t)m * (d == 2 ? 2 : 4) * R)) != FFA_OK) return st;
@@ -773,7 +784,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   const int64_t ps = d == 2 ? 3 : 6, us = d == 2 ? 2 : 4;
   ctx->info.bytes_local_step =
       (int64_t)m * ((d + 1) * 4 + (int64_t)(d * d + 2) * R + (ps + d * d) * R * 2 + us * R + (int64_t)(d + 1) * d * R) +
-      (int64_t)n * d * 16;
+      (int64_t)n * d * 16 + (ctx->e.hmu ? (int64_t)m * (us + 1) * R : 0);   // prox_h: U^{k-1} and h/mu read
   int64_t nz = 0;
   for (const Supernode& sn : fac.nodes) nz += (int64_t)sn.ncol * sn.nrow + (int64_t)sn.ncol * (sn.ncol + 1) / 2;
   int64_t nstruct = 0;
@@ -1270,6 +1281,7 @@ ffa_status ffa_default_params(ffa_params* p) {
   p->rescale_rho = 5.0;
   p->local_variant = 0;
   p->solve_subtree_height[0] = p->solve_subtree_height[1] = -1;
+  p->prox_h = 0;
   return FFA_OK;
 }
 
@@ -1436,7 +1448,7 @@ ffa_status ffa_set_constraints(ffa_ctx* ctx, int32_t c, const int64_t* row_ptr, 
   return constraint_rhs(ctx);
 }
 
-ffa_status ffa_init(ffa_ctx* ctx, const double* W0) {
+static ffa_status init_body(ffa_ctx* ctx, const double* W0) {
   if (!ctx) return FFA_ERR_INVALID_ARG;
   if (!W0) return fail(ctx, FFA_ERR_INVALID_ARG, "W0 is NULL");
   ctx->err.clear();
@@ -1444,6 +1456,10 @@ ffa_status ffa_init(ffa_ctx* ctx, const double* W0) {
   if (st != FFA_OK) return st;
   launch_init_polar(local_launch(ctx, false, ctx->vrec), ctx->stream);
   FFA_CUDA(cudaGetLastError());
+  if (ctx->e.hmu) {
+    launch_prox_weight(local_launch(ctx, false, ctx->vrec), ctx->stream);
+    FFA_CUDA(cudaGetLastError());
+  }
   if (ctx->prm.penalty_schedule == 1) {
     // Algorithm 2: mu_i = max(mu_min,i, w_i) from P^0, then decompose(L)
     launch_penalty(local_launch(ctx, false, ctx->vrec), 0, ctx->mu64, ctx->prm.rescale_rho, ctx->stream);
@@ -1458,7 +1474,7 @@ ffa_status ffa_init(ffa_ctx* ctx, const double* W0) {
   return FFA_OK;
 }
 
-ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_stats* stats) {
+static ffa_status iterate_body(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_stats* stats) {
   if (!ctx) return FFA_ERR_INVALID_ARG;
   ctx->err.clear();
   if (!ctx->initialized) return fail(ctx, FFA_ERR_NOT_INITIALIZED, "ffa_init has not been called");
@@ -1525,6 +1541,34 @@ ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_
   ctx->last.rescales = ctx->n_rescales;
   if (stats) *stats = ctx->last;
   return FFA_OK;
+}
+
+// The penalty schedule's host work (operator assembly, factorization on several
+// threads) can throw; nothing may leave the C ABI as an exception.
+ffa_status ffa_init(ffa_ctx* ctx, const double* W0) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  try {
+    return init_body(ctx, W0);
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, FFA_ERR_OOM, "host allocation failed in ffa_init");
+  } catch (const std::exception& e) {
+    return fail(ctx, FFA_ERR_INVALID_ARG, std::string("ffa_init: ") + e.what());
+  } catch (...) {
+    return fail(ctx, FFA_ERR_INVALID_ARG, "ffa_init: unexpected host error");
+  }
+}
+
+ffa_status ffa_iterate(ffa_ctx* ctx, int32_t max_iter, int32_t stop_at_tol, ffa_stats* stats) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  try {
+    return iterate_body(ctx, max_iter, stop_at_tol, stats);
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, FFA_ERR_OOM, "host allocation failed in ffa_iterate");
+  } catch (const std::exception& e) {
+    return fail(ctx, FFA_ERR_INVALID_ARG, std::string("ffa_iterate: ") + e.what());
+  } catch (...) {
+    return fail(ctx, FFA_ERR_INVALID_ARG, "ffa_iterate: unexpected host error");
+  }
 }
 
 ffa_status ffa_get_W(ffa_ctx* ctx, double* W_out) {
@@ -1629,6 +1673,10 @@ ffa_status ffa_set_state(ffa_ctx* ctx, const double* W, const double* U, const d
     if ((st = load_W_records(ctx, hW.data(), true, ctx->W, ctx->vrec)) != FFA_OK) return st;
     launch_rhs_terms(local_launch(ctx, false, ctx->vrec), ctx->stream);
     FFA_CUDA(cudaGetLastError());
+    if (ctx->e.hmu) {   // the proximal weight from the P given here
+      launch_prox_weight(local_launch(ctx, false, ctx->vrec), ctx->stream);
+      FFA_CUDA(cudaGetLastError());
+    }
     FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   } catch (const std::bad_alloc&) {
     return fail(ctx, FFA_ERR_OOM, "host allocation failed");
@@ -1749,6 +1797,8 @@ ffa_status ffa_forward_unrolled(ffa_ctx* ctx, int32_t K, int32_t ckpt_every) {
     return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation needs fixed penalties (penalty_schedule 0)");
   if (ctx->prm.local_variant != 0)
     return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation is implemented for the paper's local step (local_variant 0)");
+  if (ctx->e.hmu)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation is implemented for the U step without the proximal term (prox_h 0)");
   if (ctx->n_con > 0)
     return fail(ctx, FFA_ERR_INVALID_ARG, "differentiation is implemented for pinned constraints only");
   ffa_status st = ensure_graphs(ctx);
@@ -2046,6 +2096,18 @@ ffa_status ffa_last_wstep_residual(ffa_ctx* ctx, double* rel) {
   FFA_CUDA(cudaMemcpyAsync(ctx->sums_h, ctx->sums_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   *rel = ctx->sums_h[1] > 0 ? std::sqrt(ctx->sums_h[0] / ctx->sums_h[1]) : std::sqrt(ctx->sums_h[0]);
+  return FFA_OK;
+}
+
+ffa_status ffa_set_wait_limit(ffa_ctx* ctx, int64_t polls) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (polls < 0) return fail(ctx, FFA_ERR_INVALID_ARG, "polls must be >= 0");
+  ctx->spin_limit = (long long)polls;
+  // the graphs hold the launch parameters they were captured with
+  if (ctx->g_batch) { cudaGraphExecDestroy(ctx->g_batch); ctx->g_batch = nullptr; }
+  if (ctx->g_one) { cudaGraphExecDestroy(ctx->g_one); ctx->g_one = nullptr; }
+  if (ctx->g_one_check) { cudaGraphExecDestroy(ctx->g_one_check); ctx->g_one_check = nullptr; }
   return FFA_OK;
 }
 

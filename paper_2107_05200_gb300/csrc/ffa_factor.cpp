@@ -8,7 +8,9 @@
 #include <cmath>
 #include <functional>
 #include <limits>
+#include <exception>
 #include <memory>
+#include <mutex>
 #include <thread>
 
 namespace ffa {
@@ -41,11 +43,7 @@ void parallel_for(int64_t n, int threads, int64_t grain,
       fn(b, std::min(n, b + grain));
     }
   };
-  std::vector<std::thread> pool;
-  pool.reserve(t - 1);
-  for (int i = 1; i < t; ++i) pool.emplace_back(worker);
-  worker();
-  for (auto& th : pool) th.join();
+  run_threads(t, [&](int) { worker(); });
 }
 
 // ---------------------------------------------------------------------------
@@ -488,11 +486,8 @@ int numeric(const FactorInput& in, Factor& f, std::string& err, int threads) {
         for (int s = first_desc[r]; s <= r; ++s) factor_node(s, wk, 1);
       }
     };
-    std::vector<std::thread> pool;
     const int tcount = std::max(1, std::min<int>(threads, (int)tasks.size()));
-    for (int i = 1; i < tcount; ++i) pool.emplace_back(worker);
-    worker();
-    for (auto& th : pool) th.join();
+    run_threads(tcount, [&](int) { worker(); });
   }
   {
     NumericWork wk(in.nF);
@@ -633,6 +628,30 @@ void host_solve(const Factor& f, const double* b, double* x, int nrhs) {
   }
   for (int64_t c = 0; c < nF; ++c)
     for (int k = 0; k < nrhs; ++k) x[(int64_t)f.perm[c] * nrhs + k] = xs[c * nrhs + k];
+}
+
+void run_threads(int count, const std::function<void(int)>& worker) {
+  std::exception_ptr first;
+  std::mutex mu;
+  auto guarded = [&](int i) {
+    try {
+      worker(i);
+    } catch (...) {
+      std::lock_guard<std::mutex> lock(mu);
+      if (!first) first = std::current_exception();
+    }
+  };
+  std::vector<std::thread> pool;
+  try {
+    pool.reserve(count > 1 ? count - 1 : 0);
+    for (int i = 1; i < count; ++i) pool.emplace_back(guarded, i);
+  } catch (...) {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!first) first = std::current_exception();
+  }
+  guarded(0);
+  for (auto& th : pool) th.join();
+  if (first) std::rethrow_exception(first);
 }
 
 }  // namespace ffa

@@ -13,10 +13,18 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
 namespace ffa {
+
+// Runs worker(0) on the calling thread and worker(1 .. count-1) on new threads,
+// then joins every thread that was started, also when starting one fails.  An
+// exception thrown by any worker (or by starting a thread) is rethrown on the
+// calling thread after the joins, so no joinable thread is ever destroyed and no
+// exception escapes a thread.
+void run_threads(int count, const std::function<void(int)>& worker);
 
 struct Supernode {
   int32_t col0 = 0;     // first column in the eliminated order

@@ -65,6 +65,7 @@ struct ElemBufs {
   const int32_t* mesh_of = nullptr;    // m: mesh of each element
   double* mesh_acc = nullptr;          // n_mesh x (NQ + 1) per-mesh sums of the check quantities
   int32_t joint = 0;                   // 1: the joint (U, P) prox variant of the local step
+  void* hmu = nullptr;                 // m: h_i / mu_i of the proximal U term (null: h = 0)
 };
 
 struct LocalLaunch {
@@ -79,6 +80,9 @@ struct LocalLaunch {
 
 void launch_local_step(const LocalLaunch& L, cudaStream_t s);
 void launch_init_polar(const LocalLaunch& L, cudaStream_t s);
+// h_i / mu_i of the proximal U term at the bound of Prop. 1 from the current P:
+// 4 w_i^2 B_i^2 / mu_i^2, B_i^2 = 5 (1 + |grad f(P_i)|^2) (single-energy contexts)
+void launch_prox_weight(const LocalLaunch& L, cudaStream_t s);
 // W-step right-hand-side terms from the stored U, P, Lambda (after a state restore)
 void launch_rhs_terms(const LocalLaunch& L, cudaStream_t s);
 // the paper's penalty schedule: mode 0 mu = max(mu_min(P), w) after the polar
@@ -141,6 +145,10 @@ struct GatherLaunch {
 };
 void launch_gather(const GatherLaunch& G, cudaStream_t s);
 
+// polls (of ~100 ns each) a dynamic-schedule block makes on an empty queue slot
+// before it gives up, sets err_flag and exits (about 0.4 s)
+constexpr long long kDefaultSpinLimit = 1LL << 22;
+
 struct SolveData {
   int d;
   int nF;
@@ -158,6 +166,7 @@ struct SolveData {
   int bottom_levels = 0;         // levels below run as one launch per level (schedule 1)
   int n_nodes = 0;
   int32_t* err_flag = nullptr;      // set to 1 if a wait ran out of polls
+  long long spin_limit = kDefaultSpinLimit;  // polls per wait before giving up
   int grid_f = 0, grid_b = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional: before forward, between, after backward
   float* y;                  // nF x d residual / forward work vector

@@ -207,7 +207,11 @@ __device__ __forceinline__ void mesh_reduce(const R v[NQ], const ElemBufs& e, in
 // float: 64 registers (4 blocks of 256 or 8 of 128 per SM).  The per-element math is issue
 // bound, and the extra resident warps hide its latencies better than the spilled
 // registers cost (measured 0.215 -> 0.167 ms on the 64^3-cell cube).
-template <int D, typename R, int EN, bool CHECK, bool JOINT>
+// local-step variants: the paper's (h = 0), the joint (U, P) prox (not the
+// paper's scheme), and the paper's with the proximal U term h_i > 0
+constexpr int kVarPaper = 0, kVarJoint = 1, kVarProx = 2;
+
+template <int D, typename R, int EN, bool CHECK, int VAR>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(ElemBufs e, int m, const void* __restrict__ vrec,
                                                     double* __restrict__ partials) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -238,12 +242,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
       P[0][0] = Pp[i]; P[0][1] = P[1][0] = Pp[(int64_t)m + i]; P[0][2] = P[2][0] = Pp[2 * (int64_t)m + i];
       P[1][1] = Pp[3 * (int64_t)m + i]; P[1][2] = P[2][1] = Pp[4 * (int64_t)m + i]; P[2][2] = Pp[5 * (int64_t)m + i];
     }
-    // ---- U step: nearest rotation to Q = (J + Lambda) P (eqs. rawoptimizationinudecoupled/optimizationinudecoupled, h = 0);
+    // ---- U step: nearest rotation to Q = (J + Lambda) P + (h / mu) U^{k-1}
+    // (eqs. rawoptimizationinudecoupled/optimizationinudecoupled; h = 0 unless VAR is kVarProx);
     // the joint (U, P) prox variant (not the paper's scheme) takes Q = J + Lambda:
     // for a rotation-invariant f the joint minimizer of w f(P) + mu/2 |U P - A|^2 is
     // the rotation nearest to A with P the prox of symm(U^T A)
     R Q[D][D], U[D][D];
-    if constexpr (JOINT) {
+    if constexpr (VAR == kVarJoint) {
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -258,6 +263,24 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
           for (int l = 0; l < D; ++l) s = fma(A[a][l], P[l][k], s);
           Q[a][k] = s;
         }
+      if constexpr (VAR == kVarProx) {
+        // + (h_i / mu_i) U^{k-1}, the stored rotation of the previous iteration
+        const R hm = reinterpret_cast<const R*>(e.hmu)[i];
+        R Uo[D][D];
+        if constexpr (D == 2) {
+          const R c = Up[i], sn = Up[(int64_t)m + i];
+          Uo[0][0] = c; Uo[0][1] = -sn; Uo[1][0] = sn; Uo[1][1] = c;
+        } else {
+          R qt[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) qt[k] = Up[(int64_t)k * m + i];
+          quat_to_rot<R>(qt, Uo);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int k = 0; k < D; ++k) Q[a][k] = fma(hm, Uo[a][k], Q[a][k]);
+      }
     }
     if constexpr (D == 2) {
       // maximize U(phi) . Q: (cos, sin) along (q00 + q11, q10 - q01); tie keeps U^{k-1}
@@ -786,16 +809,58 @@ __global__ void __launch_bounds__(kLocalBlock) k_penalty(ElemBufs e, int m, cons
   reinterpret_cast<R*>(e.mu)[i] = (R)mu_new;
 }
 
+// h_i / mu_i = 4 w_i^2 B_i^2 / mu_i^2 with B_i^2 = 5 (1 + |grad f(P_i)|^2): the
+// proximal weight of eq. proximalfunctionu at the bound of Prop. 1 (gamma = 1,
+// eps = 0, as Sec. 6 sets them), from the current P (after the polar
+// initialization: P^0).  grad f(P) for symmetric P has the eigenvalues
+// p - p^-3 (SD), p - 1/p (SG), p - 1 - p^-3 + p^-2 (SA).
+template <int D, typename R, int EN>
+__global__ void __launch_bounds__(kLocalBlock) k_prox_weight(ElemBufs e, int m) {
+  const int i = blockIdx.x * kLocalBlock + threadIdx.x;
+  if (i >= m) return;
+  const R* Pp = reinterpret_cast<const R*>(e.P);
+  double ev[3];
+  if constexpr (D == 2) {
+    const double p00 = Pp[i], p01 = Pp[(int64_t)m + i], p11 = Pp[2 * (int64_t)m + i];
+    const double h = 0.5 * (p00 + p11), dd = 0.5 * (p00 - p11);
+    const double r = sqrt(dd * dd + p01 * p01);
+    ev[0] = h + r;
+    ev[1] = h - r;
+  } else {
+    double V[3][3];
+    sym3_eig<double>(Pp[i], Pp[(int64_t)m + i], Pp[2 * (int64_t)m + i], Pp[3 * (int64_t)m + i],
+                     Pp[4 * (int64_t)m + i], Pp[5 * (int64_t)m + i], ev, V);
+  }
+  double gn2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double p = ev[k];
+    double gk;
+    if constexpr (EN == kEnSG) gk = p - 1.0 / p;
+    else if constexpr (EN == kEnSD) gk = p - 1.0 / (p * p * p);
+    else gk = p - 1.0 - 1.0 / (p * p * p) + 1.0 / (p * p);
+    gn2 += gk * gk;
+  }
+  const double w = (double)reinterpret_cast<const R*>(e.w)[i];
+  const double mu = (double)reinterpret_cast<const R*>(e.mu)[i];
+  reinterpret_cast<R*>(e.hmu)[i] = (R)(4.0 * w * w * 5.0 * (1.0 + gn2) / (mu * mu));
+}
+
 template <int D, typename R, int EN>
 void dispatch_local(const LocalLaunch& L, cudaStream_t s) {
   const int bs = L.block > 0 ? L.block : kLocalBlock;
   const int grid = (L.m + bs - 1) / bs;
   if (L.e.joint) {
-    if (L.check) k_local_step<D, R, EN, true, true><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
-    else k_local_step<D, R, EN, false, true><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+    if (L.check) k_local_step<D, R, EN, true, kVarJoint><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+    else k_local_step<D, R, EN, false, kVarJoint><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+  } else if (L.e.hmu) {
+    if constexpr (EN != kEnMixed) {
+      if (L.check) k_local_step<D, R, EN, true, kVarProx><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+      else k_local_step<D, R, EN, false, kVarProx><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+    }
   } else {
-    if (L.check) k_local_step<D, R, EN, true, false><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
-    else k_local_step<D, R, EN, false, false><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+    if (L.check) k_local_step<D, R, EN, true, kVarPaper><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
+    else k_local_step<D, R, EN, false, kVarPaper><<<grid, bs, 0, s>>>(L.e, L.m, L.vrec, L.partials);
   }
 }
 
@@ -845,6 +910,17 @@ void launch_init_polar(const LocalLaunch& L, cudaStream_t s) {
   if (L.d == 2) { if (L.fp64) FFA_INIT(2, double); else FFA_INIT(2, float); }
   else { if (L.fp64) FFA_INIT(3, double); else FFA_INIT(3, float); }
 #undef FFA_INIT
+}
+
+void launch_prox_weight(const LocalLaunch& L, cudaStream_t s) {
+  const int grid = (L.m + kLocalBlock - 1) / kLocalBlock;
+#define FFA_PW(D, R) \
+  do { if (L.energy == kEnSD) k_prox_weight<D, R, kEnSD><<<grid, kLocalBlock, 0, s>>>(L.e, L.m); \
+       else if (L.energy == kEnSG) k_prox_weight<D, R, kEnSG><<<grid, kLocalBlock, 0, s>>>(L.e, L.m); \
+       else if (L.energy == kEnSA) k_prox_weight<D, R, kEnSA><<<grid, kLocalBlock, 0, s>>>(L.e, L.m); } while (0)
+  if (L.d == 2) { if (L.fp64) FFA_PW(2, double); else FFA_PW(2, float); }
+  else { if (L.fp64) FFA_PW(3, double); else FFA_PW(3, float); }
+#undef FFA_PW
 }
 
 void launch_energy_terms(const LocalLaunch& L, int mode, cudaStream_t s) {

@@ -11,10 +11,16 @@
 // contents; each call overwrites exactly the slots it then reads, so nothing
 // needs clearing, but calls that overlap on the GPU (different streams, or
 // host threads calling concurrently) race on it.
+//
+// Invalid meshes are reported through the result, because the call only
+// enqueues work and never waits for it: an element with a vertex index outside
+// [0, n) is skipped before any load through that index, and a source element of
+// zero (or non-finite) measure is not evaluated; either makes *E a NaN, where a
+// valid mesh with a flipped element gives +infinity.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
+#include <string>
 
 #include "ffa_internal.h"
 
@@ -22,23 +28,26 @@ namespace {
 
 constexpr int kNaBlock = 256;
 constexpr int kNaMaxBlocks = 1 << 16;  // 65,536 blocks -> up to 16,777,216 elements
-constexpr int kNaMaxDevices = 64;
 
-// two doubles per block: sum of w_i f(J_i) over unflipped elements, flip count
-static __device__ __align__(256) double g_na_partials[2 * kNaMaxBlocks];
-
-std::mutex g_na_mutex;
-double* g_na_addr[kNaMaxDevices] = {nullptr};
+constexpr int kNaSlots = 3;
+// three doubles per block: sum of w_i f(J_i) over unflipped elements, flip count,
+// invalid elements (an index outside [0, n) or a source element of zero measure)
+static __device__ __align__(256) double g_na_partials[kNaSlots * kNaMaxBlocks];
 
 // Per element: source edge matrix in the element frame (intrinsic for a triangle
 // in R^3), hat gradients as the columns of its inverse, J = G W with column k
 // the gradient of target coordinate k, then w f(J) (Supplemental "Computing the
 // Jacobian Map"; eq. genericdeformationenergy with eq. symmetricdirichletdefiningfunction
 // or eq. symmetricgradientdefiningfunction).
+enum NaResult { kNaValue = 0, kNaFlipped = 1, kNaInvalid = 2 };
+
 template <int D>
-__device__ bool na_element(int d_in, const double* __restrict__ V, const int32_t* __restrict__ T,
-                           const double* __restrict__ W, int i, int energy, double& wf) {
+__device__ NaResult na_element(int n, int d_in, const double* __restrict__ V, const int32_t* __restrict__ T,
+                               const double* __restrict__ W, int i, int energy, double& wf) {
   const int32_t* t = T + (int64_t)i * (D + 1);
+  // every index is checked before anything is loaded through it
+  for (int j = 0; j <= D; ++j)
+    if (t[j] < 0 || t[j] >= n) return kNaInvalid;
   double E[D][D];
   const double* v0 = V + (int64_t)t[0] * d_in;
   if (d_in == D) {
@@ -79,6 +88,7 @@ __device__ bool na_element(int d_in, const double* __restrict__ V, const int32_t
     Ei[2][2] = (E[0][0] * E[1][1] - E[0][1] * E[1][0]) / detE;
   }
   const double w = fabs(detE) / (D == 2 ? 2.0 : 6.0);
+  if (!(w > 0.0) || !isfinite(w)) return kNaInvalid;   // zero-measure source element (or NaN frame)
   // J[a][k] = sum_j g_j[a] (W_j - W_0)[k], g_j[a] = Ei[a][j-1]
   double J[D][D];
   const double* w0 = W + (int64_t)t[0] * D;
@@ -111,64 +121,60 @@ __device__ bool na_element(int d_in, const double* __restrict__ V, const int32_t
   }
   for (int a = 0; a < D; ++a)
     for (int k = 0; k < D; ++k) fro += J[a][k] * J[a][k];
-  if (!(det > 0.0)) return false;
+  if (!(det > 0.0)) return kNaFlipped;
   wf = w * (energy == FFA_SYM_DIRICHLET ? 0.5 * (fro + fri) : 0.5 * fro - log(det));
-  return true;
+  return kNaValue;
 }
 
 template <int D>
-__global__ void __launch_bounds__(kNaBlock) k_na_energy(int m, int d_in, const double* __restrict__ V,
+__global__ void __launch_bounds__(kNaBlock) k_na_energy(int n, int m, int d_in, const double* __restrict__ V,
                                                         const int32_t* __restrict__ T, const double* __restrict__ W,
                                                         int energy, double* __restrict__ partials) {
   const int i = blockIdx.x * kNaBlock + threadIdx.x;
-  double e = 0.0, flips = 0.0;
+  double q[kNaSlots] = {0.0, 0.0, 0.0};   // energy, flips, invalid elements
   if (i < m) {
-    double wf;
-    if (na_element<D>(d_in, V, T, W, i, energy, wf)) e = wf;
-    else flips = 1.0;
+    double wf = 0.0;
+    const NaResult r = na_element<D>(n, d_in, V, T, W, i, energy, wf);
+    if (r == kNaValue) q[0] = wf;
+    else if (r == kNaFlipped) q[1] = 1.0;
+    else q[2] = 1.0;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_xor_sync(0xffffffffu, e, o);
-    flips += __shfl_xor_sync(0xffffffffu, flips, o);
-  }
-  __shared__ double red[2][kNaBlock / 32];
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = e;
-    red[1][threadIdx.x >> 5] = flips;
-  }
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < kNaSlots; ++k) q[k] += __shfl_xor_sync(0xffffffffu, q[k], o);
+  __shared__ double red[kNaSlots][kNaBlock / 32];
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < kNaSlots; ++k) red[k][threadIdx.x >> 5] = q[k];
   __syncthreads();
-  if (threadIdx.x < 2) {
+  if (threadIdx.x < kNaSlots) {
     double s = 0.0;
     for (int w = 0; w < kNaBlock / 32; ++w) s += red[threadIdx.x][w];
-    partials[2 * (int64_t)blockIdx.x + threadIdx.x] = s;
+    partials[kNaSlots * (int64_t)blockIdx.x + threadIdx.x] = s;
   }
 }
 
 __global__ void k_na_finish(const double* __restrict__ partials, int nblocks, double* __restrict__ E) {
-  double e = 0.0, flips = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    e += partials[2 * (int64_t)b];
-    flips += partials[2 * (int64_t)b + 1];
-  }
+  double q[kNaSlots] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_xor_sync(0xffffffffu, e, o);
-    flips += __shfl_xor_sync(0xffffffffu, flips, o);
-  }
-  __shared__ double red[2][32];
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = e;
-    red[1][threadIdx.x >> 5] = flips;
-  }
+    for (int k = 0; k < kNaSlots; ++k) q[k] += partials[kNaSlots * (int64_t)b + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < kNaSlots; ++k) q[k] += __shfl_xor_sync(0xffffffffu, q[k], o);
+  __shared__ double red[kNaSlots][32];
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < kNaSlots; ++k) red[k][threadIdx.x >> 5] = q[k];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double te = 0.0, tf = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      te += red[0][w];
-      tf += red[1][w];
-    }
-    *E = tf > 0.5 ? INFINITY : te;
+    double t[kNaSlots] = {0.0, 0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+      for (int k = 0; k < kNaSlots; ++k) t[k] += red[k][w];
+    *E = t[2] > 0.5 ? NAN : (t[1] > 0.5 ? INFINITY : t[0]);
   }
 }
 
@@ -191,28 +197,30 @@ ffa_status ffa_energy_noalloc(int32_t n, int32_t m, int32_t d, int32_t d_in, con
                    FFA_ERR_INVALID_ARG);
   if (!V || !T || !W || !E) return na_fail("a pointer argument is NULL", FFA_ERR_INVALID_ARG);
   if (energy != FFA_SYM_DIRICHLET && energy != FFA_SYM_GRADIENT) return na_fail("unknown energy", FFA_ERR_INVALID_ARG);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
-    return na_fail("no usable current CUDA device", FFA_ERR_CUDA);
-  double* scratch = nullptr;
-  {
-    // set-up, once per device, with that device current: the device address of
-    // the static array (its host-side name is only a stand-in)
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_na_partials) != cudaSuccess || !p)
-        return na_fail("cudaGetSymbolAddress of the static scratch failed", FFA_ERR_CUDA);
-      g_na_addr[dev] = static_cast<double*>(p);
-    }
-    scratch = g_na_addr[dev];
+  // an error left pending by earlier work on this thread is reported as its own
+  // and left in place for its owner
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess)
+    return na_fail((std::string("a CUDA error was pending before the call: ") + cudaGetErrorString(pending)).c_str(),
+                   FFA_ERR_CUDA);
+  // the device address of the static array on the current device (its host-side
+  // name is only a stand-in); looked up on every call, so it follows the current
+  // device and survives a device reset.  The first call on a device loads the
+  // library's device code there, so make it before any stream capture.
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_na_partials) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return na_fail("cudaGetSymbolAddress of the static scratch failed", FFA_ERR_CUDA);
   }
+  double* scratch = static_cast<double*>(p);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int nb = (m + kNaBlock - 1) / kNaBlock;
-  if (d == 2) k_na_energy<2><<<nb, kNaBlock, 0, s>>>(m, d_in, V, T, W, (int)energy, scratch);
-  else k_na_energy<3><<<nb, kNaBlock, 0, s>>>(m, d_in, V, T, W, (int)energy, scratch);
+  if (d == 2) k_na_energy<2><<<nb, kNaBlock, 0, s>>>(n, m, d_in, V, T, W, (int)energy, scratch);
+  else k_na_energy<3><<<nb, kNaBlock, 0, s>>>(n, m, d_in, V, T, W, (int)energy, scratch);
   k_na_finish<<<1, 1024, 0, s>>>(scratch, nb, E);
-  if (cudaGetLastError() != cudaSuccess) return na_fail("kernel launch failed", FFA_ERR_CUDA);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return na_fail((std::string("kernel launch failed: ") + cudaGetErrorString(e)).c_str(), FFA_ERR_CUDA);
   return FFA_OK;
 }
 

@@ -132,12 +132,7 @@ void assemble_operator(const OperatorHost& H, const double* mu, std::vector<int6
       C.nc.push_back((int32_t)cr.size());
     }
   };
-  {
-    std::vector<std::thread> pool;
-    for (int ck = 1; ck < nchunk; ++ck) pool.emplace_back(assemble_rows, ck);
-    assemble_rows(0);
-    for (auto& th : pool) th.join();
-  }
+  run_threads(nchunk, assemble_rows);
   Ap.assign(nF + 1, 0);
   Cp.assign(nF + 1, 0);
   Ai.clear(); Ax.clear(); Ci.clear(); Cx.clear();

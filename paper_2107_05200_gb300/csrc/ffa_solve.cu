@@ -772,8 +772,6 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_backward(con
 // node becomes ready once), so the waits end; each is still bounded and sets
 // err_flag instead of spinning on.
 // ---------------------------------------------------------------------------
-constexpr long long kSpinLimit = 1LL << 22;   // polls of ~100 ns (~0.4 s) before giving up
-
 struct DynView {
   DynPass P;
   const NodeDev* sub;   // merged subtrees' nodes
@@ -783,6 +781,7 @@ struct DynView {
   float* z;
   float* x;
   int32_t* err_flag;
+  long long spin_limit;   // polls of an empty slot before the wait gives up
 };
 
 __device__ __forceinline__ int ld_acquire(const int32_t* p) {
@@ -827,7 +826,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
         if (t < 0) {
           long long it = 0;
           while ((t = ld_acquire(P.queue + h)) < 0) {
-            if (++it > kSpinLimit || ld_acquire(V.err_flag) != 0) {
+            if (++it > V.spin_limit || ld_acquire(V.err_flag) != 0) {
               atomicExch(V.err_flag, 1);
               t = -1;
               break;
@@ -1113,8 +1112,8 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   if (S.ev[0]) cudaEventRecord(S.ev[0], s);
   const int L = (int)S.fwd_off.size() - 1;
   if (S.schedule == 1) {
-    const DynView vf{S.fdyn, S.sub_nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
-    const DynView vb{S.bdyn, S.sub_nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag};
+    const DynView vf{S.fdyn, S.sub_nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag, S.spin_limit};
+    const DynView vb{S.bdyn, S.sub_nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag, S.spin_limit};
     const int nb = std::min(S.bottom_levels, L);
     launch_levels(S, 0, nb, true, s);
     if (S.d == 2) k_solve_dynamic<2, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);

@@ -49,7 +49,7 @@ class Solver:
                  precision: str = "fp32", refine_sweeps: int = 2, leaf_size: int = 64,
                  require_flip_free: bool = True, host_threads: int = 0, schedule: int = 1,
                  penalties: str = "fixed", rescale_rho: float = 5.0, local_variant: str = "paper",
-                 subtree_height=None, stream=None):
+                 subtree_height=None, prox_h: bool = False, stream=None):
         self._lib = N.load()
         self._ctx = None
         Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
@@ -80,6 +80,7 @@ class Solver:
         if local_variant not in ("paper", "joint"):
             raise ValueError("local_variant must be 'paper' or 'joint'")
         prm.local_variant = 1 if local_variant == "joint" else 0
+        prm.prox_h = 1 if prox_h else 0
         if subtree_height is not None:   # (forward, backward) merged bottom subtree heights
             prm.solve_subtree_height[0], prm.solve_subtree_height[1] = (int(h) for h in subtree_height)
         n_pin = 0 if pins is None else int(len(pins))
@@ -212,6 +213,10 @@ class Solver:
         po, _ = _ptr(out, np.float64)
         self._check(self._lib.ffa_backward_unrolled(self._ctx, p, po))
         return out
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls of an empty queue slot before a W-step wait gives up (FFA_ERR_TIMEOUT)."""
+        self._check(self._lib.ffa_set_wait_limit(self._ctx, int(polls)))
 
     def wstep_residual(self) -> float:
         r = C.c_double()

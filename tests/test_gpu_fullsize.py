@@ -3,10 +3,25 @@ times (FP32 local step, two refinement sweeps).
 
 The oracle cannot run these meshes end to end, so each check uses what it can
 compute one element at a time or what holds at any size:
-* the local step of one GPU iteration, recomputed by the oracle for sampled
-  elements from the GPU's own inputs (W^{k+1} and the state after iteration k);
+* the local step of one GPU iteration, recomputed by the oracle for EVERY
+  element from the GPU's own inputs (W^{k+1} and the state after iteration k,
+  read back exactly as the GPU holds them), with a bound per element that
+  scales with the conditioning of its rotation (below);
 * the W step's residual |L_FF W_F - b_F| / |b_F| in double;
 * flip-freeness of every P_i (all eigenvalues positive).
+
+Error bound.  The GPU's local step runs in float on the same inputs, so each
+output differs from the oracle's by a few float roundings of the element's
+scale, amplified only where the U step is ill-conditioned: the nearest rotation
+to Q = (J + Lambda) P^{k-1} moves by |dQ| / (s_{d-1} + sign(det Q) s_d) for a
+perturbation dQ (s the singular values of Q, descending; the denominator is the
+smallest sum of two signed singular values), which enters S = symm(U^T (J +
+Lambda)) and from there P (the prox of a convex spectral function is
+1-Lipschitz) and Lambda.  With kappa_i = |Q_i| / that sum, every element must
+satisfy
+    |U_gpu - U_oracle|_max        <= C eps32 (1 + kappa_i)
+    |P_gpu - P_oracle|_max / s_i   <= C eps32 (1 + kappa_i)   (same for Lambda)
+with s_i = |J_i|_max + |Lambda_i|_max + 1, eps32 = 2^-24 and C = 64.
 """
 import numpy as np
 import pytest
@@ -16,6 +31,9 @@ from paper_2107_05200_gb300 import workloads as wk
 
 pytestmark = pytest.mark.gpu
 
+EPS32 = 2.0 ** -24
+C_BOUND = 64.0
+
 
 def _need_gpu():
     torch = pytest.importorskip("torch")
@@ -23,7 +41,7 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-def _sampled_local_step(wl, iters, n_sample, seed):
+def _local_step_all_elements(wl, iters):
     from paper_2107_05200_gb300.solver import Solver
     with Solver.from_workload(wl, precision="fp32", refine_sweeps=2, check_every=50) as sol:
         sol.init(wl.W0)
@@ -33,45 +51,51 @@ def _sampled_local_step(wl, iters, n_sample, seed):
         W1 = sol.W()
         U1, P1, L1 = sol.state()
         resid = sol.wstep_residual()
-    rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(wl.m, size=n_sample, replace=False))
-    T = wl.T[idx].astype(np.int64)
+    T = wl.T.astype(np.int64)
     g, w = admm.element_gradients(wl.V, T)
     mu = wl.rho * w
     J = admm.jacobians(g, T, W1)
-    A = J + L0[idx]
-    U = admm.procrustes(A @ P0[idx], U0[idx])
+    A = J + L0
+    Q = A @ P0
+    U = admm.procrustes(Q, U0)
     S = admm.symm(np.transpose(U, (0, 2, 1)) @ A)
     P = admm.p_step(S, w, mu, wl.energy)
-    Lam = L0[idx] + J - U @ P
-    return resid, (U1[idx], P1[idx], L1[idx], P1), (U, P, Lam), J
+    Lam = L0 + J - U @ P
+    sv = np.linalg.svd(Q, compute_uv=False)
+    sign = np.sign(np.linalg.det(Q))
+    gap = sv[:, -2] + sign * sv[:, -1]
+    kappa = np.linalg.norm(Q, axis=(1, 2)) / np.maximum(gap, 1e-300)
+    return resid, (U1, P1, L1), (U, P, Lam), J, kappa
 
 
 def _check(wl, iters):
-    resid, gpu, ref, J = _sampled_local_step(wl, iters, 4000, 61)
-    Ug, Pg, Lg, Pall = gpu
+    resid, gpu, ref, J, kappa = _local_step_all_elements(wl, iters)
+    Ug, Pg, Lg = gpu
     Ur, Pr, Lr = ref
     assert resid < 1e-9
     # flip-free local output everywhere (eigenvalues of every P_i positive)
-    assert np.linalg.eigvalsh(Pall).min() > 0
+    assert np.linalg.eigvalsh(Pg).min() > 0
     scale = np.abs(J).max(axis=(1, 2)) + np.abs(Lr).max(axis=(1, 2)) + 1.0
-    errP = np.abs(Pg - Pr).max(axis=(1, 2)) / scale
-    errL = np.abs(Lg - Lr).max(axis=(1, 2)) / scale
-    errU = np.abs(Ug - Ur).max(axis=(1, 2))
-    # float inputs (W, U, P, Lambda rounded to float) and float arithmetic: a few
-    # ulps of the element's scale, more where the rotation is ill-conditioned
-    assert np.quantile(errP, 0.99) < 1e-5 and np.quantile(errL, 0.99) < 1e-5
-    assert np.quantile(errU, 0.99) < 1e-4
-    assert errP.max() < 1e-2 and errL.max() < 1e-2
+    allow = C_BOUND * EPS32 * (1.0 + kappa)
+    rU = np.abs(Ug - Ur).max(axis=(1, 2)) / allow
+    rP = np.abs(Pg - Pr).max(axis=(1, 2)) / scale / allow
+    rL = np.abs(Lg - Lr).max(axis=(1, 2)) / scale / allow
+    q = lambda r: f"max {r.max():.3g} (element {int(r.argmax())}, kappa {kappa[r.argmax()]:.3g}), " \
+                  f"99.9% {np.quantile(r, 0.999):.3g}"
+    print(f"\n{wl.name}: {wl.m} elements; kappa median {np.median(kappa):.3g} max {kappa.max():.3g}; "
+          f"error / bound: U {q(rU)}; P {q(rP)}; Lambda {q(rL)}")
+    assert rU.max() <= 1.0, q(rU)
+    assert rP.max() <= 1.0, q(rP)
+    assert rL.max() <= 1.0, q(rL)
 
 
-def test_cube_deform_64_sampled_local_step_and_residual():
+def test_cube_deform_64_every_element_local_step_and_residual():
     """1,572,864 tets, the benchmark workload and launch configuration."""
     _need_gpu()
     _check(wk.cube_deform(), iters=20)
 
 
-def test_uv_heightfield_512_sampled_local_step_and_residual():
+def test_uv_heightfield_512_every_element_local_step_and_residual():
     """522,242 intrinsic triangles, symmetric gradient energy."""
     _need_gpu()
     _check(wk.uv_heightfield(), iters=20)

@@ -196,3 +196,41 @@ def test_invalid_inputs_are_rejected():
         sol.init(W0)
         with pytest.raises(FFAError, match="NAN"):
             sol.iterate(2, stop_at_tol=False)
+
+
+@pytest.mark.parametrize("seed", [7, 61, 62, 63, 64, 65])
+def test_disk_trajectory_for_any_seed(seed):
+    """The generated starts hold no element at det J = 0 to rounding, so the GPU and the oracle
+    take the same branch of eq. polardecompositionapplied for every element, whatever the seed."""
+    wl = wk.uv_disk(grid=12, seed=seed)
+    iters = 25
+    o, s, hist = _oracle_run(wl, iters)
+    with _solver(wl, precision="fp64", check_every=5) as sol:
+        sol.init(wl.W0)
+        sol.iterate(iters, stop_at_tol=False)
+        W = sol.W()
+        U, P, L = sol.state()
+    assert _rel(W, s.W) < 1e-8
+    assert _rel(P, s.P) < 1e-7
+    assert _rel(L, s.Lam) < 1e-6
+
+
+def test_cube_deform_recipe_fp64_trajectory_200_iterations():
+    """The benchmark's recipe (jittered cube, bottom fixed, top rotated 45 degrees and shifted,
+    symmetric Dirichlet, mu = 3 w) at 16^3 cells (24,576 tets): 200 iterations of the FP64 GPU
+    path against the oracle, W within 1e-8."""
+    wl = wk.cube_deform(cells=16)
+    iters = 200
+    o, s, hist = _oracle_run(wl, iters)
+    with _solver(wl, precision="fp64", check_every=50) as sol:
+        sol.init(wl.W0)
+        st = sol.iterate(iters, stop_at_tol=False)
+        W = sol.W()
+        U, P, L = sol.state()
+    err = _rel(W, s.W)
+    print(f"\ncube 16^3, {iters} iterations: W rel. err {err:.3e}, P {_rel(P, s.P):.3e}, "
+          f"Lambda {_rel(L, s.Lam):.3e}; e_prim {st['e_prim']:.3e} (oracle {hist[-1].e_prim:.3e}), "
+          f"flips {st['n_flipped']} (oracle {hist[-1].n_flipped})")
+    assert err < 1e-8
+    assert st["n_flipped"] == hist[-1].n_flipped
+    assert math.isclose(st["e_prim"], hist[-1].e_prim, rel_tol=1e-5)

@@ -93,3 +93,21 @@ def test_large_proximal_weight_keeps_the_previous_rotation(d):
     # and h = 0 (no proximal term) moves U away from U^{k-1}
     o0, t, t1 = _state_before_u_step(d, 0.0)
     assert max(np.abs(t1.U[i] - t.U[i]).max() for i in range(o0.m)) > 1e-4
+
+
+def test_h_bound_against_hand_values():
+    """h_i = 4 w_i^2 B_i^2 / mu_i with B_i^2 = 5 (1 + |grad f(P_i)|^2) (Prop. 1 with gamma = 1,
+    eps = 0; Sec. 6), worked by hand for w = 1/2, mu = 3/2:
+      P = I (both energies): grad f = 0, B^2 = 5, h = 4 * 0.25 * 5 / 1.5 = 10/3;
+      SD, P = diag(2, 1): grad f = P - P^-3 = diag(2 - 1/8, 0), |grad f|^2 = 3.515625,
+          B^2 = 5 * 4.515625 = 22.578125, h = 22.578125 / 1.5;
+      SG, P = diag(2, 1): grad f = P - P^-1 = diag(1.5, 0), B^2 = 5 * 3.25 = 16.25, h = 16.25 / 1.5."""
+    from oracle import schedule
+    w = np.array([0.5, 0.5])
+    mu = np.array([1.5, 1.5])
+    P = np.stack([np.eye(2), np.diag([2.0, 1.0])])
+    hd = schedule.h_bound(P, w, mu, "sd")
+    hg = schedule.h_bound(P, w, mu, "sg")
+    assert math.isclose(hd[0], 10.0 / 3.0, rel_tol=1e-14) and math.isclose(hg[0], 10.0 / 3.0, rel_tol=1e-14)
+    assert math.isclose(hd[1], 22.578125 / 1.5, rel_tol=1e-14)
+    assert math.isclose(hg[1], 16.25 / 1.5, rel_tol=1e-14)

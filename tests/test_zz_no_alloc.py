@@ -4,9 +4,9 @@ Such callers (a frozen or custom allocator, a pool that must not grow, a process
 that only receives device buffers) cannot create a context, so this entry point
 evaluates the energy of a map straight from device buffers, keeping its partial
 sums in a fixed static device array.  It must agree with the context-based
-ffa_energy (double precision local step) to the FP64 tolerance used elsewhere in
-these tests, on consecutive calls that share that array.  This file is collected
-last on purpose.
+ffa_energy (double precision local step) and with the FP64 oracle's energy to the
+FP64 tolerance used elsewhere in these tests, on consecutive calls that share
+that array.  This file is collected last on purpose.
 """
 import ctypes as C
 import math
@@ -14,6 +14,7 @@ import math
 import numpy as np
 import pytest
 
+from oracle import admm
 from paper_2107_05200_gb300 import workloads as wk
 
 pytestmark = pytest.mark.gpu
@@ -60,6 +61,9 @@ def test_noalloc_energy_matches_context_energy_on_consecutive_calls():
     for wl, W in _cases():
         with Solver.from_workload(wl, precision="fp64") as sol:
             refs.append(sol.energy(W))
+        E_oracle = admm.Oracle.from_workload(wl).energy(W)
+        st, E = _noalloc_energy(torch, lib, wl, W, E_dev)
+        assert st == 0 and math.isclose(E, E_oracle, rel_tol=RTOL), (wl.name, E, E_oracle)
     # two calls in a row per case, alternating sizes so stale partials would show
     for rep in range(2):
         for (wl, W), ref in zip(_cases(), refs):
@@ -83,3 +87,24 @@ def test_noalloc_energy_flipped_and_limits():
     assert b"16,777,216" in lib.ffa_last_error(None)
     st = lib.ffa_energy_noalloc(10, 5, 4, 3, dummy, dummy, dummy, 0, dummy, None)
     assert st == 1
+
+
+def test_noalloc_energy_reports_invalid_meshes_as_nan():
+    """An index outside [0, n) (too large or negative) is caught before any load through
+    it, and a zero-measure source element is not evaluated: both give NaN, which a
+    flipped map of a valid mesh (+inf) never does.  A valid call afterwards is exact."""
+    torch, N, lib = _setup()
+    wl, W = _cases()[0]
+    E_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    for bad in (wl.n + 5, -1):
+        T = wl.T.copy()
+        T[3, 2] = bad
+        st, E = _noalloc_energy(torch, lib, wk.Workload("bad", wl.V, T, wl.pins, wl.pin_pos, W, wl.energy), W, E_dev)
+        assert st == 0 and math.isnan(E), bad
+    T = wl.T.copy()
+    T[7, 1] = T[7, 0]          # two equal vertices: zero volume
+    st, E = _noalloc_energy(torch, lib, wk.Workload("degenerate", wl.V, T, wl.pins, wl.pin_pos, W, wl.energy), W,
+                            E_dev)
+    assert st == 0 and math.isnan(E)
+    st, E = _noalloc_energy(torch, lib, wl, W, E_dev)
+    assert st == 0 and math.isclose(E, admm.Oracle.from_workload(wl).energy(W), rel_tol=RTOL)
