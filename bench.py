@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--check-every", type=int, default=50)
-    ap.add_argument("--schedule", type=int, default=1, choices=[0, 1],
-                    help="supernodal solves: 0 one launch per tree level, 1 dynamic ready queue")
+    ap.add_argument("--schedule", type=int, default=1, choices=[0, 1, 2],
+                    help="supernodal solves: 0 one launch per tree level, 1 dynamic ready queue, "
+                         "2 dynamic ready queue with a bulk-copy ring per block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -186,7 +187,7 @@ def bench_config(args, m, n, rho, world):
     return {"workload": f"cube_deform_{args.cells}", "tets": m, "vertices": n,
             "energy": "sym_dirichlet", "rho": rho, "local_precision": args.precision,
             "refine_sweeps": args.sweeps, "check_every": args.check_every,
-            "solve_schedule": "dynamic" if args.schedule == 1 else "per_level",
+            "solve_schedule": {0: "per_level", 1: "dynamic", 2: "pipelined"}[args.schedule],
             "l2": "working set > L2 (factor + element state), no flush",
             "parallelism": "replicas" if world > 1 else "single"}
 

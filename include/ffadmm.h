@@ -93,7 +93,9 @@ typedef struct {
   int32_t host_threads;    /* W step setup: host threads for the factorization (0 = all) */
   int32_t solve_schedule;  /* W step: 0 one launch per elimination-tree level, 1 one launch per
                               triangular solve whose blocks take ready tasks from a queue that
-                              finished supernodes refill (default) */
+                              finished supernodes refill (default), 2 the same queue with each
+                              block split into a producer warp that streams the factor with bulk
+                              copies into a shared-memory ring and eight consumer warps */
   int32_t penalty_schedule;/* 0: mu_i = rho * w_i, fixed (default; L is decomposed once).
                               1: the paper's Algorithm 2 (Sec. 6, "Rescaling mu_i and Lambda"):
                               mu_i = max(mu_min,i, w_i) at ffa_init (mu_min of Prop. 1 with the
@@ -310,12 +312,13 @@ typedef struct {
   int32_t local_block;  /* threads per block of the local step: 64, 128 or 256 */
   int32_t narrow_cols;  /* supernodes with at most this many columns (and at most 1024 rows and
                            64 KB of factor) run as one task on one block: 32 or 64 */
-  int32_t schedule;     /* supernodal solves: 0 per-level launches, 1 dynamic ready queue */
-  int32_t bottom_levels;/* schedule 1: lowest tree levels run as one launch per level: 0, 2, 3 or 4 */
+  int32_t schedule;     /* supernodal solves: 0 per-level launches, 1 dynamic ready queue,
+                           2 dynamic ready queue with the bulk-copy ring */
+  int32_t bottom_levels;/* schedules 1, 2: lowest tree levels run as one launch per level: 0, 2, 3 or 4 */
   double ms_local[3];   /* measured local step for 64, 128, 256 threads */
   double ms_solve[2];   /* measured supernodal solve (forward + backward) for 32, 64 */
-  double ms_schedule[2];/* measured supernodal solve for schedules 0 and 1 */
-  double ms_bottom[4];  /* measured supernodal solve (schedule 1) for bottom_levels 0, 2, 3, 4 */
+  double ms_schedule[3];/* measured supernodal solve for schedules 0, 1 and 2 */
+  double ms_bottom[4];  /* measured supernodal solve (schedules 1, 2) for bottom_levels 0, 2, 3, 4 */
   int32_t subtree_height[2]; /* schedule 1 with bottom_levels 0: bottom subtrees of at most this
                            height run as one task, forward and backward pass: 0 (off) .. 3 */
   double ms_subtree[2][4];   /* measured forward / backward pass for heights 0 .. 3 */

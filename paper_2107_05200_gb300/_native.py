@@ -73,7 +73,7 @@ class Info(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("local_block", C.c_int32), ("narrow_cols", C.c_int32), ("schedule", C.c_int32),
                 ("bottom_levels", C.c_int32), ("ms_local", C.c_double * 3), ("ms_solve", C.c_double * 2),
-                ("ms_schedule", C.c_double * 2), ("ms_bottom", C.c_double * 4),
+                ("ms_schedule", C.c_double * 3), ("ms_bottom", C.c_double * 4),
                 ("subtree_height", C.c_int32 * 2), ("ms_subtree", (C.c_double * 4) * 2)]
 
     def as_dict(self) -> dict:

@@ -126,6 +126,7 @@ struct ffa_ctx {
   int32_t* err_flag = nullptr;
   long long spin_limit = kDefaultSpinLimit;  // ffa_set_wait_limit
   int grid_f = 0, grid_b = 0;
+  int pgrid_f = 0, pgrid_b = 0;
   std::vector<Supernode> nodes_h;  // host copy of the supernode table (task lists are rebuilt from it)
   int n_levels = 0;
   Slot tune_slot;
@@ -273,6 +274,8 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.spin_limit = ctx->spin_limit;
   S.grid_f = ctx->grid_f;
   S.grid_b = ctx->grid_b;
+  S.pgrid_f = ctx->pgrid_f;
+  S.pgrid_b = ctx->pgrid_b;
   S.y = ctx->y;
   S.z = ctx->z;
   S.x = ctx->x;
@@ -421,7 +424,7 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   else if (p.refine_sweeps < 1 || p.refine_sweeps > 16) msg = "refine_sweeps must be in [1, 16]";
   else if (p.nd_leaf_size < 8 || p.nd_leaf_size > 512) msg = "nd_leaf_size must be in [8, 512]";
   else if (p.host_threads < 0) msg = "host_threads must be >= 0";
-  else if (p.solve_schedule != 0 && p.solve_schedule != 1) msg = "solve_schedule must be 0 or 1";
+  else if (p.solve_schedule < 0 || p.solve_schedule > 2) msg = "solve_schedule must be 0, 1 or 2";
   else if (p.penalty_schedule != 0 && p.penalty_schedule != 1) msg = "penalty_schedule must be 0 or 1";
   else if (p.local_variant != 0 && p.local_variant != 1) msg = "local_variant must be 0 or 1";
   else if (p.penalty_schedule == 1 && !(p.rescale_rho > 2.0 && std::isfinite(p.rescale_rho)))
@@ -445,7 +448,7 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
 // corrections, the vertex update and the local step
 int kernels_per_iteration(const ffa_ctx* ctx) {
   int solve = 2;
-  for (int l = 0; l < ctx->bottom_used && ctx->schedule == 1; ++l)
+  for (int l = 0; l < ctx->bottom_used && ctx->schedule >= 1; ++l)
     solve += (ctx->fwd_off[l + 1] > ctx->fwd_off[l]) + (ctx->bwd_off[l + 1] > ctx->bwd_off[l]);
   if (ctx->schedule == 0) {
     solve = 0;
@@ -501,6 +504,24 @@ ffa_status build_tasks(ffa_ctx* ctx) {
   build_schedule(ctx->nodes_h, ctx->n_levels, opt, sch);
   ctx->grid_f = persistent_grid(ctx->d, true);
   ctx->grid_b = persistent_grid(ctx->d, false);
+  ctx->pgrid_f = persistent_pipe_grid(ctx->d, true);
+  ctx->pgrid_b = persistent_pipe_grid(ctx->d, false);
+  if (ctx->schedule == 2 && (ctx->pgrid_f < 1 || ctx->pgrid_b < 1))
+    return fail(ctx, FFA_ERR_CUDA, "the pipelined solve kernels cannot be made resident on this device");
+  // the task shapes the solve kernels' shared-memory buffers assume
+  for (int pass = 0; pass < 2; ++pass) {
+    const PassSchedule& P = pass ? sch.bwd : sch.fwd;
+    for (const Task& t : P.tasks) {
+      const bool node_ok = t.nd.ld > 0 && t.nd.ld % 4 == 0;
+      const bool shape_ok = t.kind == 0 ? (t.c0 >= 1 && t.c0 <= kSubtreeMaxNodes)
+                          : t.kind == 1 ? t.nd.ld <= kNodeMaxLd
+                          : (pass == 0 ? t.kind <= kFwdCols && t.r0 % kFwdRows == 0 : t.kind <= kBwdRows && t.r0 % 4 == 0);
+      if (!node_ok || !shape_ok) return fail(ctx, FFA_ERR_INVALID_ARG, "internal: a solve task exceeds the kernels' tile limits");
+    }
+  }
+  for (const NodeDev& nd : sch.sub_nodes)
+    if (nd.ld > kNodeMaxLd || nd.ld % 4 != 0)
+      return fail(ctx, FFA_ERR_INVALID_ARG, "internal: a merged subtree node exceeds the kernels' tile limits");
   ctx->fwd_off = sch.fwd_off;
   ctx->bwd_off = sch.bwd_off;
   ffa_status st;
@@ -519,6 +540,8 @@ ffa_status build_tasks(ffa_ctx* ctx) {
   const int n_top_f = (int)sch.fwd.tasks.size(), n_top_b = (int)sch.bwd.tasks.size();
   ctx->grid_f = std::max(1, std::min(ctx->grid_f, n_top_f));
   ctx->grid_b = std::max(1, std::min(ctx->grid_b, n_top_b));
+  ctx->pgrid_f = std::max(1, std::min(ctx->pgrid_f, n_top_f));
+  ctx->pgrid_b = std::max(1, std::min(ctx->pgrid_b, n_top_b));
   FFA_CUDA(cudaStreamSynchronize(ctx->stream));
   return FFA_OK;
 }
@@ -1979,8 +2002,12 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
   // 3) supernodal solves: per-level launches or one persistent launch per pass
   best = 1e300;
   int best_sched = ctx->schedule;
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < 3; ++c) {
     ctx->schedule = c;
+    if (c == 2 && (ctx->pgrid_f < 1 || ctx->pgrid_b < 1)) {
+      t.ms_schedule[c] = 0.0;
+      continue;
+    }
     SolveData S = solve_data(ctx);
     launch_supernodal_solve(S, s);
     FFA_CUDA(cudaEventRecord(e0, s));
@@ -1996,8 +2023,8 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
     }
   }
   ctx->schedule = best_sched;
-  // 4) dynamic schedule: how many of the lowest tree levels run as one launch per level
-  if (ctx->schedule == 1) {
+  // 4) dynamic schedules: how many of the lowest tree levels run as one launch per level
+  if (ctx->schedule >= 1) {
     const int bottoms[4] = {0, 2, 3, 4};
     best = 1e300;
     int best_bottom = ctx->bottom_levels;
@@ -2026,7 +2053,7 @@ ffa_status ffa_autotune(ffa_ctx* ctx, int32_t reps, ffa_tuning* out) {
   t.subtree_height[0] = ctx->subtree_height_f;
   t.subtree_height[1] = ctx->subtree_height_b;
   for (int c = 0; c < 4; ++c) t.ms_subtree[0][c] = t.ms_subtree[1][c] = 0.0;
-  if (ctx->schedule == 1 && ctx->bottom_levels == 0) {
+  if (ctx->schedule >= 1 && ctx->bottom_levels == 0) {
     for (auto& e : ctx->solve_ev) FFA_CUDA(cudaEventCreate(&e));
     double best_f = 1e300, best_b = 1e300;
     int hf = ctx->subtree_height_f, hb = ctx->subtree_height_b;

@@ -161,13 +161,15 @@ struct SolveData {
   const Task* bwd_tasks;
   const NodeDev* sub_nodes;  // merged subtrees of the dynamic passes
   std::vector<int64_t> fwd_off, bwd_off;  // per level task ranges (host)
-  int schedule = 0;          // 0: one launch per level, 1: one dynamic launch per pass
+  int schedule = 0;          // 0: one launch per level, 1: one dynamic launch per pass,
+                             // 2: one pipelined launch per pass (bulk-copy ring)
   DynPass fdyn, bdyn;            // dynamic passes over the levels >= bottom_levels
   int bottom_levels = 0;         // levels below run as one launch per level (schedule 1)
   int n_nodes = 0;
   int32_t* err_flag = nullptr;      // set to 1 if a wait ran out of polls
   long long spin_limit = kDefaultSpinLimit;  // polls per wait before giving up
-  int grid_f = 0, grid_b = 0;
+  int grid_f = 0, grid_b = 0;     // resident blocks of the dynamic passes (schedule 1)
+  int pgrid_f = 0, pgrid_b = 0;   // resident blocks of the pipelined passes (schedule 2)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional: before forward, between, after backward
   float* y;                  // nF x d residual / forward work vector
   float* z;                  // nF x d forward result
@@ -180,6 +182,7 @@ void launch_residual(const SolveData& S, double* partials, int n_blocks, cudaStr
 void launch_axpy_correction(const SolveData& S, cudaStream_t s);   // X += x
 void launch_supernodal_solve(const SolveData& S, cudaStream_t s);  // x = L_FF^{-1} y (FP32)
 int persistent_grid(int d, bool forward);  // resident blocks of the dynamic solve kernels
+int persistent_pipe_grid(int d, bool forward);  // resident blocks of the pipelined ones (0: unavailable)
 
 // constant part of the right-hand side: cst = -L_FC b (eliminated order)
 void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, const double* val,

@@ -914,6 +914,589 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_solve_dynami
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined schedule (solve_schedule 2).  The same ready queue, task lists and
+// release protocol as the dynamic schedule above, but each block is one producer
+// warp and kPipeConsumers consumer warps.  The producer claims the next queue slot
+// as soon as one of kPipeSlots task entries is free, copies the task record, its
+// node's push record and a merged subtree's node list into shared memory, and
+// streams the task's factor data with 1D bulk copies (cp.async.bulk, completion
+// counted in transaction bytes on an mbarrier) into a ring of kPipeStages chunks
+// of kPipeChunkFloats floats.  The consumers stage the right-hand side, compute
+// from the ring, release each chunk, and do the reduction, scatter and completion
+// of the dynamic schedule.  The bytes in flight are set by the ring (64 KB per
+// block), not by registers, and the next task's factor streams while the current
+// one reduces and completes.  A producer claims a task only after it has issued
+// every chunk of the previous one, so the consumers never wait on a task that
+// depends on the producer.  Every wait is bounded: a producer that gives up on a
+// queue slot sets err_flag and ends the block's task stream; a consumer wait that
+// runs out sets err_flag and the consumers skip the remaining waits; the producer
+// waits (bounded) for its own copies before it exits.
+//
+// Chunks (computed identically on both sides):
+//   forward wide   : 32 columns of the task's 128-row band, one copy per column,
+//                    stored 128 floats apart; rows above the diagonal of
+//                    inv(L_ss) (row < column, stored zeros) start the copy at the
+//                    column's 4-row group instead of the band's first row;
+//   backward wide  : one 128-row band of the task's 32 columns, laid out the same;
+//                    bands wholly above the diagonal of the first column are skipped;
+//   node (whole supernode, also inside a merged subtree): floor(kPipeChunkFloats /
+//                    ld) whole columns, contiguous in B_s, one copy.
+// ---------------------------------------------------------------------------
+constexpr int kPipeConsumers = kSolveWarps;                 // consumer warps (the task mappings assume 8)
+constexpr int kPipeThreads = 32 * (kPipeConsumers + 1);     // plus one producer warp
+constexpr int kPipeStages = 4;
+constexpr int kPipeChunkFloats = 4096;                      // 16 KB per chunk
+constexpr int kPipeSlots = 2;                               // task entries in flight
+constexpr int kPipeEnd = -1000;                             // task kind that ends the stream
+static_assert(kPipeConsumers * 32 == kSolveThreads, "consumers take the roles of a solve block");
+
+template <int D>
+struct PipeSmem {
+  float ring[kPipeStages][kPipeChunkFloats];
+  float rhs[D * 1024];      // f ([cols][D]) forward, v ([D][rows]) backward
+  float red[D * 1024];      // forward partial sums
+  Task task[kPipeSlots];
+  int4 rec[kPipeSlots][1 + kPushKids];
+  NodeDev sub[kPipeSlots][kSubtreeMaxNodes];
+  unsigned long long full[kPipeStages], empty[kPipeStages], tfull[kPipeSlots], tempty[kPipeSlots];
+  int base_s, stop_s;
+  volatile int err_s;   // a consumer wait ran out: later waits are skipped
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" :: "r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+               :: "r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity; false when `limit` polls ran out
+// or *stop became nonzero
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, long long limit,
+                                          const volatile int* stop) {
+  long long it = 0;
+  while (!mbar_test(b, parity)) {
+    if (++it > limit || *stop) return false;
+    if (it > 64) __nanosleep(32);
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar,
+                                              uint64_t pol) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" :: "n"(kSolveThreads) : "memory"); }
+
+// chunks of a whole node and of the wide tasks (see above)
+__device__ __forceinline__ int node_cpc(const NodeDev& nd) { return max(1, kPipeChunkFloats / nd.ld); }
+__device__ __forceinline__ int node_chunks(const NodeDev& nd) {
+  const int c = node_cpc(nd);
+  return (nd.ncol + c - 1) / c;
+}
+__device__ __forceinline__ int fwd_wide_cols(const Task& t) { return min(t.kind, t.nd.ncol - t.c0); }
+__device__ __forceinline__ int bwd_wide_rows(const Task& t) { return min(t.kind, t.nd.ld - t.r0); }
+__device__ __forceinline__ int bwd_first_band(const Task& t) { return max(0, (t.c0 & ~3) - t.r0) / 128; }
+
+__device__ __forceinline__ const float* blocks_at(const DynView& V, const NodeDev& nd, int col, int row) {
+  return V.blocks + nd.blk_off + (int64_t)col * nd.ld + row;
+}
+
+// the bytes of column `col` of B_s from row max(row0, col & ~3) to row0 + nrows
+// (rows above the diagonal of inv(L_ss) are not copied); 0 if none
+__device__ __forceinline__ uint32_t band_copy(const NodeDev& nd, int col, int row0, int nrows, int& start) {
+  start = max(row0, col & ~3);
+  return start < row0 + nrows ? (uint32_t)(row0 + nrows - start) * 4u : 0u;
+}
+
+template <int D, bool FWD>
+__device__ void pipe_producer(PipeSmem<D>& S, const DynView& V) {
+  const int lane = threadIdx.x & 31;
+  const DynPass& P = V.P;
+  constexpr int kRec = FWD ? 1 : 1 + kPushKids;
+  const long long wait_limit = 4 * V.spin_limit + (1 << 16);
+  long long last_k[kPipeStages];
+#pragma unroll
+  for (int s = 0; s < kPipeStages; ++s) last_k[s] = -1;
+  long long k = 0;   // chunks issued so far
+  bool ok = true;
+  // one chunk into the next stage: `bytes` of this lane's copy from src to the
+  // stage at float offset dst_off (0 bytes: no copy)
+  auto acquire_stage = [&]() -> int {
+    const int s = (int)(k % kPipeStages);
+    if (k >= kPipeStages) {
+      bool w = true;
+      if (lane == 0) w = mbar_wait(&S.empty[s], (uint32_t)(((k / kPipeStages) - 1) & 1), wait_limit, &S.err_s);
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (!w) return -1;
+    }
+    return s;
+  };
+  auto commit = [&](int s, const float* src, int dst_off, uint32_t bytes, uint64_t pol) {
+    uint32_t tot = bytes;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) mbar_expect_tx(&S.full[s], tot);
+    __syncwarp();
+    if (bytes) bulk_copy_g2s(&S.ring[s][dst_off], src, bytes, &S.full[s], pol);
+    last_k[s] = k;
+    ++k;
+  };
+  auto node_stream = [&](const NodeDev& nd) -> bool {
+    const uint64_t pol = l2_policy(nd.l2_keep);
+    const int cpc = node_cpc(nd), nq = node_chunks(nd);
+    for (int q = 0; q < nq; ++q) {
+      const int s = acquire_stage();
+      if (s < 0) return false;
+      const int nc = min(cpc, nd.ncol - q * cpc);
+      commit(s, blocks_at(V, nd, q * cpc, 0), 0, lane == 0 ? (uint32_t)nc * nd.ld * 4u : 0u, pol);
+    }
+    return true;
+  };
+  for (int n = 0; ok; ++n) {
+    const int e = n % kPipeSlots;
+    if (n >= kPipeSlots) {
+      bool w = true;
+      if (lane == 0) w = mbar_wait(&S.tempty[e], (uint32_t)(((n / kPipeSlots) - 1) & 1), wait_limit, &S.err_s);
+      if (!__shfl_sync(0xffffffffu, w, 0)) {
+        ok = false;
+        break;
+      }
+    }
+    int t = -1;
+    if (lane == 0) {
+      const int h = atomicAdd(P.ctr, 1);
+      if (h < P.n_tasks) {
+        long long it = 0;
+        while ((t = ld_acquire(P.queue + h)) < 0) {
+          if (++it > V.spin_limit || ld_acquire(V.err_flag) != 0) {
+            atomicExch(V.err_flag, 1);
+            t = -1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t < 0) {
+      if (lane == 0) {
+        S.task[e].kind = kPipeEnd;
+        __threadfence_block();
+        mbar_arrive(&S.tfull[e]);
+      }
+      break;
+    }
+    // the task, its node's push record and a merged subtree's nodes
+    if (lane < 4) reinterpret_cast<int4*>(&S.task[e])[lane] = __ldg(reinterpret_cast<const int4*>(P.tasks + t) + lane);
+    __syncwarp();
+    const Task& tk = S.task[e];
+    if (lane < kRec) S.rec[e][lane] = __ldg(P.push + (int64_t)tk.node * kRec + lane);
+    if (tk.kind == 0) {
+      constexpr int kw = (int)(sizeof(NodeDev) / 4);
+      for (int i = lane; i < tk.c0 * kw; i += 32)
+        reinterpret_cast<int32_t*>(S.sub[e])[i] = __ldg(reinterpret_cast<const int32_t*>(V.sub + tk.r0) + i);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      mbar_arrive(&S.tfull[e]);
+    }
+    // the factor chunks, in the order the consumers take them
+    if (tk.kind == 0) {
+      for (int i = 0; i < tk.c0 && ok; ++i) ok = node_stream(S.sub[e][FWD ? i : tk.c0 - 1 - i]);
+    } else if (tk.kind == 1) {
+      ok = node_stream(tk.nd);
+    } else if (FWD) {
+      const NodeDev& nd = tk.nd;
+      const uint64_t pol = l2_policy(nd.l2_keep);
+      const int nc = fwd_wide_cols(tk), R = min(kFwdRows, nd.ld - tk.r0);
+      for (int q = 0; q * 32 < nc && ok; ++q) {
+        const int s = acquire_stage();
+        if (s < 0) { ok = false; break; }
+        const int col = tk.c0 + 32 * q + lane;
+        int start = 0;
+        const uint32_t bytes = (32 * q + lane < nc) ? band_copy(nd, col, tk.r0, R, start) : 0u;
+        commit(s, bytes ? blocks_at(V, nd, col, start) : nullptr, lane * kFwdRows + (start - tk.r0), bytes, pol);
+      }
+    } else {
+      const NodeDev& nd = tk.nd;
+      const uint64_t pol = l2_policy(nd.l2_keep);
+      const int nr = bwd_wide_rows(tk), ncw = min(32, nd.ncol - tk.c0);
+      for (int b = bwd_first_band(tk); b * 128 < nr && ok; ++b) {
+        const int s = acquire_stage();
+        if (s < 0) { ok = false; break; }
+        const int rb = tk.r0 + 128 * b, Rb = min(128, nr - 128 * b);
+        const int col = tk.c0 + lane;
+        int start = 0;
+        const uint32_t bytes = lane < ncw ? band_copy(nd, col, rb, Rb, start) : 0u;
+        commit(s, bytes ? blocks_at(V, nd, col, start) : nullptr, lane * 128 + (start - rb), bytes, pol);
+      }
+    }
+  }
+  if (!ok) atomicExch(V.err_flag, 1);
+  // every copy this warp issued has landed before the block may exit
+  if (lane == 0) {
+    const long long drain_limit = 4 * V.spin_limit + (1 << 16);
+    volatile int never = 0;
+#pragma unroll
+    for (int s = 0; s < kPipeStages; ++s)
+      if (last_k[s] >= 0) mbar_wait(&S.full[s], (uint32_t)((last_k[s] / kPipeStages) & 1), drain_limit, &never);
+  }
+}
+
+template <int D, bool FWD>
+__device__ void pipe_consumer(PipeSmem<D>& S, const DynView& V) {
+  const DynPass& P = V.P;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long wait_limit = 4 * V.spin_limit + (1 << 16);
+  const long long task_limit = 64 * V.spin_limit + (1 << 20);
+  long long k = 0;   // chunks consumed so far
+  // chunk k is in stage k % kPipeStages; a wait that runs out marks the block
+  // failed (the remaining waits are skipped, the results are invalid)
+  auto take = [&]() -> int {
+    const int s = (int)(k % kPipeStages);
+    if (!S.err_s && !mbar_wait(&S.full[s], (uint32_t)((k / kPipeStages) & 1), wait_limit, &S.err_s)) {
+      S.err_s = 1;
+      atomicExch(V.err_flag, 1);
+    }
+    return s;
+  };
+  auto release = [&](int s) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.empty[s]);
+    ++k;
+  };
+
+  // forward, whole node: z_s = inv(L_ss) y_s, y_r -= (L_rs inv(L_ss)) y_s
+  auto fwd_node = [&](const NodeDev& nd) {
+    float (*f)[D] = reinterpret_cast<float (*)[D]>(S.rhs);
+    const int ntot = nd.ncol + nd.nrow;
+    const int G = nd.ld >> 2, Sl = kSolveThreads / G;
+    const int g = threadIdx.x % G, j = threadIdx.x / G;
+    const bool active = j < Sl;
+    for (int q = threadIdx.x; q < nd.ncol * D; q += kSolveThreads) {
+      const int c = q / D, kk = q - c * D;
+      f[c][kk] = __ldcg(V.y + (int64_t)(nd.col0 + c) * D + kk);
+    }
+    consumer_sync();
+    float acc[4][D];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) acc[q][kk] = 0.f;
+    const int cpc = node_cpc(nd), nq = node_chunks(nd);
+    for (int q = 0; q < nq; ++q) {
+      const int s = take();
+      if (active) {
+        const int cb = q * cpc, ce = min(nd.ncol, cb + cpc);
+        for (int c = cb + j; c < ce; c += Sl) {
+          const float4 bv = *reinterpret_cast<const float4*>(&S.ring[s][(c - cb) * nd.ld + 4 * g]);
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) {
+            const float fv = f[c][kk];
+            acc[0][kk] = fmaf(bv.x, fv, acc[0][kk]);
+            acc[1][kk] = fmaf(bv.y, fv, acc[1][kk]);
+            acc[2][kk] = fmaf(bv.z, fv, acc[2][kk]);
+            acc[3][kk] = fmaf(bv.w, fv, acc[3][kk]);
+          }
+        }
+      }
+      release(s);
+    }
+    if (active) {
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk)
+        *reinterpret_cast<float4*>(S.red + (kk * Sl + j) * nd.ld + 4 * g) =
+            make_float4(acc[0][kk], acc[1][kk], acc[2][kk], acc[3][kk]);
+    }
+    consumer_sync();
+    for (int r = threadIdx.x; r < ntot; r += kSolveThreads) {
+      float sm[D];
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) {
+        float a = 0.f;
+        for (int jj = 0; jj < Sl; ++jj) a += S.red[(kk * Sl + jj) * nd.ld + r];
+        sm[kk] = a;
+      }
+      if (r < nd.ncol) {
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) V.z[(int64_t)(nd.col0 + r) * D + kk] = sm[kk];
+      } else {
+        const int rr = __ldg(V.rows + nd.row_off + (r - nd.ncol));
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) atomicAdd(V.y + (int64_t)rr * D + kk, -sm[kk]);
+      }
+    }
+  };
+
+  // backward, whole node: x_s = inv(L_ss)^T z_s - (L_rs inv(L_ss))^T x_r
+  auto bwd_node = [&](const NodeDev& nd) {
+    const int ld = nd.ld;
+    stage_v<D>(nd, 0, ld, V.rows, V.z, V.x, S.rhs, ld);
+    consumer_sync();
+    const int cg = lane >> 3, rl = lane & 7;
+    const int cpc = node_cpc(nd), nq = node_chunks(nd);
+    for (int q = 0; q < nq; ++q) {
+      const int s = take();
+      const int cb = q * cpc, ce = min(nd.ncol, cb + cpc);
+      for (int jj = cb + 4 * warp; jj < ce; jj += 4 * kPipeConsumers) {   // warp-uniform
+        const int j = jj + cg;
+        float acc[D];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) acc[kk] = 0.f;
+        if (j < ce) {
+          const float* Bc = &S.ring[s][(j - cb) * ld];
+          for (int r = (j & ~31) + 4 * rl; r < ld; r += 32) {
+            const float4 b = *reinterpret_cast<const float4*>(Bc + r);
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) {
+              const float4 v = *reinterpret_cast<const float4*>(S.rhs + kk * ld + r);
+              acc[kk] = fmaf(b.x, v.x, acc[kk]);
+              acc[kk] = fmaf(b.y, v.y, acc[kk]);
+              acc[kk] = fmaf(b.z, v.z, acc[kk]);
+              acc[kk] = fmaf(b.w, v.w, acc[kk]);
+            }
+          }
+        }
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) {
+          float a = acc[kk];
+          a += __shfl_xor_sync(0xffffffffu, a, 4);
+          a += __shfl_xor_sync(0xffffffffu, a, 2);
+          a += __shfl_xor_sync(0xffffffffu, a, 1);
+          acc[kk] = a;
+        }
+        if (rl == 0 && j < ce) {
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) V.x[(int64_t)(nd.col0 + j) * D + kk] = acc[kk];
+        }
+      }
+      release(s);
+    }
+  };
+
+  // forward wide task: rows [r0, r0 + 128) of B_s times columns [c0, c0 + nc) of f
+  auto fwd_wide = [&](const Task& t) {
+    const NodeDev& nd = t.nd;
+    const int nc = fwd_wide_cols(t), R = min(kFwdRows, nd.ld - t.r0), ntot = nd.ncol + nd.nrow;
+    float (*fs)[D] = reinterpret_cast<float (*)[D]>(S.rhs);
+    for (int q = threadIdx.x; q < nc * D; q += kSolveThreads) {
+      const int c = q / D, kk = q - c * D;
+      fs[c][kk] = __ldcg(V.y + (int64_t)(nd.col0 + t.c0 + c) * D + kk);
+    }
+    consumer_sync();
+    float acc[4][D];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) acc[q][kk] = 0.f;
+    const int r = 4 * lane;
+    for (int q = 0; q * 32 < nc; ++q) {
+      const int s = take();
+      if (r < R) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cl = 32 * q + 4 * warp + u;
+          const int col = t.c0 + cl;
+          if (cl < nc && t.r0 + r >= (col & ~3)) {
+            const float4 bv = *reinterpret_cast<const float4*>(&S.ring[s][(4 * warp + u) * kFwdRows + r]);
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) {
+              const float fv = fs[cl][kk];
+              acc[0][kk] = fmaf(bv.x, fv, acc[0][kk]);
+              acc[1][kk] = fmaf(bv.y, fv, acc[1][kk]);
+              acc[2][kk] = fmaf(bv.z, fv, acc[2][kk]);
+              acc[3][kk] = fmaf(bv.w, fv, acc[3][kk]);
+            }
+          }
+        }
+      }
+      release(s);
+    }
+    float (*red)[kFwdRows][D] = reinterpret_cast<float (*)[kFwdRows][D]>(S.red);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) red[warp][4 * lane + q][kk] = acc[q][kk];
+    consumer_sync();
+    if (threadIdx.x < kFwdRows) {
+      const int row = t.r0 + threadIdx.x;
+      if (row < ntot && !(row < nd.ncol && row < t.c0)) {
+        float sm[D];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) {
+          float a = 0.f;
+#pragma unroll
+          for (int w = 0; w < kPipeConsumers; ++w) a += red[w][threadIdx.x][kk];
+          sm[kk] = a;
+        }
+        if (row < nd.ncol) {
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) atomicAdd(V.z + (int64_t)(nd.col0 + row) * D + kk, sm[kk]);
+        } else {
+          const int rr = __ldg(V.rows + nd.row_off + (row - nd.ncol));
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) atomicAdd(V.y + (int64_t)rr * D + kk, -sm[kk]);
+        }
+      }
+    }
+  };
+
+  // backward wide task: output columns [c0, c0 + 32) against rows [r0, r0 + nr)
+  auto bwd_wide = [&](const Task& t) {
+    const NodeDev& nd = t.nd;
+    const int nr = bwd_wide_rows(t);
+    float (*vs)[kBwdRows] = reinterpret_cast<float (*)[kBwdRows]>(S.rhs);
+    stage_v<D>(nd, t.r0, nr, V.rows, V.z, V.x, &vs[0][0], kBwdRows);
+    consumer_sync();
+    const int j0 = t.c0 + 4 * warp;
+    const int ncw = max(0, min(4, nd.ncol - j0));
+    float acc[4][D];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) acc[q][kk] = 0.f;
+    const int r = 4 * lane;
+    for (int b = bwd_first_band(t); b * 128 < nr; ++b) {
+      const int s = take();
+      const int rb = t.r0 + 128 * b, Rb = min(128, nr - 128 * b);
+      if (r < Rb) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int col = j0 + u;
+          if (u < ncw && rb + r >= (col & ~3)) {
+            const float4 bv = *reinterpret_cast<const float4*>(&S.ring[s][(4 * warp + u) * 128 + r]);
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) {
+              const float4 v = *reinterpret_cast<const float4*>(&vs[kk][rb - t.r0 + r]);
+              acc[u][kk] = fmaf(bv.x, v.x, acc[u][kk]);
+              acc[u][kk] = fmaf(bv.y, v.y, acc[u][kk]);
+              acc[u][kk] = fmaf(bv.z, v.z, acc[u][kk]);
+              acc[u][kk] = fmaf(bv.w, v.w, acc[u][kk]);
+            }
+          }
+        }
+      }
+      release(s);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) {
+        float a = acc[u][kk];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        acc[u][kk] = a;
+      }
+    if (lane == 0) {
+      for (int u = 0; u < ncw; ++u)
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) atomicAdd(V.x + (int64_t)(nd.col0 + j0 + u) * D + kk, acc[u][kk]);
+    }
+  };
+
+  for (int n = 0;; ++n) {
+    const int e = n % kPipeSlots;
+    if (threadIdx.x == 0) {
+      if (!S.err_s && !mbar_wait(&S.tfull[e], (uint32_t)((n / kPipeSlots) & 1), task_limit, &S.err_s)) {
+        S.err_s = 1;
+        atomicExch(V.err_flag, 1);
+      }
+      S.stop_s = (S.err_s || S.task[e].kind == kPipeEnd) ? 1 : 0;
+    }
+    consumer_sync();
+    if (S.stop_s) break;
+    const Task& t = S.task[e];
+    if (t.kind == 0) {
+      // a merged bottom subtree: its nodes in order (forward children first,
+      // backward parents first), each on all consumers
+      const int n_sub = t.c0;
+      for (int i = 0; i < n_sub; ++i) {
+        if constexpr (FWD) fwd_node(S.sub[e][i]);
+        else bwd_node(S.sub[e][n_sub - 1 - i]);
+        consumer_sync();
+      }
+    } else if (t.kind == 1) {
+      if constexpr (FWD) fwd_node(t.nd);
+      else bwd_node(t.nd);
+    } else {
+      if constexpr (FWD) fwd_wide(t);
+      else bwd_wide(t);
+    }
+    // completion, as in the dynamic schedule: one fence, one counter atomic and,
+    // when something is released, one queue reservation; then every consumer
+    // writes released task ids
+    consumer_sync();
+    if (threadIdx.x == 0) {
+      const int4 r = S.rec[e][0];
+      int base = -1;
+      __threadfence();
+      if constexpr (FWD) {
+        if (r.x >= 0 && atomicSub(P.pending + r.x, 1) == 1) base = atomicAdd(P.ctr + 1, r.z);
+      } else if (r.z > 0 && (t.kind <= 1 || atomicAdd(P.done + t.node, 1) == r.w - 1)) {
+        base = atomicAdd(P.ctr + 1, r.z);
+      }
+      if (base >= 0) __threadfence();
+      S.base_s = base;
+    }
+    consumer_sync();
+    const int base = S.base_s;
+    if (base >= 0) {
+      __threadfence();
+      const int4 r = S.rec[e][0];
+      if constexpr (FWD) {
+        for (int i = threadIdx.x; i < r.z; i += kSolveThreads) st_relaxed(P.queue + base + i, r.y + i);
+      } else {
+        for (int kq = r.x; kq < r.y; ++kq) {   // block-uniform
+          const int jq = kq - r.x;
+          const int4 ev = jq < kPushKids ? S.rec[e][1 + jq] : P.kids[kq];
+          for (int i = threadIdx.x; i < ev.y; i += kSolveThreads) st_relaxed(P.queue + base + ev.z + i, ev.x + i);
+        }
+      }
+    }
+    consumer_sync();   // the entry (task, push record) and rhs / red are free again
+    if (threadIdx.x == 0) mbar_arrive(&S.tempty[e]);
+  }
+}
+
+template <int D, bool FWD>
+__global__ void __launch_bounds__(kPipeThreads, 2) k_solve_pipe(DynView V) {
+  extern __shared__ __align__(128) unsigned char ffa_pipe_smem[];
+  PipeSmem<D>& S = *reinterpret_cast<PipeSmem<D>*>(ffa_pipe_smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < kPipeStages; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], kPipeConsumers);
+    }
+#pragma unroll
+    for (int e = 0; e < kPipeSlots; ++e) {
+      mbar_init(&S.tfull[e], 1);
+      mbar_init(&S.tempty[e], 1);
+    }
+    S.err_s = 0;
+    S.stop_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x >= kSolveThreads) pipe_producer<D, FWD>(S, V);
+  else pipe_consumer<D, FWD>(S, V);
+}
+
 // restores the ready queues, pending counts and completion counts of both passes
 // and zeroes z and x (both are accumulated with atomics)
 __global__ void k_dyn_reset(DynPass F, DynPass B, int n_nodes, float* __restrict__ z, float* __restrict__ x,
@@ -1111,16 +1694,26 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
   k_dyn_reset<<<reset_grid, 256, 0, s>>>(S.fdyn, S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
   if (S.ev[0]) cudaEventRecord(S.ev[0], s);
   const int L = (int)S.fwd_off.size() - 1;
-  if (S.schedule == 1) {
+  if (S.schedule == 1 || S.schedule == 2) {
     const DynView vf{S.fdyn, S.sub_nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag, S.spin_limit};
     const DynView vb{S.bdyn, S.sub_nodes, S.rows, S.blocks, S.y, S.z, S.x, S.err_flag, S.spin_limit};
     const int nb = std::min(S.bottom_levels, L);
     launch_levels(S, 0, nb, true, s);
-    if (S.d == 2) k_solve_dynamic<2, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);
-    else k_solve_dynamic<3, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);
+    if (S.schedule == 2) {
+      if (S.d == 2) k_solve_pipe<2, true><<<S.pgrid_f, kPipeThreads, sizeof(PipeSmem<2>), s>>>(vf);
+      else k_solve_pipe<3, true><<<S.pgrid_f, kPipeThreads, sizeof(PipeSmem<3>), s>>>(vf);
+    } else {
+      if (S.d == 2) k_solve_dynamic<2, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);
+      else k_solve_dynamic<3, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);
+    }
     if (S.ev[1]) cudaEventRecord(S.ev[1], s);
-    if (S.d == 2) k_solve_dynamic<2, false><<<S.grid_b, kSolveThreads, 0, s>>>(vb);
-    else k_solve_dynamic<3, false><<<S.grid_b, kSolveThreads, 0, s>>>(vb);
+    if (S.schedule == 2) {
+      if (S.d == 2) k_solve_pipe<2, false><<<S.pgrid_b, kPipeThreads, sizeof(PipeSmem<2>), s>>>(vb);
+      else k_solve_pipe<3, false><<<S.pgrid_b, kPipeThreads, sizeof(PipeSmem<3>), s>>>(vb);
+    } else {
+      if (S.d == 2) k_solve_dynamic<2, false><<<S.grid_b, kSolveThreads, 0, s>>>(vb);
+      else k_solve_dynamic<3, false><<<S.grid_b, kSolveThreads, 0, s>>>(vb);
+    }
     launch_levels(S, 0, nb, false, s);
     if (S.ev[2]) cudaEventRecord(S.ev[2], s);
     return;
@@ -1161,6 +1754,26 @@ int persistent_grid(int d, bool forward) {
                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_dynamic<3, false>, kSolveThreads, 0);
   if (e != cudaSuccess || per < 1) per = 1;
   return sms * per;
+}
+
+// resident blocks of the pipelined solve kernels (dynamic shared memory above the
+// default 48 KB limit is enabled here, once, before any launch or capture)
+template <int D, bool FWD>
+int pipe_grid_for() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int bytes = (int)sizeof(PipeSmem<D>);
+  if (cudaFuncSetAttribute(k_solve_pipe<D, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_pipe<D, FWD>, kPipeThreads, bytes) != cudaSuccess)
+    return 0;
+  return sms * per;
+}
+
+int persistent_pipe_grid(int d, bool forward) {
+  if (d == 2) return forward ? pipe_grid_for<2, true>() : pipe_grid_for<2, false>();
+  return forward ? pipe_grid_for<3, true>() : pipe_grid_for<3, false>();
 }
 
 void launch_pin_rhs(int d, int nF, const int64_t* ptr, const int32_t* pin_col, const double* val,

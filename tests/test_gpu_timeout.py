@@ -25,7 +25,8 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def test_wait_limit_runs_out_and_the_context_recovers():
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_wait_limit_runs_out_and_the_context_recovers(schedule):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -39,7 +40,7 @@ def test_wait_limit_runs_out_and_the_context_recovers():
     for _ in range(iters):
         s, _ = o.step(s)
 
-    with Solver.from_workload(wl, precision="fp64", check_every=1, schedule=1) as sol:
+    with Solver.from_workload(wl, precision="fp64", check_every=1, schedule=schedule) as sol:
         assert sol.info()["n_levels"] >= 4
         sol.init(wl.W0)
         sol.set_wait_limit(0)
@@ -57,7 +58,7 @@ def test_wait_limit_runs_out_and_the_context_recovers():
     with pytest.raises(FFAError, match="INVALID_ARG"):
         with Solver.from_workload(wl, precision="fp64") as sol:
             sol.set_wait_limit(-1)
-    with Solver.from_workload(wl, precision="fp64", check_every=1, schedule=1) as fresh:
+    with Solver.from_workload(wl, precision="fp64", check_every=1, schedule=schedule) as fresh:
         fresh.init(wl.W0)
         fresh.iterate(iters, stop_at_tol=False)
         W_fresh = fresh.W()
