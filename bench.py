@@ -48,9 +48,13 @@ def parse():
                          "2 dynamic ready queue with a bulk-copy ring per block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cells", type=int, default=16)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--growth-cells", type=int, nargs="*", default=[24, 32],
+                    help="cube sizes at which the oracle is also timed to measure its growth exponent")
+    ap.add_argument("--oracle-probe", type=float, nargs=3, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="cube_deform",
-                    choices=["cube_deform", "batch256", "uv_disk", "uv_heightfield", "cube_handles", "tutte"],
+                    choices=["cube_deform", "cube_outcome", "batch256", "uv_disk", "uv_heightfield", "cube_handles",
+                             "tutte"],
                     help="cube_deform: the throughput benchmark; the others report time to tolerance "
                          "(uv_disk, uv_heightfield), batched meshes, or forward + adjoint (cube_handles)")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -163,23 +167,75 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_sample(cells: int, seconds: float, steps: int | None = None):
-    """Time the FP64 oracle on a smaller cube of the same recipe; returns per-iteration seconds."""
+def oracle_probe(cells: int, iters: int, seconds: float = 0.0):
+    """Per-iteration wall time of the FP64 oracle on the cube of `cells`^3 cells:
+    setup and one iteration untimed, then `iters` iterations (or as many as fit in
+    `seconds`, at least `iters`).  Returns (tets, list of per-iteration seconds)."""
     from oracle import admm
     from paper_2107_05200_gb300 import workloads as wk
     wl = wk.cube_deform(cells=cells)
     o = admm.Oracle.from_workload(wl)
     s = o.init(wl.W0)
-    s, _ = o.step(s)                     # first iteration outside the timing
+    s, _ = o.step(s)
     times = []
     t_end = time.perf_counter() + seconds
-    n = 0
-    while (steps is None and time.perf_counter() < t_end) or (steps is not None and n < steps):
+    while len(times) < iters or time.perf_counter() < t_end:
         t0 = time.perf_counter()
         s, _ = o.step(s)
         times.append(time.perf_counter() - t0)
-        n += 1
-    return wl, times
+    return wl.m, times
+
+
+def oracle_timings(sizes, iters, seconds, threads):
+    """oracle_probe for each (cells) in `sizes`, each in a fresh process whose
+    numerical libraries are limited to `threads` threads (None: their default).
+    Returns {cells: (tets, per-iteration seconds list)}."""
+    env = dict(os.environ)
+    if threads is not None:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = str(threads)
+    out = {}
+    for c, it, sec in zip(sizes, iters, seconds):
+        proc = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-probe", str(c), str(it), str(sec)],
+                              env=env, capture_output=True, text=True, check=True)
+        d = json.loads(proc.stdout.strip().splitlines()[-1])
+        out[c] = (d["tets"], d["times"])
+    return out
+
+
+def extrapolate(samples, m_full):
+    """Per-iteration seconds at m_full tets from the medians measured at the sampled
+    sizes: a least-squares fit of log t = a + alpha log m.  Returns (seconds, alpha)."""
+    import numpy as np
+    ms = np.array([samples[c][0] for c in sorted(samples)], float)
+    ts = np.array([statistics.median(samples[c][1]) for c in sorted(samples)], float)
+    alpha, a = np.polyfit(np.log(ms), np.log(ts), 1)
+    return float(math.exp(a) * m_full ** alpha), float(alpha)
+
+
+def oracle_baseline(m_full: int, n_full: int, sample_cells: int, seconds: float, growth_cells, threads):
+    """The oracle timed on a bounded sample (the same recipe on smaller cubes) and
+    extrapolated to the full workload with the growth exponent measured across the
+    sampled sizes.  Returns the cpu_baseline / reference description."""
+    sizes = [sample_cells] + list(growth_cells)
+    samples = oracle_timings(sizes, [3] + [2] * len(growth_cells), [seconds] + [0.0] * len(growth_cells), threads)
+    per_it, alpha = extrapolate(samples, m_full)
+    m_s, t_s = samples[sample_cells]
+    per_s = statistics.median(t_s)
+    return {
+        "value": 1.0 / per_it, "unit": UNIT, "kind": "oracle",
+        "cores": 1 if threads == 1 else (os.cpu_count() or 1),
+        "threads": threads if threads is not None else "library default",
+        "sample": (f"FP64 numpy/scipy oracle on the benchmark recipe at {sample_cells}^3 cells ({m_s} tets, "
+                   f"{len(t_s)} timed iterations, median {per_s:.3f} s) and at "
+                   + ", ".join(f"{c}^3 ({samples[c][0]} tets, {statistics.median(samples[c][1]):.3f} s)"
+                               for c in growth_cells)
+                   + f"; per-iteration time fitted as m^{alpha:.3f} and extrapolated to {m_full} tets"),
+        "sample_workload": f"cube_deform_{sample_cells}", "sample_tets": m_s, "sample_iter_per_s": 1.0 / per_s,
+        "growth_exponent": alpha, "extrapolated_s_per_iter": per_it,
+        "sizes": {f"cube_deform_{c}": {"tets": samples[c][0], "s_per_iter": statistics.median(samples[c][1])}
+                  for c in sizes},
+    }
 
 
 def bench_config(args, m, n, rho, world):
@@ -193,26 +249,39 @@ def bench_config(args, m, n, rho, world):
 
 
 def run_reference(args, rank):
+    """The oracle arm: the FP64 oracle timed on the host cores, on the benchmark recipe at
+    a size it finishes (its own mesh named in config), single-threaded and with the
+    numerical libraries' default threads; `value` is the single-threaded per-iteration
+    rate extrapolated to the full cube with the measured growth exponent."""
     if rank != 0:
         return 0
     from paper_2107_05200_gb300 import workloads as wk
     V, T = wk.cube_tets(args.cells)
-    m_full = T.shape[0]
+    m_full, n_full = T.shape[0], V.shape[0]
     rho_full = wk.cube_deform(cells=2).rho
-    wl, times = cpu_oracle_sample(args.cpu_sample_cells, 0.0, steps=args.warmup + args.steps)
-    t = sum(times[args.warmup:])
-    per_it = t / max(1, args.steps)
-    elem_rate = wl.m / per_it
-    value = elem_rate / m_full
-    sample = (f"FP64 numpy/scipy oracle, cube {args.cpu_sample_cells}^3 cells ({wl.m} tets), "
-              f"{args.steps} timed iterations after {args.warmup} warm-up; value = element-updates/s "
-              f"divided by the {m_full} tets of the full workload")
+    # the timed steps: `steps` iterations after `warmup` on the sample cube, one thread
+    samples = oracle_timings([args.cpu_sample_cells], [args.warmup + args.steps], [0.0], 1)
+    m_s, times = samples[args.cpu_sample_cells]
+    per_s = sum(times[args.warmup:]) / max(1, args.steps)
+    single = oracle_baseline(m_full, n_full, args.cpu_sample_cells, 0.0, args.growth_cells, 1)
+    multi = oracle_baseline(m_full, n_full, args.cpu_sample_cells, 0.0, args.growth_cells, None)
+    value = single["value"]
+    Vs, Ts = wk.cube_tets(args.cpu_sample_cells)
+    cfg = bench_config(args, m_s, Vs.shape[0], rho_full, args.gpus)
+    cfg["workload"] = f"cube_deform_{args.cpu_sample_cells}"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "elem_updates_per_s": elem_rate,
-            "config": bench_config(args, m_full, V.shape[0], rho_full, args.gpus),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "elem_updates_per_s": value * m_full,
+            "config": cfg,
+            "extrapolated_to": {"workload": f"cube_deform_{args.cells}", "tets": m_full, "vertices": n_full,
+                                "rule": "per-iteration time fitted as a power of the element count over the "
+                                        "sampled sizes, evaluated at the full cube",
+                                "growth_exponent": single["growth_exponent"],
+                                "s_per_iter": single["extrapolated_s_per_iter"]},
+            "sample_timed": {"workload": cfg["workload"], "tets": m_s, "iterations": args.steps,
+                             "s_per_iter": per_s, "iter_per_s": 1.0 / per_s},
+            "cpu_baseline": single, "cpu_baseline_all_threads": multi,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -378,6 +447,50 @@ def run_handles(args, local):
     return 0
 
 
+def run_outcome(args, local):
+    """The benchmark cube run to its configured 1000 iterations in both precisions
+    (fixed mu = 3 w): the statistics of eq. primaldualerror / primaldualthresholds every
+    100 iterations, flipped elements and energy at the end, the FP32 iterate's
+    difference from the FP64 one, and the wall time of each run (setup excluded)."""
+    import numpy as np
+    import torch
+
+    from paper_2107_05200_gb300 import workloads as wk
+    from paper_2107_05200_gb300.solver import Solver
+
+    torch.cuda.set_device(local)
+    wl = wk.cube_deform(cells=args.cells)
+    iters = wl.max_iter
+    out, Ws = {}, {}
+    for prec in ("fp32", "fp64"):
+        with Solver.from_workload(wl, precision=prec, check_every=100, refine_sweeps=args.sweeps) as sol:
+            sol.init(wl.W0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hist = []
+            for _ in range(iters // 100):
+                st = sol.iterate(100, stop_at_tol=False)
+                hist.append({"iter": st["checked_iter"], "e_prim": st["e_prim"], "thr_prim": st["thr_prim"],
+                             "e_dual": st["e_dual"], "thr_dual": st["thr_dual"], "n_flipped": st["n_flipped"],
+                             "energy_P": st["energy_P"]})
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            W = sol.W()
+            E = sol.energy()
+            Ws[prec] = W
+            out[prec] = {"seconds": secs, "iter_per_s": iters / secs, "energy": E, "final": hist[-1],
+                         "converged": st["converged"], "history": hist}
+    d = float(np.abs(Ws["fp32"] - Ws["fp64"]).max() / np.abs(Ws["fp64"]).max())
+    line = {"metric": "outcome after the configured iterations", "unit": "s", "value": out["fp32"]["seconds"],
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": wl.name, "elements": wl.m, "vertices": wl.n, "energy": wl.energy, "rho": wl.rho,
+                       "eps_abs": wl.eps_abs, "eps_rel": wl.eps_rel, "iterations": iters,
+                       "refine_sweeps": args.sweeps},
+            "fp32": out["fp32"], "fp64": out["fp64"], "W_fp32_vs_fp64_max_rel": d}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_tutte(args, local):
     """The Tutte initializer on a 1024^2-vertex disk (2.1M triangles): one ffa_tutte
     call (host ordering and factorization, GPU solve), against the oracle's sparse
@@ -419,6 +532,11 @@ def run_tutte(args, local):
 
 def main():
     args = parse()
+    if args.oracle_probe is not None:
+        cells, iters, secs = args.oracle_probe
+        m, times = oracle_probe(int(cells), int(iters), float(secs))
+        print(json.dumps({"tets": m, "times": times}), flush=True)
+        return 0
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank)
@@ -430,6 +548,8 @@ def main():
         return run_handles(args, local) if rank == 0 else 0
     if args.workload == "tutte":
         return run_tutte(args, local) if rank == 0 else 0
+    if args.workload == "cube_outcome":
+        return run_outcome(args, local) if rank == 0 else 0
 
     import numpy as np
     import torch
@@ -533,14 +653,7 @@ def main():
         "setup_s": {"analyze": info["setup_seconds_analyze"], "factor": info["setup_seconds_factor"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cwl, times = cpu_oracle_sample(args.cpu_sample_cells, args.cpu_seconds)
-        per_it = statistics.median(times)
-        rate = cwl.m / per_it
-        line["cpu_baseline"] = {
-            "value": rate / wl.m, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle on cube {args.cpu_sample_cells}^3 ({cwl.m} tets), {len(times)} iterations "
-                      f"in ~{args.cpu_seconds:.0f} s, element-updates/s scaled to {wl.m} tets",
-            "elem_updates_per_s": rate}
+        line["cpu_baseline"] = oracle_baseline(wl.m, wl.n, args.cpu_sample_cells, args.cpu_seconds, args.growth_cells, 1)
     if rank == 0:
         print(json.dumps(line), flush=True)
     sol.close()

@@ -26,7 +26,8 @@ def _run(args, timeout=600):
 
 
 def test_reference_arm_prints_one_contract_line():
-    r = _run(["--impl", "reference", "--steps", "2", "--warmup", "0"])
+    r = _run(["--impl", "reference", "--steps", "2", "--warmup", "0", "--cpu-sample-cells", "6",
+              "--growth-cells", "8", "10"])
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
     assert len(lines) == 1, r.stdout
@@ -38,7 +39,13 @@ def test_reference_arm_prints_one_contract_line():
     assert out["value"] > 0 and out["ms_per_step"] > 0
     assert out["steps"] == 2 and out["warmup"] == 0 and out["n_gpus"] == 1
     assert out["higher_is_better"] is True
-    assert "workload" in out["config"]
+    # the config names the mesh the oracle actually ran; the extrapolation is separate
+    assert out["config"]["workload"] == "cube_deform_6" and out["config"]["tets"] == 6 * 6 ** 3
+    ext = out["extrapolated_to"]
+    assert ext["workload"] == "cube_deform_64" and ext["tets"] == 6 * 64 ** 3
+    assert 0.5 < ext["growth_exponent"] < 2.0 and ext["s_per_iter"] > 0
+    assert out["sample_timed"]["iterations"] == 2
+    assert out["cpu_baseline_all_threads"]["cores"] >= 1
     cb = out["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == out["value"]
     e2e = out["e2e"]
