@@ -395,59 +395,80 @@ __device__ __forceinline__ void polar3(const R Q[3][3], R Rot[3][3], R Vout[3][3
     }
     if (!(worst > R(0))) break;
   }
-  R n[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) n[j] = B[0][j] * B[0][j] + B[1][j] * B[1][j] + B[2][j] * B[2][j];
-  const int k = (n[0] <= n[1] && n[0] <= n[2]) ? 0 : ((n[1] <= n[2]) ? 1 : 2);
+  // Columns by norm: big, mid and the smallest k.  The columns are picked with
+  // selects (no runtime index into a register array, which would put the arrays
+  // in local memory).
+  const R n0 = B[0][0] * B[0][0] + B[1][0] * B[1][0] + B[2][0] * B[2][0];
+  const R n1 = B[0][1] * B[0][1] + B[1][1] * B[1][1] + B[2][1] * B[2][1];
+  const R n2 = B[0][2] * B[0][2] + B[1][2] * B[1][2] + B[2][2] * B[2][2];
+  const int k = (n0 <= n1 && n0 <= n2) ? 0 : ((n1 <= n2) ? 1 : 2);
   const int a = (k + 1) % 3, b = (k + 2) % 3;
-  const int big = n[a] >= n[b] ? a : b, mid = n[a] >= n[b] ? b : a;
-  R U[3][3];
-  // u_big: normalized largest column (Q = 0: any rotation is optimal, take I)
-  R ub[3], um[3];
-  if (n[big] > Tr<R>::tiny()) {
-    const R inv = Tr<R>::rsqrt_(n[big]);
+  const R na = (a == 0) ? n0 : ((a == 1) ? n1 : n2);
+  const R nb = (b == 0) ? n0 : ((b == 1) ? n1 : n2);
+  const int big = na >= nb ? a : b, mid = na >= nb ? b : a;
+  const R nbig = na >= nb ? na : nb, nmid = na >= nb ? nb : na;
+  auto pick = [](int c, R x0, R x1, R x2) { return c == 0 ? x0 : (c == 1 ? x1 : x2); };
+  R Bb[3], Bm[3], Bk[3], Vb[3], Vm[3], Vk[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) ub[r] = B[r][big] * inv;
+  for (int r = 0; r < 3; ++r) {
+    Bb[r] = pick(big, B[r][0], B[r][1], B[r][2]);
+    Bm[r] = pick(mid, B[r][0], B[r][1], B[r][2]);
+    Bk[r] = pick(k, B[r][0], B[r][1], B[r][2]);
+    Vb[r] = pick(big, V[r][0], V[r][1], V[r][2]);
+    Vm[r] = pick(mid, V[r][0], V[r][1], V[r][2]);
+    Vk[r] = pick(k, V[r][0], V[r][1], V[r][2]);
+  }
+  // u_big: normalized largest column (Q = 0: any rotation is optimal, take I)
+  R ub[3], um[3], uk[3];
+  if (nbig > Tr<R>::tiny()) {
+    const R inv = Tr<R>::rsqrt_(nbig);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) ub[r] = Bb[r] * inv;
   } else {
-    ub[0] = R(big == 0); ub[1] = R(big == 1); ub[2] = R(big == 2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) ub[r] = R(big == r);
   }
   // u_mid: middle column made orthogonal to u_big (rank-1 Q: any orthogonal unit vector)
-  R dp = B[0][mid] * ub[0] + B[1][mid] * ub[1] + B[2][mid] * ub[2];
+  const R dp = Bm[0] * ub[0] + Bm[1] * ub[1] + Bm[2] * ub[2];
 #pragma unroll
-  for (int r = 0; r < 3; ++r) um[r] = B[r][mid] - dp * ub[r];
+  for (int r = 0; r < 3; ++r) um[r] = Bm[r] - dp * ub[r];
   R nm = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
-  if (!(nm > Tr<R>::eps() * Tr<R>::eps() * n[big]) || !(nm > Tr<R>::tiny())) {
-    // pick the coordinate axis least aligned with u_big and orthogonalize it
+  if (!(nm > Tr<R>::eps() * Tr<R>::eps() * nbig) || !(nm > Tr<R>::tiny())) {
+    // the coordinate axis least aligned with u_big, orthogonalized
     const int ax = (Tr<R>::abs_(ub[0]) <= Tr<R>::abs_(ub[1]) && Tr<R>::abs_(ub[0]) <= Tr<R>::abs_(ub[2])) ? 0
                    : (Tr<R>::abs_(ub[1]) <= Tr<R>::abs_(ub[2]) ? 1 : 2);
+    const R uax = pick(ax, ub[0], ub[1], ub[2]);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) um[r] = R(r == ax) - ub[ax] * ub[r];
+    for (int r = 0; r < 3; ++r) um[r] = R(r == ax) - uax * ub[r];
     nm = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
   }
   const R invm = Tr<R>::rsqrt_(nm);
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    um[r] *= invm;
-    U[r][big] = ub[r];
-    U[r][mid] = um[r];
-  }
-  // u_k = u_a x u_b (cyclic order keeps det U = +1)
-  U[0][k] = U[1][a] * U[2][b] - U[2][a] * U[1][b];
-  U[1][k] = U[2][a] * U[0][b] - U[0][a] * U[2][b];
-  U[2][k] = U[0][a] * U[1][b] - U[1][a] * U[0][b];
+  for (int r = 0; r < 3; ++r) um[r] *= invm;
+  // u_k = u_a x u_b (cyclic order keeps det U = +1): u_big x u_mid when big = a,
+  // its negative otherwise
+  const R sgn = (big == a) ? R(1) : R(-1);
+  uk[0] = sgn * (ub[1] * um[2] - ub[2] * um[1]);
+  uk[1] = sgn * (ub[2] * um[0] - ub[0] * um[2]);
+  uk[2] = sgn * (ub[0] * um[1] - ub[1] * um[0]);
+  // Rot = U V^T = u_big V_big^T + u_mid V_mid^T + u_k V_k^T
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Rot[i][j] = U[i][0] * V[j][0] + U[i][1] * V[j][1] + U[i][2] * V[j][2];
-  // signed singular values: s_j = u_j . B_j (s_k < 0 when det Q < 0)
+    for (int j = 0; j < 3; ++j) Rot[i][j] = ub[i] * Vb[j] + um[i] * Vm[j] + uk[i] * Vk[j];
+  // signed singular values s_j = u_j . B_j (s_k < 0 when det Q < 0), in the
+  // original column order
+  const R sb = ub[0] * Bb[0] + ub[1] * Bb[1] + ub[2] * Bb[2];
+  const R sm = um[0] * Bm[0] + um[1] * Bm[1] + um[2] * Bm[2];
+  const R sk = uk[0] * Bk[0] + uk[1] * Bk[1] + uk[2] * Bk[2];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) sig[j] = U[0][j] * B[0][j] + U[1][j] * B[1][j] + U[2][j] * B[2][j];
+  for (int j = 0; j < 3; ++j) sig[j] = (j == big) ? sb : ((j == mid) ? sm : sk);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) Vout[i][j] = V[i][j];
-  const R smax = Tr<R>::sqrt_(n[big]);
-  cond = (smax > R(0)) ? (Tr<R>::sqrt_(n[mid]) + sig[k]) / smax : R(1);
+  const R smax = Tr<R>::sqrt_(nbig);
+  cond = (smax > R(0)) ? (Tr<R>::sqrt_(nmid) + sk) / smax : R(1);
 }
 
 template <typename R>
