@@ -136,6 +136,8 @@ struct ffa_ctx {
   int8_t* energy_of = nullptr;
   int32_t *mesh_of_elem = nullptr, *mesh_of_vertex = nullptr, *mesh_d = nullptr, *mesh_m = nullptr;
   double *mesh_eps = nullptr, *mesh_acc = nullptr;
+  int64_t *mesh_eoff = nullptr, *mesh_voff = nullptr;   // per-mesh element / vertex offsets (n_mesh + 1)
+  double *mesh_part_local = nullptr, *mesh_part_vert = nullptr;   // block sums of boundary meshes
   ffa_stats* mesh_stats = nullptr;
   int32_t* n_converged = nullptr;
 };
@@ -340,6 +342,17 @@ void enqueue_iteration(ffa_ctx* ctx, bool check, cudaEvent_t* ev = nullptr) {
   launch_local_step(local_launch(ctx, check, ctx->vrec), s);
   if (ev) cudaEventRecord(ev[PH_LOCAL], s);
   if (check && ctx->n_mesh > 0) {
+    MeshPartialsLaunch PL;
+    PL.n_mesh = ctx->n_mesh;
+    PL.nq = NQ;
+    PL.q0 = 0;
+    PL.seg_off = ctx->mesh_eoff;
+    PL.seg_of = ctx->mesh_of_elem;
+    PL.n_items = ctx->m;
+    PL.items_per_block = ctx->local_block;
+    PL.part = ctx->mesh_part_local;
+    PL.acc = ctx->mesh_acc;
+    launch_mesh_partials(PL, s);
     GatherLaunch H{};
     H.d = ctx->d;
     H.fp64 = ctx->fp64;
@@ -353,7 +366,19 @@ void enqueue_iteration(ffa_ctx* ctx, bool check, cudaEvent_t* ev = nullptr) {
     H.partials = nullptr;
     H.mesh_of = ctx->mesh_of_vertex;
     H.mesh_acc = ctx->mesh_acc;
+    H.mesh_part = ctx->mesh_part_vert;
     launch_gather(H, s);
+    MeshPartialsLaunch PV;
+    PV.n_mesh = ctx->n_mesh;
+    PV.nq = 1;
+    PV.q0 = NQ;
+    PV.seg_off = ctx->mesh_voff;
+    PV.seg_of = ctx->mesh_of_vertex;
+    PV.n_items = ctx->n;
+    PV.items_per_block = kVertexBlock / kGatherLanes;
+    PV.part = ctx->mesh_part_vert;
+    PV.acc = ctx->mesh_acc;
+    launch_mesh_partials(PV, s);
     MeshStatsLaunch M{};
     M.n_mesh = ctx->n_mesh;
     M.mesh_acc = ctx->mesh_acc;
@@ -757,9 +782,32 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     if ((st = dalloc(ctx, &ctx->mesh_acc, (size_t)ctx->n_mesh * (NQ + 1))) != FFA_OK) return st;
     if ((st = dalloc(ctx, &ctx->mesh_stats, (size_t)ctx->n_mesh)) != FFA_OK) return st;
     if ((st = dalloc(ctx, &ctx->n_converged, 1)) != FFA_OK) return st;
+    {
+      // per-mesh element and vertex offsets (meshes are concatenated in order)
+      std::vector<int64_t> eoff(ctx->n_mesh + 1, 0), voff(ctx->n_mesh + 1, 0);
+      for (int i = 0; i < m; ++i) eoff[batch->mesh_of_elem[i] + 1]++;
+      for (int v = 0; v < n; ++v) voff[batch->mesh_of_vertex[v] + 1]++;
+      for (int k = 0; k < ctx->n_mesh; ++k) {
+        eoff[k + 1] += eoff[k];
+        voff[k + 1] += voff[k];
+      }
+      for (int i = 1; i < m; ++i)
+        if (batch->mesh_of_elem[i] < batch->mesh_of_elem[i - 1])
+          return fail(ctx, FFA_ERR_INVALID_ARG, "internal: batched elements are not sorted by mesh");
+      for (int v = 1; v < n; ++v)
+        if (batch->mesh_of_vertex[v] < batch->mesh_of_vertex[v - 1])
+          return fail(ctx, FFA_ERR_INVALID_ARG, "internal: batched vertices are not sorted by mesh");
+      if ((st = upload(ctx, &ctx->mesh_eoff, eoff)) != FFA_OK) return st;
+      if ((st = upload(ctx, &ctx->mesh_voff, voff)) != FFA_OK) return st;
+      // block sums, sized for the smallest local-step block the autotuner may pick (64)
+      if ((st = dalloc(ctx, &ctx->mesh_part_local, (size_t)((m + 63) / 64) * 2 * NQ)) != FFA_OK) return st;
+      const int64_t vblocks = ((int64_t)n * kGatherLanes + kVertexBlock - 1) / kVertexBlock;
+      if ((st = dalloc(ctx, &ctx->mesh_part_vert, (size_t)vblocks * 2)) != FFA_OK) return st;
+    }
     ctx->e.energy_of = ctx->energy_of;
     ctx->e.mesh_of = ctx->mesh_of_elem;
     ctx->e.mesh_acc = ctx->mesh_acc;
+    ctx->e.mesh_part = ctx->mesh_part_local;
   }
   ctx->e.joint = ctx->prm.local_variant == 1 ? 1 : 0;
   const size_t R = ctx->rsz;
@@ -822,7 +870,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   ctx->info.n_pin = n_pin;
   ctx->info.n_free = nF;
   ctx->info.kernels_per_iteration = kernels_per_iteration(ctx);
-  ctx->info.kernels_per_check = 3;
+  ctx->info.kernels_per_check = ctx->n_mesh > 0 ? 4 : 3;
   if (ctx->prm.penalty_schedule == 1) {
     if ((st = upload(ctx, &ctx->mu64, H.mu)) != FFA_OK) return st;
     FFA_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -64,6 +64,7 @@ struct ElemBufs {
   const int8_t* energy_of = nullptr;   // m: 0 = SD, 1 = SG (kernels instantiated with EN = 2)
   const int32_t* mesh_of = nullptr;    // m: mesh of each element
   double* mesh_acc = nullptr;          // n_mesh x (NQ + 1) per-mesh sums of the check quantities
+  double* mesh_part = nullptr;         // blocks x 2 x NQ: sums of each block's first and last mesh
   int32_t joint = 0;                   // 1: the joint (U, P) prox variant of the local step
   void* hmu = nullptr;                 // m: h_i / mu_i of the proximal U term (null: h = 0)
 };
@@ -140,8 +141,9 @@ struct GatherLaunch {
   const double* add;         // optional row-aligned addend (rows x d)
   double* out;               // rows x d
   double* partials;          // optional: sum of squares of out per block (QV_GTL)
-  const int32_t* mesh_of;    // optional (batched meshes): mesh of each row's vertex
+  const int32_t* mesh_of;    // optional (batched meshes): mesh of each row's vertex (rows sorted by mesh)
   double* mesh_acc;          // with mesh_of: sums of squares go to mesh_acc[mesh * (NQ + 1) + NQ]
+  double* mesh_part;         // with mesh_of: blocks x 2 sums of each block's first and last mesh
 };
 void launch_gather(const GatherLaunch& G, cudaStream_t s);
 
@@ -212,6 +214,21 @@ struct MeshStatsLaunch {
   int32_t* n_converged;       // incremented per converged mesh (zeroed by the caller)
 };
 void launch_mesh_stats(const MeshStatsLaunch& M, cudaStream_t s);
+// Deterministic per-mesh sums of batched meshes, second pass: items (elements or
+// vertex rows) are sorted by mesh; each block of items_per_block items has
+// written the sums of a mesh that lies wholly inside it to acc directly and the
+// sums of its first and last mesh to part[block][0 / 1][nq]; here one warp per
+// mesh adds those block sums in block order into acc[mesh * (NQ + 1) + q0 + q].
+struct MeshPartialsLaunch {
+  int n_mesh = 0, nq = 0, q0 = 0;
+  const int64_t* seg_off = nullptr;  // n_mesh + 1 item offsets
+  const int32_t* seg_of = nullptr;   // mesh of each item
+  int64_t n_items = 0;
+  int items_per_block = 0;
+  const double* part = nullptr;
+  double* acc = nullptr;
+};
+void launch_mesh_partials(const MeshPartialsLaunch& M, cudaStream_t s);
 void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s);
 
 // adjoint of one unrolled iteration, per element (ffa_adjoint.cu)

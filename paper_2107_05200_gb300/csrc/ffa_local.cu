@@ -165,39 +165,68 @@ __device__ __forceinline__ void block_reduce(R v[N], double* out) {
 template <typename R>
 __device__ __forceinline__ bool finite_(R x) { return isfinite(x); }
 
-// batched meshes: per-mesh sums of the check quantities.  A warp whose elements
-// all belong to one mesh reduces first (double-float for float values) and adds
-// once per quantity; otherwise every lane adds its own values.
-template <typename R>
-__device__ __forceinline__ void mesh_reduce(const R v[NQ], const ElemBufs& e, int m, int i) {
-  const int mesh = (i < m) ? e.mesh_of[i] : -1;
-  const int m0 = __shfl_sync(0xffffffffu, mesh, 0);
-  const bool uniform = __all_sync(0xffffffffu, mesh == m0);
-  const int lane = threadIdx.x & 31;
-  if (uniform) {
-    if (m0 < 0) return;
+// Block sum of N per-thread values in a fixed order (warp shuffles, then the
+// warps in index order; float values in double-float): the result in thread 0.
+// Ends with a barrier, so it can be called again in a block-uniform loop.
+template <typename R, int N>
+__device__ __forceinline__ void block_sum_to0(const R v[N], double tot[N]) {
+  __shared__ double red[8][N];   // up to 256 threads
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      double tot;
-      if constexpr (sizeof(R) == 4) {
-        FF a{v[q], 0.0f};
+  for (int q = 0; q < N; ++q) {
+    double t;
+    if constexpr (sizeof(R) == 4) {
+      FF a{v[q], 0.0f};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-          a = ff_add(a, b);
-        }
-        tot = (double)a.hi + (double)a.lo;
-      } else {
-        double a = v[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        tot = a;
+      for (int o = 16; o > 0; o >>= 1) {
+        FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        a = ff_add(a, b);
       }
-      if (lane == 0) atomicAdd(e.mesh_acc + (int64_t)m0 * (NQ + 1) + q, tot);
-    }
-  } else if (mesh >= 0) {
+      t = (double)a.hi + (double)a.lo;
+    } else {
+      double a = v[q];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) atomicAdd(e.mesh_acc + (int64_t)mesh * (NQ + 1) + q, (double)v[q]);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      t = a;
+    }
+    if (lane == 0) red[warp][q] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      double s = 0.0;
+      for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += red[wv][q];
+      tot[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// batched meshes: per-mesh sums of the check quantities, deterministic.  The
+// elements are sorted by mesh, so a block holds a run of meshes: each is summed
+// over the block in a fixed order; a mesh wholly inside the block is written to
+// mesh_acc (this block is its only contributor), the block's first and last
+// meshes go to mesh_part, which launch_mesh_partials adds up in block order.
+template <typename R>
+__device__ __forceinline__ void mesh_block_sums(const R v[NQ], const ElemBufs& e, int m, int i) {
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t i1 = min((int64_t)m, i0 + blockDim.x);
+  const int first = e.mesh_of[i0], last = e.mesh_of[i1 - 1];
+  const int mine = (i < m) ? e.mesh_of[i] : -1;
+  for (int k = first; k <= last; ++k) {   // block-uniform
+    R w[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) w[q] = (mine == k) ? v[q] : R(0);
+    double tot[NQ];
+    block_sum_to0<R, NQ>(w, tot);
+    if (threadIdx.x == 0) {
+      double* dst = (k == first) ? e.mesh_part + ((int64_t)blockIdx.x * 2 + 0) * NQ
+                  : (k == last) ? e.mesh_part + ((int64_t)blockIdx.x * 2 + 1) * NQ
+                                : e.mesh_acc + (int64_t)k * (NQ + 1);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) dst[q] = tot[q];
+    }
   }
 }
 
@@ -422,7 +451,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
     }
   }
   if constexpr (CHECK) {
-    if (e.mesh_of) mesh_reduce<R>(qv, e, m, i);
+    if (e.mesh_of) mesh_block_sums<R>(qv, e, m, i);
     else block_reduce<R, NQ>(qv, partials);
   }
 }

@@ -173,15 +173,30 @@ __global__ void __launch_bounds__(kVertexBlock) k_gather(GatherLaunch G) {
     }
   }
   if (G.mesh_of) {
-    // batched meshes: per-mesh sum of squares, warp-aggregated when the warp is uniform
-    const int mesh = active ? G.mesh_of[G.row_vertex ? G.row_vertex[row] : row] : -1;
-    const int m0 = __shfl_sync(0xffffffffu, mesh, 0);
-    if (__all_sync(0xffffffffu, mesh == m0)) {
+    // batched meshes (rows are the vertices, sorted by mesh): per-mesh sums of
+    // squares in a fixed order; a mesh wholly inside the block is written to
+    // mesh_acc, the block's first and last meshes to mesh_part (added up in block
+    // order by launch_mesh_partials)
+    constexpr int kRowsPerBlock = kVertexBlock / kGatherLanes;
+    const int r0 = blockIdx.x * kRowsPerBlock;
+    const int r1 = min(G.rows, r0 + kRowsPerBlock);
+    const int first = G.mesh_of[r0], last = G.mesh_of[r1 - 1];
+    const int mine = (active && sub == 0) ? G.mesh_of[row] : -1;
+    __shared__ double red_m[kVertexBlock / 32];
+    for (int k = first; k <= last; ++k) {   // block-uniform
+      double w = (mine == k) ? sq : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      if ((threadIdx.x & 31) == 0 && m0 >= 0) atomicAdd(G.mesh_acc + (int64_t)m0 * (NQ + 1) + NQ, sq);
-    } else if (mesh >= 0 && sub == 0) {
-      atomicAdd(G.mesh_acc + (int64_t)mesh * (NQ + 1) + NQ, sq);
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if ((threadIdx.x & 31) == 0) red_m[threadIdx.x >> 5] = w;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int wv = 0; wv < kVertexBlock / 32; ++wv) t += red_m[wv];
+        if (k == first) G.mesh_part[(int64_t)blockIdx.x * 2 + 0] = t;
+        else if (k == last) G.mesh_part[(int64_t)blockIdx.x * 2 + 1] = t;
+        else G.mesh_acc[(int64_t)k * (NQ + 1) + NQ] = t;
+      }
+      __syncthreads();
     }
   } else if (G.partials) {
     __shared__ double red[kVertexBlock / 32];
@@ -1612,6 +1627,31 @@ __global__ void k_mesh_stats(MeshStatsLaunch M) {
   M.out[k] = st;
 }
 
+// one warp per mesh: the block sums of the mesh's first and last blocks in block
+// order (lanes stride over the blocks, then a fixed shuffle tree)
+__global__ void k_mesh_partials(MeshPartialsLaunch M) {
+  const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= M.n_mesh) return;   // warp-uniform
+  const int64_t e0 = M.seg_off[k], e1 = M.seg_off[k + 1];
+  if (e1 <= e0) return;
+  const int64_t b0 = e0 / M.items_per_block, b1 = (e1 - 1) / M.items_per_block;
+  auto first_of = [&](int64_t b) { return M.seg_of[b * M.items_per_block]; };
+  auto last_of = [&](int64_t b) { return M.seg_of[min(M.n_items, (b + 1) * M.items_per_block) - 1]; };
+  if (b0 == b1 && first_of(b0) != k && last_of(b0) != k) return;   // written by its block
+  for (int q = 0; q < M.nq; ++q) {
+    double s = 0.0;
+    for (int64_t b = b0 + lane; b <= b1; b += 32) {
+      const int fo = first_of(b), la = last_of(b);
+      if (fo == k) s += M.part[(b * 2 + 0) * M.nq + q];
+      else if (la == k) s += M.part[(b * 2 + 1) * M.nq + q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) M.acc[(int64_t)k * (NQ + 1) + M.q0 + q] = s;
+  }
+}
+
 __global__ void k_sum_partials(const double* __restrict__ p, int64_t nb, int nq, double* __restrict__ out) {
   const int q = blockIdx.x;
   double s = 0.0;
@@ -1790,6 +1830,11 @@ void launch_final_reduce(const FinalLaunch& F, cudaStream_t s) {
 
 void launch_mesh_stats(const MeshStatsLaunch& M, cudaStream_t s) {
   k_mesh_stats<<<(M.n_mesh + 127) / 128, 128, 0, s>>>(M);
+}
+
+void launch_mesh_partials(const MeshPartialsLaunch& M, cudaStream_t s) {
+  if (M.n_mesh <= 0) return;
+  k_mesh_partials<<<(M.n_mesh * 32 + 255) / 256, 256, 0, s>>>(M);
 }
 
 void launch_sum_partials(const double* partials, int64_t n_blocks, int nq, double* out, cudaStream_t s) {

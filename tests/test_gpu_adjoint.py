@@ -142,3 +142,26 @@ def test_handle_workload_full_size_directional_derivatives():
             ad64 = float(np.sum(gb64 * v))
             assert abs(ad64 - fd) <= 1e-5 * np.linalg.norm(gh64) * np.linalg.norm(v), (ad64, fd)
             assert abs(ad - fd) <= 1e-4 * np.linalg.norm(gh64) * np.linalg.norm(v), (ad, fd)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
+def test_bent_handles_directional_derivatives_against_the_oracle(precision, tol):
+    """Handles a quarter of the way along the bend on an 8^3-cell cube (16 handles,
+    40 targets): 100 iterations reach the fixed point (the oracle's e_prim falls to
+    1e-13), so the loss is a smooth function of the handle positions.  The adjoint's
+    directional derivatives along random handle directions against central
+    differences (h = 1e-4) of the FP64 oracle, within tol |g_handles| |v|."""
+    _need_gpu()
+    wl = wk.cube_handles(cells=8, seed=53, n_targets=40, lattice_start=1, lattice_step=2, pre_bend=0.25)
+    K, ckpt = 100, 20
+    _, gb, _, _ = _gpu_grad(wl, precision, K, ckpt)
+    nb = wl.meta["n_bottom"]
+    o = admm.Oracle.from_workload(wl)
+    rng = np.random.default_rng(54)
+    h = 1e-4
+    for _ in range(2):
+        v = np.zeros_like(wl.pin_pos)
+        v[nb:] = rng.normal(size=(len(wl.pin_pos) - nb, 3))
+        fd = (_oracle_loss(o, wl, wl.pin_pos + h * v, K) - _oracle_loss(o, wl, wl.pin_pos - h * v, K)) / (2 * h)
+        ad = float(np.sum(gb * v))
+        assert abs(ad - fd) <= tol * np.linalg.norm(gb[nb:]) * np.linalg.norm(v), (ad, fd)

@@ -68,3 +68,36 @@ def test_batch_matches_the_oracle_and_stops_when_all_meshes_converged():
         assert np.abs(Wb[j] - s.W).max() / np.abs(s.W).max() < 1e-8, j
     assert nconv == len(wls)
     assert all(st["converged"] == 1 and st["n_flipped"] == 0 for st in stats)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_statistics_are_bitwise_repeatable(precision):
+    """The per-mesh sums of the termination test are formed in a fixed order (no
+    floating-point atomics), so two runs of the same batch give identical
+    statistics; tiny meshes (a single element, a few elements) share blocks with
+    their neighbours and still get exactly their own sums (checked against their
+    single-mesh solves)."""
+    _need_gpu()
+    from paper_2107_05200_gb300.solver import BatchSolver, Solver
+    wls = wk.batched_meshes(count=5, seed=11, m_min=300, m_max=4000)
+    V = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
+    tri = wk.Workload("tri", V, np.array([[0, 1, 2]], np.int32), np.array([0], np.int32), V[:1].copy(),
+                      V * 1.3 + 0.05, "sd", rho=3.0, eps_abs=1e-5, eps_rel=1e-4)
+    small = wk.uv_disk(grid=4, seed=12, rho=3.0, tol=1e-5)
+    wls = [wls[0], tri, small, wls[1], tri, wls[2], small, wls[3], wls[4]]
+    runs = []
+    for _ in range(2):
+        with BatchSolver(wls, precision=precision, check_every=5) as bs:
+            bs.init([wl.W0 for wl in wls])
+            stats, _ = bs.iterate(15, stop_at_tol=False)
+            runs.append(stats)
+    for a, b in zip(*runs):
+        for key in ("e_prim", "e_dual", "thr_prim", "thr_dual", "energy_P", "norm_GtLambda"):
+            assert a[key] == b[key], key
+    for j in (1, 2):
+        with Solver.from_workload(wls[j], precision=precision, check_every=5) as sol:
+            sol.init(wls[j].W0)
+            st = sol.iterate(15, stop_at_tol=False)
+        for key in ("e_prim", "e_dual", "thr_prim", "thr_dual", "energy_P"):
+            assert math.isclose(runs[0][j][key], st[key], rel_tol=1e-6 if precision == "fp64" else 1e-2,
+                                abs_tol=1e-12), (j, key)
