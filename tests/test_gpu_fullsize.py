@@ -21,7 +21,8 @@ Lambda)) and from there P (the prox of a convex spectral function is
 satisfy
     |U_gpu - U_oracle|_max        <= C eps32 (1 + kappa_i)
     |P_gpu - P_oracle|_max / s_i   <= C eps32 (1 + kappa_i)   (same for Lambda)
-with s_i = |J_i|_max + |Lambda_i|_max + 1, eps32 = 2^-24 and C = 64.
+with s_i = |J_i|_max + |Lambda_i|_max + 1, eps32 = 2^-24 and C = 16 (measured worst cases: 0.32 of
+the bound on the cube, 0.16 on the heightfield).
 """
 import numpy as np
 import pytest
@@ -32,7 +33,7 @@ from paper_2107_05200_gb300 import workloads as wk
 pytestmark = pytest.mark.gpu
 
 EPS32 = 2.0 ** -24
-C_BOUND = 64.0
+C_BOUND = 16.0
 
 
 def _need_gpu():
