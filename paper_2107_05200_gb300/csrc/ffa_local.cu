@@ -400,7 +400,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
         }
     }
     // ---- multiplier update (eq. lambdaupdate) and the next right-hand-side terms (eq. solvinginw)
-    R UP[D][D], Rm[D][D], Rhs[D][D];
+    // Lambda^k = (Lambda^{k-1} + J) - U P = A - U P: only A stays live through the
+    // U and P steps (J and Lambda^{k-1} are kept for the check iterations alone)
+    R UP[D][D], Rhs[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -409,8 +411,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
 #pragma unroll
         for (int l = 0; l < D; ++l) s = fma(U[a][l], P[l][k], s);
         UP[a][k] = s;
-        Rm[a][k] = J[a][k] - s;
-        Lam[a][k] += Rm[a][k];
+        Lam[a][k] = A[a][k] - s;
         Rhs[a][k] = mu * (s - Lam[a][k]);
       }
 #pragma unroll
@@ -423,15 +424,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
       Pp[i] = P[0][0]; Pp[(int64_t)m + i] = P[0][1]; Pp[2 * (int64_t)m + i] = P[0][2];
       Pp[3 * (int64_t)m + i] = P[1][1]; Pp[4 * (int64_t)m + i] = P[1][2]; Pp[5 * (int64_t)m + i] = P[2][2];
     }
-    store_terms<D, R>(e.contrib, i, g, Rhs);
+    // the hat gradients again (an L1 hit) rather than kept live through the steps
+    R g2[D][D];
+    {
+      const R* gp = reinterpret_cast<const R*>(e.g);
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int a = 0; a < D; ++a) g2[j][a] = __ldg(gp + (int64_t)(j * D + a) * m + i);
+    }
+    store_terms<D, R>(e.contrib, i, g2, Rhs);
     if constexpr (CHECK) {
-      store_terms<D, R>(e.contrib2, i, g, Lam);
+      store_terms<D, R>(e.contrib2, i, g2, Lam);
       R ep = 0, ed = 0, gw = 0, pp = 0;
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          ep = fma(Rm[a][k], Rm[a][k], ep);
+          const R rm = J[a][k] - UP[a][k];
+          ep = fma(rm, rm, ep);
           ed = fma(dJ[a][k], dJ[a][k], ed);
           gw = fma(J[a][k], J[a][k], gw);
           pp = fma(P[a][k], P[a][k], pp);
