@@ -478,6 +478,132 @@ __device__ __forceinline__ void nearest_rotation3(const R Q[3][3], R Rot[3][3], 
 }
 
 // ---------------------------------------------------------------------------
+// Nearest rotation as a unit quaternion (the float U step of the 3D local step).
+// For R(q), q = (w, x, y, z) unit (the matrix of quat_to_rot below),
+// tr(R(q)^T Q) = q^T K q with the symmetric, traceless 4x4
+//   K = [ Q00+Q11+Q22  Q21-Q12      Q02-Q20      Q10-Q01     ]
+//       [ Q21-Q12      Q00-Q11-Q22  Q01+Q10      Q02+Q20     ]
+//       [ Q02-Q20      Q01+Q10     -Q00+Q11-Q22  Q12+Q21     ]
+//       [ Q10-Q01      Q02+Q20      Q12+Q21     -Q00-Q11+Q22 ]
+// (expand R(q) entry by entry), so the rotation maximizing tr(R^T Q) -- the one
+// nearest to Q, eq. optimizationinudecoupled -- is the unit eigenvector of K's
+// largest eigenvalue (Horn's closed-form absolute orientation, 1987).  That
+// eigenvalue is the largest root of det(K - l I) = l^4 - 2|Q|^2 l^2 - 8 det(Q) l
+// + det K (the power sums of K's eigenvalues are 0, 4|Q|^2 and 24 det Q).  All its
+// roots are real, so Newton started above the largest root, at sqrt(3)|Q| (the
+// sum of the singular values is at most that), falls monotonically onto it.  The
+// eigenvector is the column of adj(K - l I) with the largest diagonal entry.
+// adj(K - l I) = c v v^T with c the product of the gaps between l and the other
+// three eigenvalues, so |column|^2 / |diagonal entry| = |c|; cond = |c| / |Q|^3 is
+// about 8 (s_mid + s_min,signed) / s_max for a flat Q and 12 for a rotation.  In
+// float the eigenvector is accurate to a few eps (1 + kappa) only while the gaps
+// are large; for cond below about 1 the caller takes another method.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R det3(R a00, R a01, R a02, R a10, R a11, R a12, R a20, R a21, R a22) {
+  return a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) + a02 * (a10 * a21 - a11 * a20);
+}
+
+template <typename R>
+__device__ __forceinline__ void nearest_rotation3_quat(const R Q[3][3], R qv[4], R& cond) {
+  R K[4][4];
+  K[0][0] = Q[0][0] + Q[1][1] + Q[2][2];
+  K[1][1] = Q[0][0] - Q[1][1] - Q[2][2];
+  K[2][2] = -Q[0][0] + Q[1][1] - Q[2][2];
+  K[3][3] = -Q[0][0] - Q[1][1] + Q[2][2];
+  K[0][1] = K[1][0] = Q[2][1] - Q[1][2];
+  K[0][2] = K[2][0] = Q[0][2] - Q[2][0];
+  K[0][3] = K[3][0] = Q[1][0] - Q[0][1];
+  K[1][2] = K[2][1] = Q[0][1] + Q[1][0];
+  K[1][3] = K[3][1] = Q[0][2] + Q[2][0];
+  K[2][3] = K[3][2] = Q[1][2] + Q[2][1];
+  R n2 = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) n2 = fma(Q[a][b], Q[a][b], n2);
+  if (!(n2 > Tr<R>::tiny())) {   // Q = 0: every rotation is optimal, take I
+    qv[0] = R(1); qv[1] = qv[2] = qv[3] = R(0);
+    cond = R(1);
+    return;
+  }
+  const R dQ = det3<R>(Q[0][0], Q[0][1], Q[0][2], Q[1][0], Q[1][1], Q[1][2], Q[2][0], Q[2][1], Q[2][2]);
+  // det K by 2x2 minors of the first two and the last two rows
+  const R m01 = K[0][0] * K[1][1] - K[0][1] * K[1][0], m02 = K[0][0] * K[1][2] - K[0][2] * K[1][0];
+  const R m03 = K[0][0] * K[1][3] - K[0][3] * K[1][0], m12 = K[0][1] * K[1][2] - K[0][2] * K[1][1];
+  const R m13 = K[0][1] * K[1][3] - K[0][3] * K[1][1], m23 = K[0][2] * K[1][3] - K[0][3] * K[1][2];
+  const R n01 = K[2][0] * K[3][1] - K[2][1] * K[3][0], n02 = K[2][0] * K[3][2] - K[2][2] * K[3][0];
+  const R n03 = K[2][0] * K[3][3] - K[2][3] * K[3][0], n12 = K[2][1] * K[3][2] - K[2][2] * K[3][1];
+  const R n13 = K[2][1] * K[3][3] - K[2][3] * K[3][1], n23 = K[2][2] * K[3][3] - K[2][3] * K[3][2];
+  const R dK = m01 * n23 - m02 * n13 + m03 * n12 + m12 * n03 - m13 * n02 + m23 * n01;
+  const R c2 = R(-2) * n2, c1 = R(-8) * dQ;
+  R l = Tr<R>::sqrt_(R(3) * n2);
+#pragma unroll 1
+  for (int it = 0; it < 32; ++it) {
+    const R l2 = l * l;
+    const R p = (l2 + c2) * l2 + c1 * l + dK;
+    const R dp = (R(4) * l2 + R(2) * c2) * l + c1;
+    if (!(dp > R(0))) break;
+    const R step = p / dp;
+    l -= step;
+    if (!(Tr<R>::abs_(step) > R(4) * Tr<R>::eps() * l)) break;
+  }
+  // adjugate of M = K - l I: the diagonal cofactors pick the best column
+  R M[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) M[a][b] = K[a][b] - (a == b ? l : R(0));
+  const R a0 = det3<R>(M[1][1], M[1][2], M[1][3], M[2][1], M[2][2], M[2][3], M[3][1], M[3][2], M[3][3]);
+  const R a1 = det3<R>(M[0][0], M[0][2], M[0][3], M[2][0], M[2][2], M[2][3], M[3][0], M[3][2], M[3][3]);
+  const R a2 = det3<R>(M[0][0], M[0][1], M[0][3], M[1][0], M[1][1], M[1][3], M[3][0], M[3][1], M[3][3]);
+  const R a3 = det3<R>(M[0][0], M[0][1], M[0][2], M[1][0], M[1][1], M[1][2], M[2][0], M[2][1], M[2][2]);
+  // the eigenvalue is the largest, so every diagonal cofactor is <= 0 (a product of
+  // three non-positive gaps times v_j^2): take the largest in magnitude
+  const R b0 = Tr<R>::abs_(a0), b1 = Tr<R>::abs_(a1), b2 = Tr<R>::abs_(a2), b3 = Tr<R>::abs_(a3);
+  int j = 0;
+  R best = b0;
+  if (b1 > best) { best = b1; j = 1; }
+  if (b2 > best) { best = b2; j = 2; }
+  if (b3 > best) { best = b3; j = 3; }
+  // column j of the adjugate: cofactors C_ij = (-1)^(i+j) det(M minus row i, column j);
+  // M is symmetric, so column j equals row j of the cofactor matrix
+  R v[4];
+  {
+    // rows other than j, in order
+    const int r0 = j == 0 ? 1 : 0, r1 = j <= 1 ? 2 : 1, r2 = j <= 2 ? 3 : 2;
+    R A[3][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      A[0][c] = r0 == 0 ? M[0][c] : (r0 == 1 ? M[1][c] : M[2][c]);
+      A[1][c] = r1 == 1 ? M[1][c] : (r1 == 2 ? M[2][c] : M[3][c]);
+      A[2][c] = r2 == 2 ? M[2][c] : M[3][c];
+    }
+    // v_i = (-1)^(i+j) det(A minus column i)
+    const R d0 = det3<R>(A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3], A[2][1], A[2][2], A[2][3]);
+    const R d1 = det3<R>(A[0][0], A[0][2], A[0][3], A[1][0], A[1][2], A[1][3], A[2][0], A[2][2], A[2][3]);
+    const R d2 = det3<R>(A[0][0], A[0][1], A[0][3], A[1][0], A[1][1], A[1][3], A[2][0], A[2][1], A[2][3]);
+    const R d3 = det3<R>(A[0][0], A[0][1], A[0][2], A[1][0], A[1][1], A[1][2], A[2][0], A[2][1], A[2][2]);
+    const R sj = (j & 1) ? R(-1) : R(1);
+    v[0] = sj * d0;
+    v[1] = -sj * d1;
+    v[2] = sj * d2;
+    v[3] = -sj * d3;
+  }
+  const R vn = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  const R sc = n2 * Tr<R>::sqrt_(n2);
+  cond = (best > R(0)) ? vn / (best * sc) : R(0);
+  if (!(vn > Tr<R>::tiny())) {
+    qv[0] = R(1); qv[1] = qv[2] = qv[3] = R(0);
+    cond = R(0);
+    return;
+  }
+  const R inv = Tr<R>::rsqrt_(vn);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) qv[k] = v[k] * inv;
+}
+
+// ---------------------------------------------------------------------------
 // rotations <-> compact storage
 // ---------------------------------------------------------------------------
 template <typename R>
