@@ -392,23 +392,65 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
       P[1][1] = pm - dd * dl;
       P[0][1] = P[1][0] = dd * s01;
     } else {
-      R ev[3], E[3][3];
-      sym3_eig<R>(S[0][0], R(0.5) * (S[0][1] + S[1][0]), R(0.5) * (S[0][2] + S[2][0]), S[1][1],
-                  R(0.5) * (S[1][2] + S[2][1]), S[2][2], ev, E);
+      // the prox of the spectral function: P = f(S) with f the per-eigenvalue prox
+      // map.  In float it is formed without eigenvectors: S's eigenvalues in closed
+      // form (l1 >= l2 >= l3), the roots p_j = f(l_j), and the Newton form
+      // P = p1 I + f[l1,l2] (S - l1 I) + f[l1,l2,l3] (S - l1 I)(S - l2 I) with the
+      // first divided differences 1 / h[p_j, p_k] (cancellation-free, also for
+      // equal eigenvalues).  Near a cluster the eigenvalues lose accuracy but the
+      // interpolant evaluated at S does not: S - l1 I is then small.
+      bool done = false;
+      if constexpr (sizeof(R) == 4) {
+        R lam[3];
+        sym3_eigvals<R>(S[0][0], R(0.5) * (S[0][1] + S[1][0]), R(0.5) * (S[0][2] + S[2][0]), S[1][1],
+                        R(0.5) * (S[1][2] + S[2][1]), S[2][2], lam);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) p[j] = prox_root_en<R, EN>(ev[j], w, mu, en);
-      if (p[0] * p[1] * p[2] < R(kSqrtEpsM) || p[0] + p[1] + p[2] < R(kSqrtEpsM)) {
+        for (int j = 0; j < 3; ++j) p[j] = prox_root_en<R, EN>(lam[j], w, mu, en);
+        if (!(p[0] * p[1] * p[2] < R(kSqrtEpsM) || p[0] + p[1] + p[2] < R(kSqrtEpsM))) {
+          const R d12 = R(1) / prox_inverse_dd<R, EN>(p[0], p[1], w, mu, en);
+          const R d23 = R(1) / prox_inverse_dd<R, EN>(p[1], p[2], w, mu, en);
+          const R g13 = lam[0] - lam[2];
+          const R d123 = (g13 > R(0)) ? (d12 - d23) / g13 : R(0);
+          R A1[3][3], A2[3][3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) p[j] = fmax(p[j], R(kSqrtEpsM));
-      }
+          for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k) {
+              const R sym = R(0.5) * (S[a][k] + S[k][a]);
+              A1[a][k] = sym - (a == k ? lam[0] : R(0));
+              A2[a][k] = sym - (a == k ? lam[1] : R(0));
+            }
 #pragma unroll
-        for (int k = a; k < 3; ++k) {
-          const R v = E[a][0] * p[0] * E[k][0] + E[a][1] * p[1] * E[k][1] + E[a][2] * p[2] * E[k][2];
-          P[a][k] = v;
-          P[k][a] = v;
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = a; k < 3; ++k) {
+              const R quad = A1[a][0] * A2[0][k] + A1[a][1] * A2[1][k] + A1[a][2] * A2[2][k];
+              const R v = (a == k ? p[0] : R(0)) + d12 * A1[a][k] + d123 * quad;
+              P[a][k] = v;
+              P[k][a] = v;
+            }
+          done = true;
         }
+      }
+      if (!done) {
+        R ev[3], E[3][3];
+        sym3_eig<R>(S[0][0], R(0.5) * (S[0][1] + S[1][0]), R(0.5) * (S[0][2] + S[2][0]), S[1][1],
+                    R(0.5) * (S[1][2] + S[2][1]), S[2][2], ev, E);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) p[j] = prox_root_en<R, EN>(ev[j], w, mu, en);
+        if (p[0] * p[1] * p[2] < R(kSqrtEpsM) || p[0] + p[1] + p[2] < R(kSqrtEpsM)) {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) p[j] = fmax(p[j], R(kSqrtEpsM));
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int k = a; k < 3; ++k) {
+            const R v = E[a][0] * p[0] * E[k][0] + E[a][1] * p[1] * E[k][1] + E[a][2] * p[2] * E[k][2];
+            P[a][k] = v;
+            P[k][a] = v;
+          }
+      }
     }
     // ---- multiplier update (eq. lambdaupdate) and the next right-hand-side terms (eq. solvinginw)
     // Lambda^k = (Lambda^{k-1} + J) - U P = A - U P: only A stays live through the

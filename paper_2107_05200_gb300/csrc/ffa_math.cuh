@@ -218,6 +218,53 @@ __device__ __forceinline__ void sym3_eig(R a00, R a01, R a02, R a11, R a12, R a2
 }
 
 // ---------------------------------------------------------------------------
+// Eigenvalues of a symmetric 3x3 in closed form (the trigonometric solution of
+// the characteristic cubic): with q = tr S / 3, B = S - q I, s = |B|_F / sqrt(6)
+// and r = det(B / s) / 2 in [-1, 1], the eigenvalues are q + 2 s cos(phi + 2 pi
+// k / 3), phi = acos(r) / 3; returned in descending order.  Near a repeated
+// eigenvalue acos loses accuracy, which the matrix-function form below tolerates.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void sym3_eigvals(R a00, R a01, R a02, R a11, R a12, R a22, R lam[3]) {
+  const R q = (a00 + a11 + a22) * R(1.0 / 3.0);
+  const R b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+  const R off = a01 * a01 + a02 * a02 + a12 * a12;
+  const R s2 = (b00 * b00 + b11 * b11 + b22 * b22 + R(2) * off) * R(1.0 / 6.0);
+  if (!(s2 > Tr<R>::tiny())) {
+    lam[0] = lam[1] = lam[2] = q;
+    return;
+  }
+  const R sd = Tr<R>::sqrt_(s2);
+  const R is = R(1) / sd;
+  const R c00 = b00 * is, c11 = b11 * is, c22 = b22 * is, c01 = a01 * is, c02 = a02 * is, c12 = a12 * is;
+  R r = R(0.5) * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02));
+  r = fmin(fmax(r, R(-1)), R(1));
+  const R phi = acos(r) * R(1.0 / 3.0);
+  lam[0] = q + R(2) * sd * cos(phi);
+  lam[2] = q + R(2) * sd * cos(phi + R(2.0943951023931957));   // + 2 pi / 3
+  lam[1] = R(3) * q - lam[0] - lam[2];
+}
+
+// h[p1, p2], the divided difference of the inverse of the scalar prox map,
+// q = h(p) = p + (w / mu) phi'(p) (w phi'(p) + mu (p - q) = 0, the per-eigenvalue
+// form of eq. rootfindinginp), written without cancellation so that it also holds
+// at p1 = p2 (then it is h'(p)): SD phi' = p - p^-3, SG phi' = p - 1/p, SA phi' =
+// p - 1 - p^-3 + p^-2.  1 / h[p1, p2] is the divided difference of the prox map.
+template <typename R, int EN>
+__device__ __forceinline__ R prox_inverse_dd(R p1, R p2, R w, R mu, int en) {
+  const int e = (EN == kEnMixed) ? en : EN;
+  const R pp = p1 * p2;
+  R dphi;
+  if (e == kEnSG) {
+    dphi = R(1) + R(1) / pp;
+  } else {
+    const R a = (p1 * p1 + pp + p2 * p2) / (pp * pp * pp);
+    dphi = (e == kEnSD) ? R(1) + a : R(1) + a - (p1 + p2) / (pp * pp);
+  }
+  return R(1) + (w / mu) * dphi;
+}
+
+// ---------------------------------------------------------------------------
 // The penalty bound of the paper's schedule (Lemma 1, Proposition 1, Sec. 6), in
 // double.  gnorm2 = |grad f(P)|^2; B = sqrt(5 (1 + gnorm2)); C^L (SG) is the
 // positive root of x^2 + B x - 1 (written as 2 / (B + sqrt(B^2 + 4)) to avoid
