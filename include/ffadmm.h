@@ -124,6 +124,17 @@ typedef struct {
                               Q_i = (J_i + Lambda_i) P_i + (h_i / mu_i) U_i^{k-1}.  Fixed penalties,
                               the paper's local step and single meshes only (not with
                               penalty_schedule 1, local_variant 1, batches or ffa_forward_unrolled). */
+  int32_t factor_device;   /* numeric decomposition of L_FF (Algorithm 2, decompose(L)), at setup and at
+                              every rescaling of penalty_schedule 1: 0 on the host in double (default), 1 on
+                              the device in float, 2 on the device in double.  The ordering and the
+                              supernodes stay a host analysis; the device runs the multifrontal method over
+                              the same tree and writes the same float blocks (1: each within float rounding
+                              times the growth of the elimination; the W step's double residual sweeps
+                              restore double accuracy).  With penalty_schedule 1 it also assembles the new
+                              L on the device, so a rescaling event has no host work.  Device memory: every
+                              front and every inv(L_ss) at once (sum over supernodes of (n_s + m_s)^2 +
+                              n_s^2 elements), kept for the context's life with penalty_schedule 1 and
+                              released after setup otherwise. */
 } ffa_params;
 
 typedef struct {
@@ -301,6 +312,13 @@ ffa_status ffa_gradient(ffa_ctx* ctx, const double* W, double* dEdW);
 
 /* Sizes, setup timings and the algorithmic byte counts used for roofline reports. */
 ffa_status ffa_get_info(ffa_ctx* ctx, ffa_info* info);
+
+/* The current decomposition of L_FF (Algorithm 2, decompose(L)) as the W-step passes read it: for
+ * every supernode s the float block B_s = [inv(L_ss); L_rs inv(L_ss)], column-major, zero above the
+ * diagonal of inv(L_ss), concatenated with zero padding, factor_entries floats in all (ffa_info).
+ * out (host or device, caller-owned) takes exactly count = factor_entries floats; another count is
+ * FFA_ERR_INVALID_ARG.  A diagnostic for comparing where the decomposition ran (factor_device). */
+ffa_status ffa_copy_factor(ffa_ctx* ctx, float* out, int64_t count);
 
 /* Average device time of each phase of an iteration, measured with CUDA events
  * on the context stream over reps iterations launched eagerly (not as a graph).

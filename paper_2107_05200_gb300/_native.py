@@ -25,7 +25,7 @@ EXPORTED = [
     "ffa_forward_unrolled", "ffa_backward_unrolled",
     "ffa_batch_create", "ffa_batch_destroy", "ffa_batch_last_error", "ffa_batch_init", "ffa_batch_iterate",
     "ffa_batch_get_W", "ffa_autotune", "ffa_batch_autotune", "ffa_batch_groups", "ffa_tutte",
-    "ffa_set_wait_limit",
+    "ffa_set_wait_limit", "ffa_copy_factor",
 ]
 
 
@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("host_threads", C.c_int32), ("solve_schedule", C.c_int32),
                 ("penalty_schedule", C.c_int32), ("rescale_rho", C.c_double),
                 ("local_variant", C.c_int32), ("solve_subtree_height", C.c_int32 * 2),
-                ("prox_h", C.c_int32)]
+                ("prox_h", C.c_int32), ("factor_device", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -123,6 +123,7 @@ def load() -> C.CDLL:
         "ffa_energy": ([vp, vp, C.POINTER(dbl)], C.c_int),
         "ffa_gradient": ([vp, vp, vp], C.c_int),
         "ffa_get_info": ([vp, C.POINTER(Info)], C.c_int),
+        "ffa_copy_factor": ([vp, vp, C.c_int64], C.c_int),
         "ffa_last_wstep_residual": ([vp, C.POINTER(dbl)], C.c_int),
         "ffa_profile_phases": ([vp, i32, C.POINTER(PhaseTimes)], C.c_int),
         "ffa_energy_noalloc": ([i32, i32, i32, i32, vp, vp, vp, C.c_int, vp, vp], C.c_int),

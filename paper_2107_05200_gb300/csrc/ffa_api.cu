@@ -15,6 +15,7 @@
 
 #include "ffa_internal.h"
 #include "ffa_constraint_host.h"
+#include "ffa_devfactor_launch.h"
 #include "ffa_operator_host.h"
 #include "ffa_state.h"
 
@@ -130,6 +131,11 @@ struct ffa_ctx {
   std::vector<Supernode> nodes_h;  // host copy of the supernode table (task lists are rebuilt from it)
   int n_levels = 0;
   Slot tune_slot;
+  // numeric decomposition on the device (factor_device 1 or 2): the plan's device
+  // arrays and launch program, and the device assembly of L for rescaling events
+  DevFactorDev df;
+  std::vector<DfLaunch> df_prog;
+  DevAssemblyDev da;
 
   // batched meshes (set for contexts made by ffa_batch_create)
   int n_mesh = 0;
@@ -235,6 +241,94 @@ ffa_status upload_real(ffa_ctx* ctx, void** p, const std::vector<double>& h) {
 
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// frees one of the context's device allocations before the context ends
+void dfree(ffa_ctx* ctx, void* p, size_t bytes) {
+  auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+  if (it == ctx->allocs.end()) return;
+  cudaFree(p);
+  ctx->allocs.erase(it);
+  ctx->info.device_bytes -= (int64_t)bytes;
+}
+
+// factor_device 1 or 2: the plan of the device decomposition (fronts, extend-add
+// maps, launch program) and its work arrays; with H (the penalty schedule) also
+// the term lists of the device assembly of L and the gradients in double
+ffa_status devfactor_setup(ffa_ctx* ctx, const Factor& fac, const OperatorArrays& OA, const std::vector<int64_t>& Ap,
+                           const OperatorHost* H) {
+  std::vector<int32_t> cnt(fac.nF);
+  for (int c = 0; c < fac.nF; ++c) cnt[c] = (int32_t)(Ap[fac.perm[c] + 1] - Ap[fac.perm[c]]);
+  DevFactorPlan P;
+  std::string msg;
+  if (!build_devfactor_plan(fac, OA.width, OA.ell_col, cnt, P, msg)) return fail(ctx, FFA_ERR_INVALID_ARG, msg);
+  DevFactorDev& D = ctx->df;
+  D.fp64 = ctx->prm.factor_device == 2 ? 1 : 0;
+  const size_t tsz = D.fp64 ? 8 : 4;
+  ffa_status st;
+  DfNode* nodes = nullptr;
+  int64_t *rel_off = nullptr, *orig_dst = nullptr;
+  int32_t* rel = nullptr;
+  DfItem* items = nullptr;
+  if ((st = upload(ctx, &nodes, P.nodes)) != FFA_OK) return st;
+  if ((st = upload(ctx, &rel_off, P.rel_off)) != FFA_OK) return st;
+  if ((st = upload(ctx, &rel, P.rel)) != FFA_OK) return st;
+  if ((st = upload(ctx, &items, P.items)) != FFA_OK) return st;
+  if ((st = upload(ctx, &orig_dst, P.orig_dst)) != FFA_OK) return st;
+  D.nodes = nodes;
+  D.rel_off = rel_off;
+  D.rel = rel;
+  D.items = items;
+  D.orig_dst = orig_dst;
+  D.front_elems = P.front_elems;
+  D.linv_elems = P.linv_elems;
+  D.n_slots = (int64_t)P.orig_dst.size();
+  if ((st = dalloc_bytes(ctx, &D.F, (size_t)P.front_elems * tsz)) != FFA_OK) return st;
+  if ((st = dalloc_bytes(ctx, &D.Lv, (size_t)P.linv_elems * tsz)) != FFA_OK) return st;
+  if ((st = dalloc(ctx, &D.err, 1)) != FFA_OK) return st;
+  FFA_CUDA(cudaMemsetAsync(D.err, 0, sizeof(int32_t), ctx->stream));
+  ctx->df_prog = P.prog;
+  if (H) {
+    DevAssemblyPlan Q;
+    if (!build_assembly_plan(*H, fac, OA, Ap, Q, msg)) return fail(ctx, FFA_ERR_INVALID_ARG, msg);
+    DevAssemblyDev& A = ctx->da;
+    int64_t *ell_ptr = nullptr, *fc_ptr = nullptr;
+    int32_t *ell_src = nullptr, *fc_src = nullptr, *cf_src = nullptr;
+    double* g = nullptr;
+    if ((st = upload(ctx, &ell_ptr, Q.ell_ptr)) != FFA_OK) return st;
+    if ((st = upload(ctx, &ell_src, Q.ell_src)) != FFA_OK) return st;
+    if ((st = upload(ctx, &fc_ptr, Q.fc_ptr)) != FFA_OK) return st;
+    if ((st = upload(ctx, &fc_src, Q.fc_src)) != FFA_OK) return st;
+    if ((st = upload(ctx, &cf_src, Q.cf_src)) != FFA_OK) return st;
+    if ((st = upload(ctx, &g, H->g)) != FFA_OK) return st;
+    A.ell_ptr = ell_ptr;
+    A.ell_src = ell_src;
+    A.n_ell = (int64_t)Q.ell_ptr.size() - 1;
+    A.fc_ptr = fc_ptr;
+    A.fc_src = fc_src;
+    A.cf_src = cf_src;
+    A.n_fc = (int64_t)Q.fc_ptr.size() - 1;
+    A.g = g;
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));   // the host vectors above end here
+  }
+  FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  return FFA_OK;
+}
+
+// the decomposition on the device from the current ELL of L_FF into ctx->blocks;
+// a pivot that is not positive gives FFA_ERR_SINGULAR_SYSTEM
+ffa_status devfactor_run(ffa_ctx* ctx) {
+  FFA_CUDA(launch_devfactor(ctx->df, ctx->df_prog, ctx->ell_val, ctx->blocks, ctx->stream));
+  int32_t flag = 0;
+  FFA_CUDA(cudaMemcpyAsync(&flag, ctx->df.err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (flag) {
+    FFA_CUDA(cudaMemsetAsync(ctx->df.err, 0, sizeof(int32_t), ctx->stream));
+    FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+    return fail(ctx, FFA_ERR_SINGULAR_SYSTEM,
+                "the W-step matrix is not positive definite (a pivot of the device decomposition)");
+  }
+  return FFA_OK;
 }
 
 LocalLaunch local_launch(ffa_ctx* ctx, bool check, const void* vrec) {
@@ -463,6 +557,7 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   else if (p.prox_h == 1 && p.penalty_schedule == 1)
     msg = "prox_h 1 is implemented with fixed penalties (its bound depends on mu_i)";
   else if (p.prox_h == 1 && p.local_variant == 1) msg = "the joint (U, P) variant has no proximal U term";
+  else if (p.factor_device < 0 || p.factor_device > 2) msg = "factor_device must be 0, 1 or 2";
   else return FFA_OK;
   return FFA_ERR_INVALID_ARG;
 }
@@ -700,6 +795,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
     in.coords = coords.data();
     in.leaf_size = ctx->prm.nd_leaf_size;
     in.threads = ctx->prm.host_threads;
+    in.numeric = ctx->prm.factor_device == 0;
     std::string msg;
     int rc = build_factor(in, fac, msg);
     if (rc == 3) return fail(ctx, FFA_ERR_SINGULAR_SYSTEM, msg);
@@ -707,7 +803,9 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   }
   ctx->info.setup_seconds_analyze = fac.t_analyze;
   ctx->info.setup_seconds_factor = fac.t_factor;
-  ctx->info.factor_entries = (int64_t)fac.blocks.size();
+  int64_t block_floats = 0;
+  for (const Supernode& sn : fac.nodes) block_floats = std::max<int64_t>(block_floats, sn.blk_off + (int64_t)sn.ld * sn.ncol);
+  ctx->info.factor_entries = block_floats;
   ctx->info.factor_flops = fac.flops;
   ctx->info.n_supernodes = (int32_t)fac.nodes.size();
   ctx->info.n_levels = fac.n_levels;
@@ -735,7 +833,13 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   ctx->n_levels = fac.n_levels;
   // ---- device uploads
   if ((st = upload(ctx, &ctx->rows, fac.rows)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->blocks, fac.blocks)) != FFA_OK) return st;
+  if (ctx->prm.factor_device == 0) {
+    if ((st = upload(ctx, &ctx->blocks, fac.blocks)) != FFA_OK) return st;
+  } else {
+    // written by the device decomposition below; the padding rows stay zero
+    if ((st = dalloc(ctx, &ctx->blocks, (size_t)block_floats)) != FFA_OK) return st;
+    FFA_CUDA(cudaMemsetAsync(ctx->blocks, 0, (size_t)block_floats * sizeof(float), ctx->stream));
+  }
   if ((st = build_tasks(ctx)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->ell_col, ell_col)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->ell_val, ell_val)) != FFA_OK) return st;
@@ -753,6 +857,20 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   if ((st = upload(ctx, &ctx->cf_ptr, cf_ptr)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->cf_row, cf_row)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->cf_val, cf_val)) != FFA_OK) return st;
+  if (ctx->prm.factor_device != 0) {
+    const bool keep = ctx->prm.penalty_schedule == 1;
+    if ((st = devfactor_setup(ctx, fac, OA, Ap, keep ? &H : nullptr)) != FFA_OK) return st;
+    const double t0 = now_s();
+    if ((st = devfactor_run(ctx)) != FFA_OK) return st;
+    ctx->info.setup_seconds_factor = now_s() - t0;
+    if (!keep) {
+      // fixed penalties: the fronts and inverses are not needed again
+      const size_t tsz = ctx->df.fp64 ? 8 : 4;
+      dfree(ctx, ctx->df.F, (size_t)ctx->df.front_elems * tsz);
+      dfree(ctx, ctx->df.Lv, (size_t)ctx->df.linv_elems * tsz);
+      ctx->df.F = ctx->df.Lv = nullptr;
+    }
+  }
   // element arrays: indices (d+1) x m, gradients d*d x m, w, mu
   {
     std::vector<int32_t> idx((size_t)(d + 1) * m);
@@ -890,6 +1008,22 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
 ffa_status apply_penalties(ffa_ctx* ctx) {
   OperatorHost& H = ctx->op;
   cudaStream_t s = ctx->stream;
+  if (ctx->prm.factor_device != 0) {
+    // all on the device: L from the new penalties, its decomposition, and the
+    // terms that depend on it
+    FFA_CUDA(cudaStreamSynchronize(s));
+    const double t0 = now_s();
+    FFA_CUDA(launch_device_assembly(ctx->da, ctx->d, ctx->mu64, ctx->ell_val, ctx->fc_val, ctx->cf_val, s));
+    launch_pin_rhs(ctx->d, ctx->nF, ctx->fc_ptr, ctx->fc_col, ctx->fc_val, ctx->pin_pos, ctx->cst, s);
+    FFA_CUDA(cudaGetLastError());
+    ffa_status st = devfactor_run(ctx);
+    if (st != FFA_OK) return st;
+    launch_rhs_terms(local_launch(ctx, false, ctx->vrec), s);
+    FFA_CUDA(cudaGetLastError());
+    FFA_CUDA(cudaStreamSynchronize(s));
+    ctx->seconds_refactor += now_s() - t0;
+    return FFA_OK;
+  }
   FFA_CUDA(cudaMemcpyAsync(H.mu.data(), ctx->mu64, (size_t)H.m * sizeof(double), cudaMemcpyDeviceToHost, s));
   FFA_CUDA(cudaStreamSynchronize(s));
   const double t0 = now_s();
@@ -1064,6 +1198,7 @@ ffa_status tutte_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* bnd_in,
     in.coords = coords.data();
     in.leaf_size = ctx->prm.nd_leaf_size;
     in.threads = ctx->prm.host_threads;
+    in.numeric = ctx->prm.factor_device == 0;
     std::string msg;
     const int rc = build_factor(in, fac, msg);
     if (rc == 3) return fail(ctx, FFA_ERR_SINGULAR_SYSTEM, "Tutte system: " + msg + " (an interior part without a boundary vertex?)");
@@ -1088,13 +1223,28 @@ ffa_status tutte_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* bnd_in,
   std::vector<int32_t> v2e(n, -1);
   for (int c = 0; c < nF; ++c) v2e[free_vertex[fac.perm[c]]] = c;
   if ((st = upload(ctx, &ctx->rows, fac.rows)) != FFA_OK) return st;
-  if ((st = upload(ctx, &ctx->blocks, fac.blocks)) != FFA_OK) return st;
+  int64_t block_floats = 0;
+  for (const Supernode& sn : fac.nodes) block_floats = std::max<int64_t>(block_floats, sn.blk_off + (int64_t)sn.ld * sn.ncol);
+  if (ctx->prm.factor_device == 0) {
+    if ((st = upload(ctx, &ctx->blocks, fac.blocks)) != FFA_OK) return st;
+  } else {
+    if ((st = dalloc(ctx, &ctx->blocks, (size_t)block_floats)) != FFA_OK) return st;
+    FFA_CUDA(cudaMemsetAsync(ctx->blocks, 0, (size_t)block_floats * sizeof(float), ctx->stream));
+  }
   if ((st = build_tasks(ctx)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->ell_col, OA.ell_col)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->ell_val, OA.ell_val)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->fc_ptr, OA.fc_ptr)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->fc_col, OA.fc_col)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->fc_val, OA.fc_val)) != FFA_OK) return st;
+  if (ctx->prm.factor_device != 0) {
+    if ((st = devfactor_setup(ctx, fac, OA, Ap, nullptr)) != FFA_OK) return st;
+    if ((st = devfactor_run(ctx)) != FFA_OK) {
+      if (st == FFA_ERR_SINGULAR_SYSTEM)
+        return fail(ctx, st, "Tutte system: " + ctx->err + " (an interior part without a boundary vertex?)");
+      return st;
+    }
+  }
   if ((st = upload(ctx, &ctx->pin_pos, bpos)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->v2e, v2e)) != FFA_OK) return st;
   if ((st = upload(ctx, &ctx->v2pin, v2pin)) != FFA_OK) return st;
@@ -1353,6 +1503,7 @@ ffa_status ffa_default_params(ffa_params* p) {
   p->local_variant = 0;
   p->solve_subtree_height[0] = p->solve_subtree_height[1] = -1;
   p->prox_h = 0;
+  p->factor_device = 0;
   return FFA_OK;
 }
 
@@ -1810,6 +1961,15 @@ ffa_status ffa_get_info(ffa_ctx* ctx, ffa_info* info) {
   ctx->info.seconds_refactor = ctx->seconds_refactor;
   *info = ctx->info;
   return FFA_OK;
+}
+
+ffa_status ffa_copy_factor(ffa_ctx* ctx, float* out, int64_t count) {
+  if (!ctx) return FFA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!out) return fail(ctx, FFA_ERR_INVALID_ARG, "out is NULL");
+  if (count != ctx->info.factor_entries)
+    return fail(ctx, FFA_ERR_INVALID_ARG, "count must equal factor_entries (" + std::to_string(ctx->info.factor_entries) + ")");
+  return copy_out(ctx, out, ctx->blocks, (size_t)count * sizeof(float));
 }
 
 ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out) {

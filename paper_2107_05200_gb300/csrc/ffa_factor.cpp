@@ -585,7 +585,7 @@ int build_factor(const FactorInput& in, Factor& f, std::string& err) {
   f.flops = flops;
   const double t1 = now_s();
   f.t_analyze = t1 - t0;
-
+  if (!in.numeric) return 0;
   return numeric(in, f, err, threads);
 }
 

@@ -59,6 +59,7 @@ struct FactorInput {
   int32_t leaf_size = 64;
   int32_t threads = 0;             // 0 = hardware concurrency
   bool keep_double = false;
+  bool numeric = true;             // false: analysis only (the blocks are computed on the device)
 };
 
 // Returns 0 on success, 3 if L_FF is not positive definite, 1 on bad input.

@@ -15,6 +15,7 @@ from . import _native as N
 
 ENERGIES = {"sd": 0, "sg": 1, "sa": 2}
 PRECISIONS = {"fp32": 0, "fp64": 1}
+FACTORS = {"host": 0, "device": 1, "device64": 2}
 
 
 def _ptr(a, dtype):
@@ -42,14 +43,16 @@ class Solver:
 
     penalties="fixed": mu_i = rho w_i, L decomposed once; penalties="paper": the
     paper's schedule (initial mu_i = max(mu_min,i, w_i) and per-element rescaling by
-    rescale_rho/2 at the paper's events, L decomposed again after each event)."""
+    rescale_rho/2 at the paper's events, L decomposed again after each event).
+    factor: where the numeric decomposition of L runs, "host" (double), "device"
+    (float) or "device64" (double); the analysis is on the host either way."""
 
     def __init__(self, V, T, pins=None, pin_pos=None, energy: str = "sd", rho: float = 1.0,
                  eps_abs: float = 1e-6, eps_rel: float = 1e-5, check_every: int = 10,
                  precision: str = "fp32", refine_sweeps: int = 2, leaf_size: int = 64,
                  require_flip_free: bool = True, host_threads: int = 0, schedule: int = 1,
                  penalties: str = "fixed", rescale_rho: float = 5.0, local_variant: str = "paper",
-                 subtree_height=None, prox_h: bool = False, stream=None):
+                 subtree_height=None, prox_h: bool = False, factor: str = "host", stream=None):
         self._lib = N.load()
         self._ctx = None
         Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
@@ -81,6 +84,9 @@ class Solver:
             raise ValueError("local_variant must be 'paper' or 'joint'")
         prm.local_variant = 1 if local_variant == "joint" else 0
         prm.prox_h = 1 if prox_h else 0
+        if factor not in FACTORS:
+            raise ValueError("factor must be one of " + ", ".join(FACTORS))
+        prm.factor_device = FACTORS[factor]
         if subtree_height is not None:   # (forward, backward) merged bottom subtree heights
             prm.solve_subtree_height[0], prm.solve_subtree_height[1] = (int(h) for h in subtree_height)
         n_pin = 0 if pins is None else int(len(pins))
@@ -214,6 +220,14 @@ class Solver:
         self._check(self._lib.ffa_backward_unrolled(self._ctx, p, po))
         return out
 
+    def factor_blocks(self) -> np.ndarray:
+        """The float blocks B_s of the current decomposition of L_FF, concatenated as
+        the W-step passes read them (ffa_copy_factor)."""
+        n = int(self.info()["factor_entries"])
+        out = np.empty(n, np.float32)
+        self._check(self._lib.ffa_copy_factor(self._ctx, out.ctypes.data, n))
+        return out
+
     def set_wait_limit(self, polls: int) -> None:
         """Polls of an empty queue slot before a W-step wait gives up (FFA_ERR_TIMEOUT)."""
         self._check(self._lib.ffa_set_wait_limit(self._ctx, int(polls)))
@@ -233,7 +247,7 @@ class Solver:
 
 
 def tutte(V, T, boundary, boundary_pos, leaf_size: int = 64, host_threads: int = 0, schedule: int = 1,
-          stream=None, out=None):
+          factor: str = "host", stream=None, out=None):
     """The minimizer of Tutte's energy with the boundary held (ffa_tutte).
 
     Returns (W, relative residual); W is a new (n, d) float64 array unless `out`
@@ -257,6 +271,9 @@ def tutte(V, T, boundary, boundary_pos, leaf_size: int = 64, host_threads: int =
     prm.nd_leaf_size = int(leaf_size)
     prm.host_threads = int(host_threads)
     prm.solve_schedule = int(schedule)
+    if factor not in FACTORS:
+        raise ValueError("factor must be one of " + ", ".join(FACTORS))
+    prm.factor_device = FACTORS[factor]
     if out is None:
         out = np.empty((n, d), np.float64)
     po, ko = _ptr(out, np.float64)
