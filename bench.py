@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--oracle-probe", type=float, nargs=3, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="cube_deform",
                     choices=["cube_deform", "cube_outcome", "batch256", "uv_disk", "uv_heightfield", "cube_handles",
-                             "tutte"],
+                             "tutte", "decompose"],
                     help="cube_deform: the throughput benchmark; the others report time to tolerance "
                          "(uv_disk, uv_heightfield), batched meshes, or forward + adjoint (cube_handles)")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--factor", default="host", choices=["host", "device", "device64"],
                     help="where the numeric decomposition of L runs (setup and every rescaling event of "
                          "--penalties paper): host in double, device in float, device in double")
+    ap.add_argument("--factors", nargs="*", default=["host", "device", "device64"],
+                    choices=["host", "device", "device64"],
+                    help="decompose: the placements of the decomposition to time")
     ap.add_argument("--penalties", default="fixed", choices=["fixed", "paper"],
                     help="uv_disk / uv_heightfield / cube_outcome: mu = rho w fixed, or the paper's rescaling schedule")
     return ap.parse_args()
@@ -499,6 +502,42 @@ def run_outcome(args, local):
     return 0
 
 
+def run_decompose(args, local):
+    """The numeric decomposition of L_FF of the benchmark cube (Algorithm 2,
+    decompose(L)) where each of --factors puts it: wall time at setup, and under the
+    paper's penalty schedule the cost of one rescaling event (new L assembled and
+    decomposed, right-hand-side terms refreshed) averaged over the events of the
+    first 12 iterations, with the W-step residual after them."""
+    import torch
+
+    from paper_2107_05200_gb300 import workloads as wk
+    from paper_2107_05200_gb300.solver import Solver
+
+    torch.cuda.set_device(local)
+    wl = wk.cube_deform(cells=args.cells)
+    out = {}
+    for factor in args.factors:
+        with Solver.from_workload(wl, precision="fp32", factor=factor) as sol:
+            info = sol.info()
+        entry = {"setup_s": info["setup_seconds_factor"], "flops": info["factor_flops"]}
+        with Solver.from_workload(wl, precision="fp32", penalties="paper", check_every=10, factor=factor) as sol:
+            sol.init(wl.W0)
+            r0 = sol.info()["seconds_refactor"]
+            st = sol.iterate(12, stop_at_tol=False)
+            entry["event_s"] = (sol.info()["seconds_refactor"] - r0) / max(1, st["rescales"])
+            entry["events"] = st["rescales"]
+            entry["wstep_residual"] = sol.wstep_residual()
+        out[factor] = entry
+    first = out[args.factors[0]]
+    line = {"metric": "decomposition of L_FF", "unit": "s", "value": first["setup_s"], "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": wl.name, "elements": wl.m, "vertices": wl.n,
+                       "factor": args.factors[0]},
+            "placements": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_tutte(args, local):
     """The Tutte initializer on a 1024^2-vertex disk (2.1M triangles): one ffa_tutte
     call (host ordering and factorization, GPU solve), against the oracle's sparse
@@ -558,6 +597,8 @@ def main():
         return run_tutte(args, local) if rank == 0 else 0
     if args.workload == "cube_outcome":
         return run_outcome(args, local) if rank == 0 else 0
+    if args.workload == "decompose":
+        return run_decompose(args, local) if rank == 0 else 0
 
     import numpy as np
     import torch

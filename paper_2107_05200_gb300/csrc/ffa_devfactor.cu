@@ -3,9 +3,10 @@
 // device assembly of L = sum_i mu_i G_i^T G_i from new penalties.
 //
 // Every tile product runs on one block of 256 threads: a 64 x 64 output tile,
-// each thread 4 x 4 outputs (rows tx + 16 i, columns ty + 16 j, so that a warp's
-// stores of one output column are contiguous), operands staged in shared memory
-// 32 columns of the sum at a time.  Rows and columns past the end of a front are
+// each thread 4 x 4 outputs (rows 4 tx + i, columns 4 ty + j: its operands are one
+// 16-byte shared load each per step of the sum, and the 16 threads of a half warp
+// store 64 consecutive rows of one output column), operands staged in shared
+// memory 32 steps of the sum at a time.  Rows and columns past the end of a front are
 // read as zero and not written.  Divisions and square roots are IEEE (no
 // approximate forms in this file).
 #include <cuda_runtime.h>
@@ -20,13 +21,34 @@ constexpr int kT = kDfTile;
 constexpr int kKc = 32;
 constexpr int kThreads = 256;
 
+// operand tiles in shared memory: 32 steps of the sum x 64 rows, rows padded to
+// 68 elements so that every group of four starts on 16 bytes
+constexpr int kLd = kT + 4;
 template <typename T>
-struct GemmSmem {
-  T a[kKc][kT + 1];
-  T b[kKc][kT + 1];
+struct __align__(16) GemmSmem {
+  T a[kKc][kLd];
+  T b[kKc][kLd];
 };
 
-// acc[i][j] += sum_{k < K} A(tx + 16 i, k) B(ty + 16 j, k), where A(r, k) =
+// four consecutive elements from shared memory (one 16-byte load for float, two
+// for double)
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x;
+  v[1] = q.y;
+  v[2] = q.z;
+  v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 q0 = *reinterpret_cast<const double2*>(p);
+  const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = q0.x;
+  v[1] = q0.y;
+  v[2] = q1.x;
+  v[3] = q1.y;
+}
+
+// acc[i][j] += sum_{k < K} A(4 tx + i, k) B(4 ty + j, k), where A(r, k) =
 // A[k lda + r] for r < ra and B(c, k) = B[c ldb + k] (BK) or B[k ldb + c] (!BK)
 // for c < cb.  Ends with a barrier, after which every read of A and B is done.
 template <typename T, bool BK>
@@ -54,10 +76,8 @@ __device__ __forceinline__ void gemm_acc(T (&acc)[4][4], const T* A, int64_t lda
 #pragma unroll 4
     for (int k = 0; k < kc; ++k) {
       T a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sm.a[k][tx + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = sm.b[k][ty + 16 * j];
+      ld4(&sm.a[k][4 * tx], a);
+      ld4(&sm.b[k][4 * ty], b);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -105,8 +125,12 @@ __global__ void __launch_bounds__(kThreads) k_df_extend_add(const DfNode* __rest
   for (int32_t a = b + (int)(threadIdx.x & 31); a < ms; a += 32) dst[rl[a]] += src[a];
 }
 
-// diagonal block of panel p: Cholesky (one warp, left-looking, two rows per lane)
-// and its inverse (one thread per column), in shared memory
+// diagonal block of panel p: Cholesky and inverse together, right-looking over
+// the columns k in shared memory with the whole block: column k of L and row k of
+// X = inv(L) are scaled by 1 / sqrt(pivot), then the trailing lower triangle takes
+// -L_ik L_jk and the rows below k of X take -L_ik X_kj (X starts as the identity,
+// so this is forward substitution of L X = I by columns).  Threads (tx, ty) cover
+// column tx of rows k + 1 + ty, k + 5 + ty, ...
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_df_diag(const DfNode* __restrict__ nodes,
                                                       const DfItem* __restrict__ items, int p, T* __restrict__ F,
@@ -117,58 +141,37 @@ __global__ void __launch_bounds__(kThreads) k_df_diag(const DfNode* __restrict__
   const DfItem it = items[blockIdx.x];
   const DfNode d = nodes[it.node];
   const DfPanel g = df_panel(d, p);
-  const int w = g.w, tid = threadIdx.x;
+  const int w = g.w, tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
   T* Fd = F + d.fr_off + (int64_t)g.c0 * d.ldF + g.c0;
   T* Ld = Lv + d.li_off + (int64_t)g.c0 * d.ldL + g.c0;
   for (int e = tid; e < kT * kT; e += kThreads) {
     const int i = e & 63, j = e >> 6;
     D[i][j] = (i < w && j < w && i >= j) ? Fd[(int64_t)j * d.ldF + i] : T(0);
+    X[i][j] = i == j ? T(1) : T(0);
   }
   __syncthreads();
-  if (tid < 32) {
-    const int lane = tid;
-    for (int j = 0; j < w; ++j) {
-      T v[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i = lane + 32 * h;
-        T s = T(0);
-        if (i >= j && i < w) {
-          s = D[i][j];
-          for (int k = 0; k < j; ++k) s -= D[i][k] * D[j][k];
-        }
-        v[h] = s;
-      }
-      const T mine = (j >> 5) ? v[1] : v[0];
-      T pv = __shfl_sync(0xffffffffu, mine, j & 31);
-      if (!(pv > T(0)) || !(pv < T(INFINITY))) {
-        if (lane == 0) atomicExch(err, 1);
-        pv = T(1);
-      }
-      const T dj = sqrt(pv);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i = lane + 32 * h;
-        if (i == j) D[i][j] = dj;
-        else if (i > j && i < w) D[i][j] = v[h] / dj;
-      }
-      __syncwarp();
+  for (int k = 0; k < w; ++k) {
+    T pv = D[k][k];
+    if (!(pv > T(0)) || !(pv < T(INFINITY))) {
+      if (tid == 0) atomicExch(err, 1);
+      pv = T(1);
     }
-  }
-  __syncthreads();
-  if (tid < kT) {
-    const int j = tid;
-    for (int i = 0; i < kT; ++i) X[i][j] = T(0);
-    if (j < w) {
-      X[j][j] = T(1) / D[j][j];
-      for (int i = j + 1; i < w; ++i) {
-        T s = T(0);
-        for (int k = j; k < i; ++k) s += D[i][k] * X[k][j];
-        X[i][j] = -s / D[i][i];
-      }
+    const T dk = sqrt(pv), inv = T(1) / dk;
+    if (tid < kT) {
+      if (tid > k && tid < w) D[tid][k] *= inv;
+    } else if (tid < 2 * kT) {
+      const int j = tid - kT;
+      if (j <= k) X[k][j] *= inv;
     }
+    __syncthreads();
+    for (int i = k + 1 + ty; i < w; i += kThreads / kT) {
+      const T lik = D[i][k];
+      if (tx <= k) X[i][tx] -= lik * X[k][tx];
+      else if (tx <= i) D[i][tx] -= lik * D[tx][k];
+    }
+    if (tid == 0) D[k][k] = dk;
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = tid; e < kT * kT; e += kThreads) {
     const int i = e & 63, j = e >> 6;
     if (i < w && j < w) {
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_df_solve(const DfNode* __restrict_
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int r = tx + 16 * i, c = ty + 16 * j;
+        const int r = 4 * tx + i, c = 4 * ty + j;
         if (r < ra && c < g.w) Fs[(int64_t)(g.c0 + c) * d.ldF + R0 + r] = acc[i][j];
       }
   } else {
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_df_solve(const DfNode* __restrict_
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int r = tx + 16 * i, c = ty + 16 * j;
+        const int r = 4 * tx + i, c = 4 * ty + j;
         if (r < g.w) L[(int64_t)(j0 + c) * d.ldL + g.c0 + r] = -acc[i][j];
       }
   }
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) k_df_update(const DfNode* __restrict
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int r = tx + 16 * i, c = ty + 16 * j;
+        const int r = 4 * tx + i, c = 4 * ty + j;
         if (r < ra && c < cb) Fs[(int64_t)(C0 + c) * d.ldF + R0 + r] -= acc[i][j];
       }
   } else {
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) k_df_update(const DfNode* __restrict
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int r = tx + 16 * i, c = ty + 16 * j;
+        const int r = 4 * tx + i, c = 4 * ty + j;
         if (r < rq && c < cb) L[(int64_t)(j0 + c) * d.ldL + r0 + r] += acc[i][j];
       }
   }
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_df_brs(const DfNode* __restrict__ 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int r = tx + 16 * i, c = ty + 16 * j;
+      const int r = 4 * tx + i, c = 4 * ty + j;
       if (r < ra && c < cb) B[(int64_t)(col0 + c) * d.ld + R0 + r] = (float)acc[i][j];
     }
 }
