@@ -137,8 +137,20 @@ struct Dissection {
   }
 };
 
-// Postorder numbering of the dissection tree into supernodes.
+// Postorder numbering of the dissection tree into supernodes.  Of two children
+// the shallower subtree is numbered first, so that a node's last child (the one
+// whose columns end where the node's begin) is on its longest path to a leaf.
 void number_tree(const std::vector<TreeNode>& tree, int t, Factor& f, std::vector<int>& tree2node) {
+  // heights (children are created after their parent, so they have larger ids)
+  std::vector<int> height(tree.size(), 0);
+  for (int id = (int)tree.size() - 1; id >= 0; --id)
+    for (int k = 0; k < 2; ++k)
+      if (tree[id].child[k] >= 0) height[id] = std::max(height[id], height[tree[id].child[k]] + 1);
+  auto ordered = [&](int id, int k) {
+    const int a = tree[id].child[0], b = tree[id].child[1];
+    const bool swap = a >= 0 && b >= 0 && height[a] > height[b];
+    return tree[id].child[swap ? 1 - k : k];
+  };
   // iterative postorder
   std::vector<std::pair<int, int>> st;  // (tree node, state)
   st.push_back({t, 0});
@@ -146,7 +158,7 @@ void number_tree(const std::vector<TreeNode>& tree, int t, Factor& f, std::vecto
     auto& top = st.back();
     int id = top.first;
     if (top.second < 2) {
-      int c = tree[id].child[top.second++];
+      int c = ordered(id, top.second++);
       if (c >= 0) st.push_back({c, 0});
       continue;
     }

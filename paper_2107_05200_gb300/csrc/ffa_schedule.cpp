@@ -171,9 +171,17 @@ void build_schedule(const std::vector<Supernode>& nd, int n_levels, const Schedu
       F.push[s] = PushRec{p, t0f[p], ntf[p], 0};
       F.pending[p] += ntf[s];
     }
+  // the ready nodes enter the queue deepest first (the distance to the root is
+  // the length of the chain each one starts), ties in node order
+  std::vector<int32_t> depth(nn, 0);
+  for (int s = nn - 1; s >= 0; --s)   // parents after children: walk down from the roots
+    if (nd[s].parent >= 0) depth[s] = depth[nd[s].parent] + 1;
+  std::vector<int32_t> ready;
   for (int s = 0; s < nn; ++s)
-    if (ntf[s] > 0 && F.pending[s] == 0)
-      for (int i = 0; i < ntf[s]; ++i) F.queue.push_back(t0f[s] + i);
+    if (ntf[s] > 0 && F.pending[s] == 0) ready.push_back(s);
+  std::stable_sort(ready.begin(), ready.end(), [&](int a, int b) { return depth[a] > depth[b]; });
+  for (int s : ready)
+    for (int i = 0; i < ntf[s]; ++i) F.queue.push_back(t0f[s] + i);
   F.n_init = (int)F.queue.size();
   F.queue.resize(F.tasks.size(), -1);
 
@@ -182,6 +190,9 @@ void build_schedule(const std::vector<Supernode>& nd, int n_levels, const Schedu
   std::vector<std::vector<int32_t>> kids(nn);
   for (int s = 0; s < nn; ++s)
     if (ntb[s] > 0 && up_b[s] >= 0) kids[up_b[s]].push_back(s);
+  // a completion releases the node with the tallest subtree first: its chain to
+  // the leaves is the longest
+  for (auto& k : kids) std::stable_sort(k.begin(), k.end(), [&](int a, int b) { return nd[a].level > nd[b].level; });
   B.push.assign((size_t)nn * (1 + kPushKids), PushRec{0, 0, 0, 0});
   for (int s = 0; s < nn; ++s) {
     const int k0 = (int)B.kids.size();

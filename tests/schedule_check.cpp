@@ -263,6 +263,24 @@ int main(int argc, char** argv) {
               if (dyn != (seen[s] + (own[s] > 0) == 1)) return fail(tag + "node missing from the dynamic list");
               if (!dyn && own[s]) return fail(tag + "bottom-level node in the dynamic list");
             }
+            // the forward pass's ready nodes are queued deepest first; a backward
+            // completion releases the node with the tallest subtree first
+            {
+              std::vector<int> depth(nn, 0);
+              for (int s = nn - 1; s >= 0; --s)
+                if (nd[s].parent >= 0) depth[s] = depth[nd[s].parent] + 1;
+              if (pass == 0)
+                for (int i = 1; i < P.n_init; ++i)
+                  if (depth[P.tasks[P.queue[i]].node] > depth[P.tasks[P.queue[i - 1]].node])
+                    return fail(tag + "forward ready queue not deepest first");
+              if (pass == 1)
+                for (int s = 0; s < nn; ++s) {
+                  const PushRec& r = P.push[(size_t)s * (1 + kPushKids)];
+                  for (int k = r.x + 1; k < r.y; ++k)
+                    if (nd[P.tasks[P.kids[k].x].node].level > nd[P.tasks[P.kids[k - 1].x].node].level)
+                      return fail(tag + "backward release not tallest first");
+                }
+            }
             // replay the protocol; dependencies hold in the execution order
             for (int threads : {1, 24}) {
               Replay R;

@@ -26,4 +26,6 @@ def test_device_decomposition_plan_reproduces_the_host_factor(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
     # the multi-panel paths ran
-    assert "max panels 4" in r.stdout and "max panels 3" in r.stdout, r.stdout
+    import re
+    panels = [int(x) for x in re.findall(r"max panels (\d+)", r.stdout)]
+    assert len(panels) == 7 and max(panels) >= 4 and sorted(panels)[-2] >= 3, r.stdout
