@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--oracle-probe", type=float, nargs=3, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="cube_deform",
                     choices=["cube_deform", "cube_outcome", "batch256", "uv_disk", "uv_heightfield", "cube_handles",
-                             "tutte", "decompose"],
+                             "tutte", "decompose", "volume_correspondence"],
                     help="cube_deform: the throughput benchmark; the others report time to tolerance "
                          "(uv_disk, uv_heightfield), batched meshes, or forward + adjoint (cube_handles)")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -538,6 +538,54 @@ def run_decompose(args, local):
     return 0
 
 
+def run_volume_correspondence(args, local):
+    """Volume correspondence (Sec. Results): the Tutte start on the GPU (ffa_tutte),
+    then the method to its termination test; wall times of both (setup excluded,
+    the solver's graphs captured by a warm-up run), flips at the start and at the
+    end."""
+    import numpy as np
+    import torch
+
+    from paper_2107_05200_gb300 import workloads as wk
+    from paper_2107_05200_gb300.solver import Solver, tutte
+
+    torch.cuda.set_device(local)
+    wl = wk.volume_correspondence(cells=args.cells, start=False)
+    Vs, Ts = wk.cube_tets(2)                    # load the library, touch the device: one free vertex
+    face = np.nonzero(np.any((Vs < 0.25) | (Vs > 0.75), axis=1))[0].astype(np.int32)
+    tutte(Vs, Ts, face, Vs[face].copy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W0, rel = tutte(wl.V, wl.T, wl.pins, wl.pin_pos, factor=args.factor)
+    t_tutte = time.perf_counter() - t0
+    flipped0 = wk.flipped_fraction(W0, wl.T)
+    t0 = time.perf_counter()
+    sol = Solver.from_workload(wl, precision=args.precision, check_every=10, refine_sweeps=args.sweeps,
+                               factor=args.factor)
+    t_setup = time.perf_counter() - t0
+    sol.init(W0)
+    sol.iterate(10, stop_at_tol=False)          # warm-up (graph capture)
+    sol.init(W0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = sol.iterate(wl.max_iter, stop_at_tol=True)
+    torch.cuda.synchronize()
+    t_admm = time.perf_counter() - t0
+    E = sol.energy()
+    sol.close()
+    line = {"metric": "volume correspondence: Tutte start + the method to tolerance", "unit": "s",
+            "value": t_tutte + t_admm, "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "elements": wl.m, "vertices": wl.n, "pinned": int(len(wl.pins)),
+                       "energy": wl.energy, "rho": wl.rho, "eps_abs": wl.eps_abs, "eps_rel": wl.eps_rel,
+                       "max_iter": wl.max_iter, "factor": args.factor},
+            "tutte_s": t_tutte, "tutte_rel_residual": rel, "flipped_at_start": flipped0, "setup_s": t_setup,
+            "admm_s": t_admm, "iterations": st["iters"], "converged": st["converged"],
+            "n_flipped": st["n_flipped"], "energy": E, "e_prim": st["e_prim"], "e_dual": st["e_dual"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_tutte(args, local):
     """The Tutte initializer on a 1024^2-vertex disk (2.1M triangles): one ffa_tutte
     call (host ordering and factorization, GPU solve), against the oracle's sparse
@@ -599,6 +647,8 @@ def main():
         return run_outcome(args, local) if rank == 0 else 0
     if args.workload == "decompose":
         return run_decompose(args, local) if rank == 0 else 0
+    if args.workload == "volume_correspondence":
+        return run_volume_correspondence(args, local) if rank == 0 else 0
 
     import numpy as np
     import torch

@@ -359,6 +359,58 @@ def cube_handles(cells: int = 32, seed: int = 5, n_targets: int = 1000,
     return wl
 
 
+def twist_bend_map(X: np.ndarray, twist: float = 4.0, radius: float = 2.0) -> np.ndarray:
+    """Analytic target of the volume-correspondence workload: a twist by
+    twist * z radians about the vertical axis through (0.5, 0.5), then the bend map."""
+    x, y, z = X[:, 0] - 0.5, X[:, 1] - 0.5, X[:, 2]
+    a = twist * z
+    Y = np.column_stack([0.5 + x * np.cos(a) - y * np.sin(a), 0.5 + x * np.sin(a) + y * np.cos(a), z])
+    return bend_map(Y, radius)
+
+
+def volume_correspondence(cells: int = 32, seed: int = 6, twist: float = 4.0, radius: float = 2.0,
+                          energy: str = SYM_GRADIENT, rho: float = 20.0, max_iter: int = 1000,
+                          start: bool = True) -> Workload:
+    """Volume correspondence (Sec. Results, "Volume Correspondence"): the interior of
+    one closed surface mapped onto the interior of a second one whose boundary
+    corresponds to it, with the boundary held on the second surface and the
+    interior started from the minimizer of Tutte's energy (App. A).
+
+    Synthetic stand-in for the paper's human and teddy-bear meshes: the unit cube
+    (cells^3 cubes, 6 tets each, interior jittered by +-0.1 cell) is the first
+    volume; every vertex on its boundary is pinned to its image under
+    twist_bend_map (a twist by twist * z radians about the vertical axis through
+    the centre, then a bend of radius `radius`), which carries the cube's boundary
+    onto the second surface.  W0 is the Tutte map with that boundary (weights
+    1 / |V_i - V_j|); on coarse meshes it folds some tets (0.07% at 8^3 cells), on
+    fine ones it need not.  The symmetric gradient energy, as the paper uses for
+    volume correspondence; eps_abs / eps_rel at the paper's defaults; mu_i = 20 w_i
+    (with 10 w_i the 6^3 case oscillates flip-free above its tolerance; with 20 it
+    converges at 6^3 to 16^3 within about 100 iterations).  Refuses a boundary
+    map that inverts a tet whose four vertices are all pinned (no flip-free map
+    would then exist).  start=False leaves W0 at the source positions with the
+    boundary on the second surface (for callers that compute the Tutte start
+    themselves).
+    """
+    rng = np.random.default_rng(seed)
+    V, T = cube_tets(cells)
+    h = 1.0 / cells
+    on_face = np.any((V < 0.5 * h) | (V > 1 - 0.5 * h), axis=1)
+    V[~on_face] += rng.uniform(-0.1 * h, 0.1 * h, size=((~on_face).sum(), 3))
+    pins = np.nonzero(on_face)[0].astype(np.int32)
+    pin_pos = twist_bend_map(V[pins], twist, radius)
+    Wt = V.copy()
+    Wt[pins] = pin_pos
+    all_pinned = on_face[T].all(axis=1)
+    if np.any(_signed_measure(Wt, T)[all_pinned] <= 0):
+        raise ValueError("the boundary map inverts a tetrahedron whose vertices are all pinned")
+    W0 = tutte_embedding(V, T, pins, pin_pos) if start else Wt
+    wl = Workload(f"volume_correspondence_{cells}", V, T, pins, pin_pos, W0, energy, rho,
+                  eps_abs=1e-6, eps_rel=1e-5, max_iter=max_iter)
+    wl.meta = dict(flipped0=flipped_fraction(W0, T) if start else None, twist=twist, radius=radius)
+    return wl
+
+
 def batched_meshes(count: int = 256, seed: int = 4, m_min: int = 500, m_max: int = 50_000,
                    rho: float = 3.0, tol: float = 1e-5) -> list[Workload]:
     """Independent meshes for the batched solver.
@@ -413,4 +465,6 @@ def by_name(name: str) -> Workload:
         return cube_deform()
     if name == "cube_handles_32":
         return cube_handles()
+    if name == "volume_correspondence_32":
+        return volume_correspondence()
     raise KeyError(name)
