@@ -403,8 +403,8 @@ void enqueue_iteration(ffa_ctx* ctx, bool check, cudaEvent_t* ev = nullptr) {
   SolveData S = solve_data(ctx);
   for (int sw = 0; sw < ctx->prm.refine_sweeps; ++sw) {
     if (sw > 0) launch_axpy_correction(S, s);
-    launch_residual(S, nullptr, 0, s);
-    launch_supernodal_solve(S, s);
+    launch_residual_reset(S, s);
+    launch_supernodal_solve(S, s, false);
   }
   if (ctx->n_con > 0) {
     // general constraints: the last correction joins X, which is then projected
@@ -562,8 +562,8 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
   return FFA_ERR_INVALID_ARG;
 }
 
-// kernels one iteration launches: the gather, per refinement sweep the residual,
-// the schedule reset and the solve launches (2 dynamic plus one per non-empty
+// kernels one iteration launches: the gather, per refinement sweep the residual
+// (which also resets the schedules) and the solve launches (2 dynamic plus one per non-empty
 // bottom level and pass, or one per non-empty level and pass), the sweeps - 1
 // corrections, the vertex update and the local step
 int kernels_per_iteration(const ffa_ctx* ctx) {
@@ -576,7 +576,7 @@ int kernels_per_iteration(const ffa_ctx* ctx) {
       solve += (ctx->fwd_off[l + 1] > ctx->fwd_off[l]) + (ctx->bwd_off[l + 1] > ctx->bwd_off[l]);
   }
   const int sweeps = ctx->prm.refine_sweeps;
-  return 1 + sweeps * (2 + solve) + (sweeps - 1) + 1 + 1 + (ctx->n_con > 0 ? 3 : 0);
+  return 1 + sweeps * (1 + solve) + (sweeps - 1) + 1 + 1 + (ctx->n_con > 0 ? 3 : 0);
 }
 
 // Supernode table and task lists of the supernodal solves.  A node with at most

@@ -182,7 +182,10 @@ struct SolveData {
 // y = float(b - L_FF X); partials (optional) gets |b - L X|^2 and |b|^2
 void launch_residual(const SolveData& S, double* partials, int n_blocks, cudaStream_t s);
 void launch_axpy_correction(const SolveData& S, cudaStream_t s);   // X += x
-void launch_supernodal_solve(const SolveData& S, cudaStream_t s);  // x = L_FF^{-1} y (FP32)
+// x = L_FF^{-1} y (FP32); reset = false when launch_residual_reset already reset the passes
+void launch_supernodal_solve(const SolveData& S, cudaStream_t s, bool reset = true);
+// the residual y = b - L_FF X of a sweep together with the reset of its passes (one launch)
+void launch_residual_reset(const SolveData& S, cudaStream_t s);
 int persistent_grid(int d, bool forward);  // resident blocks of the dynamic solve kernels
 int persistent_pipe_grid(int d, bool forward);  // resident blocks of the pipelined ones (0: unavailable)
 

@@ -329,34 +329,33 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
       Up[(int64_t)m + i] = s;
     } else {
       R cond, qt[4];
-      if constexpr (sizeof(R) == 4) {
-        // float: the quaternion of the nearest rotation in closed form (the top
-        // eigenvector of Horn's 4x4 matrix) when the eigenvalue gaps are large
-        // (cond >= 0.8: s_mid + s_min,signed above about 0.1 s_max), which is
-        // where its float eigenvector is accurate; otherwise one-sided Jacobi.
-        // When even that rotation is ill-determined (s_mid + s_min,signed below
-        // 1e-5 s_max) Q itself carries float rounding, so double cannot add
-        // accuracy there; those (near-)degenerate cases are redone in double, so
-        // that the orthonormal frame is built from well-separated columns.
-        nearest_rotation3_quat<R>(Q, qt, cond);
-        if (cond >= R(0.8)) {
-          quat_to_rot<R>(qt, U);
-        } else {
-          nearest_rotation3<R>(Q, U, cond);
-          if (cond < R(1e-5)) {
-            double Qd[3][3], Ud[3][3], cd;
+      // the quaternion of the nearest rotation in closed form (the top eigenvector
+      // of Horn's 4x4 matrix) when the product of the eigenvalue gaps is large
+      // enough relative to |Q|^3 for the precision (float 0.8: s_mid +
+      // s_min,signed above about 0.1 s_max; double 0.1), which is where the
+      // closed-form eigenvector is accurate; otherwise one-sided Jacobi.
+      nearest_rotation3_quat<R>(Q, qt, cond);
+      if (cond >= Tr<R>::rotation_gate()) {
+        quat_to_rot<R>(qt, U);
+      } else if constexpr (sizeof(R) == 4) {
+        // float: when even the Jacobi rotation is ill-determined (s_mid +
+        // s_min,signed below 1e-5 s_max) Q itself carries float rounding, so double
+        // cannot add accuracy there; those (near-)degenerate cases are redone in
+        // double, so that the orthonormal frame is built from well-separated columns.
+        nearest_rotation3<R>(Q, U, cond);
+        if (cond < R(1e-5)) {
+          double Qd[3][3], Ud[3][3], cd;
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+          for (int a = 0; a < 3; ++a)
 #pragma unroll
-              for (int k = 0; k < 3; ++k) Qd[a][k] = (double)Q[a][k];
-            nearest_rotation3<double>(Qd, Ud, cd);
+            for (int k = 0; k < 3; ++k) Qd[a][k] = (double)Q[a][k];
+          nearest_rotation3<double>(Qd, Ud, cd);
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+          for (int a = 0; a < 3; ++a)
 #pragma unroll
-              for (int k = 0; k < 3; ++k) U[a][k] = (R)Ud[a][k];
-          }
-          rot_to_quat<R>(U, qt);
+            for (int k = 0; k < 3; ++k) U[a][k] = (R)Ud[a][k];
         }
+        rot_to_quat<R>(U, qt);
       } else {
         nearest_rotation3<R>(Q, U, cond);
         rot_to_quat<R>(U, qt);
@@ -400,7 +399,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
       // equal eigenvalues).  Near a cluster the eigenvalues lose accuracy but the
       // interpolant evaluated at S does not: S - l1 I is then small.
       bool done = false;
-      if constexpr (sizeof(R) == 4) {
+      {
         R lam[3];
         sym3_eigvals<R>(S[0][0], R(0.5) * (S[0][1] + S[1][0]), R(0.5) * (S[0][2] + S[2][0]), S[1][1],
                         R(0.5) * (S[1][2] + S[2][1]), S[2][2], lam);

@@ -21,6 +21,9 @@ template <> struct Tr<float> {
   static __device__ __forceinline__ float eps() { return 1.1920929e-07f; }
   // quotient for rotation angles only (c and s are then formed consistently from it)
   static __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+  // nearest rotation in closed form when the product of its eigenvalue gaps is at
+  // least this fraction of |Q|^3 (error up to ~6 eps (1 + kappa) there, float)
+  static __device__ __forceinline__ float rotation_gate() { return 0.8f; }
   static constexpr int jacobi_sweeps = 6;
   static constexpr int newton_iters = 24;
 };
@@ -33,6 +36,8 @@ template <> struct Tr<double> {
   static __device__ __forceinline__ double tiny() { return 1e-300; }
   static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
   static __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+  // (double: its error grows like eps / gate^2, below 1.2e-13 at 0.1)
+  static __device__ __forceinline__ double rotation_gate() { return 0.1; }
   static constexpr int jacobi_sweeps = 10;
   static constexpr int newton_iters = 48;
 };

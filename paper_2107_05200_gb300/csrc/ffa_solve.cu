@@ -216,45 +216,51 @@ __global__ void __launch_bounds__(kVertexBlock) k_gather(GatherLaunch G) {
 // residual y = float(b - L_FF X) in double (ELL, column-major, eliminated order)
 // ---------------------------------------------------------------------------
 template <int D>
+__device__ __forceinline__ void residual_row(const int32_t* __restrict__ col, const double* __restrict__ val,
+                                             int width, int nF, const double* __restrict__ X,
+                                             const double* __restrict__ b, float* __restrict__ y, int i, double& rr,
+                                             double& bb) {
+  double acc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = b[(int64_t)i * D + k];
+  // the index and value loads of 4 entries go out together, then their X gathers
+  int q = 0;
+  for (; q + 4 <= width; q += 4) {
+    int j[4];
+    double a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      j[u] = __ldg(col + (int64_t)(q + u) * nF + i);
+      a[u] = __ldg(val + (int64_t)(q + u) * nF + i);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = fma(-a[u], __ldg(X + (int64_t)j[u] * D + k), acc[k]);
+  }
+  for (; q < width; ++q) {
+    const int j = __ldg(col + (int64_t)q * nF + i);
+    const double a = __ldg(val + (int64_t)q * nF + i);
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = fma(-a, __ldg(X + (int64_t)j * D + k), acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    y[(int64_t)i * D + k] = (float)acc[k];
+    rr += acc[k] * acc[k];
+    const double bk = b[(int64_t)i * D + k];
+    bb += bk * bk;
+  }
+}
+
+template <int D>
 __global__ void __launch_bounds__(kVertexBlock) k_residual(const int32_t* __restrict__ col, const double* __restrict__ val,
                                                             int width, int nF, const double* __restrict__ X,
                                                             const double* __restrict__ b, float* __restrict__ y,
                                                             double* __restrict__ partials) {
   const int i = blockIdx.x * kVertexBlock + threadIdx.x;
   double rr = 0.0, bb = 0.0;
-  if (i < nF) {
-    double acc[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) acc[k] = b[(int64_t)i * D + k];
-    // the index and value loads of 4 entries go out together, then their X gathers
-    int q = 0;
-    for (; q + 4 <= width; q += 4) {
-      int j[4];
-      double a[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        j[u] = __ldg(col + (int64_t)(q + u) * nF + i);
-        a[u] = __ldg(val + (int64_t)(q + u) * nF + i);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc[k] = fma(-a[u], __ldg(X + (int64_t)j[u] * D + k), acc[k]);
-    }
-    for (; q < width; ++q) {
-      const int j = __ldg(col + (int64_t)q * nF + i);
-      const double a = __ldg(val + (int64_t)q * nF + i);
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc[k] = fma(-a, __ldg(X + (int64_t)j * D + k), acc[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      y[(int64_t)i * D + k] = (float)acc[k];
-      rr += acc[k] * acc[k];
-      const double bk = b[(int64_t)i * D + k];
-      bb += bk * bk;
-    }
-  }
+  if (i < nF) residual_row<D>(col, val, width, nF, X, b, y, i, rr, bb);
   if (partials) {
     __shared__ double red[2][kVertexBlock / 32];
 #pragma unroll
@@ -1514,8 +1520,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2) k_solve_pipe(DynView V) {
 
 // restores the ready queues, pending counts and completion counts of both passes
 // and zeroes z and x (both are accumulated with atomics)
-__global__ void k_dyn_reset(DynPass F, DynPass B, int n_nodes, float* __restrict__ z, float* __restrict__ x,
-                            int64_t nzx, int64_t n_all) {
+__device__ __forceinline__ void dyn_reset_body(const DynPass& F, const DynPass& B, int n_nodes, float* __restrict__ z,
+                                               float* __restrict__ x, int64_t nzx, int64_t n_all) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_all; i += stride) {
     if (i < nzx) {
@@ -1535,6 +1541,28 @@ __global__ void k_dyn_reset(DynPass F, DynPass B, int n_nodes, float* __restrict
       B.ctr[1] = B.n_init;
     }
   }
+}
+
+__global__ void k_dyn_reset(DynPass F, DynPass B, int n_nodes, float* __restrict__ z, float* __restrict__ x,
+                            int64_t nzx, int64_t n_all) {
+  dyn_reset_body(F, B, n_nodes, z, x, nzx, n_all);
+}
+
+// the residual of a refinement sweep and the reset of the two passes that follow
+// it in one launch (the residual writes y only; the reset touches z, x and the
+// schedules' counters, which the previous passes no longer use)
+template <int D>
+__global__ void __launch_bounds__(kVertexBlock) k_residual_reset(const int32_t* __restrict__ col,
+                                                                 const double* __restrict__ val, int width, int nF,
+                                                                 const double* __restrict__ X,
+                                                                 const double* __restrict__ b, float* __restrict__ y,
+                                                                 DynPass F, DynPass B, int n_nodes,
+                                                                 float* __restrict__ z, float* __restrict__ x,
+                                                                 int64_t nzx, int64_t n_all) {
+  const int i = blockIdx.x * kVertexBlock + threadIdx.x;
+  double rr = 0.0, bb = 0.0;
+  if (i < nF) residual_row<D>(col, val, width, nF, X, b, y, i, rr, bb);
+  dyn_reset_body(F, B, n_nodes, z, x, nzx, n_all);
 }
 
 template <int D>
@@ -1726,12 +1754,25 @@ void launch_axpy_correction(const SolveData& S, cudaStream_t s) {
 
 void launch_levels(const SolveData& S, int l0, int l1, bool forward, cudaStream_t s);
 
-void launch_supernodal_solve(const SolveData& S, cudaStream_t s) {
+void launch_residual_reset(const SolveData& S, cudaStream_t s) {
+  const int64_t nzx = (int64_t)S.nF * S.d;
+  const int64_t n_all = std::max<int64_t>(std::max<int64_t>(nzx, S.n_nodes),
+                                          std::max<int64_t>(S.fdyn.n_tasks, S.bdyn.n_tasks));
+  const int g = blocks_for(S.nF, kVertexBlock);
+  if (S.d == 2)
+    k_residual_reset<2><<<g, kVertexBlock, 0, s>>>(S.ell_col, S.ell_val, S.ell_width, S.nF, S.X, S.b, S.y, S.fdyn,
+                                                   S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
+  else
+    k_residual_reset<3><<<g, kVertexBlock, 0, s>>>(S.ell_col, S.ell_val, S.ell_width, S.nF, S.X, S.b, S.y, S.fdyn,
+                                                   S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
+}
+
+void launch_supernodal_solve(const SolveData& S, cudaStream_t s, bool reset) {
   const int64_t nzx = (int64_t)S.nF * S.d;
   const int64_t n_all = std::max<int64_t>(std::max<int64_t>(nzx, S.n_nodes),
                                           std::max<int64_t>(S.fdyn.n_tasks, S.bdyn.n_tasks));
   const int reset_grid = (int)std::min<int64_t>((n_all + 255) / 256, 4096);
-  k_dyn_reset<<<reset_grid, 256, 0, s>>>(S.fdyn, S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
+  if (reset) k_dyn_reset<<<reset_grid, 256, 0, s>>>(S.fdyn, S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
   if (S.ev[0]) cudaEventRecord(S.ev[0], s);
   const int L = (int)S.fwd_off.size() - 1;
   if (S.schedule == 1 || S.schedule == 2) {
