@@ -91,14 +91,15 @@ SOLVE_PROFILE = os.path.join(ROOT, "profiles", "k_solve_dynamic_cube48.md")
 
 
 def solve_fingerprint() -> str:
-    """sha256 of the device code of the supernodal solves (the kernels the ncu
-    traffic figure was taken on), of the task-shape constants and of the code
+    """sha256 of the device code of the supernodal solves (the task code and the
+    per-level, dynamic and pipelined kernels the ncu traffic figure was taken on,
+    up to the reset of their queues), of the task-shape constants and of the code
     that builds the task lists."""
     csrc = os.path.join(ROOT, "paper_2107_05200_gb300", "csrc")
     with open(os.path.join(csrc, "ffa_solve.cu")) as f:
         src = f.read()
     a = src.index("// supernodal solves.")
-    b = src.index("}  // namespace\n", a)
+    b = src.index("// restores the ready queues", a)
     with open(os.path.join(csrc, "ffa_schedule.h")) as f:
         consts = "".join(line for line in f if line.startswith("constexpr"))
     with open(os.path.join(csrc, "ffa_schedule.cpp")) as f:
