@@ -287,7 +287,7 @@ class BatchSolver:
     """Many independent meshes solved together (one graph launch for all of them)."""
 
     def __init__(self, workloads, precision: str = "fp32", check_every: int = 10, refine_sweeps: int = 2,
-                 leaf_size: int = 64, eps_abs=None, eps_rel=None, stream=None):
+                 leaf_size: int = 64, eps_abs=None, eps_rel=None, factor: str = "host", stream=None):
         self._lib = N.load()
         self._b = None
         k = len(workloads)
@@ -321,6 +321,9 @@ class BatchSolver:
         prm.nd_leaf_size = int(leaf_size)
         prm.eps_abs = float(workloads[0].eps_abs if eps_abs is None else eps_abs)
         prm.eps_rel = float(workloads[0].eps_rel if eps_rel is None else eps_rel)
+        if factor not in FACTORS:
+            raise ValueError("factor must be one of " + ", ".join(FACTORS))
+        prm.factor_device = FACTORS[factor]
         self._keep += [npin, energies, rho]
         b = C.c_void_p()
         st = self._lib.ffa_batch_create(k, meshes, pin_ptrs, C.c_void_p(npin.ctypes.data), pos_ptrs,

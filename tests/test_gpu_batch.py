@@ -50,6 +50,28 @@ def test_batch_matches_single_mesh_solves(precision, tol):
         assert stats[j]["n_flipped"] == st["n_flipped"]
 
 
+@pytest.mark.parametrize("factor", ["device", "device64"])
+def test_batch_with_the_device_decomposition_matches_single_mesh_solves(factor):
+    """Each group's block-diagonal L_FF decomposed on the device (float or double):
+    FP64 local step, every mesh within 1e-9 of its own solve with the host's
+    decomposition."""
+    _need_gpu()
+    from paper_2107_05200_gb300.solver import BatchSolver, Solver
+    wls = _batch_workloads()
+    K = 20
+    with BatchSolver(wls, precision="fp64", check_every=10, factor=factor) as bs:
+        bs.init([wl.W0 for wl in wls])
+        bs.iterate(K, stop_at_tol=False)
+        Wb = [bs.W(j) for j in range(len(wls))]
+    for j, wl in enumerate(wls):
+        with Solver.from_workload(wl, precision="fp64", check_every=10) as sol:
+            sol.init(wl.W0)
+            sol.iterate(K, stop_at_tol=False)
+            W = sol.W()
+        err = np.abs(Wb[j] - W).max() / np.abs(W).max()
+        assert err < 1e-9, (factor, j, err)
+
+
 def test_batch_matches_the_oracle_and_stops_when_all_meshes_converged():
     _need_gpu()
     from paper_2107_05200_gb300.solver import BatchSolver
