@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--factors", nargs="*", default=["host", "device", "device64"],
                     choices=["host", "device", "device64"],
                     help="decompose: the placements of the decomposition to time")
+    ap.add_argument("--top-inverse", type=int, default=0,
+                    help="cube_deform: the top levels of the elimination tree solved as x_T = S^-1 t_T between "
+                         "the passes (0 off, -1 automatic, k > 0 the top k levels)")
     ap.add_argument("--penalties", default="fixed", choices=["fixed", "paper"],
                     help="uv_disk / uv_heightfield / cube_outcome: mu = rho w fixed, or the paper's rescaling schedule")
     return ap.parse_args()
@@ -247,12 +250,15 @@ def oracle_baseline(m_full: int, n_full: int, sample_cells: int, seconds: float,
 
 def bench_config(args, m, n, rho, world):
     """The workload description both arms print (the GPU arm and the oracle arm)."""
-    return {"workload": f"cube_deform_{args.cells}", "tets": m, "vertices": n,
-            "energy": "sym_dirichlet", "rho": rho, "local_precision": args.precision,
-            "refine_sweeps": args.sweeps, "check_every": args.check_every,
-            "solve_schedule": {0: "per_level", 1: "dynamic", 2: "pipelined"}[args.schedule],
-            "l2": "working set > L2 (factor + element state), no flush",
-            "parallelism": "replicas" if world > 1 else "single"}
+    cfg = {"workload": f"cube_deform_{args.cells}", "tets": m, "vertices": n,
+           "energy": "sym_dirichlet", "rho": rho, "local_precision": args.precision,
+           "refine_sweeps": args.sweeps, "check_every": args.check_every,
+           "solve_schedule": {0: "per_level", 1: "dynamic", 2: "pipelined"}[args.schedule],
+           "l2": "working set > L2 (factor + element state), no flush",
+           "parallelism": "replicas" if world > 1 else "single"}
+    if getattr(args, "top_inverse", 0):
+        cfg["top_inverse_levels"] = args.top_inverse
+    return cfg
 
 
 def run_reference(args, rank):
@@ -668,7 +674,8 @@ def main():
     stream = torch.cuda.current_stream()
     wl = wk.cube_deform(cells=args.cells)
     sol = Solver.from_workload(wl, precision=args.precision, refine_sweeps=args.sweeps, factor=args.factor,
-                               check_every=args.check_every, schedule=args.schedule, stream=stream.cuda_stream)
+                               check_every=args.check_every, schedule=args.schedule, stream=stream.cuda_stream,
+                               top_inverse_levels=args.top_inverse)
     info = sol.info()
     W0 = torch.tensor(wl.W0, dtype=torch.float64, device="cuda")
     sol.init(W0)
@@ -703,7 +710,8 @@ def main():
     # dominant kernel: the triangular passes of the W step (forward + backward per sweep)
     ms_pass = 0.5 * (ph["ms_solve_forward"] + ph["ms_solve_backward"])
     solve_gbs = info["bytes_solve_pass"] / (ms_pass / 1e3) / 1e9
-    traffic = profiled_solve_traffic() if args.cells == 64 and args.precision == "fp32" else None
+    traffic = (profiled_solve_traffic() if args.cells == 64 and args.precision == "fp32" and
+               info["top_inverse_levels"] == 0 else None)
     resid = sol.wstep_residual()
 
     # end to end through the public API with host buffers: init from pinned host W0,
@@ -740,6 +748,12 @@ def main():
             "k_local_step": {"ms": ph["ms_local"], "gbs": local_gbs, "frac": local_gbs / hbm_peak,
                              "bytes": info["bytes_local_step"]},
         },
+        "top_inverse": None if info["top_inverse_levels"] == 0 else {
+            "levels": info["top_inverse_levels"], "cols": info["top_inverse_cols"],
+            "ms": ph["ms_top_product"], "bytes": info["bytes_top_product"],
+            "gbs": info["bytes_top_product"] / ph["ms_top_product"] / 1e6,
+            "frac": info["bytes_top_product"] / ph["ms_top_product"] / 1e6 / hbm_peak,
+            "setup_s": info["setup_seconds_top_inverse"]},
         "phases_ms": {k: v for k, v in ph.items() if k != "reps"},
         "wstep": {"achieved_gbs": wstep_gbs, "frac": wstep_gbs / hbm_peak,
                   "factor_entries": info["factor_entries"], "rel_residual": resid},

@@ -135,6 +135,17 @@ typedef struct {
                               front and every inv(L_ss) at once (sum over supernodes of (n_s + m_s)^2 +
                               n_s^2 elements), kept for the context's life with penalty_schedule 1 and
                               released after setup otherwise. */
+  int32_t top_inverse_levels; /* the top levels of the elimination tree in the W step's solve (Sec. 4,
+                              "Efficient Evaluation"): with T the columns of the supernodes on the top k
+                              levels and S = L_TT L_TT^T the Schur complement of the rest, a solve runs the
+                              forward pass below T, x_T = S^-1 t_T (t_T: the forward pass's right-hand
+                              side at T) as one symmetric matrix-vector product, and the backward pass below
+                              T.  S^-1 (float, lower 64 x 64 tiles) is computed on the device from the
+                              factor blocks after every decomposition.  0 (default): off; -1: the
+                              largest k whose S^-1 takes no more bytes than the factor blocks of those
+                              levels (at most 16 supernodes and 16384 columns); k > 0: exactly the top k
+                              levels (FFA_ERR_INVALID_ARG if that leaves no level below or exceeds those
+                              limits).  Single-mesh contexts only (batched contexts use 0). */
 } ffa_params;
 
 typedef struct {
@@ -165,6 +176,11 @@ typedef struct {
   int32_t kernels_per_iteration; /* kernel launches of one iteration without the test */
   int32_t kernels_per_check;     /* extra launches of an iteration that runs the test */
   double seconds_refactor;       /* host time spent decomposing L again (penalty_schedule 1) */
+  int32_t top_inverse_levels;    /* levels solved by S^-1 (top_inverse_levels), 0 if none */
+  int32_t top_inverse_cols;      /* columns of those levels (the order of S) */
+  int64_t bytes_top_product;     /* algorithmic bytes of one x_T = S^-1 t_T: the tiles of S^-1 and
+                                    the two vectors */
+  double setup_seconds_top_inverse; /* time of the last computation of S^-1 (device) */
 } ffa_info;
 
 typedef struct {
@@ -177,6 +193,7 @@ typedef struct {
   double ms_iteration; /* whole iteration, launched one kernel at a time */
   double ms_solve_forward;   /* one forward triangular pass of the W step (last sweep) */
   double ms_solve_backward;  /* one backward triangular pass of the W step (last sweep) */
+  double ms_top_product;     /* x_T = S^-1 t_T between the passes (last sweep; 0 without it) */
 } ffa_phase_times;
 
 /* Initial map (the paper has no GPU counterpart; App. A, "Tutte's Energy"): the
@@ -204,7 +221,8 @@ ffa_status ffa_tutte(const ffa_mesh* mesh, const int32_t* boundary, int32_t n_bo
 /* Fill *p with the defaults: symmetric Dirichlet, rho 1, eps_abs 1e-6, eps_rel 1e-5,
  * check_every 10, require_flip_free 1, FP32 local step, 2 refine sweeps,
  * leaf size 64, all host threads, solve schedule 1, fixed penalties (penalty
- * schedule 0), rescale_rho 5, the paper's local step, prox_h 0. */
+ * schedule 0), rescale_rho 5, the paper's local step, prox_h 0, factor_device 0,
+ * top_inverse_levels 0. */
 ffa_status ffa_default_params(ffa_params* p);
 
 /* Prepare a solver for one mesh: element gradients and measures w_i (Supplemental,

@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("host_threads", C.c_int32), ("solve_schedule", C.c_int32),
                 ("penalty_schedule", C.c_int32), ("rescale_rho", C.c_double),
                 ("local_variant", C.c_int32), ("solve_subtree_height", C.c_int32 * 2),
-                ("prox_h", C.c_int32), ("factor_device", C.c_int32)]
+                ("prox_h", C.c_int32), ("factor_device", C.c_int32), ("top_inverse_levels", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -64,7 +64,9 @@ class Info(C.Structure):
                 ("device_bytes", C.c_int64), ("bytes_local_step", C.c_int64),
                 ("bytes_global_sweep", C.c_int64), ("bytes_solve_pass", C.c_int64),
                 ("kernels_per_iteration", C.c_int32),
-                ("kernels_per_check", C.c_int32), ("seconds_refactor", C.c_double)]
+                ("kernels_per_check", C.c_int32), ("seconds_refactor", C.c_double),
+                ("top_inverse_levels", C.c_int32), ("top_inverse_cols", C.c_int32),
+                ("bytes_top_product", C.c_int64), ("setup_seconds_top_inverse", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,7 +90,7 @@ class PhaseTimes(C.Structure):
     _fields_ = [("reps", C.c_int32), ("ms_gather", C.c_double), ("ms_wstep", C.c_double),
                 ("ms_vertex", C.c_double), ("ms_local", C.c_double), ("ms_check", C.c_double),
                 ("ms_iteration", C.c_double), ("ms_solve_forward", C.c_double),
-                ("ms_solve_backward", C.c_double)]
+                ("ms_solve_backward", C.c_double), ("ms_top_product", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -17,9 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libffadmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["ffa_api.cu", "ffa_local.cu", "ffa_solve.cu", "ffa_adjoint.cu", "ffa_noalloc.cu", "ffa_devfactor.cu"]
+CU_SOURCES = ["ffa_api.cu", "ffa_local.cu", "ffa_solve.cu", "ffa_adjoint.cu", "ffa_noalloc.cu", "ffa_devfactor.cu",
+              "ffa_topinv.cu"]
 CXX_SOURCES = ["ffa_factor.cpp", "ffa_schedule.cpp", "ffa_state.cpp", "ffa_constraint_host.cpp",
-               "ffa_operator_host.cpp", "ffa_devfactor_plan.cpp"]
+               "ffa_operator_host.cpp", "ffa_devfactor_plan.cpp", "ffa_topinv_plan.cpp"]
 # The per-element kernels' float divisions and square roots (Newton steps of the
 # prox roots, Jacobi rotation parameters, normalizations) take the hardware's
 # approximate forms: each is followed by iterations or renormalizations that

@@ -16,6 +16,7 @@
 #include "ffa_internal.h"
 #include "ffa_constraint_host.h"
 #include "ffa_devfactor_launch.h"
+#include "ffa_topinv.h"
 #include "ffa_operator_host.h"
 #include "ffa_state.h"
 
@@ -123,7 +124,7 @@ struct ffa_ctx {
   int bottom_used = 0;          // min(bottom_levels, levels) of the current task lists
   int subtree_height_f = 2;     // dynamic schedule: bottom subtrees up to this height run as one task
   int subtree_height_b = 1;     // (forward / backward pass; measured best on the benchmark cube)
-  cudaEvent_t solve_ev[3] = {nullptr, nullptr, nullptr};  // set only while ffa_profile_phases runs
+  cudaEvent_t solve_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // set only while ffa_profile_phases runs
   int32_t* err_flag = nullptr;
   long long spin_limit = kDefaultSpinLimit;  // ffa_set_wait_limit
   int grid_f = 0, grid_b = 0;
@@ -136,6 +137,11 @@ struct ffa_ctx {
   DevFactorDev df;
   std::vector<DfLaunch> df_prog;
   DevAssemblyDev da;
+  // the top levels of the tree as one operator, x_T = S^-1 t_T (top_inverse_levels)
+  TopInvPlan ti_plan;
+  TopInvSetup ti_setup;
+  TopInvDev ti;
+  float* ti_tiles = nullptr;
 
   // batched meshes (set for contexts made by ffa_batch_create)
   int n_mesh = 0;
@@ -331,6 +337,66 @@ ffa_status devfactor_run(ffa_ctx* ctx) {
   return FFA_OK;
 }
 
+// The top levels of the elimination tree as one operator (top_inverse_levels):
+// which levels, their column numbering, and the device buffers of S^-1 and of
+// its product.  Batched contexts (block-diagonal operators) do not use it.
+ffa_status topinv_setup(ffa_ctx* ctx, const Factor& fac, bool batch) {
+  std::string msg;
+  if (!plan_top_inverse(fac, batch ? 0 : ctx->prm.top_inverse_levels, ctx->ti_plan, msg))
+    return fail(ctx, FFA_ERR_INVALID_ARG, msg);
+  const TopInvPlan& P = ctx->ti_plan;
+  if (P.levels == 0) return FFA_OK;
+  ffa_status st;
+  TopInvSetup& U = ctx->ti_setup;
+  U = TopInvSetup{};
+  U.nT = P.nT;
+  U.ldG = P.ldG;
+  U.tiles = P.tiles;
+  U.pos = P.pos;
+  U.lo = P.lo;
+  U.rmap_off = P.rmap_off;
+  TopInvDev& T = ctx->ti;
+  T = TopInvDev{};
+  T.nT = P.nT;
+  T.tiles_n = P.tiles;
+  T.nblk = P.nblk;
+  T.n_nodes = (int32_t)P.nodes.size();
+  for (size_t q = 0; q < P.nodes.size(); ++q) {
+    const Supernode& sn = fac.nodes[P.nodes[q]];
+    U.ncol.push_back(sn.ncol);
+    U.ld.push_back(sn.ld);
+    U.nrow.push_back(sn.nrow);
+    U.blk_off.push_back(sn.blk_off);
+    T.pos[q] = P.pos[q];
+    T.col0[q] = sn.col0;
+    T.n[q] = sn.ncol;
+  }
+  int32_t* rmap = nullptr;
+  if ((st = upload(ctx, &rmap, P.rmap)) != FFA_OK) return st;
+  U.rmap = rmap;
+  if ((st = dalloc(ctx, &ctx->ti_tiles, (size_t)(P.tile_bytes / 4))) != FFA_OK) return st;
+  T.tiles = ctx->ti_tiles;
+  {
+    const std::vector<int32_t> units = top_product_units(P.tiles);
+    int32_t* ud = nullptr;
+    if ((st = upload(ctx, &ud, units)) != FFA_OK) return st;
+    T.units = reinterpret_cast<const int2*>(ud);
+    T.n_units = (int32_t)(units.size() / 2);
+  }
+  FFA_CUDA(prepare_top_product());
+  FFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  return FFA_OK;
+}
+
+// S^-1 from the current factor blocks (after every decomposition of L)
+ffa_status topinv_compute(ffa_ctx* ctx) {
+  if (ctx->ti_plan.levels == 0) return FFA_OK;
+  const double t0 = now_s();
+  FFA_CUDA(compute_top_inverse(ctx->ti_setup, ctx->blocks, ctx->ti_tiles, ctx->stream));
+  ctx->info.setup_seconds_top_inverse = now_s() - t0;
+  return FFA_OK;
+}
+
 LocalLaunch local_launch(ffa_ctx* ctx, bool check, const void* vrec) {
   LocalLaunch L;
   L.d = ctx->d;
@@ -364,7 +430,11 @@ SolveData solve_data(ffa_ctx* ctx) {
   S.fdyn = ctx->fdyn;
   S.bdyn = ctx->bdyn;
   S.bottom_levels = ctx->bottom_used;
-  for (int i = 0; i < 3; ++i) S.ev[i] = ctx->solve_ev[i];
+  for (int i = 0; i < 4; ++i) S.ev[i] = ctx->solve_ev[i];
+  S.top_on = ctx->ti_plan.levels > 0;
+  S.top = ctx->ti;
+  S.top.err = ctx->err_flag;
+  S.top.wait_limit = ctx->spin_limit;
   S.n_nodes = (int)ctx->nodes_h.size();
   S.err_flag = ctx->err_flag;
   S.spin_limit = ctx->spin_limit;
@@ -558,6 +628,7 @@ ffa_status validate_params(const ffa_params& p, std::string& msg) {
     msg = "prox_h 1 is implemented with fixed penalties (its bound depends on mu_i)";
   else if (p.prox_h == 1 && p.local_variant == 1) msg = "the joint (U, P) variant has no proximal U term";
   else if (p.factor_device < 0 || p.factor_device > 2) msg = "factor_device must be 0, 1 or 2";
+  else if (p.top_inverse_levels < -1 || p.top_inverse_levels > 32) msg = "top_inverse_levels must be in [-1, 32]";
   else return FFA_OK;
   return FFA_ERR_INVALID_ARG;
 }
@@ -575,6 +646,7 @@ int kernels_per_iteration(const ffa_ctx* ctx) {
     for (size_t l = 0; l + 1 < ctx->fwd_off.size(); ++l)
       solve += (ctx->fwd_off[l + 1] > ctx->fwd_off[l]) + (ctx->bwd_off[l + 1] > ctx->bwd_off[l]);
   }
+  if (ctx->ti_plan.levels > 0) solve += 1;   // the top product between the passes
   const int sweeps = ctx->prm.refine_sweeps;
   return 1 + sweeps * (1 + solve) + (sweeps - 1) + 1 + 1 + (ctx->n_con > 0 ? 3 : 0);
 }
@@ -620,6 +692,7 @@ ffa_status build_tasks(ffa_ctx* ctx) {
   opt.bottom_levels = ctx->bottom_levels;
   opt.subtree_height_f = ctx->subtree_height_f;
   opt.subtree_height_b = ctx->subtree_height_b;
+  opt.top_levels = ctx->ti_plan.levels;
   Schedule sch;
   build_schedule(ctx->nodes_h, ctx->n_levels, opt, sch);
   ctx->grid_f = persistent_grid(ctx->d, true);
@@ -831,6 +904,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
 
   ctx->nodes_h = fac.nodes;
   ctx->n_levels = fac.n_levels;
+  if ((st = topinv_setup(ctx, fac, batch != nullptr)) != FFA_OK) return st;
   // ---- device uploads
   if ((st = upload(ctx, &ctx->rows, fac.rows)) != FFA_OK) return st;
   if (ctx->prm.factor_device == 0) {
@@ -871,6 +945,7 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
       ctx->df.F = ctx->df.Lv = nullptr;
     }
   }
+  if ((st = topinv_compute(ctx)) != FFA_OK) return st;
   // element arrays: indices (d+1) x m, gradients d*d x m, w, mu
   {
     std::vector<int32_t> idx((size_t)(d + 1) * m);
@@ -974,13 +1049,21 @@ ffa_status create_impl(ffa_ctx* ctx, const ffa_mesh* mesh, const int32_t* pin_id
   ctx->info.bytes_local_step =
       (int64_t)m * ((d + 1) * 4 + (int64_t)(d * d + 2) * R + (ps + d * d) * R * 2 + us * R + (int64_t)(d + 1) * d * R) +
       (int64_t)n * d * 16 + (ctx->e.hmu ? (int64_t)m * (us + 1) * R : 0);   // prox_h: U^{k-1} and h/mu read
-  int64_t nz = 0;
-  for (const Supernode& sn : fac.nodes) nz += (int64_t)sn.ncol * sn.nrow + (int64_t)sn.ncol * (sn.ncol + 1) / 2;
-  int64_t nstruct = 0;
-  for (const Supernode& sn : fac.nodes) nstruct += sn.nrow;
-  // (forward and backward each read every nonzero of every B_s once)
-  ctx->info.bytes_global_sweep = 2 * nz * 4 + (int64_t)width * nF * 12 + (int64_t)nF * d * (8 * 3 + 4 * 6);
+  // the passes read every nonzero of every B_s below the top levels once (and
+  // its structure indices); the top product reads the tiles of S^-1 once
+  const int top_min = ctx->ti_plan.levels > 0 ? fac.n_levels - ctx->ti_plan.levels : INT32_MAX;
+  int64_t nz = 0, nstruct = 0;
+  for (const Supernode& sn : fac.nodes) {
+    if (sn.level >= top_min) continue;
+    nz += (int64_t)sn.ncol * sn.nrow + (int64_t)sn.ncol * (sn.ncol + 1) / 2;
+    nstruct += sn.nrow;
+  }
+  const int64_t top_bytes = ctx->ti_plan.levels > 0 ? ctx->ti_plan.tile_bytes + (int64_t)2 * ctx->ti_plan.nT * d * 4 : 0;
+  ctx->info.bytes_global_sweep = 2 * nz * 4 + top_bytes + (int64_t)width * nF * 12 + (int64_t)nF * d * (8 * 3 + 4 * 6);
   ctx->info.bytes_solve_pass = nz * 4 + nstruct * 4 + (int64_t)2 * nF * d * 4;
+  ctx->info.top_inverse_levels = ctx->ti_plan.levels;
+  ctx->info.top_inverse_cols = ctx->ti_plan.nT;
+  ctx->info.bytes_top_product = top_bytes;
   ctx->info.n = n;
   ctx->info.m = m;
   ctx->info.d = d;
@@ -1018,6 +1101,7 @@ ffa_status apply_penalties(ffa_ctx* ctx) {
     FFA_CUDA(cudaGetLastError());
     ffa_status st = devfactor_run(ctx);
     if (st != FFA_OK) return st;
+    if ((st = topinv_compute(ctx)) != FFA_OK) return st;
     launch_rhs_terms(local_launch(ctx, false, ctx->vrec), s);
     FFA_CUDA(cudaGetLastError());
     FFA_CUDA(cudaStreamSynchronize(s));
@@ -1050,6 +1134,10 @@ ffa_status apply_penalties(ffa_ctx* ctx) {
                            cudaMemcpyHostToDevice, s));
   FFA_CUDA(cudaStreamSynchronize(s));
   std::vector<float>().swap(H.fac.blocks);
+  {
+    const ffa_status st = topinv_compute(ctx);
+    if (st != FFA_OK) return st;
+  }
   OperatorArrays OA;
   operator_arrays(H.fac, H.nF, H.n_pin, Ap, Ai, Ax, Cp, Ci, Cx, OA);
   FFA_CUDA(cudaMemcpyAsync(ctx->ell_val, OA.ell_val.data(), OA.ell_val.size() * sizeof(double), cudaMemcpyHostToDevice,
@@ -1504,6 +1592,7 @@ ffa_status ffa_default_params(ffa_params* p) {
   p->solve_subtree_height[0] = p->solve_subtree_height[1] = -1;
   p->prox_h = 0;
   p->factor_device = 0;
+  p->top_inverse_levels = 0;
   return FFA_OK;
 }
 
@@ -1981,17 +2070,24 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out) 
   for (auto& e : ev) FFA_CUDA(cudaEventCreate(&e));
   for (auto& e : ctx->solve_ev) FFA_CUDA(cudaEventCreate(&e));
   double acc[PH_N + 1] = {0};
-  double acc_f = 0.0, acc_b = 0.0;
+  double acc_f = 0.0, acc_b = 0.0, acc_t = 0.0;
+  const bool top = ctx->ti_plan.levels > 0;
   for (int r = 0; r < reps; ++r) {
     FFA_CUDA(cudaEventRecord(ev[PH_N], ctx->stream));
     enqueue_iteration(ctx, r == reps - 1, ev);
     FFA_CUDA(cudaGetLastError());
     FFA_CUDA(cudaEventSynchronize(ev[PH_CHECK]));
-    float tf, tb;
+    float tf, tb, tt = 0.f;
     FFA_CUDA(cudaEventElapsedTime(&tf, ctx->solve_ev[0], ctx->solve_ev[1]));
-    FFA_CUDA(cudaEventElapsedTime(&tb, ctx->solve_ev[1], ctx->solve_ev[2]));
+    if (top) {
+      FFA_CUDA(cudaEventElapsedTime(&tt, ctx->solve_ev[1], ctx->solve_ev[3]));
+      FFA_CUDA(cudaEventElapsedTime(&tb, ctx->solve_ev[3], ctx->solve_ev[2]));
+    } else {
+      FFA_CUDA(cudaEventElapsedTime(&tb, ctx->solve_ev[1], ctx->solve_ev[2]));
+    }
     acc_f += tf;
     acc_b += tb;
+    acc_t += tt;
     float t[PH_N];
     FFA_CUDA(cudaEventElapsedTime(&t[PH_GATHER], ev[PH_N], ev[PH_GATHER]));
     for (int p = 1; p < PH_N; ++p) FFA_CUDA(cudaEventElapsedTime(&t[p], ev[p - 1], ev[p]));
@@ -2010,6 +2106,7 @@ ffa_status ffa_profile_phases(ffa_ctx* ctx, int32_t reps, ffa_phase_times* out) 
   out->reps = reps;
   out->ms_solve_forward = acc_f / reps;
   out->ms_solve_backward = acc_b / reps;
+  out->ms_top_product = acc_t / reps;
   out->ms_gather = acc[PH_GATHER] / reps;
   out->ms_wstep = acc[PH_WSTEP] / reps;
   out->ms_vertex = acc[PH_VERTEX] / reps;

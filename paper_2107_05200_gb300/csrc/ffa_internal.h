@@ -10,6 +10,7 @@
 #include "../../include/ffadmm.h"
 #include "ffa_factor.h"
 #include "ffa_schedule.h"
+#include "ffa_topinv_launch.h"
 
 namespace ffa {
 
@@ -172,7 +173,10 @@ struct SolveData {
   long long spin_limit = kDefaultSpinLimit;  // polls per wait before giving up
   int grid_f = 0, grid_b = 0;     // resident blocks of the dynamic passes (schedule 1)
   int pgrid_f = 0, pgrid_b = 0;   // resident blocks of the pipelined passes (schedule 2)
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // optional: before forward, between, after backward
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // optional: before forward, after forward,
+                                                               // after backward, after the top product
+  bool top_on = false;       // the top levels run as x_T = S^-1 t_T between the passes
+  TopInvDev top;
   float* y;                  // nF x d residual / forward work vector
   float* z;                  // nF x d forward result
   float* x;                  // nF x d correction

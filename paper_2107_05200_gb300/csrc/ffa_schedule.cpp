@@ -92,7 +92,7 @@ void build_schedule(const std::vector<Supernode>& nd, int n_levels, const Schedu
     const Supernode& sn = nd[s];
     nodes[s] = NodeDev{sn.col0, sn.ncol, sn.nrow, sn.ld, 0, 0, sn.row_off, sn.blk_off};
     const int ntot = sn.ncol + sn.nrow;
-    if (sn.ncol == 0) continue;
+    if (sn.ncol == 0 || sn.level >= nl - opt.top_levels) continue;
     if (is_node_task(sn)) {
       fl[sn.level].push_back(Task{s, 0, 0, 1, nodes[s]});
       bl[sn.level].push_back(Task{s, 0, 0, 1, nodes[s]});
@@ -138,7 +138,8 @@ void build_schedule(const std::vector<Supernode>& nd, int n_levels, const Schedu
   std::vector<int32_t> size(nn, 0);          // nodes with columns in the subtree
   for (int s = 0; s < nn; ++s) {             // postorder: children first
     const Supernode& sn = nd[s];
-    all_node_tasks[s] = all_node_tasks[s] && (sn.ncol == 0 || is_node_task(sn));
+    // a merged subtree holds no node of the top levels (they have no tasks)
+    all_node_tasks[s] = all_node_tasks[s] && (sn.ncol == 0 || is_node_task(sn)) && sn.level < nl - opt.top_levels;
     size[s] += sn.ncol > 0 ? 1 : 0;
     if (sn.parent >= 0) {
       all_node_tasks[sn.parent] = all_node_tasks[sn.parent] && all_node_tasks[s];
@@ -147,7 +148,7 @@ void build_schedule(const std::vector<Supernode>& nd, int n_levels, const Schedu
   }
   std::vector<char> keep_f(nn, 0), keep_b(nn, 0);
   for (int s = 0; s < nn; ++s) {
-    keep_f[s] = nd[s].level >= nl - opt.l2_keep_top;
+    keep_f[s] = nd[s].level >= nl - opt.top_levels - opt.l2_keep_top;
     keep_b[s] = nd[s].level < opt.l2_keep_bottom;
   }
   out.fwd.tasks = dynamic_list(nd, nodes, all_node_tasks, size, out.fwd_levels, out.fwd_off, nb, opt.subtree_height_f,
@@ -205,9 +206,14 @@ void build_schedule(const std::vector<Supernode>& nd, int n_levels, const Schedu
     B.push[(size_t)s * (1 + kPushKids)] = PushRec{k0, k1, total, ntb[s]};
     for (int j = 0; j < kPushKids && k0 + j < k1; ++j) B.push[(size_t)s * (1 + kPushKids) + 1 + j] = B.kids[k0 + j];
   }
+  // the nodes that wait on nothing (the root, or the nodes below the top levels
+  // without tasks) start tallest subtree first
+  std::vector<int32_t> roots;
   for (int s = nn - 1; s >= 0; --s)
-    if (ntb[s] > 0 && up_b[s] < 0)
-      for (int i = 0; i < ntb[s]; ++i) B.queue.push_back(t0b[s] + i);
+    if (ntb[s] > 0 && up_b[s] < 0) roots.push_back(s);
+  std::stable_sort(roots.begin(), roots.end(), [&](int a, int b) { return nd[a].level > nd[b].level; });
+  for (int s : roots)
+    for (int i = 0; i < ntb[s]; ++i) B.queue.push_back(t0b[s] + i);
   B.n_init = (int)B.queue.size();
   B.queue.resize(B.tasks.size(), -1);
 }

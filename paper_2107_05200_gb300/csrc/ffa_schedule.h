@@ -78,8 +78,10 @@ struct ScheduleOptions {
   // the backward pass reads them first (and the other way round for the bottom
   // levels and the next sweep's forward pass), so those blocks are streamed with
   // a keep-resident hint and all others with an evict-first hint
-  int l2_keep_top = 2;             // forward: the top this-many levels (0: none)
+  int l2_keep_top = 2;             // forward: the top this-many levels with tasks (0: none)
   int l2_keep_bottom = 2;          // backward: levels below this one (0: none)
+  int top_levels = 0;              // the top this-many levels have no tasks (their columns are
+                                   // solved by the top-of-tree inverse between the passes)
 };
 
 struct Schedule {

@@ -1767,6 +1767,14 @@ void launch_residual_reset(const SolveData& S, cudaStream_t s) {
                                                    S.bdyn, S.n_nodes, S.z, S.x, nzx, n_all);
 }
 
+// with the top levels as one operator: x_T = S^-1 t_T, t_T the forward pass's
+// running right-hand side at the T columns
+static void top_product(const SolveData& S, cudaStream_t s) {
+  if (!S.top_on) return;
+  launch_top_product(S.top, S.d, S.y, S.x, s);
+  if (S.ev[3]) cudaEventRecord(S.ev[3], s);
+}
+
 void launch_supernodal_solve(const SolveData& S, cudaStream_t s, bool reset) {
   const int64_t nzx = (int64_t)S.nF * S.d;
   const int64_t n_all = std::max<int64_t>(std::max<int64_t>(nzx, S.n_nodes),
@@ -1788,6 +1796,7 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s, bool reset) {
       else k_solve_dynamic<3, true><<<S.grid_f, kSolveThreads, 0, s>>>(vf);
     }
     if (S.ev[1]) cudaEventRecord(S.ev[1], s);
+    top_product(S, s);
     if (S.schedule == 2) {
       if (S.d == 2) k_solve_pipe<2, false><<<S.pgrid_b, kPipeThreads, sizeof(PipeSmem<2>), s>>>(vb);
       else k_solve_pipe<3, false><<<S.pgrid_b, kPipeThreads, sizeof(PipeSmem<3>), s>>>(vb);
@@ -1801,6 +1810,7 @@ void launch_supernodal_solve(const SolveData& S, cudaStream_t s, bool reset) {
   }
   launch_levels(S, 0, L, true, s);
   if (S.ev[1]) cudaEventRecord(S.ev[1], s);
+  top_product(S, s);
   launch_levels(S, 0, L, false, s);
   if (S.ev[2]) cudaEventRecord(S.ev[2], s);
 }

@@ -45,14 +45,18 @@ class Solver:
     paper's schedule (initial mu_i = max(mu_min,i, w_i) and per-element rescaling by
     rescale_rho/2 at the paper's events, L decomposed again after each event).
     factor: where the numeric decomposition of L runs, "host" (double), "device"
-    (float) or "device64" (double); the analysis is on the host either way."""
+    (float) or "device64" (double); the analysis is on the host either way.
+    top_inverse_levels: the top levels of the elimination tree solved as
+    x_T = S^-1 t_T between the triangular passes (0 off, -1 automatic, k > 0 exactly
+    the top k levels)."""
 
     def __init__(self, V, T, pins=None, pin_pos=None, energy: str = "sd", rho: float = 1.0,
                  eps_abs: float = 1e-6, eps_rel: float = 1e-5, check_every: int = 10,
                  precision: str = "fp32", refine_sweeps: int = 2, leaf_size: int = 64,
                  require_flip_free: bool = True, host_threads: int = 0, schedule: int = 1,
                  penalties: str = "fixed", rescale_rho: float = 5.0, local_variant: str = "paper",
-                 subtree_height=None, prox_h: bool = False, factor: str = "host", stream=None):
+                 subtree_height=None, prox_h: bool = False, factor: str = "host", top_inverse_levels: int = 0,
+                 stream=None):
         self._lib = N.load()
         self._ctx = None
         Vn = np.asarray(V) if isinstance(V, (list, tuple)) else V
@@ -87,6 +91,7 @@ class Solver:
         if factor not in FACTORS:
             raise ValueError("factor must be one of " + ", ".join(FACTORS))
         prm.factor_device = FACTORS[factor]
+        prm.top_inverse_levels = int(top_inverse_levels)
         if subtree_height is not None:   # (forward, backward) merged bottom subtree heights
             prm.solve_subtree_height[0], prm.solve_subtree_height[1] = (int(h) for h in subtree_height)
         n_pin = 0 if pins is None else int(len(pins))

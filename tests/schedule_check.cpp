@@ -186,21 +186,28 @@ int main(int argc, char** argv) {
     const int narrows[] = {32, 64};
     const int bottoms[] = {0, 2, 3};
     const int heights[][2] = {{0, 0}, {1, 1}, {2, 1}, {3, 0}, {0, 3}, {8, 8}};
+    const int tops[] = {0, 1, 3};
     for (int na : narrows)
       for (int nb : bottoms)
-        for (auto& hh : heights) {
+        for (auto& hh : heights)
+          for (int top : tops) {
           if (nb > 0 && (hh[0] | hh[1]) && !(hh[0] == 2 && hh[1] == 1)) continue;
+          if (top > 0 && !(na == 64 && (nb == 0 || nb == 2) && hh[0] == 2 && hh[1] == 1)) continue;
+          if (top >= f.n_levels) continue;
           ScheduleOptions o;
           o.narrow_cols = na;
           o.bottom_levels = nb;
           o.subtree_height_f = hh[0];
           o.subtree_height_b = hh[1];
+          o.top_levels = top;
           Schedule S;
           build_schedule(nd, f.n_levels, o, S);
           const std::string tag = "grid " + std::to_string(g.nx) + "x" + std::to_string(g.ny) + "x" +
                                   std::to_string(g.nz) + " narrow " + std::to_string(na) + " bottom " +
                                   std::to_string(nb) + " heights " + std::to_string(hh[0]) + "," +
-                                  std::to_string(hh[1]) + ": ";
+                                  std::to_string(hh[1]) + " top " + std::to_string(top) + ": ";
+          // the top levels have no tasks (their columns are solved between the passes)
+          auto in_top = [&](int s) { return nd[s].level >= f.n_levels - top; };
           // level lists: tiles cover every block once, tasks sit on their node's level
           for (int pass = 0; pass < 2; ++pass) {
             const auto& L = pass == 0 ? S.fwd_levels : S.bwd_levels;
@@ -213,8 +220,8 @@ int main(int argc, char** argv) {
                 per[L[i].node].push_back(L[i]);
               }
             for (int s = 0; s < nn; ++s) {
-              if (nd[s].ncol == 0) {
-                if (!per[s].empty()) return fail(tag + "tasks for an empty node");
+              if (nd[s].ncol == 0 || in_top(s)) {
+                if (!per[s].empty()) return fail(tag + "tasks for an empty or top node");
                 continue;
               }
               if (!covers(nd[s], per[s], pass == 0, err)) return fail(tag + (pass ? "backward " : "forward ") + err);
@@ -258,6 +265,10 @@ int main(int argc, char** argv) {
             }
             for (int s = 0; s < nn; ++s) {
               if (nd[s].ncol == 0) continue;
+              if (in_top(s)) {
+                if (seen[s] || own[s]) return fail(tag + "top node in the dynamic list");
+                continue;
+              }
               const bool dyn = nd[s].level >= S.bottom_used;
               if (seen[s] > 1 || (seen[s] && own[s])) return fail(tag + "node in the dynamic list twice");
               if (dyn != (seen[s] + (own[s] > 0) == 1)) return fail(tag + "node missing from the dynamic list");
@@ -273,6 +284,10 @@ int main(int argc, char** argv) {
                 for (int i = 1; i < P.n_init; ++i)
                   if (depth[P.tasks[P.queue[i]].node] > depth[P.tasks[P.queue[i - 1]].node])
                     return fail(tag + "forward ready queue not deepest first");
+              if (pass == 1)   // the nodes that wait on nothing start tallest first
+                for (int i = 1; i < P.n_init; ++i)
+                  if (nd[P.tasks[P.queue[i]].node].level > nd[P.tasks[P.queue[i - 1]].node].level)
+                    return fail(tag + "backward start not tallest first");
               if (pass == 1)
                 for (int s = 0; s < nn; ++s) {
                   const PushRec& r = P.push[(size_t)s * (1 + kPushKids)];
@@ -305,7 +320,7 @@ int main(int argc, char** argv) {
             }
           }
           ++checked;
-        }
+          }
   }
   std::printf("ok %d schedules\n", checked);
   return 0;
