@@ -45,6 +45,7 @@ def test_default_params_and_struct_layout():
     assert p.check_every == 10 and p.require_flip_free == 1 and p.refine_sweeps == 2
     assert p.nd_leaf_size == 64
     assert list(p.solve_subtree_height) == [-1, -1]
+    assert p.factor_device == 0 and p.top_inverse_levels == 0
     assert lib.ffa_default_params(None) == 1
     assert isinstance(lib.ffa_last_error(None), bytes)
 
@@ -74,6 +75,11 @@ def test_bad_parameters_are_rejected_before_any_device_work():
     p.solve_subtree_height[1] = 9
     assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
     assert b"solve_subtree_height" in lib.ffa_last_error(None)
+    for bad in (-2, 33):
+        lib.ffa_default_params(C.byref(p))
+        p.top_inverse_levels = bad
+        assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
+        assert b"top_inverse_levels" in lib.ffa_last_error(None)
     lib.ffa_default_params(C.byref(p))
     mesh.d = 4
     assert lib.ffa_create(C.byref(mesh), None, 0, None, C.byref(p), None, C.byref(out)) == 1
