@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(kThreads) k_ti_gram(const float* __restrict__ 
 // returns.
 // ---------------------------------------------------------------------------
 constexpr int kTiSlots = 4;
-constexpr int kTiRowTiles = 2;   // i
-constexpr int kTiColTiles = 4;   // j
+constexpr int kTiRowTiles = kTiUnitRows;   // i
+constexpr int kTiColTiles = kTiUnitCols;   // j
 
 __device__ __forceinline__ int top_column(const TopInvDev& T, int p) {
   int q = 0;
@@ -427,23 +427,6 @@ cudaError_t prepare_top_product() {
     e = cudaFuncSetAttribute(k_ti_product<3>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   return e;
-}
-
-}  // namespace ffa
-
-namespace ffa {
-
-std::vector<int32_t> top_product_units(int32_t tiles) {
-  std::vector<int32_t> u;
-  const int nrow = (tiles + kTiRowTiles - 1) / kTiRowTiles;
-  for (int a = 0; a < nrow; ++a) {
-    const int last_col = std::min(tiles - 1, kTiRowTiles * a + kTiRowTiles - 1);   // J <= I
-    for (int c = 0; c * kTiColTiles <= last_col; ++c) {
-      u.push_back(a);
-      u.push_back(c);
-    }
-  }
-  return u;
 }
 
 }  // namespace ffa

@@ -33,6 +33,8 @@ constexpr int kTiTile = 64;             // tile edge of S^-1
 constexpr int kTiBlk = 2 * kTiTile;     // the product's work unit: a block of 2 x 2 tiles
 constexpr int kTiMaxNodes = 16;         // T supernodes at most
 constexpr int kTiMaxCols = 16384;       // n_T at most (packed tiles: 512 MB)
+constexpr int kTiUnitRows = 2;          // the product's work unit: 2 rows of tiles ...
+constexpr int kTiUnitCols = 4;          // ... times 4 columns of tiles
 
 struct TopInvPlan {
   int levels = 0;                    // k (0: not used)
@@ -58,5 +60,10 @@ bool plan_top_inverse(const Factor& f, int k, TopInvPlan& P, std::string& err);
 
 // T position of each eliminated column (-1 outside T)
 std::vector<int32_t> top_positions(const Factor& f, const TopInvPlan& P);
+
+// The product's work units (a, c), flattened: unit (a, c) covers the tiles (I, J)
+// with I in [2a, 2a + 2), J in [4c, 4c + 4), J <= I < tiles; every lower tile lies
+// in exactly one unit.
+std::vector<int32_t> top_product_units(int32_t tiles);
 
 }  // namespace ffa

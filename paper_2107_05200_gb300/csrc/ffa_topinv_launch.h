@@ -37,8 +37,6 @@ cudaError_t compute_top_inverse(const TopInvSetup& U, const float* blocks, float
 
 // x at the T columns += S^-1 (y at the T columns); y and x are n x d, d = 2 or 3
 void launch_top_product(const TopInvDev& T, int d, const float* y, float* x, cudaStream_t s);
-// the product's work units for a tile count: (a, c) pairs, flattened
-std::vector<int32_t> top_product_units(int32_t tiles);
 // enables the product kernels' shared memory (above the default limit); once,
 // before any launch or graph capture
 cudaError_t prepare_top_product();

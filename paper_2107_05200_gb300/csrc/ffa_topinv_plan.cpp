@@ -68,6 +68,19 @@ std::vector<int32_t> top_positions(const Factor& f, const TopInvPlan& P) {
   return tpos;
 }
 
+std::vector<int32_t> top_product_units(int32_t tiles) {
+  std::vector<int32_t> u;
+  const int nrow = (tiles + kTiUnitRows - 1) / kTiUnitRows;
+  for (int a = 0; a < nrow; ++a) {
+    const int last_col = std::min(tiles - 1, kTiUnitRows * a + kTiUnitRows - 1);   // J <= I
+    for (int c = 0; c * kTiUnitCols <= last_col; ++c) {
+      u.push_back(a);
+      u.push_back(c);
+    }
+  }
+  return u;
+}
+
 bool plan_top_inverse(const Factor& f, int k, TopInvPlan& P, std::string& err) {
   P = TopInvPlan{};
   if (k == 0) return true;

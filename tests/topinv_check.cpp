@@ -3,7 +3,8 @@
 //   * the plan: T is the set of supernodes with columns on the top k levels, in
 //     node order with contiguous positions; lo(s) is the first position of s's T
 //     subtree; the structure rows map to their T positions; T is closed under
-//     ancestors; the automatic choice satisfies its byte rule;
+//     ancestors; the automatic choice satisfies its byte rule; the product's work
+//     units cover every lower tile of S^-1 exactly once;
 //   * the setup's arithmetic, emulated in double from the float blocks (G = I,
 //     F_s = inv(L_ss) G_s, G_r -= (L_rs inv(L_ss)) G_s, S^-1 = F^T F over the lower
 //     tiles): it equals the T block of the solution of L_FF X = [0; I] from a dense
@@ -173,7 +174,28 @@ static std::vector<double> reference(const Factor& f, const TopInvPlan& P, const
   return S;
 }
 
+// every lower tile (J <= I < tiles) lies in exactly one work unit of the product
+static bool check_units(int tiles, std::string& err) {
+  const std::vector<int32_t> u = top_product_units(tiles);
+  std::vector<int> hit((size_t)tiles * tiles, 0);
+  for (size_t q = 0; q + 1 < u.size(); q += 2)
+    for (int i = 0; i < kTiUnitRows; ++i)
+      for (int j = 0; j < kTiUnitCols; ++j) {
+        const int I = kTiUnitRows * u[q] + i, J = kTiUnitCols * u[q + 1] + j;
+        if (I < tiles && J <= I) ++hit[(size_t)I * tiles + J];
+      }
+  for (int I = 0; I < tiles; ++I)
+    for (int J = 0; J < tiles; ++J)
+      if (hit[(size_t)I * tiles + J] != (J <= I ? 1 : 0)) return err = "work units at " + std::to_string(tiles) + " tiles", false;
+  return true;
+}
+
 int main() {
+  {
+    std::string err;
+    for (int tiles : {1, 2, 3, 4, 5, 7, 8, 9, 146, 147, 256})
+      if (!check_units(tiles, err)) return fail(err);
+  }
   struct Grid { int nx, ny, nz, leaf; };
   const Grid grids[] = {{6, 6, 6, 8}, {10, 9, 8, 16}, {30, 30, 1, 16}, {5, 4, 3, 4}};
   int checked = 0;
