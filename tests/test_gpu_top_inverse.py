@@ -123,3 +123,64 @@ def test_phase_times_and_launch_count():
     assert p0["ms_top_product"] == 0.0 and p2["ms_top_product"] > 0.0
     assert i2["kernels_per_iteration"] == i0["kernels_per_iteration"] + 2   # two sweeps
     assert i2["setup_seconds_top_inverse"] > 0.0
+
+
+@pytest.mark.parametrize("factor", ["host", "device"])
+@pytest.mark.parametrize("make", [lambda: wk.uv_disk(grid=16, seed=31),
+                                  lambda: wk.cube_deform(cells=12, seed=35)])
+def test_paper_schedule_recomputes_the_inverse(make, factor):
+    """50 iterations of the paper's schedule (6 rescaling events), FP64 local
+    step: after each decomposition S^-1 is computed again from the new blocks, so
+    the trajectory, penalties and multipliers stay the oracle's."""
+    _need_gpu()
+    from oracle import schedule
+    from paper_2107_05200_gb300.solver import Solver
+    wl = make()
+    K = 50
+    o = admm.Oracle.from_workload(wl)
+    s, st_o, ne = schedule.run(o, wl.W0, K, stop_at_tol=False)
+    with Solver.from_workload(wl, precision="fp64", top_inverse_levels=0) as probe:
+        k = min(2, probe.info()["n_levels"] - 1)
+    assert k >= 1
+    with Solver.from_workload(wl, precision="fp64", penalties="paper", check_every=10, factor=factor,
+                              top_inverse_levels=k) as sol:
+        assert sol.info()["top_inverse_levels"] == k
+        sol.init(wl.W0)
+        st = sol.iterate(K, stop_at_tol=False)
+        W = sol.W()
+        mu = sol.penalties()
+        U, P, L = sol.state()
+        res = sol.wstep_residual()
+    assert st["rescales"] == ne == 6
+    np.testing.assert_allclose(mu, o.mu, rtol=1e-8)
+    assert np.abs(W - s.W).max() / np.abs(s.W).max() < 1e-8
+    assert np.abs(L - s.Lam).max() < 1e-6 * (1.0 + np.abs(s.Lam).max())
+    assert res < 1e-12, res
+
+
+def test_constraints_solve_through_the_inverse():
+    """General constraints A W = b: Z = L_FF^-1 A_F^T is formed by solves that run
+    through the top product; the FP64 trajectory matches the oracle's KKT solve and
+    every iterate is feasible."""
+    _need_gpu()
+    import scipy.sparse as sp
+    from paper_2107_05200_gb300.solver import Solver
+    wl = wk.cube_deform(cells=8, seed=47)
+    n = wl.V.shape[0]
+    pinned = set(int(p) for p in wl.pins)
+    free = [v for v in range(n) if v not in pinned]
+    rows = np.zeros((2, n))
+    rows[0][free[:6]] = 1.0 / 6
+    rows[1][free[10]], rows[1][free[-10]] = 1.0, -1.0
+    A = sp.csr_matrix(rows)
+    b = A @ wl.W0
+    K = 20
+    o = admm.Oracle.from_workload(wl, constraints=(A, b))
+    s, _ = o.run(wl.W0, K, stop_at_tol=False)
+    with Solver.from_workload(wl, precision="fp64", check_every=10, top_inverse_levels=2) as sol:
+        sol.set_constraints(A, b)
+        sol.init(wl.W0)
+        sol.iterate(K, stop_at_tol=False)
+        W = sol.W()
+    np.testing.assert_allclose(A @ W, b, rtol=0, atol=1e-11)
+    assert np.abs(W - s.W).max() / np.abs(s.W).max() < 1e-8
