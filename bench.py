@@ -3,7 +3,7 @@
 
 Workload: 3D deformation of a jittered unit cube, 64^3 cells x 6 tetrahedra
 (1,572,864 tets, 274,625 vertices), bottom face fixed, top face rotated 45
-degrees and shifted, symmetric Dirichlet energy, mu_i = 3 w_i, FP32 local step
+degrees and shifted, symmetric Dirichlet energy, mu_i = 10 w_i, FP32 local step
 with the W step and reductions in double.  One step = one ADMM iteration
 (W step, U/P/Lambda steps, error terms; the termination test every
 check_every iterations).  The per-iteration working set (factor blocks and
@@ -464,7 +464,7 @@ def run_handles(args, local):
 
 def run_outcome(args, local):
     """The benchmark cube run to its configured 1000 iterations in both precisions
-    (fixed mu = 3 w, or the paper's penalty schedule with --penalties paper): the statistics of eq. primaldualerror / primaldualthresholds every
+    (fixed mu = 10 w, or the paper's penalty schedule with --penalties paper): the statistics of eq. primaldualerror / primaldualthresholds every
     100 iterations, flipped elements and energy at the end, the FP32 iterate's
     difference from the FP64 one, and the wall time of each run (setup excluded)."""
     import numpy as np

@@ -48,9 +48,9 @@ def _disk_rows():
     centroid of four, a link W_a - W_b = 0, and W_f - W_p = t tying an interior
     vertex to a pinned one (its pinned part moves to the right-hand side).  The
     start is the scaled square with the pins on the circle (36 flipped triangles,
-    |det J| >= 1.4): the disk workload's own start holds triangles degenerate to
-    rounding (|det J| ~ 1e-16), whose orientation each side decides by its own
-    rounding."""
+    |det J| >= 1.4), so every element is far from the flip threshold; the start was
+    chosen at a time when the disk generator could still leave one triangle
+    degenerate to rounding, which it no longer does."""
     wl = wk.uv_disk(grid=12, seed=61, rho=3.0)
     n = wl.V.shape[0]
     W0 = 1.4 * (wl.V - 0.5)

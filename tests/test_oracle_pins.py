@@ -305,6 +305,67 @@ def test_polar_init(d):
         np.testing.assert_allclose(U[~ok], O, atol=1e-12)
 
 
+def _sym_power(A, p):
+    """A^p for a batch of symmetric positive definite matrices, via eigh."""
+    lam, E = np.linalg.eigh(A)
+    return np.einsum("mij,mj,mkj->mik", E, lam ** p, E)
+
+
+def _random_orthogonal(rng, d, count, det_sign):
+    Q, R = np.linalg.qr(rng.normal(size=(count, d, d)))
+    Q = Q * np.sign(np.diagonal(R, axis1=1, axis2=2))[:, None, :]
+    wrong = np.sign(np.linalg.det(Q)) != det_sign
+    Q[wrong, :, 0] *= -1.0
+    return Q
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_polar_init_against_the_closed_form_polar_factor(d):
+    """Eqs. initialpolardecomposition / polardecompositionapplied without an SVD:
+    the orthogonal polar factor of an invertible J is J (J^T J)^{-1/2} and its
+    symmetric factor (J^T J)^{1/2} (both from eigh of J^T J).  Unflipped: U is that
+    factor (a rotation) and P has the eigenvalues of (J^T J)^{1/2} raised to eps.
+    Flipped (det J < 0): the polar factor is a reflection, the best one for J
+    (tr(O^T J) >= tr(Q^T J) for every reflection Q), and U is it with its last
+    column negated, so det U = 1 and U diag(1, .., 1, -1) recovers it."""
+    rng = np.random.default_rng(12)
+    # well-conditioned draws plus some with one tiny singular value (below eps)
+    J = rng.normal(size=(60, d, d))
+    Qa = _random_orthogonal(rng, d, 20, 1.0)
+    Qb = _random_orthogonal(rng, d, 20, 1.0)
+    sv = np.abs(rng.normal(size=(20, d))) + 0.5
+    sv[:, -1] = 1e-9
+    J = np.concatenate([J, np.einsum("mij,mj,mkj->mik", Qa, sv, Qb)])
+    J[-5:, :, 0] *= -1.0          # a few near-singular flipped ones too
+    D = np.diag([1.0] * (d - 1) + [-1.0])
+    JtJ = np.transpose(J, (0, 2, 1)) @ J
+    lam, E = np.linalg.eigh(JtJ)
+    det = np.linalg.det(J)
+    # the closed form J (J^T J)^{-1/2} loses accuracy as J nears singularity, so
+    # the polar factor is checked where the smallest singular value is above 1e-3
+    good = lam[:, 0] > 1e-6
+    O = np.full_like(J, np.nan)
+    O[good] = J[good] @ _sym_power(JtJ[good], -0.5)
+    pos, neg = det > 0, det < 0
+    assert (pos & good).sum() > 10 and (neg & good).sum() > 10 and (pos & ~good).sum() > 5
+    for energy, eps in (("sd", 2.0 ** -6.5), ("sg", 2.0 ** -13)):
+        U, P = admm.polar_init(J, energy)
+        # unflipped: U = J (J^T J)^{-1/2}, P = (J^T J)^{1/2} with eigenvalues raised to eps
+        np.testing.assert_allclose(U[pos & good], O[pos & good], atol=1e-9)
+        P_ref = np.einsum("mij,mj,mkj->mik", E, np.maximum(np.sqrt(np.maximum(lam, 0.0)), eps), E)
+        np.testing.assert_allclose(P[pos], P_ref[pos], atol=1e-9)
+        # flipped: O is a reflection, the best reflection for J, and U = O with its last column negated
+        fl = neg & good
+        np.testing.assert_allclose(np.linalg.det(O[fl]), -1.0, atol=1e-9)
+        Qs = _random_orthogonal(rng, d, 4000, -1.0)
+        for k in np.flatnonzero(fl):
+            trials = np.einsum("qij,ij->q", Qs, J[k])
+            assert np.all(trials <= np.einsum("ij,ij->", O[k], J[k]) + 1e-12)
+        np.testing.assert_allclose(np.linalg.det(U[neg]), 1.0, atol=1e-12)
+        np.testing.assert_allclose(U[fl] @ D, O[fl], atol=1e-9)
+        np.testing.assert_allclose(P[neg], np.broadcast_to(eps * np.eye(d), P[neg].shape), atol=1e-15)
+
+
 # --------------------------------------------------------------------------
 # W step (eq. solvinginw) against a dense least-squares solve
 # --------------------------------------------------------------------------
