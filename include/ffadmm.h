@@ -104,7 +104,7 @@ typedef struct {
                               events so far) each mu_i is multiplied (divided) by rescale_rho/2
                               when e_prim_i > rescale_rho e_dual_i (e_dual_i > rescale_rho
                               e_prim_i), never below mu_min,i/2, Lambda_i keeps mu_i Lambda_i, and L
-                              is decomposed again on the host.  rho is ignored.  Single meshes of
+                              is decomposed again (where factor_device says).  rho is ignored.  Single meshes of
                               one energy, SD or SG, only; not with ffa_forward_unrolled. */
   double rescale_rho;      /* the paper's rho of the rescaling rule (default 5) */
   int32_t local_variant;   /* 0: the paper's local step (Algorithm 1: U from (J + Lambda) P^{k-1}, then P;
@@ -175,7 +175,9 @@ typedef struct {
                                  the pass's input and output vectors */
   int32_t kernels_per_iteration; /* kernel launches of one iteration without the test */
   int32_t kernels_per_check;     /* extra launches of an iteration that runs the test */
-  double seconds_refactor;       /* host time spent decomposing L again (penalty_schedule 1) */
+  double seconds_refactor;       /* wall time spent assembling and decomposing L again at the rescaling
+                                    events of penalty_schedule 1 (on the host or, with factor_device, on
+                                    the device) */
   int32_t top_inverse_levels;    /* levels solved by S^-1 (top_inverse_levels), 0 if none */
   int32_t top_inverse_cols;      /* columns of those levels (the order of S) */
   int64_t bytes_top_product;     /* algorithmic bytes of one x_T = S^-1 t_T: the tiles of S^-1 and
