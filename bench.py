@@ -179,12 +179,15 @@ class ClockSampler:
 
 def oracle_probe(cells: int, iters: int, seconds: float = 0.0):
     """Per-iteration wall time of the FP64 oracle on the cube of `cells`^3 cells:
-    setup and one iteration untimed, then `iters` iterations (or as many as fit in
-    `seconds`, at least `iters`).  Returns (tets, list of per-iteration seconds)."""
+    setup (the operator and its sparse LU, timed on its own) and one iteration
+    untimed, then `iters` iterations (or as many as fit in `seconds`, at least
+    `iters`).  Returns (tets, list of per-iteration seconds, setup seconds)."""
     from oracle import admm
     from paper_2107_05200_gb300 import workloads as wk
     wl = wk.cube_deform(cells=cells)
+    t0 = time.perf_counter()
     o = admm.Oracle.from_workload(wl)
+    setup_s = time.perf_counter() - t0
     s = o.init(wl.W0)
     s, _ = o.step(s)
     times = []
@@ -193,13 +196,13 @@ def oracle_probe(cells: int, iters: int, seconds: float = 0.0):
         t0 = time.perf_counter()
         s, _ = o.step(s)
         times.append(time.perf_counter() - t0)
-    return wl.m, times
+    return wl.m, times, setup_s
 
 
 def oracle_timings(sizes, iters, seconds, threads):
     """oracle_probe for each (cells) in `sizes`, each in a fresh process whose
     numerical libraries are limited to `threads` threads (None: their default).
-    Returns {cells: (tets, per-iteration seconds list)}."""
+    Returns {cells: (tets, per-iteration seconds list, setup seconds)}."""
     env = dict(os.environ)
     if threads is not None:
         for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -209,7 +212,7 @@ def oracle_timings(sizes, iters, seconds, threads):
         proc = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-probe", str(c), str(it), str(sec)],
                               env=env, capture_output=True, text=True, check=True)
         d = json.loads(proc.stdout.strip().splitlines()[-1])
-        out[c] = (d["tets"], d["times"])
+        out[c] = (d["tets"], d["times"], d["setup_s"])
     return out
 
 
@@ -239,7 +242,7 @@ def oracle_baseline(m_full: int, n_full: int, sample_cells: int, seconds: float,
     sizes = [sample_cells] + list(growth_cells)
     samples = oracle_timings(sizes, [3] + [2] * len(growth_cells), [seconds] + [0.0] * len(growth_cells), threads)
     per_it, alpha = extrapolate(samples, m_full)
-    m_s, t_s = samples[sample_cells]
+    m_s, t_s, _ = samples[sample_cells]
     per_s = statistics.median(t_s)
     return {
         "value": 1.0 / per_it, "unit": UNIT, "kind": "oracle",
@@ -253,7 +256,8 @@ def oracle_baseline(m_full: int, n_full: int, sample_cells: int, seconds: float,
                      "the exponent measured between the two largest sizes"),
         "sample_workload": f"cube_deform_{sample_cells}", "sample_tets": m_s, "sample_iter_per_s": 1.0 / per_s,
         "growth_exponent": alpha, "extrapolated_s_per_iter": per_it,
-        "sizes": {f"cube_deform_{c}": {"tets": samples[c][0], "s_per_iter": statistics.median(samples[c][1])}
+        "sizes": {f"cube_deform_{c}": {"tets": samples[c][0], "s_per_iter": statistics.median(samples[c][1]),
+                                       "setup_s": samples[c][2]}
                   for c in sizes},
     }
 
@@ -284,7 +288,7 @@ def run_reference(args, rank):
     rho_full = wk.cube_deform(cells=2).rho
     # the timed steps: `steps` iterations after `warmup` on the sample cube, one thread
     samples = oracle_timings([args.cpu_sample_cells], [args.warmup + args.steps], [0.0], 1)
-    m_s, times = samples[args.cpu_sample_cells]
+    m_s, times, setup_s = samples[args.cpu_sample_cells]
     per_s = sum(times[args.warmup:]) / max(1, args.steps)
     single = oracle_baseline(m_full, n_full, args.cpu_sample_cells, 0.0, args.growth_cells, 1)
     multi = oracle_baseline(m_full, n_full, args.cpu_sample_cells, 0.0, args.growth_cells, None)
@@ -304,7 +308,7 @@ def run_reference(args, rank):
                                 "growth_exponent": single["growth_exponent"],
                                 "s_per_iter": single["extrapolated_s_per_iter"]},
             "sample_timed": {"workload": cfg["workload"], "tets": m_s, "iterations": args.steps,
-                             "s_per_iter": per_s, "iter_per_s": 1.0 / per_s},
+                             "s_per_iter": per_s, "iter_per_s": 1.0 / per_s, "setup_s": setup_s},
             "cpu_baseline": single, "cpu_baseline_all_threads": multi,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -647,8 +651,8 @@ def main():
     args = parse()
     if args.oracle_probe is not None:
         cells, iters, secs = args.oracle_probe
-        m, times = oracle_probe(int(cells), int(iters), float(secs))
-        print(json.dumps({"tets": m, "times": times}), flush=True)
+        m, times, setup_s = oracle_probe(int(cells), int(iters), float(secs))
+        print(json.dumps({"tets": m, "times": times, "setup_s": setup_s}), flush=True)
         return 0
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -44,7 +44,8 @@ def test_reference_arm_prints_one_contract_line():
     ext = out["extrapolated_to"]
     assert ext["workload"] == "cube_deform_64" and ext["tets"] == 6 * 64 ** 3
     assert 0.5 < ext["growth_exponent"] < 2.0 and ext["s_per_iter"] > 0
-    assert out["sample_timed"]["iterations"] == 2
+    assert out["sample_timed"]["iterations"] == 2 and out["sample_timed"]["setup_s"] > 0
+    assert all(v["setup_s"] > 0 and v["s_per_iter"] > 0 for v in out["cpu_baseline"]["sizes"].values())
     assert out["cpu_baseline_all_threads"]["cores"] >= 1
     cb = out["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == out["value"]
