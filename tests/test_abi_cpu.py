@@ -115,3 +115,43 @@ def test_build_compiles_every_source_file():
     csrc = os.path.join(os.path.dirname(os.path.abspath(build.__file__)), "csrc")
     on_disk = {f for f in os.listdir(csrc) if f.endswith((".cu", ".cpp"))}
     assert on_disk == set(build.CU_SOURCES) | set(build.CXX_SOURCES)
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every structure the binding passes by pointer has, field by field, the
+    offset and size that a C compiler gives the header's declaration, and the
+    same total size; a field the binding names but the header lacks fails to
+    compile.  The header is compiled as plain C (it promises a C ABI)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    native, _ = _lib()
+    pairs = [(native.Mesh, "ffa_mesh"), (native.Params, "ffa_params"), (native.Stats, "ffa_stats"),
+             (native.Info, "ffa_info"), (native.Tuning, "ffa_tuning"), (native.PhaseTimes, "ffa_phase_times")]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ffadmm.h"', "int main(void) {"]
+    for cls, cname in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu %zu\\n", offsetof({cname}, {fname}), '
+                         f'sizeof((({cname}*)0)->{fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        parts = ln.split()
+        if len(parts) == 3 and parts[1] == "size":
+            got[(parts[0], None)] = (int(parts[2]),)
+        elif len(parts) == 4:
+            got[(parts[0], parts[1])] = (int(parts[2]), int(parts[3]))
+    for cls, cname in pairs:
+        assert got[(cname, None)] == (C.sizeof(cls),), cname
+        for fname, _ in cls._fields_:
+            f = getattr(cls, fname)
+            assert got[(cname, fname)] == (f.offset, f.size), (cname, fname)
