@@ -155,3 +155,53 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
         for fname, _ in cls._fields_:
             f = getattr(cls, fname)
             assert got[(cname, fname)] == (f.offset, f.size), (cname, fname)
+
+
+def test_ctypes_signatures_match_the_header_prototypes():
+    """Every prototype of the header against the binding's argtypes and restype:
+    the same number of arguments, integers and doubles of the same width, enums as
+    a C int, pointers as pointers (to the matching structure where the binding
+    names one)."""
+    native, lib = _lib()
+    with open(os.path.join(ROOT, "include", "ffadmm.h")) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    protos = re.findall(r"([A-Za-z_][\w \t\*]*?)\b(ffa_\w+)\s*\(([^;{}]*?)\)\s*;", text)
+    assert len(protos) >= 30
+    structs = {"ffa_mesh": native.Mesh, "ffa_params": native.Params, "ffa_stats": native.Stats,
+               "ffa_info": native.Info, "ffa_tuning": native.Tuning, "ffa_phase_times": native.PhaseTimes}
+    scalars = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double}
+    enums = {"ffa_energy_kind", "ffa_status", "ffa_precision"}
+
+    def check(ctype_str, ct, where):
+        t = ctype_str.replace("const", " ").split()
+        stars = "".join(t).count("*")
+        base = "".join(t).replace("*", "")
+        if stars:
+            assert ct is not None and (ct is C.c_void_p or ct is C.c_char_p or issubclass(ct, C._Pointer)), where
+            if stars == 1 and base in structs and ct is not C.c_void_p:
+                assert ct._type_ is structs[base], where
+            if stars == 2 and ct is not C.c_void_p:
+                assert ct._type_ is C.c_void_p, where
+        elif base in scalars:
+            assert ct is scalars[base], where
+        elif base in enums:
+            assert ct in (C.c_int, C.c_int32, C.c_uint32) and C.sizeof(ct) == 4, where
+        else:
+            raise AssertionError(f"unmapped C type {ctype_str!r} in {where}")
+
+    for ret, name, args in protos:
+        fn = getattr(lib, name)
+        params = [a.strip() for a in args.split(",") if a.strip() and a.strip() != "void"]
+        assert fn.argtypes is not None and len(fn.argtypes) == len(params), name
+        for p, ct in zip(params, fn.argtypes):
+            ctype_str = p.rsplit(None, 1)[0] if not p.endswith("*") else p
+            if "*" in p.rsplit(None, 1)[-1]:          # 'double *x' spelled with the star on the name
+                ctype_str = p.replace(p.rsplit(None, 1)[-1], "*")
+            check(ctype_str, ct, f"{name}({p})")
+        r = ret.strip()
+        if r == "void":
+            assert fn.restype is None, name
+        elif r == "const char*":
+            assert fn.restype is C.c_char_p, name
+        else:
+            check(r, fn.restype, f"{name} return")
