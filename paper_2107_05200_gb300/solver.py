@@ -19,7 +19,14 @@ FACTORS = {"host": 0, "device": 1, "device64": 2}
 
 
 def _ptr(a, dtype):
-    """Pointer of a contiguous numpy array / torch tensor of the given dtype."""
+    """Pointer of a contiguous numpy array / torch tensor of the given dtype.
+
+    A CUDA tensor of another dtype or layout is converted on torch's current
+    stream, which need not be the stream the library copies on; that stream is
+    synchronized before the pointer is handed over, so the library never reads
+    the converted copy before it is written.  (The calls this module wraps
+    synchronize the library's stream before they return successfully, so the
+    copy may be released once the call returns.)"""
     if a is None:
         return None, None
     if isinstance(a, np.ndarray):
@@ -33,6 +40,8 @@ def _ptr(a, dtype):
         tdt = torch.float64 if dtype == np.float64 else torch.int32
         if a.dtype != tdt or not a.is_contiguous():
             a = a.to(tdt).contiguous()
+            if a.is_cuda:
+                torch.cuda.current_stream(a.device).synchronize()
         return C.c_void_p(a.data_ptr()), a
     a = np.ascontiguousarray(np.asarray(a), dtype=dtype)
     return C.c_void_p(a.ctypes.data), a
