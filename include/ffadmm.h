@@ -29,6 +29,13 @@
  *     next call on it).  A context is used by one host thread at a time.
  *   - All GPU work of a context runs on its stream, in order.  Calls that return
  *     values to the host synchronize that stream.
+ *   - A context made without a stream works on a private non-blocking stream,
+ *     which does not wait for work on any other stream (the legacy default
+ *     stream included).  Device memory passed to a call must therefore already
+ *     hold its contents (the work that writes it finished, or ordered before the
+ *     call on the context's stream), and device memory the call writes must not
+ *     be in use by pending work elsewhere.  The Python binding synchronizes
+ *     torch's current stream before it passes a CUDA tensor.
  */
 #ifndef FFADMM_H
 #define FFADMM_H

@@ -18,33 +18,71 @@ PRECISIONS = {"fp32": 0, "fp64": 1}
 FACTORS = {"host": 0, "device": 1, "device64": 2}
 
 
-def _ptr(a, dtype):
-    """Pointer of a contiguous numpy array / torch tensor of the given dtype.
+def _torch():
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return None
+    return torch
 
-    A CUDA tensor of another dtype or layout is converted on torch's current
-    stream, which need not be the stream the library copies on; that stream is
-    synchronized before the pointer is handed over, so the library never reads
-    the converted copy before it is written.  (The calls this module wraps
+
+def _count_ok(size: int, count, what: str) -> None:
+    if count is not None and size != count:
+        raise ValueError(f"{what} has {size} entries, the call reads {count}")
+
+
+def _ptr(a, dtype, count=None, what="array"):
+    """Pointer of an input array (numpy array or torch tensor, host or CUDA) as
+    a contiguous array of the given dtype, with `count` entries when given.
+
+    For a CUDA tensor, torch's current stream is synchronized before the
+    pointer is handed over: the library works on its own stream, which does not
+    wait for torch's, so this is what keeps it from reading the tensor before
+    the work that writes it (a host-to-device copy, a kernel, or the dtype
+    conversion done here) has finished.  The calls this module wraps
     synchronize the library's stream before they return successfully, so the
-    copy may be released once the call returns.)"""
+    array may be released once the call returns.  Returns (pointer, the array
+    to keep alive during the call)."""
     if a is None:
         return None, None
     if isinstance(a, np.ndarray):
         a = np.ascontiguousarray(a, dtype=dtype)
+        _count_ok(a.size, count, what)
         return C.c_void_p(a.ctypes.data), a
-    try:
-        import torch
-    except ImportError:  # pragma: no cover
-        torch = None
+    torch = _torch()
     if torch is not None and isinstance(a, torch.Tensor):
         tdt = torch.float64 if dtype == np.float64 else torch.int32
         if a.dtype != tdt or not a.is_contiguous():
             a = a.to(tdt).contiguous()
-            if a.is_cuda:
-                torch.cuda.current_stream(a.device).synchronize()
+        _count_ok(a.numel(), count, what)
+        if a.is_cuda:
+            torch.cuda.current_stream(a.device).synchronize()
         return C.c_void_p(a.data_ptr()), a
     a = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+    _count_ok(a.size, count, what)
     return C.c_void_p(a.ctypes.data), a
+
+
+def _out(out, count: int, what: str):
+    """Pointer of a caller's output buffer, which the library writes in place: a
+    contiguous float64 numpy array or torch tensor (host or CUDA) of exactly
+    `count` entries.  Anything else is refused rather than converted, since a
+    converted copy would receive the results and drop them.  For a CUDA tensor,
+    torch's current stream is synchronized first (see _ptr)."""
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.float64 or not out.flags.c_contiguous or not out.flags.writeable:
+            raise ValueError(f"{what} must be a writeable C-contiguous float64 array")
+        _count_ok(out.size, count, what)
+        return C.c_void_p(out.ctypes.data)
+    torch = _torch()
+    if torch is not None and isinstance(out, torch.Tensor):
+        if out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous float64 tensor")
+        _count_ok(out.numel(), count, what)
+        if out.is_cuda:
+            torch.cuda.current_stream(out.device).synchronize()
+        return C.c_void_p(out.data_ptr())
+    raise TypeError(f"{what} must be a numpy array or a torch tensor")
 
 
 class Solver:
@@ -106,7 +144,7 @@ class Solver:
         n_pin = 0 if pins is None else int(len(pins))
         self.n_pin = max(n_pin, 1)
         pP, self._pins = _ptr(pins, np.int32) if n_pin else (None, None)
-        pB, self._pinpos = _ptr(pin_pos, np.float64) if n_pin else (None, None)
+        pB, self._pinpos = _ptr(pin_pos, np.float64, n_pin * d, "pin_pos") if n_pin else (None, None)
         ctx = C.c_void_p()
         st = self._lib.ffa_create(C.byref(mesh), pP, n_pin, pB, C.byref(prm),
                                   C.c_void_p(stream) if stream else None, C.byref(ctx))
@@ -138,7 +176,7 @@ class Solver:
 
     # -- the method ----------------------------------------------------------
     def set_handles(self, pin_pos) -> None:
-        p, keep = _ptr(pin_pos, np.float64)
+        p, keep = _ptr(pin_pos, np.float64, self.n_pin * self.d, "pin_pos")
         self._check(self._lib.ffa_set_handles(self._ctx, p))
 
     def set_constraints(self, A, b) -> None:
@@ -157,7 +195,7 @@ class Solver:
                                                   val.ctypes.data, b.ctypes.data))
 
     def init(self, W0) -> None:
-        p, keep = _ptr(W0, np.float64)
+        p, keep = _ptr(W0, np.float64, self.n * self.d, "W0")
         self._check(self._lib.ffa_init(self._ctx, p))
 
     def iterate(self, max_iter: int, stop_at_tol: bool = True) -> dict:
@@ -168,8 +206,8 @@ class Solver:
     def W(self, out=None):
         if out is None:
             out = np.empty((self.n, self.d), np.float64)
-        p, _ = _ptr(out, np.float64)
-        self._check(self._lib.ffa_get_W(self._ctx, p))
+        po = _out(out, self.n * self.d, "out")
+        self._check(self._lib.ffa_get_W(self._ctx, po))
         return out
 
     def state(self):
@@ -182,27 +220,29 @@ class Solver:
 
     def set_state(self, W, U, P, Lam) -> None:
         """Resume from (W, U, P, Lambda) instead of init (W n x d; U, P, Lambda m x d x d)."""
-        keep = [_ptr(a, np.float64) for a in (W, U, P, Lam)]
+        mdd = self.m * self.d * self.d
+        keep = [_ptr(a, np.float64, c, w) for a, c, w in ((W, self.n * self.d, "W"), (U, mdd, "U"), (P, mdd, "P"),
+                                                          (Lam, mdd, "Lambda"))]
         self._check(self._lib.ffa_set_state(self._ctx, *(k[0] for k in keep)))
 
     def penalties(self) -> np.ndarray:
         """The current penalties mu_i (m values)."""
         out = np.empty(self.m, np.float64)
-        po, _ = _ptr(out, np.float64)
+        po = _out(out, self.m, "out")
         self._check(self._lib.ffa_get_penalties(self._ctx, po))
         return out
 
     def energy(self, W=None) -> float:
-        p, keep = _ptr(W, np.float64)
+        p, keep = _ptr(W, np.float64, self.n * self.d, "W")
         E = C.c_double()
         self._check(self._lib.ffa_energy(self._ctx, p, C.byref(E)))
         return E.value
 
     def gradient(self, W=None, out=None):
-        p, keep = _ptr(W, np.float64)
+        p, keep = _ptr(W, np.float64, self.n * self.d, "W")
         if out is None:
             out = np.empty((self.n, self.d), np.float64)
-        po, _ = _ptr(out, np.float64)
+        po = _out(out, self.n * self.d, "out")
         self._check(self._lib.ffa_gradient(self._ctx, p, po))
         return out
 
@@ -227,10 +267,10 @@ class Solver:
 
     def backward_unrolled(self, dL_dW, out=None):
         """dL/db for the pinned positions b, given dL/dW^K of the last forward_unrolled."""
-        p, keep = _ptr(dL_dW, np.float64)
+        p, keep = _ptr(dL_dW, np.float64, self.n * self.d, "dL_dW")
         if out is None:
             out = np.empty((self.n_pin, self.d), np.float64)
-        po, _ = _ptr(out, np.float64)
+        po = _out(out, self.n_pin * self.d, "out")
         self._check(self._lib.ffa_backward_unrolled(self._ctx, p, po))
         return out
 
@@ -278,7 +318,7 @@ def tutte(V, T, boundary, boundary_pos, leaf_size: int = 64, host_threads: int =
     pV, kV = _ptr(Vn, np.float64)
     pT, kT = _ptr(Tn, np.int32)
     pb, kb = _ptr(boundary, np.int32)
-    pp, kp = _ptr(bp, np.float64)
+    pp, kp = _ptr(bp, np.float64, len(kb) * d, "boundary_pos")
     mesh = N.Mesh(n, m, d, d_in, pV, pT)
     prm = N.Params()
     N.check(lib, None, lib.ffa_default_params(C.byref(prm)))
@@ -290,7 +330,7 @@ def tutte(V, T, boundary, boundary_pos, leaf_size: int = 64, host_threads: int =
     prm.factor_device = FACTORS[factor]
     if out is None:
         out = np.empty((n, d), np.float64)
-    po, ko = _ptr(out, np.float64)
+    po = _out(out, n * d, "out")
     rel = C.c_double()
     N.check(lib, None, lib.ffa_tutte(C.byref(mesh), pb, int(len(kb)), pp, C.byref(prm),
                                      C.c_void_p(stream) if stream else None, po, C.byref(rel)))
@@ -317,7 +357,7 @@ class BatchSolver:
             pV, V = _ptr(wl.V, np.float64)
             pT, T = _ptr(wl.T, np.int32)
             pP, P = _ptr(wl.pins, np.int32)
-            pB, B = _ptr(wl.pin_pos, np.float64)
+            pB, B = _ptr(wl.pin_pos, np.float64, len(wl.pins) * wl.d, "pin_pos")
             self._keep += [V, T, P, B]
             meshes[j] = N.Mesh(wl.n, wl.m, wl.d, wl.V.shape[1], pV, pT)
             pin_ptrs[j] = pP
@@ -370,10 +410,13 @@ class BatchSolver:
         self.close()
 
     def init(self, W0s):
+        W0s = list(W0s)
+        if len(W0s) != self.k:
+            raise ValueError(f"{len(W0s)} initial maps for {self.k} meshes")
         ptrs = (C.c_void_p * self.k)()
         keep = []
         for j, W in enumerate(W0s):
-            p, a = _ptr(W, np.float64)
+            p, a = _ptr(W, np.float64, self.n[j] * self.d[j], f"W0[{j}]")
             ptrs[j] = p
             keep.append(a)
         self._check(self._lib.ffa_batch_init(self._b, ptrs))
@@ -394,6 +437,6 @@ class BatchSolver:
     def W(self, j: int, out=None):
         if out is None:
             out = np.empty((self.n[j], self.d[j]), np.float64)
-        p, _ = _ptr(out, np.float64)
-        self._check(self._lib.ffa_batch_get_W(self._b, int(j), p))
+        po = _out(out, self.n[j] * self.d[j], "out")
+        self._check(self._lib.ffa_batch_get_W(self._b, int(j), po))
         return out
