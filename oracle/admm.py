@@ -523,6 +523,39 @@ class Oracle:
         conv = e_prim < thr_p and e_dual < thr_d and n_flip == 0
         return Stats(k, e_prim, e_dual, thr_p, thr_d, n_flip, eP, conv)
 
+    def condition_proxies(self, s0: State, s1: State, mu0=None, mu1=None) -> tuple[float, float]:
+        """The two quantities the paper plots beside the errors as evidence for the
+        conditions of its convergence analysis (Fig. 3; Sec. 5, Conditions 1 and 2):
+
+          * max_i |grad f(P_i^{k+1})|, a proxy for the gradient bound B_i of
+            Condition 1;
+          * max_i of |D_i| / |(D_i + U_i^{k+1} M_i^{k+1 T} U_i^{k+1}
+            - U_i^k M_i^{k T} U_i^k) / 2| with D_i = M_i^{k+1} - M_i^k, a proxy for
+            gamma^{1/2} of Condition 2 (the smallest gamma that the step satisfies),
+            where M_i = mu_i Lambda_i is the multiplier with this module's scaled
+            Lambda multiplied back by the penalty, so that values compare across
+            rescalings (mu0, mu1: the penalties of s0 and s1, default the current
+            ones).  An element whose denominator vanishes with D_i != 0 makes the
+            ratio infinite; elements with D_i = 0 are skipped.
+        """
+        mu0 = self.mu if mu0 is None else np.asarray(mu0, np.float64)
+        mu1 = self.mu if mu1 is None else np.asarray(mu1, np.float64)
+        G = grad_f(s1.P, self.energy_name)
+        g = float(np.sqrt(np.sum(G * G, axis=(1, 2))).max())
+        M0 = mu0[:, None, None] * s0.Lam
+        M1 = mu1[:, None, None] * s1.Lam
+        D = M1 - M0
+        tr = lambda X: np.transpose(X, (0, 2, 1))
+        S = 0.5 * (D + s1.U @ tr(M1) @ s1.U - s0.U @ tr(M0) @ s0.U)
+        num = np.sqrt(np.sum(D * D, axis=(1, 2)))
+        den = np.sqrt(np.sum(S * S, axis=(1, 2)))
+        moved = num > 0.0
+        if not moved.any():
+            return g, 0.0
+        if np.any(den[moved] == 0.0):
+            return g, math.inf
+        return g, float((num[moved] / den[moved]).max())
+
     def run(self, W0, max_iter: int, stop_at_tol: bool = True, callback=None):
         s = self.init(W0)
         st = None
