@@ -240,7 +240,7 @@ def oracle_baseline(m_full: int, n_full: int, sample_cells: int, seconds: float,
     extrapolated to the full workload with the growth exponent measured between the
     two largest sampled sizes.  Returns the cpu_baseline / reference description."""
     sizes = [sample_cells] + list(growth_cells)
-    samples = oracle_timings(sizes, [3] + [2] * len(growth_cells), [seconds] + [0.0] * len(growth_cells), threads)
+    samples = oracle_timings(sizes, [3] * (1 + len(growth_cells)), [seconds] + [0.0] * len(growth_cells), threads)
     per_it, alpha = extrapolate(samples, m_full)
     m_s, t_s, _ = samples[sample_cells]
     per_s = statistics.median(t_s)
