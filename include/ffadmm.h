@@ -35,7 +35,7 @@
  *     hold its contents (the work that writes it finished, or ordered before the
  *     call on the context's stream), and device memory the call writes must not
  *     be in use by pending work elsewhere.  The Python binding synchronizes
- *     torch's current stream before it passes a CUDA tensor.
+ *     the tensor's device before it passes a CUDA tensor.
  */
 #ifndef FFADMM_H
 #define FFADMM_H

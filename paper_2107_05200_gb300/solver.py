@@ -35,11 +35,11 @@ def _ptr(a, dtype, count=None, what="array"):
     """Pointer of an input array (numpy array or torch tensor, host or CUDA) as
     a contiguous array of the given dtype, with `count` entries when given.
 
-    For a CUDA tensor, torch's current stream is synchronized before the
-    pointer is handed over: the library works on its own stream, which does not
-    wait for torch's, so this is what keeps it from reading the tensor before
-    the work that writes it (a host-to-device copy, a kernel, or the dtype
-    conversion done here) has finished.  The calls this module wraps
+    For a CUDA tensor, the device is synchronized (every stream on it) before
+    the pointer is handed over: the library works on its own stream, which does
+    not wait for torch's, so this is what keeps it from reading the tensor
+    before the work that writes it (a host-to-device copy, a kernel, or the
+    dtype conversion done here) has finished.  The calls this module wraps
     synchronize the library's stream before they return successfully, so the
     array may be released once the call returns.  Returns (pointer, the array
     to keep alive during the call)."""
@@ -56,7 +56,7 @@ def _ptr(a, dtype, count=None, what="array"):
             a = a.to(tdt).contiguous()
         _count_ok(a.numel(), count, what)
         if a.is_cuda:
-            torch.cuda.current_stream(a.device).synchronize()
+            torch.cuda.synchronize(a.device)
         return C.c_void_p(a.data_ptr()), a
     a = np.ascontiguousarray(np.asarray(a), dtype=dtype)
     _count_ok(a.size, count, what)
@@ -68,7 +68,7 @@ def _out(out, count: int, what: str):
     contiguous float64 numpy array or torch tensor (host or CUDA) of exactly
     `count` entries.  Anything else is refused rather than converted, since a
     converted copy would receive the results and drop them.  For a CUDA tensor,
-    torch's current stream is synchronized first (see _ptr)."""
+    the device is synchronized first (see _ptr)."""
     if isinstance(out, np.ndarray):
         if out.dtype != np.float64 or not out.flags.c_contiguous or not out.flags.writeable:
             raise ValueError(f"{what} must be a writeable C-contiguous float64 array")
@@ -80,7 +80,7 @@ def _out(out, count: int, what: str):
             raise ValueError(f"{what} must be a contiguous float64 tensor")
         _count_ok(out.numel(), count, what)
         if out.is_cuda:
-            torch.cuda.current_stream(out.device).synchronize()
+            torch.cuda.synchronize(out.device)
         return C.c_void_p(out.data_ptr())
     raise TypeError(f"{what} must be a numpy array or a torch tensor")
 

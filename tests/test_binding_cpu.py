@@ -163,3 +163,23 @@ def test_constructors_pass_valid_workloads_to_the_library():
     with pytest.raises(FFAError) as e:
         S.BatchSolver(wk.batched_meshes(count=2, m_min=200, m_max=400) + [cube])
     assert STATUS_NAMES[e.value.status] == "FFA_ERR_CUDA"
+
+
+def test_cuda_tensors_are_synchronized_before_the_library_reads_them(monkeypatch):
+    """The branch a CUDA tensor takes, run on the CPU: the tensor class is made to
+    report itself as a CUDA tensor and the device synchronization is recorded.
+    Inputs (converted or not) and outputs are synchronized on their own device
+    before their pointer is returned; host tensors are not."""
+    torch = pytest.importorskip("torch")
+    seen = []
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda device=None: seen.append(device))
+    S._ptr(torch.zeros(4, dtype=torch.float64), np.float64, 4, "W")
+    S._out(torch.zeros(4, dtype=torch.float64), 4, "out")
+    assert seen == []
+    monkeypatch.setattr(torch.Tensor, "is_cuda", property(lambda self: True))
+    a = torch.zeros(4, dtype=torch.float64)
+    p, keep = S._ptr(a, np.float64, 4, "W")
+    assert keep is a and seen == [a.device]
+    S._ptr(torch.zeros(4, dtype=torch.float32), np.float64, 4, "W")
+    S._out(a, 4, "out")
+    assert seen == [a.device] * 3
