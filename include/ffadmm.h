@@ -2,13 +2,14 @@
  * ffadmm.h - C ABI of the GB300 flip-free ADMM library (libffadmm.so).
  *
  * The library minimizes a flip-free distortion energy
- *     E(W) = sum_i w_i f((G W)_i) + chi_+(det (G W)_i)              (paper eq. genericdeformationenergy
+ *     E(W) = sum_i w_i f((G W)_i) + chi_+(det (G W)_i)              (paper eq. genericdeformationenergy)
  * over target vertex positions W with the three-block splitting scheme of
  * Stein, Li & Solomon, "A Splitting Scheme for Flip-Free Distortion Energies"
  * (Algorithm 1; Algorithm 2 without penalty rescaling): a global W step with a
  * fixed operator L = sum_i mu_i G_i^T G_i (eq. solvinginw), closed-form per-element U
- * (Procrustes, eqs. rawoptimizationinudecoupled/optimizationinudecoupled and P (prox, eqs. optimizinginp/rootfindinginp steps, and the scaled
- * multiplier update (eq. lambdaupdate), with the primal/dual errors of eqs. primaldualerror/primaldualthresholds.
+ * (Procrustes, eqs. rawoptimizationinudecoupled/optimizationinudecoupled) and P (prox,
+ * eqs. optimizinginp/rootfindinginp) steps, and the scaled multiplier update
+ * (eq. lambdaupdate), with the primal/dual errors of eqs. primaldualerror/primaldualthresholds.
  *
  * Conventions shared by every call:
  *   - Sizes: n vertices, m elements, element dimension d (2 = triangles,

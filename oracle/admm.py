@@ -11,11 +11,11 @@ Element data are batched numpy arrays; numpy/scipy primitives (SVD, symmetric
 eigendecomposition, sparse LU) serve as single steps, and the steps follow the
 paper's order (Algorithm 1 / Algorithm 2 without the rescaling branch).
 
-Notation (Sec. 3.1, Def. jacobian (Sec. 3.1)): V source vertices (n, d_in), W target vertices
+Notation (Sec. 3.1 and its definition of the Jacobian): V source vertices (n, d_in), W target vertices
 (n, d), T elements (m, d+1), w_i element area/volume, J = GW the per-element
 Jacobians with column k equal to the gradient of target coordinate k
 (Supplemental, "Computing the Jacobian map").  U_i in SO(d), P_i SPD, Lambda_i
-the scaled multiplier, mu_i the penalties (eq. augmentedlagrangian.
+the scaled multiplier, mu_i the penalties (eq. augmentedlagrangian).
 
 Readings of points the paper leaves open (each one is also listed in the
 design notes):
@@ -46,7 +46,7 @@ SQRT_EPS_M = 2.0 ** -26
 
 
 # ----------------------------------------------------------------------------
-# mesh operators (Supplemental, "Computing the Jacobian map"; Def. jacobian (Sec. 3.1))
+# mesh operators (Supplemental, "Computing the Jacobian map"; Sec. 3.1, the Jacobian)
 # ----------------------------------------------------------------------------
 
 def element_frames(V: np.ndarray, T: np.ndarray) -> np.ndarray:
@@ -177,7 +177,7 @@ def rot2(c: np.ndarray, s: np.ndarray) -> np.ndarray:
 
 
 def procrustes(Q: np.ndarray, U_prev: np.ndarray) -> np.ndarray:
-    """argmin_{U in SO(d)} |U - Q|^2 (eq. optimizationinudecoupled.
+    """argmin_{U in SO(d)} |U - Q|^2 (eq. optimizationinudecoupled).
 
     d = 2: U(phi) maximizes U(phi).Q = cos(phi)(q11+q22) + sin(phi)(q21-q12),
     so (cos, sin) is that vector normalized (Supplemental, d = 2); a zero vector
@@ -299,7 +299,7 @@ def symm(X: np.ndarray) -> np.ndarray:
 
 
 def polar_init(J0: np.ndarray, energy_name: str) -> tuple[np.ndarray, np.ndarray]:
-    """U0, P0 from the polar decomposition of GW0 (eqs. initialpolardecomposition/polardecompositionapplied.
+    """U0, P0 from the polar decomposition of GW0 (eqs. initialpolardecomposition/polardecompositionapplied).
 
     J0 = R1 S R2^T, U0 = R1 R2^T, P0 = R2 S R2^T; singular values below eps are
     raised to eps, eps = eps_m^{1/4} (SG) or eps_m^{1/8} (SD, and SA, which grows
@@ -325,7 +325,7 @@ def polar_init(J0: np.ndarray, energy_name: str) -> tuple[np.ndarray, np.ndarray
 # ----------------------------------------------------------------------------
 
 class WStep:
-    """Exact minimizer of Phi over W with pinned vertices (eq. solvinginw.
+    """Exact minimizer of Phi over W with pinned vertices (eq. solvinginw).
 
     L = sum mu_i G_i^T G_i is split into free (F) and pinned (C) blocks;
     L_FF W_F = (G^T r)_F - L_FC b.  L_FF is factored once (sparse LU), as the
@@ -470,7 +470,7 @@ class Oracle:
         return cls(wl.V, wl.T, wl.pins, wl.pin_pos, wl.energy, wl.rho, **kw)
 
     def init(self, W0) -> State:
-        """U0, P0 by polar decomposition, Lambda0 = 0 (Algorithm 2, eqs. initialpolardecomposition/polardecompositionapplied."""
+        """U0, P0 by polar decomposition, Lambda0 = 0 (Algorithm 2, eqs. initialpolardecomposition/polardecompositionapplied)."""
         W0 = np.asarray(W0, np.float64)
         J0 = jacobians(self.g, self.T, W0)
         U0, P0 = polar_init(J0, self.energy_name)

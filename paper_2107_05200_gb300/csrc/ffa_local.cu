@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_local_step(Elem
 #pragma unroll
       for (int k = 0; k < 4; ++k) Up[(int64_t)k * m + i] = qt[k];
     }
-    // ---- P step: S = symm(U^T (J + Lambda)), per-eigenvalue prox root (eqs. optimizinginp/rootfindinginp
+    // ---- P step: S = symm(U^T (J + Lambda)), per-eigenvalue prox root (eqs. optimizinginp/rootfindinginp)
     R S[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)

@@ -53,8 +53,8 @@ constexpr double kSqrtEpsM = 1.4901161193847656e-08;    // 2^-26
 // scalar prox roots: the per-eigenvalue form of w grad f(P) + mu P = mu S
 // ---------------------------------------------------------------------------
 
-// Symmetric gradient: (w + mu) p^2 - mu q p - w = 0, positive root (eq. solvesgwithquadraticformula per
-// eigenvalue).  Divided by (w + mu): p^2 - t q p - c = 0 with t = mu/(w+mu),
+// Symmetric gradient: (w + mu) p^2 - mu q p - w = 0, positive root per eigenvalue
+// (eq. solvesgwithquadraticformula).  Divided by (w + mu): p^2 - t q p - c = 0 with t = mu/(w+mu),
 // c = w/(w+mu); for q < 0 the cancellation-free form 2c / (sqrt(disc) - t q).
 template <typename R>
 __device__ __forceinline__ R prox_root_sg(R q, R w, R mu) {

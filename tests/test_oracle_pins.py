@@ -280,7 +280,7 @@ def test_procrustes_3d_against_rotation_search():
 
 
 # --------------------------------------------------------------------------
-# initialization (eqs. initialpolardecomposition/polardecompositionapplied
+# initialization (eqs. initialpolardecomposition/polardecompositionapplied)
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("d", [2, 3])
