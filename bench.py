@@ -223,8 +223,11 @@ def extrapolate(samples, m_full):
     The local slope at the top of the sampled range is used rather than a fit over
     every size because the oracle's time per iteration is not a pure power of m:
     the share of its sparse triangular solves grows with the factor's fill.  On the
-    benchmark recipe the slope between 24^3 and 32^3 cells predicted the measured
-    per-iteration time at 64^3 within 2%, a fit over 16^3, 24^3 and 32^3 within 10%.
+    benchmark recipe, against 22.3 s measured per iteration at 64^3 cells, the slope
+    between 24^3 and 32^3 cells predicted 22.7 s and 19.0 s in two runs and a fit
+    over 16^3, 24^3 and 32^3 predicted 20.2 s and 18.4 s: the slope is closer but
+    noisier (an 8x extrapolation multiplies a 5% timing difference at 32^3 into
+    13%), so the larger sizes take the median of five iterations.
     Returns (seconds, alpha)."""
     cs = sorted(samples, key=lambda c: samples[c][0])
     m1, t1 = samples[cs[-1]][0], statistics.median(samples[cs[-1]][1])
@@ -240,7 +243,7 @@ def oracle_baseline(m_full: int, n_full: int, sample_cells: int, seconds: float,
     extrapolated to the full workload with the growth exponent measured between the
     two largest sampled sizes.  Returns the cpu_baseline / reference description."""
     sizes = [sample_cells] + list(growth_cells)
-    samples = oracle_timings(sizes, [3] * (1 + len(growth_cells)), [seconds] + [0.0] * len(growth_cells), threads)
+    samples = oracle_timings(sizes, [3] + [5] * len(growth_cells), [seconds] + [0.0] * len(growth_cells), threads)
     per_it, alpha = extrapolate(samples, m_full)
     m_s, t_s, _ = samples[sample_cells]
     per_s = statistics.median(t_s)
