@@ -60,3 +60,23 @@ def test_gpu_arm_refuses_without_a_device():
     assert r.returncode != 0
     assert "CUDA" in (r.stdout + r.stderr)
     assert not any(ln.strip().startswith("{") for ln in r.stdout.splitlines())
+
+
+def test_oracle_extrapolation_rule():
+    """bench.extrapolate: the largest sample scaled by the element-count ratio to the
+    power measured between the two largest samples (medians), linear with one sample."""
+    import math
+    sys.path.insert(0, ROOT)
+    import bench
+    m_full = 1_572_864
+    # an exact power law is reproduced exactly, whatever the smaller samples do
+    samples = {16: (24_576, [9.0, 0.1, 0.2], 0.1), 24: (82_944, [2.0 * 82_944 ** 1.1] * 3, 0.1),
+               32: (196_608, [2.0 * 196_608 ** 1.1] * 5, 0.1)}
+    t, a = bench.extrapolate(samples, m_full)
+    assert math.isclose(a, 1.1, rel_tol=1e-12) and math.isclose(t, 2.0 * m_full ** 1.1, rel_tol=1e-12)
+    # the median of each size's iterations is used
+    samples[32] = (196_608, [2.0 * 196_608 ** 1.1, 1e9, 0.0, 2.0 * 196_608 ** 1.1, 1.0], 0.1)
+    assert math.isclose(bench.extrapolate(samples, m_full)[1], 1.1, rel_tol=1e-12)
+    # one sample: linear in the element count
+    t1, a1 = bench.extrapolate({16: (24_576, [0.25, 0.3, 0.2], 0.1)}, m_full)
+    assert a1 == 1.0 and math.isclose(t1, 0.25 * m_full / 24_576, rel_tol=1e-12)
